@@ -1,0 +1,224 @@
+/*
+ * asv.h -- C ABI of the adaptive SpMV/SpMSpV library for GB300 (sm_103a).
+ *
+ * Computes y = A x for a sparse m x n matrix A and an input vector x of any
+ * density (Li, Ao, Yang, "Adaptive SpMV/SpMSpV on GPUs for Input Vectors of
+ * Varied Sparsity"; problem statement Sec. II), choosing per call among a
+ * family of candidate kernels built along the paper's three axes (Sec. IV):
+ * computing pattern (row-major CSR pull, with or without value validation,
+ * versus column-major CSC push over x's nonzeros), workload distribution
+ * (one row/column per thread, a (sub-)warp per row/column, or an even split
+ * of the nonzeros) and, for the push pattern, write-back (atomics, sort +
+ * reduce-by-key, or privatised row-tile accumulation). The runtime procedure
+ * of Sec. VI (matrix features once, vector features per call, cascaded
+ * decision trees, conversion only when needed) runs on the device with no
+ * host round-trip.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are device pointers (cudaMalloc'd or torch-owned);
+ *    pointers named h_* are host pointers. Indices are int32, counts int64.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; nothing synchronises unless the comment says so.
+ *  - Every function returns an asv_status; nothing throws across the ABI.
+ *    Argument errors are detected on the host before anything is enqueued.
+ *    Errors that only the device can see (capacity overflow, bounded-wait
+ *    timeouts, checked-mode bounds) are latched in a per-handle device status
+ *    word and returned by the next call that synchronises (asv_get_status,
+ *    asv_select, asv_matrix_features).
+ *  - Value dtype is fixed per matrix handle; x and y use the same dtype:
+ *    ASV_F32 float, ASV_F64 double, ASV_I32 int32 (wrap-around (+,x)),
+ *    ASV_BOOL uint8 0/1 with the (OR, AND) semiring over a pattern matrix.
+ *  - A handle serves one stream at a time: its workspaces are reused by every
+ *    call, so calls on the same handle from different streams must be ordered
+ *    by the caller.
+ */
+#ifndef ASV_H
+#define ASV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t asv_status;
+enum {
+    ASV_OK = 0,
+    ASV_ERR_ARG = 1,           /* null/negative argument, dtype mismatch, bad kernel id      */
+    ASV_ERR_NONCANONICAL = 2,  /* ASV_VALIDATE: rowptr not monotone, column out of range,
+                                  or columns not strictly ascending within a row           */
+    ASV_ERR_OVERFLOW = 3,      /* nnz or a dimension does not fit the int32 index layout     */
+    ASV_ERR_CAPACITY = 4,      /* sparse output larger than y_cap (the count is still written) */
+    ASV_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                          */
+    ASV_ERR_CUDA = 6,          /* a CUDA runtime call failed (see asv_last_cuda_error)        */
+    ASV_ERR_CHECKED = 7,       /* checked mode: a device bounds check failed                  */
+    ASV_ERR_NOMEM = 8,         /* device allocation failed                                    */
+    ASV_ERR_UNSUPPORTED = 9    /* kernel/dtype/output combination not available               */
+};
+
+typedef enum { ASV_F32 = 0, ASV_F64 = 1, ASV_BOOL = 2, ASV_I32 = 3 } asv_dtype;
+typedef enum { ASV_OUT_DENSE = 0, ASV_OUT_SPARSE = 1 } asv_out_mode;
+
+/* Candidate kernels (Sec. IV and Sec. VI-A). The paper's eight are
+ * K1 PULL_THREAD ("SpMV direct"), K2 PULL_BAL ("SpMV load-balanced"),
+ * K3 MPULL_THREAD, K4 MPULL_BAL (row-major SpMSpV with bitvector validation),
+ * K5 PUSH_THREAD_ATOM, K6 PUSH_THREAD_SORT, K7 PUSH_BAL_ATOM, K8 PUSH_BAL_SORT
+ * (column-major SpMSpV). The (sub-)warp split and the privatised write-back
+ * are additions on the same axes. */
+typedef enum {
+    ASV_K_AUTO = -1,
+    ASV_K_PULL_THREAD = 0, ASV_K_PULL_WARP = 1, ASV_K_PULL_BAL = 2,
+    ASV_K_MPULL_THREAD = 3, ASV_K_MPULL_WARP = 4, ASV_K_MPULL_BAL = 5,
+    ASV_K_PUSH_THREAD_ATOM = 6, ASV_K_PUSH_WARP_ATOM = 7, ASV_K_PUSH_BAL_ATOM = 8,
+    ASV_K_PUSH_THREAD_SORT = 9, ASV_K_PUSH_WARP_SORT = 10, ASV_K_PUSH_BAL_SORT = 11,
+    ASV_K_PUSH_THREAD_PRIV = 12, ASV_K_PUSH_WARP_PRIV = 13, ASV_K_PUSH_BAL_PRIV = 14,
+    ASV_K_COUNT = 15
+} asv_kernel;
+
+/* Handle creation flags. */
+enum {
+    ASV_BORROW = 0,         /* default: the caller keeps the CSR arrays alive and unchanged
+                               for the handle's lifetime                                   */
+    ASV_COPY = 1u << 0,     /* the handle copies the CSR arrays into memory it owns        */
+    ASV_VALIDATE = 1u << 1  /* check canonical CSR on the device during create (syncs)     */
+};
+
+typedef struct asv_matrix_s* asv_matrix;
+
+/* Matrix features of Table 1 (models 1 and 2), computed once per matrix on
+ * the device (Sec. VI-C). relative_range = (max_row - min_row) / n as
+ * printed; var_nnz_row is the population standard deviation of the row
+ * lengths; gini is the Gini coefficient of the row lengths. */
+typedef struct {
+    int64_t m, n, nnz, max_row, min_row;
+    double avg_row, relative_range, var_nnz_row, gini;
+} asv_mfeat;
+
+/* Vector features of Table 1 (models 1 and 3), per input vector:
+ * nnz_s = number of effective matrix nonzeros = sum of the lengths of the
+ * columns j listed in x; m_sparsity = nnz_s / nnz; x_sparsity = nnz_x / n. */
+typedef struct {
+    int64_t nnz_x, nnz_s;
+    double x_sparsity, m_sparsity;
+} asv_vfeat;
+
+/* ---------------------------------------------------------------- handle */
+
+/* Create a handle for the m x n CSR matrix (d_rowptr[m+1], d_colidx[nnz],
+ * d_val[nnz] of `dtype`; d_val must be NULL for ASV_BOOL and may be NULL for
+ * ASV_I32/ASV_F32/ASV_F64 to mean all-ones). Builds, on the device, the CSC
+ * view (colptr[n+1], rowidx[nnz], values) with rows ascending in each column
+ * and the CSC->CSR position map (Sec. VI-A: both formats stay resident so no
+ * matrix conversion happens per call), the matrix features of Table 1, the
+ * nnz-balanced tile partition, and all per-call workspaces. CSR must be
+ * canonical (rowptr[0] = 0, non-decreasing, columns strictly ascending per
+ * row); ASV_VALIDATE checks this and fails with ASV_ERR_NONCANONICAL.
+ * Synchronises `stream` once at the end. The handle owns everything it
+ * allocates; with ASV_BORROW it keeps pointers to the caller's CSR arrays. */
+asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t n, int64_t nnz,
+                                 const int32_t* d_rowptr, const int32_t* d_colidx,
+                                 const void* d_val, int32_t dtype, uint32_t flags,
+                                 void* stream);
+
+/* Release the handle and everything it owns (synchronises its device). */
+asv_status asv_matrix_destroy(asv_matrix A);
+
+/* Copy the Table 1 matrix features to *h_out (synchronises). */
+asv_status asv_matrix_features(asv_matrix A, asv_mfeat* h_out);
+
+/* Expose the handle's device arrays (read-only, owned by the handle):
+ * CSR (rowptr, colidx, val) and CSC (colptr, rowidx, val_csc, perm) where
+ * perm[p] = CSR position of the entry at CSC position p. Any out-pointer may
+ * be NULL. For ASV_BOOL the value pointers are NULL. */
+asv_status asv_matrix_arrays(asv_matrix A, const int32_t** d_rowptr, const int32_t** d_colidx,
+                             const void** d_val, const int32_t** d_colptr,
+                             const int32_t** d_rowidx, const void** d_val_csc,
+                             const int32_t** d_perm);
+
+/* Copy the CSC view (Sec. VI-A) into caller-owned device buffers, any of
+ * which may be NULL: d_colptr[n+1], d_rowidx[nnz], d_val_csc[nnz] (value
+ * dtype; ignored for ASV_BOOL), d_perm[nnz] (CSC position -> CSR position).
+ * Enqueued on `stream`. */
+asv_status asv_matrix_copy_csc(asv_matrix A, int32_t* d_colptr, int32_t* d_rowidx, void* d_val_csc,
+                               int32_t* d_perm, void* stream);
+
+/* ---------------------------------------------------------------- products */
+
+/* y = A x with x dense (d_x[n]) and y dense (d_y[m]), overwritten
+ * (the traditional SpMV of Sec. IV-A when a pull kernel runs). `kernel` is a
+ * candidate id or ASV_K_AUTO; with AUTO the device computes the vector
+ * features of x, evaluates the selector and runs the chosen candidate
+ * (which may be a push kernel when x is sparse in value). */
+asv_status asv_spmv(asv_matrix A, const void* d_x, void* d_y, int32_t kernel, void* stream);
+
+/* y = A x for x given either dense (d_x_dense[n], then d_nnz_x/d_xidx/d_xval
+ * are ignored and x's nonzeros are those with x_j != 0 by IEEE comparison)
+ * or sparse (d_x_dense NULL; *d_nnz_x is a device int64 count, d_xidx[nnz_x]
+ * distinct column ids in any order, d_xval[nnz_x] values, NULL for ASV_BOOL
+ * or to mean all-ones). Listed entries are structural even when their value
+ * is zero. Output (Sec. IV-B write-back):
+ *  - ASV_OUT_DENSE: d_y[m] is overwritten with A x;
+ *  - ASV_OUT_SPARSE: the structural output set -- rows with at least one
+ *    effective entry (an entry whose column is a nonzero of x), ascending --
+ *    is written to d_yidx[], its values to d_yval[] (NULL allowed for
+ *    ASV_BOOL), and its size to the device int64 *d_nnz_y. At most y_cap
+ *    entries are written; a larger set latches ASV_ERR_CAPACITY.
+ * Dense/sparse conversion of x happens on the device only when the chosen
+ * kernel needs the other format (Sec. VI-A/VI-C). No synchronisation. */
+asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx,
+                      const void* d_xval, const void* d_x_dense, int32_t out_mode,
+                      void* d_y, int32_t* d_yidx, void* d_yval, int64_t* d_nnz_y,
+                      int64_t y_cap, int32_t kernel, void* stream);
+
+/* Run the feature pass and the selector for this x (same x arguments as
+ * asv_spmspv) and return the chosen kernel id and the vector features
+ * (Sec. V-A Table 1, Sec. VI-B cascaded trees). Synchronises `stream`. */
+asv_status asv_select(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx,
+                      const void* d_xval, const void* d_x_dense, int32_t* h_kernel,
+                      asv_vfeat* h_feat, void* stream);
+
+/* The kernel id chosen by the most recent ASV_K_AUTO call on this handle
+ * (synchronises `stream`). */
+asv_status asv_last_kernel(asv_matrix A, int32_t* h_kernel, void* stream);
+
+/* Dense -> sparse conversion of x (Sec. VI-A online conversion; Sec. VI-C
+ * stream compaction): writes the ascending indices j with x_j != 0 (IEEE;
+ * -0.0 is zero, NaN is nonzero) to d_idx[], their values to d_val[] (may be
+ * NULL), and the count to the device int64 *d_count. d_idx must hold n
+ * entries. Uses the handle's workspaces (x has length A's n). */
+asv_status asv_compact(asv_matrix A, const void* d_x_dense, int32_t* d_idx, void* d_val,
+                       int64_t* d_count, void* stream);
+
+/* ---------------------------------------------------------------- selector */
+
+/* Replace the handle's decision trees (three cascaded CART trees: computing
+ * pattern, workload distribution, write-back; Sec. V-B / VI-B). `nodes` holds
+ * n_nodes records of 5 doubles {feature, threshold, left, right, leaf_class};
+ * feature < 0 marks a leaf. roots[3] are the node indices of the three roots.
+ * Feature indices: 0 m, 1 n, 2 nnz, 3 max_row, 4 min_row, 5 avg_row,
+ * 6 relative_range, 7 var_nnz_row, 8 gini, 9 nnz_x, 10 x_sparsity, 11 nnz_s,
+ * 12 m_sparsity. A node sends x left when feature <= threshold.
+ * Pattern classes: 0 push, 1 masked pull, 2 pull. Distribution classes:
+ * 0 thread, 1 warp, 2 balanced. Write-back classes: 0 atomic, 1 sort,
+ * 2 privatised. Synchronises `stream`. */
+asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t n_nodes,
+                         const int32_t* h_roots, void* stream);
+
+/* ---------------------------------------------------------------- status */
+
+/* Latched device status of the handle (synchronises `stream`); clears it. */
+asv_status asv_get_status(asv_matrix A, void* stream);
+
+/* Last CUDA error code seen by the library on this thread (0 if none). */
+int32_t asv_last_cuda_error(void);
+
+/* Human-readable name of a status code (static string). */
+const char* asv_status_string(asv_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t asv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASV_H */

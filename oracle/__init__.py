@@ -45,9 +45,24 @@ FEATURE_NAMES = ("m", "n", "nnz", "max_row", "min_row", "avg_row",
 VECTOR_FEATURE_NAMES = ("nnz_x", "x_sparsity", "nnz_s", "m_sparsity")
 
 
+def _elf_matches_host(path: str) -> bool:
+    """True when the shared object at `path` was built for this machine."""
+    import platform
+    import struct
+    want = {"x86_64": 0x3E, "aarch64": 0xB7, "arm64": 0xB7}.get(platform.machine())
+    try:
+        with open(path, "rb") as f:
+            head = f.read(20)
+    except OSError:
+        return False
+    if len(head) < 20 or head[:4] != b"\x7fELF":
+        return False
+    return want is None or struct.unpack("<H", head[18:20])[0] == want
+
+
 def build(force: bool = False) -> str:
     """Compile oracle.c (serial, -O2, no fast-math) into liboracle.so."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+    if not force and _elf_matches_host(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
     subprocess.run(["gcc", "-O2", "-std=gnu11", "-fno-fast-math", "-ffp-contract=off",

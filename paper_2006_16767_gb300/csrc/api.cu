@@ -1,0 +1,480 @@
+// C ABI of the adaptive SpMV/SpMSpV library: handle lifetime, per-call
+// dispatch of the candidate kernels, and the selector-driven path (runtime
+// procedure of Sec. VI): vector-feature pass -> decision trees on the device
+// -> SWITCH conditional node of a CUDA graph whose branches are the
+// candidates (with their own format conversion), so the chosen kernel runs
+// with no host round-trip.
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace asv;
+
+static thread_local int32_t g_last_cuda = 0;
+
+#define CK(expr)                                      \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) {                      \
+            g_last_cuda = (int32_t)e_;                \
+            return e_ == cudaErrorMemoryAllocation ? ASV_ERR_NOMEM : ASV_ERR_CUDA; \
+        }                                             \
+    } while (0)
+
+namespace asv {
+int64_t priv_bins(int64_t m);
+
+const char* kernel_name(int k) {
+    static const char* names[ASV_K_COUNT] = {
+        "pull_thread", "pull_warp", "pull_bal", "mpull_thread", "mpull_warp", "mpull_bal",
+        "push_thread_atom", "push_warp_atom", "push_bal_atom", "push_thread_sort", "push_warp_sort",
+        "push_bal_sort", "push_thread_priv", "push_warp_priv", "push_bal_priv"};
+    return (k >= 0 && k < ASV_K_COUNT) ? names[k] : "auto";
+}
+}  // namespace asv
+
+static asv_status dalloc(asv_matrix_s* H, void** p, size_t bytes, bool zero) {
+    if (bytes < 16) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int32_t)e;
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? ASV_ERR_NOMEM : ASV_ERR_CUDA;
+    }
+    H->allocs.push_back(*p);
+    if (zero) {
+        e = cudaMemset(*p, 0, bytes);
+        if (e != cudaSuccess) {
+            g_last_cuda = (int32_t)e;
+            return ASV_ERR_CUDA;
+        }
+    }
+    return ASV_OK;
+}
+
+#define AL(ptr, bytes, zero)                                               \
+    do {                                                                   \
+        void* p_ = nullptr;                                                \
+        asv_status st_ = dalloc(H, &p_, (size_t)(bytes), zero);           \
+        if (st_ != ASV_OK) { destroy_handle(H); return st_; }              \
+        (ptr) = (decltype(ptr))p_;                                         \
+    } while (0)
+
+#define CKH(expr)                                                          \
+    do {                                                                   \
+        cudaError_t e_ = (expr);                                           \
+        if (e_ != cudaSuccess) {                                           \
+            g_last_cuda = (int32_t)e_;                                     \
+            destroy_handle(H);                                             \
+            return e_ == cudaErrorMemoryAllocation ? ASV_ERR_NOMEM : ASV_ERR_CUDA; \
+        }                                                                  \
+    } while (0)
+
+static void destroy_handle(asv_matrix_s* H) {
+    if (!H) return;
+    cudaDeviceSynchronize();
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            if (H->gexec[a][b]) cudaGraphExecDestroy(H->gexec[a][b]);
+            if (H->graph[a][b]) cudaGraphDestroy(H->graph[a][b]);
+        }
+    if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    for (void* p : H->allocs) cudaFree(p);
+    delete H;
+}
+
+static int pow2_floor(double v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t n, int64_t nnz,
+                                            const int32_t* d_rowptr, const int32_t* d_colidx, const void* d_val,
+                                            int32_t dtype, uint32_t flags, void* stream) {
+    if (!out) return ASV_ERR_ARG;
+    *out = nullptr;
+    if (m < 0 || n < 0 || nnz < 0) return ASV_ERR_ARG;
+    if (dtype < ASV_F32 || dtype > ASV_I32) return ASV_ERR_ARG;
+    if (m >= INT32_MAX || n >= INT32_MAX || nnz >= INT32_MAX) return ASV_ERR_OVERFLOW;
+    if (!d_rowptr || (nnz > 0 && !d_colidx)) return ASV_ERR_ARG;
+    if (dtype == ASV_BOOL && d_val) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    asv_matrix_s* H = new (std::nothrow) asv_matrix_s();
+    if (!H) return ASV_ERR_NOMEM;
+    H->dtype = dtype;
+    H->m = m;
+    H->n = n;
+    H->nnz = nnz;
+    H->flags = flags;
+    CKH(cudaGetDevice(&H->dev));
+    CKH(cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, H->dev));
+    H->G = H->num_sms * 4;
+    const size_t vs = vsize(dtype);
+    const bool has_val = (dtype != ASV_BOOL) && d_val != nullptr;
+
+    // CSR: borrowed or copied
+    if (flags & ASV_COPY) {
+        int32_t *rp, *ci;
+        void* v = nullptr;
+        AL(rp, 4 * (m + 1), false);
+        AL(ci, 4 * nnz, false);
+        CKH(cudaMemcpyAsync(rp, d_rowptr, 4 * (m + 1), cudaMemcpyDeviceToDevice, s));
+        if (nnz) CKH(cudaMemcpyAsync(ci, d_colidx, 4 * nnz, cudaMemcpyDeviceToDevice, s));
+        if (has_val) {
+            AL(v, vs * nnz, false);
+            if (nnz) CKH(cudaMemcpyAsync(v, d_val, vs * nnz, cudaMemcpyDeviceToDevice, s));
+        }
+        H->rowptr = rp;
+        H->col = ci;
+        H->val = v;
+    } else {
+        H->rowptr = d_rowptr;
+        H->col = d_colidx;
+        H->val = has_val ? d_val : nullptr;
+    }
+
+    if (flags & ASV_VALIDATE) {
+        int32_t* flag;
+        AL(flag, 4, true);
+        CKH(validate_csr(H, s, flag));
+        int32_t hf = 0;
+        CKH(cudaMemcpyAsync(&hf, flag, 4, cudaMemcpyDeviceToHost, s));
+        CKH(cudaStreamSynchronize(s));
+        if (hf) {
+            destroy_handle(H);
+            return ASV_ERR_NONCANONICAL;
+        }
+    }
+
+    const int64_t nw_n = (n + 31) / 32, nw_m = (m + 31) / 32;
+    const int G = H->G;
+    // CSC view
+    AL(H->colptr, 4 * (n + 1), false);
+    AL(H->rowidx, 4 * nnz, false);
+    AL(H->perm, 4 * nnz, false);
+    if (has_val) AL(H->val_csc, vs * nnz, false);
+    // features / partition / selector
+    AL(H->d_mfeat, sizeof(MatFeat), true);
+    H->ntiles = (m + nnz + pull_tile_items(dtype) - 1) / pull_tile_items(dtype);
+    AL(H->tile_row, 4 * (H->ntiles + 1), false);
+    AL(H->carry_row, 4 * (H->ntiles + 1), false);
+    AL(H->carry_val, 8 * (H->ntiles + 1), false);
+    AL(H->d_trees, sizeof(TreeNode) * kMaxTreeNodes, false);
+    AL(H->d_roots, 4 * 3, false);
+    AL(H->d_desc, sizeof(CallDesc), true);
+    AL(H->d_last_kid, 4, true);
+    // workspaces
+    Ws& w = H->ws;
+    AL(w.xbits_dense, 4 * nw_n, true);
+    AL(w.xbits_scat, 4 * nw_n, true);
+    AL(w.xdense, vs * n, true);
+    AL(w.xlist_idx, 4 * n, false);
+    AL(w.xlist_val, vs * n, false);
+    AL(w.xscan, 4 * (n + 1), false);
+    AL(w.acc, 8 * m, true);
+    AL(w.ytouch, 4 * nw_m, true);
+    AL(w.ywork, vs * m, false);
+    const size_t pv = vs == 8 ? 8 : 4;
+    AL(w.pkeys[0], 4 * nnz, false);
+    AL(w.pkeys[1], 4 * nnz, false);
+    if (dtype != ASV_BOOL) {
+        AL(w.pvals[0], pv * nnz, false);
+        AL(w.pvals[1], pv * nnz, false);
+    }
+    w.pair_cap = nnz;
+    const int64_t hist_n = std::max<int64_t>((int64_t)256 * G + 1, 2 * priv_bins(m) + 2);
+    AL(w.hist, 4 * hist_n, false);
+    AL(w.blk, 4 * (G + 1), false);
+    AL(w.status, 4, true);
+    AL(w.counters, 16, true);
+    AL(w.ticket, 4, true);
+    CKH(cudaDeviceSynchronize());  // the zero-fills above ran on the legacy stream
+
+    CKH(build_csc(H, s));
+    CKH(build_features(H, s));  // synchronises
+    CKH(build_partition(H, s));
+    {
+        std::vector<TreeNode> nodes;
+        int32_t roots[3];
+        default_trees(nodes, roots);
+        CKH(cudaMemcpyAsync(H->d_trees, nodes.data(), sizeof(TreeNode) * nodes.size(), cudaMemcpyHostToDevice, s));
+        CKH(cudaMemcpyAsync(H->d_roots, roots, sizeof(roots), cudaMemcpyHostToDevice, s));
+    }
+    H->pull_lanes = std::min(32, std::max(2, pow2_floor(H->h_mfeat.avg_row / 3.0)));
+    CKH(cudaStreamSynchronize(s));
+    CKH(cudaGetLastError());
+    *out = H;
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_matrix_destroy(asv_matrix A) {
+    if (!A) return ASV_ERR_ARG;
+    destroy_handle(A);
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_matrix_features(asv_matrix A, asv_mfeat* h_out) {
+    if (!A || !h_out) return ASV_ERR_ARG;
+    *h_out = A->h_mfeat;
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_matrix_arrays(asv_matrix A, const int32_t** rp, const int32_t** ci, const void** v,
+                                        const int32_t** cp, const int32_t** ri, const void** vc, const int32_t** perm) {
+    if (!A) return ASV_ERR_ARG;
+    if (rp) *rp = A->rowptr;
+    if (ci) *ci = A->col;
+    if (v) *v = A->val;
+    if (cp) *cp = A->colptr;
+    if (ri) *ri = A->rowidx;
+    if (vc) *vc = A->val_csc;
+    if (perm) *perm = A->perm;
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_matrix_copy_csc(asv_matrix A, int32_t* d_colptr, int32_t* d_rowidx, void* d_val_csc,
+                                          int32_t* d_perm, void* stream) {
+    if (!A) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_colptr) CK(cudaMemcpyAsync(d_colptr, A->colptr, 4 * (A->n + 1), cudaMemcpyDeviceToDevice, s));
+    if (A->nnz > 0) {
+        if (d_rowidx) CK(cudaMemcpyAsync(d_rowidx, A->rowidx, 4 * A->nnz, cudaMemcpyDeviceToDevice, s));
+        if (d_perm) CK(cudaMemcpyAsync(d_perm, A->perm, 4 * A->nnz, cudaMemcpyDeviceToDevice, s));
+        if (d_val_csc && A->val_csc)
+            CK(cudaMemcpyAsync(d_val_csc, A->val_csc, vsize(A->dtype) * A->nnz, cudaMemcpyDeviceToDevice, s));
+    }
+    return ASV_OK;
+}
+
+// ---------------------------------------------------------------- dispatch
+// One candidate, including the vector-format conversion it needs: pull
+// kernels on a sparse x first scatter it into the zero-invariant dense and
+// bitmap workspaces (and clear them afterwards); push kernels on a dense x
+// first compact its bitmap into an ascending list.
+static void enqueue_candidate(asv_matrix_s* H, int k, int x_sparse, int om, cudaStream_t s) {
+    if (k < ASV_K_PUSH_THREAD_ATOM) {
+        const bool masked = k >= ASV_K_MPULL_THREAD;
+        const int dist = k % 3;
+        if (x_sparse) launch_x_scatter(H, true, s);
+        launch_pull(H, dist, masked, om == ASV_OUT_SPARSE, nullptr, s);
+        if (om == ASV_OUT_SPARSE) launch_finalize(H, false, om, s);
+        if (x_sparse) launch_x_scatter(H, false, s);
+    } else {
+        const int q = k - ASV_K_PUSH_THREAD_ATOM;
+        const int dist = q % 3, wb = q / 3;
+        if (!x_sparse) launch_x_compact_list(H, s);
+        launch_push(H, dist, wb, om, s);
+    }
+}
+
+static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om) {
+    if (H->gexec[xs][om]) return ASV_OK;
+    if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = H->cap_stream;
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, ASV_K_PULL_BAL, cudaGraphCondAssignDefault));
+    CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    launch_select(H, (unsigned long long)h, true, cs);
+    cudaGraph_t g2;
+    CK(cudaStreamEndCapture(cs, &g2));
+    cudaGraphNode_t sel;
+    size_t nn = 1;
+    CK(cudaGraphGetNodes(g, &sel, &nn));
+    if (nn != 1) return ASV_ERR_CUDA;
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeSwitch;
+    cp.conditional.size = ASV_K_COUNT;
+    cudaGraphNode_t cn;
+    CK(cudaGraphAddNode(&cn, g, &sel, nullptr, 1, &cp));
+    for (int k = 0; k < ASV_K_COUNT; ++k) {
+        CK(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[k], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+        enqueue_candidate(H, k, xs, om, cs);
+        cudaGraph_t bk;
+        CK(cudaStreamEndCapture(cs, &bk));
+    }
+    cudaGraphExec_t ex;
+    CK(cudaGraphInstantiate(&ex, g, 0));
+    H->graph[xs][om] = g;
+    H->gexec[xs][om] = ex;
+    return ASV_OK;
+}
+
+static asv_status prepare_call(asv_matrix_s* H, const int64_t* d_nnz_x, const int32_t* d_xidx, const void* d_xval,
+                               const void* d_x_dense, int32_t om, void* d_y, int32_t* d_yidx, void* d_yval,
+                               int64_t* d_nnz_y, int64_t y_cap, DescInit& di) {
+    if (om != ASV_OUT_DENSE && om != ASV_OUT_SPARSE) return ASV_ERR_ARG;
+    if (om == ASV_OUT_DENSE && !d_y && H->m > 0) return ASV_ERR_ARG;
+    if (om == ASV_OUT_SPARSE && (!d_yidx || !d_nnz_y || y_cap < 0)) return ASV_ERR_ARG;
+    const bool xs = d_x_dense == nullptr;
+    if (xs && (!d_nnz_x || !d_xidx)) return ASV_ERR_ARG;
+    if (!xs && H->n > 0 && !d_x_dense) return ASV_ERR_ARG;
+    memset(&di, 0, sizeof(di));
+    di.y = d_y;
+    di.yidx = d_yidx;
+    di.yval = d_yval;
+    di.nnz_y = d_nnz_y;
+    di.y_cap = y_cap;
+    di.out_mode = om;
+    di.x_sparse = xs ? 1 : 0;
+    if (xs) {
+        di.x_dense = H->ws.xdense;
+        di.xbits = H->ws.xbits_scat;
+        di.xidx = d_xidx;
+        di.xval = (H->dtype == ASV_BOOL) ? nullptr : d_xval;
+        di.user_xidx = d_xidx;
+        di.user_xval = di.xval;
+        di.user_nnz_x = d_nnz_x;
+    } else {
+        di.x_dense = d_x_dense;
+        di.xbits = H->ws.xbits_dense;
+        di.xidx = H->ws.xlist_idx;
+        di.xval = (H->dtype == ASV_BOOL) ? nullptr : H->ws.xlist_val;
+        di.user_x_dense = d_x_dense;
+    }
+    return ASV_OK;
+}
+
+static void launch_features(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
+    if (di.x_sparse) launch_features_sparse(H, di, s);
+    else launch_features_dense(H, di, s);
+}
+
+extern "C" asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx, const void* d_xval,
+                                 const void* d_x_dense, int32_t out_mode, void* d_y, int32_t* d_yidx, void* d_yval,
+                                 int64_t* d_nnz_y, int64_t y_cap, int32_t kernel, void* stream) {
+    if (!A) return ASV_ERR_ARG;
+    if (kernel < ASV_K_AUTO || kernel >= ASV_K_COUNT) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    DescInit di;
+    asv_status st = prepare_call(A, d_nnz_x, d_xidx, d_xval, d_x_dense, out_mode, d_y, d_yidx, d_yval, d_nnz_y, y_cap, di);
+    if (st != ASV_OK) return st;
+    launch_features(A, di, s);
+    if (kernel == ASV_K_AUTO) {
+        st = build_auto_graph(A, di.x_sparse, out_mode);
+        if (st != ASV_OK) return st;
+        CK(cudaGraphLaunch(A->gexec[di.x_sparse][out_mode], s));
+    } else {
+        enqueue_candidate(A, kernel, di.x_sparse, out_mode, s);
+    }
+    CK(cudaGetLastError());
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_spmv(asv_matrix A, const void* d_x, void* d_y, int32_t kernel, void* stream) {
+    if (!A) return ASV_ERR_ARG;
+    if (kernel < ASV_K_AUTO || kernel >= ASV_K_COUNT) return ASV_ERR_ARG;
+    if ((!d_x && A->n > 0) || (!d_y && A->m > 0)) return ASV_ERR_ARG;
+    if (kernel >= ASV_K_PULL_THREAD && kernel <= ASV_K_PULL_BAL) {
+        // the plain SpMV needs neither the feature pass nor the descriptor
+        PullIO io{d_x, nullptr, d_y};
+        launch_pull(A, kernel, false, false, &io, (cudaStream_t)stream);
+        CK(cudaGetLastError());
+        return ASV_OK;
+    }
+    return asv_spmspv(A, nullptr, nullptr, nullptr, d_x, ASV_OUT_DENSE, d_y, nullptr, nullptr, nullptr, 0, kernel, stream);
+}
+
+extern "C" asv_status asv_select(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx, const void* d_xval,
+                                 const void* d_x_dense, int32_t* h_kernel, asv_vfeat* h_feat, void* stream) {
+    if (!A) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    DescInit di;
+    asv_status st = prepare_call(A, d_nnz_x, d_xidx, d_xval, d_x_dense, ASV_OUT_DENSE, A->ws.ywork, nullptr,
+                                 nullptr, nullptr, 0, di);
+    if (st != ASV_OK) return st;
+    launch_features(A, di, s);
+    launch_select(A, 0ull, false, s);
+    CallDesc hd;
+    CK(cudaMemcpyAsync(&hd, A->d_desc, sizeof(hd), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h_kernel) *h_kernel = hd.kid;
+    if (h_feat) {
+        h_feat->nnz_x = hd.nnz_x;
+        h_feat->nnz_s = hd.nnz_s;
+        h_feat->x_sparsity = hd.vfeat[1];
+        h_feat->m_sparsity = hd.vfeat[3];
+    }
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_last_kernel(asv_matrix A, int32_t* h_kernel, void* stream) {
+    if (!A || !h_kernel) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(h_kernel, A->d_last_kid, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_compact(asv_matrix A, const void* d_x_dense, int32_t* d_idx, void* d_val, int64_t* d_count,
+                                  void* stream) {
+    if (!A || (!d_x_dense && A->n > 0) || !d_idx || !d_count) return ASV_ERR_ARG;
+    launch_compact_public(A, d_x_dense, d_idx, d_val, d_count, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t n_nodes, const int32_t* h_roots,
+                                    void* stream) {
+    if (!A || !h_nodes || !h_roots || n_nodes <= 0 || n_nodes > kMaxTreeNodes) return ASV_ERR_ARG;
+    std::vector<TreeNode> nodes(n_nodes);
+    for (int i = 0; i < n_nodes; ++i) {
+        const double* r = h_nodes + 5 * i;
+        TreeNode& t = nodes[i];
+        t.feature = (int32_t)r[0];
+        t.thr = r[1];
+        t.left = (int32_t)r[2];
+        t.right = (int32_t)r[3];
+        t.leaf = (int32_t)r[4];
+        if (t.feature >= 13) return ASV_ERR_ARG;
+        if (t.feature >= 0 && (t.left < 0 || t.left >= n_nodes || t.right < 0 || t.right >= n_nodes)) return ASV_ERR_ARG;
+        if (t.feature < 0 && (t.leaf < 0 || t.leaf > 2)) return ASV_ERR_ARG;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (h_roots[i] < 0 || h_roots[i] >= n_nodes) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(A->d_trees, nodes.data(), sizeof(TreeNode) * n_nodes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(A->d_roots, h_roots, 12, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_get_status(asv_matrix A, void* stream) {
+    if (!A) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t v = 0;
+    CK(cudaMemcpyAsync(&v, A->ws.status, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(A->ws.status, 0, 4, s));
+    CK(cudaStreamSynchronize(s));
+    return v;
+}
+
+extern "C" int32_t asv_last_cuda_error(void) { return g_last_cuda; }
+
+extern "C" const char* asv_status_string(asv_status s) {
+    switch (s) {
+        case ASV_OK: return "ok";
+        case ASV_ERR_ARG: return "invalid argument";
+        case ASV_ERR_NONCANONICAL: return "non-canonical CSR";
+        case ASV_ERR_OVERFLOW: return "size overflows the int32 index layout";
+        case ASV_ERR_CAPACITY: return "sparse output exceeds y_cap";
+        case ASV_ERR_TIMEOUT: return "bounded device wait timed out";
+        case ASV_ERR_CUDA: return "CUDA runtime error";
+        case ASV_ERR_CHECKED: return "device bounds check failed";
+        case ASV_ERR_NOMEM: return "out of device memory";
+        case ASV_ERR_UNSUPPORTED: return "unsupported combination";
+    }
+    return "unknown status";
+}
+
+extern "C" int32_t asv_version(void) { return 100; }

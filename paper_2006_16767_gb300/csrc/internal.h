@@ -1,0 +1,105 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+struct asv_matrix_s {
+    int dev = 0;
+    int32_t dtype = ASV_F32;
+    int64_t m = 0, n = 0, nnz = 0;
+    uint32_t flags = 0;
+    int num_sms = 0;
+    // CSR (borrowed or owned) and CSC (owned)
+    const int32_t* rowptr = nullptr;
+    const int32_t* col = nullptr;
+    const void* val = nullptr;
+    int32_t* colptr = nullptr;
+    int32_t* rowidx = nullptr;
+    void* val_csc = nullptr;
+    int32_t* perm = nullptr;
+    // features (Table 1)
+    asv::MatFeat* d_mfeat = nullptr;
+    asv_mfeat h_mfeat{};
+    // nnz-balanced (merge-path) partition of the pull pattern
+    int32_t* tile_row = nullptr;
+    int64_t ntiles = 0;
+    int32_t* carry_row = nullptr;
+    void* carry_val = nullptr;
+    int pull_lanes = 8;  // lanes per row of the (sub-)warp pull kernels
+    // selector tables
+    asv::TreeNode* d_trees = nullptr;
+    int32_t* d_roots = nullptr;
+    // per-call state
+    asv::CallDesc* d_desc = nullptr;
+    asv::Ws ws{};
+    int32_t* d_last_kid = nullptr;
+    // graphs of the selector-driven path, one per (x format, output mode)
+    cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaStream_t cap_stream = nullptr;
+    int G = 0;  // fixed grid of the scan / sort / compaction primitives
+    std::vector<void*> allocs;
+};
+
+namespace asv {
+
+size_t vsize(int32_t dtype);
+const char* kernel_name(int k);
+
+// matrix.cu -- run once at handle creation
+cudaError_t build_csc(asv_matrix_s* H, cudaStream_t s);
+cudaError_t build_features(asv_matrix_s* H, cudaStream_t s);
+cudaError_t build_partition(asv_matrix_s* H, cudaStream_t s);
+int64_t pull_tile_items(int32_t dtype);
+cudaError_t validate_csr(asv_matrix_s* H, cudaStream_t s, int32_t* d_flag);
+
+// shared scan launcher (device-side count allowed)
+void scan_excl(const int32_t* in, int32_t* out, int64_t n_h, const int64_t* n_d, int32_t* blk, int G,
+               bool write_total, cudaStream_t s);
+
+// vector.cu -- per call
+struct DescInit {
+    const void* x_dense;
+    const uint32_t* xbits;
+    const int32_t* xidx;
+    const void* xval;
+    void* y;
+    int32_t* yidx;
+    void* yval;
+    int64_t* nnz_y;
+    int64_t y_cap;
+    const void* user_x_dense;
+    const int32_t* user_xidx;
+    const void* user_xval;
+    const int64_t* user_nnz_x;
+    int32_t out_mode;
+    int32_t x_sparse;
+};
+void launch_features_dense(asv_matrix_s* H, const DescInit& di, cudaStream_t s);
+void launch_features_sparse(asv_matrix_s* H, const DescInit& di, cudaStream_t s);
+void launch_x_scatter(asv_matrix_s* H, bool set, cudaStream_t s);
+void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s);
+void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s);
+void launch_compact_public(asv_matrix_s* H, const void* x, int32_t* idx, void* val, int64_t* count,
+                           cudaStream_t s);
+
+// pull.cu
+struct PullIO {
+    const void* x;
+    const uint32_t* xbits;
+    void* y;
+};
+void launch_pull(asv_matrix_s* H, int dist, bool masked, bool sparse_out, const PullIO* direct,
+                 cudaStream_t s);
+
+// push.cu
+void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s);
+
+// select.cu
+void launch_select(asv_matrix_s* H, unsigned long long cond_handle, bool set_cond, cudaStream_t s);
+void default_trees(std::vector<TreeNode>& nodes, int32_t roots[3]);
+
+}  // namespace asv

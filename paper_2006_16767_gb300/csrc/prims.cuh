@@ -1,0 +1,187 @@
+// Parallel primitives used by the runtime procedure (Sec. VI-C: "reduction,
+// prefix sum and stream compaction") and by the sort-based write-back
+// (Sec. IV-B): block/device exclusive scans, a stable LSD radix sort of
+// 32-bit keys with optional payload, and ordered bitmap compaction.
+#pragma once
+#include "common.cuh"
+
+namespace asv {
+
+// ---------------------------------------------------------------- block helpers
+template <int B, class V>
+__device__ __forceinline__ V block_reduce_sum(V v, V* sm /* >= B/32 */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if (lane == 0) sm[wid] = v;
+    __syncthreads();
+    V r = 0;
+    if (wid == 0) {
+        r = (lane < B / 32) ? sm[lane] : V(0);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) r += __shfl_xor_sync(0xffffffffu, r, d);
+        if (lane == 0) sm[0] = r;
+    }
+    __syncthreads();
+    r = sm[0];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive block scan of one value per thread; *total receives the sum.
+template <int B, class V>
+__device__ __forceinline__ V block_excl_scan(V v, V* sm /* >= B/32 + 1 */, V* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    V inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        V o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) sm[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        V w = (lane < B / 32) ? sm[lane] : V(0);
+        V wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            V o = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += o;
+        }
+        if (lane < B / 32) sm[lane] = wi - w;  // exclusive warp offsets
+        if (lane == B / 32 - 1) sm[B / 32] = wi;
+    }
+    __syncthreads();
+    V r = sm[wid] + inc - v;
+    if (total) *total = sm[B / 32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int64_t dev_count(int64_t host_n, const int64_t* dev_n) {
+    return dev_n ? *dev_n : host_n;
+}
+
+// ---------------------------------------------------------------- device exclusive scan
+// Three launches over a fixed grid of G blocks, each owning one contiguous
+// range: per-block sums, a one-block scan of the sums, then per-block scans
+// seeded with the block offset. Deterministic; n may live on the device.
+template <int B>
+__global__ void __launch_bounds__(B) k_scan_reduce(const int32_t* in, int64_t n_h, const int64_t* n_d,
+                                                   int32_t* blk) {
+    __shared__ int32_t sm[B / 32 + 1];
+    const int64_t n = dev_count(n_h, n_d);
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    int32_t s = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += B) s += in[i];
+    s = block_reduce_sum<B>(s, sm);
+    if (threadIdx.x == 0) blk[blockIdx.x] = s;
+}
+
+// Exclusive scan of blk[0..G) in place; blk[G] receives the total.
+template <int B>
+__global__ void __launch_bounds__(B) k_scan_blocks(int32_t* blk, int G) {
+    __shared__ int32_t sm[B / 32 + 1];
+    int32_t base = 0;
+    for (int off = 0; off < G; off += B) {
+        const int i = off + threadIdx.x;
+        int32_t v = i < G ? blk[i] : 0, tot;
+        int32_t e = block_excl_scan<B>(v, sm, &tot);
+        if (i < G) blk[i] = base + e;
+        base += tot;
+    }
+    if (threadIdx.x == 0) blk[G] = base;
+}
+
+template <int B>
+__global__ void __launch_bounds__(B) k_scan_down(const int32_t* in, int32_t* out, int64_t n_h,
+                                                 const int64_t* n_d, const int32_t* blk, int write_total) {
+    __shared__ int32_t sm[B / 32 + 1];
+    const int64_t n = dev_count(n_h, n_d);
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    int32_t base = blk[blockIdx.x];
+    for (int64_t off = lo; off < hi; off += B) {
+        const int64_t i = off + threadIdx.x;
+        int32_t v = i < hi ? in[i] : 0, tot;
+        int32_t e = block_excl_scan<B>(v, sm, &tot);
+        if (i < hi) out[i] = base + e;
+        base += tot;
+    }
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = blk[gridDim.x];
+}
+
+// ---------------------------------------------------------------- radix sort (LSD, 8-bit digits)
+template <int B>
+__global__ void __launch_bounds__(B) k_radix_hist(const uint32_t* keys, int64_t n_h, const int64_t* n_d,
+                                                  int shift, int32_t* hist /* [256][G] */) {
+    __shared__ int32_t h[256];
+    for (int d = threadIdx.x; d < 256; d += B) h[d] = 0;
+    __syncthreads();
+    const int64_t n = dev_count(n_h, n_d);
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += B) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += B) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
+}
+
+// Stable scatter: items of a block keep their order within each digit
+// (warp match + per-warp digit counts per round of B items), and blocks are
+// ordered by the digit-major exclusive scan of the histogram.
+template <int B, class V, bool HAS_V>
+__global__ void __launch_bounds__(B) k_radix_scatter(const uint32_t* kin, const V* vin, uint32_t* kout,
+                                                     V* vout, int64_t n_h, const int64_t* n_d, int shift,
+                                                     const int32_t* offs /* [256][G] exclusive */) {
+    constexpr int NW = B / 32;
+    __shared__ int32_t base[256];
+    __shared__ int32_t cnt[NW][257];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < 256; d += B) base[d] = offs[(int64_t)d * gridDim.x + blockIdx.x];
+    const int64_t n = dev_count(n_h, n_d);
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    for (int64_t off = lo; off < hi; off += B) {
+        for (int e = threadIdx.x; e < NW * 257; e += B) (&cnt[0][0])[e] = 0;
+        __syncthreads();
+        const int64_t i = off + threadIdx.x;
+        const bool valid = i < hi;
+        uint32_t key = valid ? kin[i] : 0u;
+        V v{};
+        if (HAS_V && valid) v = vin[i];
+        const int d = valid ? (int)((key >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lanemask_lt());
+        if (rank == 0) cnt[wid][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int32_t pos = base[d] + rank;
+            for (int w = 0; w < wid; ++w) pos += cnt[w][d];
+            kout[pos] = key;
+            if (HAS_V) vout[pos] = v;
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < 256; dd += B) {
+            int32_t s = 0;
+            for (int w = 0; w < NW; ++w) s += cnt[w][dd];
+            base[dd] += s;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- ordered bitmap compaction
+// Count phase: blk[b] = set bits in block b's contiguous word range.
+template <int B>
+__global__ void __launch_bounds__(B) k_bits_count(const uint32_t* bits, int64_t nwords, int32_t* blk) {
+    __shared__ int32_t sm[B / 32 + 1];
+    const int64_t chunk = (nwords + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
+    int32_t s = 0;
+    for (int64_t w = lo + threadIdx.x; w < hi; w += B) s += __popc(bits[w]);
+    s = block_reduce_sum<B>(s, sm);
+    if (threadIdx.x == 0) blk[blockIdx.x] = s;
+}
+
+}  // namespace asv

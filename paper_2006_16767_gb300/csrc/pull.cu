@@ -1,0 +1,369 @@
+// Row-major (CSR "pull") candidates of Sec. IV-A: the traditional SpMV
+// (solution (3,6), no validation) and the row-major SpMSpV (solution (3,5),
+// bitvector validation after GraphMat, Sec. VI-A), each with three workload
+// distributions (Sec. IV-B): one row per thread (the paper's "direct"), a
+// sub-warp of L lanes per row, and an even split of rows+nonzeros along the
+// merge path (the paper's "load-balanced", after merge-based SpMV / Hola).
+//
+// Output: dense y (y_i written exactly once per call); in sparse-output mode
+// y goes to a workspace and rows with an effective entry set their bit in the
+// zero-invariant structural-set bitmap, which a compaction pass turns into
+// the ascending output list.
+#include "internal.h"
+#include "prims.cuh"
+
+namespace asv {
+
+constexpr int kBalB = 256;   // threads per balanced tile
+constexpr int kBalIPT = 8;   // merge items per thread
+constexpr int kBalD = kBalB * kBalIPT;
+
+int64_t pull_tile_items(int32_t) { return kBalD; }
+
+struct PullArg {
+    const CallDesc* desc;  // read x/y from the call descriptor when non-null
+    PullIO io;             // otherwise the pointers given directly
+};
+
+__device__ __forceinline__ PullIO resolve(const PullArg& a, void* ywork, bool sparse_out) {
+    if (a.desc) {
+        PullIO p;
+        p.x = a.desc->x_dense;
+        p.xbits = a.desc->xbits;
+        p.y = sparse_out ? ywork : a.desc->y;
+        return p;
+    }
+    return a.io;
+}
+
+// ---------------------------------------------------------------- one row per thread
+template <class T, bool MASK, bool SOUT>
+__global__ void __launch_bounds__(256) k_pull_thread(int64_t m, const int32_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                     PullArg a, void* ywork, uint32_t* ytouch) {
+    using S = Sr<T>;
+    const PullIO p = resolve(a, ywork, SOUT);
+    const T* __restrict__ x = (const T*)p.x;
+    T* __restrict__ y = (T*)p.y;
+    for (int64_t base = (int64_t)blockIdx.x * 256; base < m; base += (int64_t)gridDim.x * 256) {
+        const int64_t i = base + threadIdx.x;
+        bool hit = false;
+        if (i < m) {
+            typename S::Acc acc;
+            S::acc_zero(acc);
+            const int32_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+            for (int32_t k = b; k < e; ++k) {
+                const int32_t c = __ldg(col + k);
+                if (MASK || SOUT) {
+                    const bool bit = test_bit(p.xbits, c);
+                    hit |= bit;
+                    if (MASK && !bit) continue;
+                }
+                S::acc_add(acc, S::mul(load_val(val, k), __ldg(x + c)));
+            }
+            y[i] = S::part_T(S::acc_part(acc));
+        }
+        if (SOUT) {
+            const unsigned w = __ballot_sync(0xffffffffu, hit);
+            if ((threadIdx.x & 31) == 0 && i < m) ytouch[i >> 5] = w;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- L lanes per row
+template <class T, bool MASK, bool SOUT, int L>
+__global__ void __launch_bounds__(256) k_pull_warp(int64_t m, const int32_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                   PullArg a, void* ywork, uint32_t* ytouch) {
+    using S = Sr<T>;
+    using P = typename S::Part;
+    constexpr int GPB = 256 / L;
+    const PullIO p = resolve(a, ywork, SOUT);
+    const T* __restrict__ x = (const T*)p.x;
+    T* __restrict__ y = (T*)p.y;
+    const int g = threadIdx.x / L, l = threadIdx.x % L;
+    for (int64_t i0 = (int64_t)blockIdx.x * GPB; i0 < m; i0 += (int64_t)gridDim.x * GPB) {
+        const int64_t i = i0 + g;
+        typename S::Acc acc;
+        S::acc_zero(acc);
+        bool hit = false;
+        if (i < m) {
+            const int32_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+            for (int32_t k = b + l; k < e; k += L) {
+                const int32_t c = __ldg(col + k);
+                if (MASK || SOUT) {
+                    const bool bit = test_bit(p.xbits, c);
+                    hit |= bit;
+                    if (MASK && !bit) continue;
+                }
+                S::acc_add(acc, S::mul(load_val(val, k), __ldg(x + c)));
+            }
+        }
+        P v = S::acc_part(acc);
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) v = S::part_add(v, shfl_xor(v, o, L));
+        if (SOUT) {
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            const unsigned gm = (0xffffffffu >> (32 - L)) << ((threadIdx.x & 31) & ~(L - 1));
+            hit = (bal & gm) != 0;
+        }
+        if (i < m && l == 0) {
+            y[i] = S::part_T(v);
+            if (SOUT && hit) set_bit_once(ytouch, i);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- merge-path balanced
+// Stages a tile's products into shared memory. Column ids (and values) are
+// read with 128-bit loads over the 16-byte-aligned span covering [k0, k1).
+template <class T, bool MASK, bool SOUT, bool VEC>
+__device__ __forceinline__ void stage_products(const int32_t* __restrict__ col, const T* __restrict__ val,
+                                               const T* __restrict__ x, const uint32_t* __restrict__ xbits,
+                                               int64_t k0, int64_t k1, int64_t nnz, typename Sr<T>::Part* s_prod,
+                                               uint32_t* s_eff) {
+    using S = Sr<T>;
+    const int64_t a0 = k0 & ~(int64_t)3;
+    const int ngroups = (int)((k1 - a0 + 3) >> 2);
+    for (int gi = threadIdx.x; gi < ngroups; gi += kBalB) {
+        const int64_t base = a0 + 4 * (int64_t)gi;
+        int32_t c[4];
+        const bool full = VEC && (base + 4 <= nnz);
+        if (full) {
+            const int4 cc = __ldg(reinterpret_cast<const int4*>(col + base));
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) c[e] = (base + e < nnz) ? __ldg(col + base + e) : 0;
+        }
+        bool in[4], bit[4], eff[4];
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            in[e] = (base + e >= k0) && (base + e < k1);
+            bit[e] = (MASK || SOUT) && in[e] ? test_bit(xbits, c[e]) : true;
+            eff[e] = in[e] && (!MASK || bit[e]);
+            any |= eff[e];
+        }
+        T v[4];
+        if (!S::kPattern && any) {
+            if (full && val != nullptr && sizeof(T) == 4) {
+                const float4 vv = __ldg(reinterpret_cast<const float4*>(val + base));
+                v[0] = *reinterpret_cast<const T*>(&vv.x);
+                v[1] = *reinterpret_cast<const T*>(&vv.y);
+                v[2] = *reinterpret_cast<const T*>(&vv.z);
+                v[3] = *reinterpret_cast<const T*>(&vv.w);
+            } else if (full && val != nullptr && sizeof(T) == 8) {
+                const double2 v01 = __ldg(reinterpret_cast<const double2*>(val + base));
+                const double2 v23 = __ldg(reinterpret_cast<const double2*>(val + base + 2));
+                v[0] = *reinterpret_cast<const T*>(&v01.x);
+                v[1] = *reinterpret_cast<const T*>(&v01.y);
+                v[2] = *reinterpret_cast<const T*>(&v23.x);
+                v[3] = *reinterpret_cast<const T*>(&v23.y);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e] = eff[e] ? load_val(val, base + e) : T(0);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = S::one();
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (!in[e]) continue;
+            const int li = (int)(base + e - k0);
+            s_prod[li] = eff[e] ? S::mul(v[e], __ldg(x + c[e])) : typename S::Part(0);
+            if (SOUT && bit[e]) atomicOr(&s_eff[li >> 5], 1u << (li & 31));
+        }
+    }
+}
+
+template <class T, bool MASK, bool SOUT, bool VEC>
+__global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, const int32_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                    const int32_t* __restrict__ tile_row, PullArg a, void* ywork,
+                                                    uint32_t* ytouch, int32_t* carry_row,
+                                                    typename Sr<T>::Atom* carry_val) {
+    using S = Sr<T>;
+    using P = typename S::Part;
+    constexpr int B = kBalB, IPT = kBalIPT, D = kBalD, NW = B / 32;
+    __shared__ int32_t s_end[D];
+    __shared__ P s_prod[D];
+    __shared__ P s_row[D];
+    __shared__ P s_scan[B];
+    __shared__ uint32_t s_eff[SOUT ? D / 32 : 1];
+    __shared__ int32_t s_wkey[NW], s_wfirst[NW];
+    __shared__ P s_wval[NW];
+
+    const PullIO p = resolve(a, ywork, SOUT);
+    const T* __restrict__ x = (const T*)p.x;
+    T* __restrict__ y = (T*)p.y;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+    const int64_t t = blockIdx.x;
+    const int64_t d0 = t * D, d1 = min(d0 + D, m + nnz);
+    const int32_t r0 = tile_row[t], r1 = tile_row[t + 1];
+    const int64_t k0 = d0 - r0, k1 = d1 - r1;
+    const int nrows = r1 - r0, nk = (int)(k1 - k0);
+
+    for (int i = threadIdx.x; i < nrows; i += B) s_end[i] = __ldg(rowptr + r0 + 1 + i);
+    if (SOUT)
+        for (int i = threadIdx.x; i < D / 32; i += B) s_eff[i] = 0u;
+    if (SOUT) __syncthreads();
+    stage_products<T, MASK, SOUT, VEC>(col, val, x, p.xbits, k0, k1, nnz, s_prod, s_eff);
+    __syncthreads();
+
+    // this thread's share of the tile's merge path
+    const int total = nrows + nk;
+    const int dt = min((int)threadIdx.x * IPT, total), dte = min(dt + IPT, total);
+    int lo = max(0, dt - nk), hi = min(dt, nrows);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int64_t)s_end[mid] <= k0 + (dt - mid - 1)) lo = mid + 1;
+        else hi = mid;
+    }
+    int ri = lo, ki = dt - lo;
+    const int ri_start = ri;
+    typename S::Acc acc;
+    S::acc_zero(acc);
+    bool hit = false;
+    for (int step = dt; step < dte; ++step) {
+        if (ri < nrows && (int64_t)s_end[ri] <= k0 + ki) {
+            s_row[ri] = S::acc_part(acc);
+            S::acc_zero(acc);
+            if (SOUT && hit) set_bit_once(ytouch, (int64_t)r0 + ri);
+            hit = false;
+            ++ri;
+        } else {
+            S::acc_add(acc, s_prod[ki]);
+            if (SOUT) hit |= (s_eff[ki >> 5] >> (ki & 31)) & 1u;
+            ++ki;
+        }
+    }
+    if (SOUT && hit) set_bit_once(ytouch, (int64_t)r0 + ri);
+
+    // segmented inclusive scan of the threads' carries (key = row still open
+    // at the thread's end; keys are non-decreasing across threads)
+    P v = S::acc_part(acc);
+    const int key = ri;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const P pv = shfl_up(v, o);
+        const int pk = shfl_up(key, o);
+        if (lane >= o && pk == key) v = S::part_add(pv, v);
+    }
+    if (lane == 31) { s_wkey[wid] = key; s_wval[wid] = v; }
+    if (lane == 0) s_wfirst[wid] = key;
+    __syncthreads();
+    if (wid > 0 && s_wkey[wid - 1] == key) {
+        P c = s_wval[wid - 1];
+        int ww = wid - 1;
+        while (ww > 0 && s_wfirst[ww] == key && s_wkey[ww - 1] == key) {
+            c = S::part_add(s_wval[ww - 1], c);
+            --ww;
+        }
+        v = S::part_add(c, v);
+    }
+    s_scan[threadIdx.x] = v;
+    __syncthreads();
+    // the first row this thread completed collects the carries of the
+    // threads before it that worked on the same row
+    if (threadIdx.x > 0 && ri > ri_start) s_row[ri_start] = S::part_add(s_scan[threadIdx.x - 1], s_row[ri_start]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrows; i += B) y[r0 + i] = S::part_T(s_row[i]);
+    if (threadIdx.x == B - 1) {
+        carry_row[t] = (r1 < m) ? r1 : -1;
+        carry_val[t] = S::to_atom(S::part_T(v));
+    }
+}
+
+// Adds the partial sums of rows that span several tiles: the first tile of a
+// run of tiles that leave the same row open sums their carries (in FP64 for
+// the floating-point types) into the value the completing tile wrote.
+template <class T>
+__global__ void k_pull_bal_fixup(int64_t ntiles, const int32_t* __restrict__ carry_row,
+                                 const typename Sr<T>::Atom* __restrict__ carry_val, const CallDesc* desc,
+                                 void* ydirect, void* ywork, int sparse_out) {
+    using S = Sr<T>;
+    T* y = (T*)(desc ? (sparse_out ? ywork : desc->y) : ydirect);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = carry_row[t];
+        if (r < 0) continue;
+        if (t > 0 && carry_row[t - 1] == r) continue;
+        typename S::Atom s = carry_val[t];
+        for (int64_t u = t + 1; u < ntiles && carry_row[u] == r; ++u) {
+            if constexpr (S::kPattern) s = s | carry_val[u];
+            else s = s + carry_val[u];
+        }
+        if constexpr (S::kPattern) y[r] = S::from_atom(S::to_atom(S::part_of(y[r])) | s);
+        else y[r] = S::from_atom(S::to_atom(S::part_of(y[r])) + s);
+    }
+}
+
+// ---------------------------------------------------------------- launcher
+template <class T, bool MASK, bool SOUT>
+static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaStream_t s) {
+    PullArg a;
+    a.desc = direct ? nullptr : H->d_desc;
+    if (direct) a.io = *direct;
+    else a.io = PullIO{nullptr, nullptr, nullptr};
+    const int64_t m = H->m;
+    const T* val = (const T*)H->val;
+    void* ywork = H->ws.ywork;
+    uint32_t* yt = H->ws.ytouch;
+    const int64_t cap = (int64_t)H->num_sms * 16;
+    if (dist == 0) {
+        const int64_t g = min(cap, max((int64_t)1, (m + 255) / 256));
+        if (m > 0) k_pull_thread<T, MASK, SOUT><<<(int)g, 256, 0, s>>>(m, H->rowptr, H->col, val, a, ywork, yt);
+    } else if (dist == 1) {
+        const int L = H->pull_lanes;
+        const int64_t gpb = 256 / L;
+        const int64_t g = min(cap, max((int64_t)1, (m + gpb - 1) / gpb));
+        if (m == 0) return;
+#define PW(LL) k_pull_warp<T, MASK, SOUT, LL><<<(int)g, 256, 0, s>>>(m, H->rowptr, H->col, val, a, ywork, yt)
+        switch (L) {
+            case 2: PW(2); break;
+            case 4: PW(4); break;
+            case 8: PW(8); break;
+            case 16: PW(16); break;
+            default: PW(32); break;
+        }
+#undef PW
+    } else {
+        if (H->ntiles == 0) return;
+        using Atom = typename Sr<T>::Atom;
+        const bool vec = ((uintptr_t)H->col % 16 == 0) && ((uintptr_t)H->val % 16 == 0);
+        if (vec)
+            k_pull_bal<T, MASK, SOUT, true><<<(int)H->ntiles, kBalB, 0, s>>>(
+                m, H->nnz, H->rowptr, H->col, val, H->tile_row, a, ywork, yt, H->carry_row, (Atom*)H->carry_val);
+        else
+            k_pull_bal<T, MASK, SOUT, false><<<(int)H->ntiles, kBalB, 0, s>>>(
+                m, H->nnz, H->rowptr, H->col, val, H->tile_row, a, ywork, yt, H->carry_row, (Atom*)H->carry_val);
+        const int64_t g = min(cap, (H->ntiles + 255) / 256);
+        k_pull_bal_fixup<T><<<(int)g, 256, 0, s>>>(H->ntiles, H->carry_row, (const Atom*)H->carry_val,
+                                                   direct ? nullptr : H->d_desc, direct ? direct->y : nullptr,
+                                                   ywork, SOUT ? 1 : 0);
+    }
+}
+
+template <class T>
+static void pull_dtype(asv_matrix_s* H, int dist, bool masked, bool sout, const PullIO* direct, cudaStream_t s) {
+    if (masked) {
+        if (sout) pull_dispatch<T, true, true>(H, dist, direct, s);
+        else pull_dispatch<T, true, false>(H, dist, direct, s);
+    } else {
+        if (sout) pull_dispatch<T, false, true>(H, dist, direct, s);
+        else pull_dispatch<T, false, false>(H, dist, direct, s);
+    }
+}
+
+void launch_pull(asv_matrix_s* H, int dist, bool masked, bool sparse_out, const PullIO* direct, cudaStream_t s) {
+    switch (H->dtype) {
+        case ASV_F32: pull_dtype<float>(H, dist, masked, sparse_out, direct, s); break;
+        case ASV_F64: pull_dtype<double>(H, dist, masked, sparse_out, direct, s); break;
+        case ASV_I32: pull_dtype<int32_t>(H, dist, masked, sparse_out, direct, s); break;
+        case ASV_BOOL: pull_dtype<bool8>(H, dist, masked, sparse_out, direct, s); break;
+    }
+}
+
+}  // namespace asv

@@ -1,0 +1,381 @@
+// Per-call vector work of the runtime procedure (Sec. VI-C): the feature pass
+// over x (nnz_x, x_sparsity, nnz_s, m_sparsity of Table 1) that also builds
+// x's bitmap (the bitvector of Sec. VI-A) and fills the call descriptor;
+// sparse<->dense conversion of x (done only inside the branches that need it);
+// ordered stream compaction; and write-out of the push kernels' accumulators.
+#include "internal.h"
+#include "prims.cuh"
+
+namespace asv {
+
+// Block totals of the feature pass go to zero-invariant counters; the last
+// block to finish (ticket) publishes them to the descriptor and re-zeroes.
+__device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di, unsigned long long nx,
+                                             unsigned long long ns, int64_t n, int64_t nnz) {
+    desc->x_dense = di.x_dense;
+    desc->xbits = di.xbits;
+    desc->xidx = di.xidx;
+    desc->xval = di.xval;
+    desc->nnz_x = (int64_t)nx;
+    desc->nnz_s = (int64_t)ns;
+    desc->y = di.y;
+    desc->yidx = di.yidx;
+    desc->yval = di.yval;
+    desc->nnz_y = di.nnz_y;
+    desc->y_cap = di.y_cap;
+    desc->user_x_dense = di.user_x_dense;
+    desc->user_xidx = di.user_xidx;
+    desc->user_xval = di.user_xval;
+    desc->out_mode = di.out_mode;
+    desc->x_sparse = di.x_sparse;
+    desc->vfeat[0] = (double)nx;
+    desc->vfeat[1] = n > 0 ? (double)nx / (double)n : 0.0;
+    desc->vfeat[2] = (double)ns;
+    desc->vfeat[3] = nnz > 0 ? (double)ns / (double)nnz : 0.0;
+}
+
+template <int B>
+__device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long* counters,
+                                              unsigned int* ticket, CallDesc* desc, const DescInit& di, int64_t n,
+                                              int64_t nnz, int32_t* status) {
+    __shared__ unsigned long long sm[B / 32 + 1];
+    __shared__ bool last;
+    cx = block_reduce_sum<B>(cx, sm);
+    cs = block_reduce_sum<B>(cs, sm);
+    if (threadIdx.x == 0) {
+        if (cx) atomicAdd(&counters[0], cx);
+        if (cs) atomicAdd(&counters[1], cs);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        unsigned long long nx = atomicExch(&counters[0], 0ull);
+        unsigned long long ns = atomicExch(&counters[1], 0ull);
+        // a list with repeated or out-of-range entries could exceed the
+        // workspaces sized for nnz_x <= n and nnz_s <= nnz: clamp and report
+        if (nx > (unsigned long long)n || ns > (unsigned long long)nnz) {
+            latch_status(status, ASV_ERR_ARG);
+            nx = nx > (unsigned long long)n ? (unsigned long long)n : nx;
+            ns = ns > (unsigned long long)nnz ? (unsigned long long)nnz : ns;
+        }
+        publish_desc(desc, di, nx, ns, n, nnz);
+        __threadfence();
+        atomicExch(ticket, 0u);
+    }
+}
+
+// Dense x: one warp per 32-element bitmap word (ballot), degree of every
+// nonzero column from colptr, block totals to the ticketed counters.
+template <class T, int B>
+__global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64_t n, const int32_t* __restrict__ colptr,
+                                                  uint32_t* xbits, unsigned long long* counters, unsigned int* ticket,
+                                                  CallDesc* desc, DescInit di, int64_t nnz, int32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwords = (n + 31) >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * (B / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (B / 32);
+    unsigned long long cx = 0, cs = 0;
+    for (int64_t w = gw; w < nwords; w += nw) {
+        const int64_t j = w * 32 + lane;
+        bool nz = false;
+        if (j < n) {
+            nz = Sr<T>::nz(__ldg(x + j));
+            if (nz) cs += (unsigned long long)(__ldg(colptr + j + 1) - __ldg(colptr + j));
+        }
+        const unsigned bits = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) {
+            xbits[w] = bits;
+            cx += __popc(bits);
+        }
+    }
+    finish_counts<B>(cx, cs, counters, ticket, desc, di, n, nnz, status);
+}
+
+// Sparse x: nnz_s = sum of the listed columns' lengths.
+template <int B>
+__global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ nnz_x_dev, const int32_t* __restrict__ xidx,
+                                                   const int32_t* __restrict__ colptr, unsigned long long* counters,
+                                                   unsigned int* ticket, CallDesc* desc, DescInit di, int64_t n,
+                                                   int64_t nnz, int32_t* status) {
+    int64_t nx = *nnz_x_dev;
+    if (nx < 0) nx = 0;
+    if (nx > n) nx = n + 1;  // reported and clamped when the totals are published
+    unsigned long long cs = 0;
+    for (int64_t t = blockIdx.x * (int64_t)B + threadIdx.x; t < min(nx, n); t += (int64_t)gridDim.x * B) {
+        const int32_t j = __ldg(xidx + t);
+        cs += (unsigned long long)(__ldg(colptr + j + 1) - __ldg(colptr + j));
+    }
+    finish_counts<B>(blockIdx.x == 0 && threadIdx.x == 0 ? (unsigned long long)nx : 0ull, cs, counters, ticket, desc,
+                     di, n, nnz, status);
+}
+
+static int feat_grid(asv_matrix_s* H, int64_t items) {
+    const int64_t g = (items + 255) / 256;
+    return (int)max((int64_t)1, min(g, (int64_t)H->num_sms * 8));
+}
+
+void launch_features_dense(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
+    const int g = feat_grid(H, ((H->n + 31) / 32) * 32);
+    auto* c = H->ws.counters;
+    auto* tk = H->ws.ticket;
+    switch (H->dtype) {
+        case ASV_F32:
+            k_feat_dense<float, 256><<<g, 256, 0, s>>>((const float*)di.user_x_dense, H->n, H->colptr, H->ws.xbits_dense,
+                                                       c, tk, H->d_desc, di, H->nnz, H->ws.status);
+            break;
+        case ASV_F64:
+            k_feat_dense<double, 256><<<g, 256, 0, s>>>((const double*)di.user_x_dense, H->n, H->colptr,
+                                                        H->ws.xbits_dense, c, tk, H->d_desc, di, H->nnz, H->ws.status);
+            break;
+        case ASV_I32:
+            k_feat_dense<int32_t, 256><<<g, 256, 0, s>>>((const int32_t*)di.user_x_dense, H->n, H->colptr,
+                                                         H->ws.xbits_dense, c, tk, H->d_desc, di, H->nnz, H->ws.status);
+            break;
+        case ASV_BOOL:
+            k_feat_dense<bool8, 256><<<g, 256, 0, s>>>((const bool8*)di.user_x_dense, H->n, H->colptr, H->ws.xbits_dense,
+                                                       c, tk, H->d_desc, di, H->nnz, H->ws.status);
+            break;
+    }
+}
+
+void launch_features_sparse(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
+    // the list length lives on the device, so size the grid for the worst case
+    const int g = feat_grid(H, H->n);
+    k_feat_sparse<256><<<g, 256, 0, s>>>(di.user_nnz_x, di.user_xidx, H->colptr, H->ws.counters, H->ws.ticket,
+                                         H->d_desc, di, H->n, H->nnz, H->ws.status);
+}
+
+// ---------------------------------------------------------------- sparse x -> dense x + bitmap
+template <class T>
+__global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32_t* xbits, int set) {
+    const int64_t nx = desc->nnz_x;
+    const int32_t* __restrict__ xidx = desc->xidx;
+    const T* __restrict__ xval = (const T*)desc->xval;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nx; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = xidx[t];
+        if (set) {
+            xdense[j] = (xval && !Sr<T>::kPattern) ? xval[t] : Sr<T>::one();
+            atomicOr(&xbits[j >> 5], 1u << (j & 31));
+        } else {
+            xdense[j] = T(0);
+            xbits[j >> 5] = 0u;
+        }
+    }
+}
+
+void launch_x_scatter(asv_matrix_s* H, bool set, cudaStream_t s) {
+    const int g = feat_grid(H, H->n);
+    switch (H->dtype) {
+        case ASV_F32: k_x_scatter<float><<<g, 256, 0, s>>>(H->d_desc, (float*)H->ws.xdense, H->ws.xbits_scat, set); break;
+        case ASV_F64: k_x_scatter<double><<<g, 256, 0, s>>>(H->d_desc, (double*)H->ws.xdense, H->ws.xbits_scat, set); break;
+        case ASV_I32: k_x_scatter<int32_t><<<g, 256, 0, s>>>(H->d_desc, (int32_t*)H->ws.xdense, H->ws.xbits_scat, set); break;
+        case ASV_BOOL: k_x_scatter<bool8><<<g, 256, 0, s>>>(H->d_desc, (bool8*)H->ws.xdense, H->ws.xbits_scat, set); break;
+    }
+}
+
+// ---------------------------------------------------------------- ordered compaction of a bitmap
+// Block b owns a contiguous word range; a block scan of the words' popcounts
+// plus the block's offset gives every set bit its ascending output position.
+template <int B, class Policy>
+__global__ void __launch_bounds__(B) k_bits_write(uint32_t* bits, int64_t nwords, const int32_t* __restrict__ blk,
+                                                  Policy pol) {
+    __shared__ int32_t sm[B / 32 + 1];
+    const int64_t chunk = (nwords + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
+    int32_t base = blk[blockIdx.x];
+    pol.begin();
+    for (int64_t off = lo; off < hi; off += B) {
+        const int64_t w = off + threadIdx.x;
+        uint32_t word = w < hi ? bits[w] : 0u;
+        int32_t tot;
+        int32_t pos = base + block_excl_scan<B>((int32_t)__popc(word), sm, &tot);
+        if (w < hi && word) {
+            pol.clear_word(bits, w);
+            while (word) {
+                const int b = __ffs(word) - 1;
+                word &= word - 1;
+                pol.emit(pos++, w * 32 + b);
+            }
+        }
+        base += tot;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) pol.count(blk[gridDim.x]);
+}
+
+// dense x -> ascending list (values gathered from x)
+template <class T>
+struct XListPolicy {
+    const CallDesc* desc;
+    int32_t* idx;
+    T* val;
+    const T* x;
+    __device__ void begin() { x = (const T*)desc->x_dense; }
+    __device__ void clear_word(uint32_t*, int64_t) {}
+    __device__ void emit(int32_t pos, int64_t j) {
+        idx[pos] = (int32_t)j;
+        if (!Sr<T>::kPattern) val[pos] = x[j];
+    }
+    __device__ void count(int32_t) {}
+};
+
+// public dense -> sparse conversion
+template <class T>
+struct PublicCompactPolicy {
+    const T* x;
+    int32_t* idx;
+    T* val;
+    int64_t* count_out;
+    __device__ void begin() {}
+    __device__ void clear_word(uint32_t*, int64_t) {}
+    __device__ void emit(int32_t pos, int64_t j) {
+        idx[pos] = (int32_t)j;
+        if (val) val[pos] = x[j];
+    }
+    __device__ void count(int32_t c) { *count_out = c; }
+};
+
+// structural output set -> (yidx, yval, nnz_y); the source is the push
+// accumulators (re-zeroed as they are read) or the pull kernels' dense y.
+template <class T, bool FROM_ACC>
+struct OutSparsePolicy {
+    const CallDesc* desc;
+    typename Sr<T>::Atom* acc;
+    const T* ywork;
+    int32_t* status;
+    int32_t* yidx;
+    T* yval;
+    int64_t cap;
+    __device__ void begin() {
+        yidx = desc->yidx;
+        yval = (T*)desc->yval;
+        cap = desc->y_cap;
+    }
+    __device__ void clear_word(uint32_t* bits, int64_t w) { bits[w] = 0u; }
+    __device__ void emit(int32_t pos, int64_t i) {
+        T v;
+        if (Sr<T>::kPattern) {
+            v = Sr<T>::one();
+        } else if (FROM_ACC) {
+            v = Sr<T>::from_atom(acc[i]);
+            acc[i] = typename Sr<T>::Atom(0);
+        } else {
+            v = ywork[i];
+        }
+        if (pos < cap) {
+            yidx[pos] = (int32_t)i;
+            if (yval) yval[pos] = v;
+        }
+    }
+    __device__ void count(int32_t c) {
+        *desc->nnz_y = c;
+        if (c > cap) latch_status(status, ASV_ERR_CAPACITY);
+    }
+};
+
+template <class Policy>
+static void compact_bits(asv_matrix_s* H, uint32_t* bits, int64_t nbits, const Policy& pol, cudaStream_t s) {
+    const int64_t nwords = (nbits + 31) / 32;
+    const int G = H->G;
+    k_bits_count<256><<<G, 256, 0, s>>>(bits, nwords, H->ws.blk);
+    k_scan_blocks<1024><<<1, 1024, 0, s>>>(H->ws.blk, G);
+    k_bits_write<256, Policy><<<G, 256, 0, s>>>(bits, nwords, H->ws.blk, pol);
+}
+
+template <class T>
+static void x_list_dtype(asv_matrix_s* H, cudaStream_t s) {
+    XListPolicy<T> pol{H->d_desc, H->ws.xlist_idx, (T*)H->ws.xlist_val, nullptr};
+    compact_bits(H, H->ws.xbits_dense, H->n, pol, s);
+}
+
+void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
+    switch (H->dtype) {
+        case ASV_F32: x_list_dtype<float>(H, s); break;
+        case ASV_F64: x_list_dtype<double>(H, s); break;
+        case ASV_I32: x_list_dtype<int32_t>(H, s); break;
+        case ASV_BOOL: x_list_dtype<bool8>(H, s); break;
+    }
+}
+
+// ---------------------------------------------------------------- dense write-out of the push accumulators
+template <class T>
+__global__ void k_finalize_dense(int64_t m, typename Sr<T>::Atom* acc, uint32_t* ytouch, const CallDesc* __restrict__ desc) {
+    T* __restrict__ y = (T*)desc->y;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t w = (i < m) ? ytouch[i >> 5] : 0u;
+        const bool bit = (w >> (i & 31)) & 1u;
+        if (i < m) {
+            if (Sr<T>::kPattern) {
+                y[i] = bit ? Sr<T>::one() : T(0);
+            } else if (bit) {
+                y[i] = Sr<T>::from_atom(acc[i]);
+                acc[i] = typename Sr<T>::Atom(0);
+            } else {
+                y[i] = T(0);
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && i < m && w) ytouch[i >> 5] = 0u;
+    }
+}
+
+template <class T>
+static void finalize_dtype(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s) {
+    using Atom = typename Sr<T>::Atom;
+    if (out_mode == ASV_OUT_DENSE) {
+        const int64_t g = max((int64_t)1, min((H->m + 255) / 256, (int64_t)H->num_sms * 16));
+        k_finalize_dense<T><<<(int)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.ytouch, H->d_desc);
+    } else if (from_acc) {
+        OutSparsePolicy<T, true> pol{H->d_desc, (Atom*)H->ws.acc, nullptr, H->ws.status, nullptr, nullptr, 0};
+        compact_bits(H, H->ws.ytouch, H->m, pol, s);
+    } else {
+        OutSparsePolicy<T, false> pol{H->d_desc, nullptr, (const T*)H->ws.ywork, H->ws.status, nullptr, nullptr, 0};
+        compact_bits(H, H->ws.ytouch, H->m, pol, s);
+    }
+}
+
+void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s) {
+    switch (H->dtype) {
+        case ASV_F32: finalize_dtype<float>(H, from_acc, out_mode, s); break;
+        case ASV_F64: finalize_dtype<double>(H, from_acc, out_mode, s); break;
+        case ASV_I32: finalize_dtype<int32_t>(H, from_acc, out_mode, s); break;
+        case ASV_BOOL: finalize_dtype<bool8>(H, from_acc, out_mode, s); break;
+    }
+}
+
+// ---------------------------------------------------------------- public dense -> sparse
+template <class T>
+__global__ void k_x_bits(const T* __restrict__ x, int64_t n, uint32_t* xbits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwords = (n + 31) >> 5;
+    for (int64_t w = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); w < nwords;
+         w += (int64_t)gridDim.x * (blockDim.x / 32)) {
+        const int64_t j = w * 32 + lane;
+        const bool nz = j < n && Sr<T>::nz(x[j]);
+        const unsigned b = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) xbits[w] = b;
+    }
+}
+
+template <class T>
+static void compact_public_dtype(asv_matrix_s* H, const void* x, int32_t* idx, void* val, int64_t* count,
+                                 cudaStream_t s) {
+    const int g = feat_grid(H, ((H->n + 31) / 32) * 32);
+    k_x_bits<T><<<g, 256, 0, s>>>((const T*)x, H->n, H->ws.xbits_dense);
+    PublicCompactPolicy<T> pol{(const T*)x, idx, (T*)val, count};
+    compact_bits(H, H->ws.xbits_dense, H->n, pol, s);
+}
+
+void launch_compact_public(asv_matrix_s* H, const void* x, int32_t* idx, void* val, int64_t* count, cudaStream_t s) {
+    switch (H->dtype) {
+        case ASV_F32: compact_public_dtype<float>(H, x, idx, val, count, s); break;
+        case ASV_F64: compact_public_dtype<double>(H, x, idx, val, count, s); break;
+        case ASV_I32: compact_public_dtype<int32_t>(H, x, idx, val, count, s); break;
+        case ASV_BOOL: compact_public_dtype<bool8>(H, x, idx, val, count, s); break;
+    }
+}
+
+}  // namespace asv

@@ -1,0 +1,273 @@
+"""Parity of the CUDA path against the oracle (through the C ABI).
+
+Every candidate kernel, with x given dense or as a list and with dense or
+sparse output, on small seeded inputs that span several tiles and a ragged
+tail: FP64 within 1e-12 * sum|a x| per row, FP32 within 2e-6 * sum|a x|,
+Boolean and int32 and every index set bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+from tests._util import TOL, assert_rows_close
+
+pytestmark = pytest.mark.gpu
+
+asv = pytest.importorskip("paper_2006_16767_gb300")
+DEV = "cuda"
+ALL_K = list(asv.KERNELS)
+
+
+def to_dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def make(m, n, rowptr, col, val, **kw):
+    return asv.Matrix(m, n, to_dev(rowptr), to_dev(col), to_dev(val), **kw)
+
+
+# ------------------------------------------------------------------ matrices under test
+def mat_laplace():
+    rp, c, v = gen.laplace2d(64)
+    return "laplace64", 4096, 4096, rp, c, v
+
+
+def mat_random(dtype):
+    rp, c, v = gen.random_csr(3001, 2503, 0.004, seed=77, values="uniform", dtype=dtype)
+    return "random", 3001, 2503, rp, c, v
+
+
+def mat_skewed(dtype):
+    # R-MAT rows (hubs, empty rows) plus two rows longer than a balanced tile
+    rp, c = gen.rmat(12, 8, seed=5)
+    n = 1 << 12
+    deg = np.diff(rp).astype(np.int64)
+    rows = [c[rp[i]:rp[i + 1]] for i in range(n)]
+    rows[7] = np.arange(0, n, 1, dtype=np.int32)
+    rows[8] = np.arange(0, n, 2, dtype=np.int32)
+    rp2 = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    c2 = np.concatenate(rows).astype(np.int32)
+    v2 = gen.uniform(len(c2), -1, 1, seed=9, dtype=np.float64).astype(dtype)
+    return "skewed", n, n, rp2, c2, v2
+
+
+def x_cases(n, seed, dtype=np.float64):
+    out = []
+    for rho in (1.0, 0.1, 0.01, 0.001):
+        k = max(1, int(round(rho * n)))
+        idx, val = gen.sparse_x(n, k, seed=seed, stream=int(rho * 1000), dtype=np.float64)
+        out.append((rho, idx, val.astype(dtype)))
+    return out
+
+
+def run(A, k, idx, val, n, dtype, dense_in, sparse_out):
+    it, vt = to_dev(idx), to_dev(val)
+    if dense_in:
+        xd = to_dev(gen.densify(n, idx, val, dtype))
+        return A.spmspv(x_dense=xd, kernel=k, sparse_out=sparse_out)
+    return A.spmspv(xidx=it, xval=vt, kernel=k, sparse_out=sparse_out)
+
+
+def check(A, k, name, n, rp, c, v, idx, val, dtype, tag, dense_in, sparse_out):
+    vv = None if v is None else v.astype(np.float64)
+    xv = val.astype(np.float64)
+    if dense_in:
+        # a dense x's nonzeros are its IEEE nonzeros
+        nzm = xv != 0
+        idx, xv = idx[nzm], xv[nzm]
+    y_ref, s, hit = oracle.spmspv_rowmajor(n, rp, c, vv, idx, xv)
+    out = run(A, k, idx, xv.astype(dtype), n, dtype, dense_in, sparse_out)
+    what = f"{name} {tag} k={k} dense_in={dense_in} sparse_out={sparse_out}"
+    if sparse_out:
+        yidx, yval, nnz_y = out
+        cnt = int(nnz_y.item())
+        got_idx = yidx[:cnt].cpu().numpy()
+        assert np.array_equal(got_idx, np.flatnonzero(hit)), what + " (structural set)"
+        assert_rows_close(yval[:cnt].cpu().numpy(), y_ref[got_idx], s[got_idx], tag, what)
+    else:
+        assert_rows_close(out.cpu().numpy(), y_ref, s, tag, what)
+
+
+@pytest.mark.parametrize("k", ["auto"] + ALL_K)
+def test_laplace_f64_all_kernels(k):
+    name, m, n, rp, c, v = mat_laplace()
+    A = make(m, n, rp, c, v)
+    for rho, idx, val in x_cases(n, gen.config_seed(1)):
+        for dense_in in (True, False):
+            for sparse_out in (False, True):
+                check(A, k, name, n, rp, c, v, idx, val, np.float64, "f64", dense_in, sparse_out)
+
+
+@pytest.mark.parametrize("k", ["auto"] + ALL_K)
+@pytest.mark.parametrize("dtype,tag", [(np.float32, "f32"), (np.float64, "f64")])
+def test_random_and_skewed_all_kernels(k, dtype, tag):
+    for maker in (mat_random, mat_skewed):
+        name, m, n, rp, c, v = maker(dtype)
+        A = make(m, n, rp, c, v)
+        for rho, idx, val in x_cases(n, 123, dtype):
+            for dense_in in (True, False):
+                for sparse_out in (False, True):
+                    check(A, k, name, n, rp, c, v, idx, val, dtype, tag, dense_in, sparse_out)
+
+
+@pytest.mark.parametrize("k", ["auto"] + ALL_K)
+def test_boolean_bit_exact(k):
+    rp, c = gen.rmat(12, 8, seed=3)
+    n = 1 << 12
+    A = make(n, n, rp, c, None)
+    for rho in (0.5, 0.05, 0.002):
+        idx = gen.sample_positions(n, max(1, int(rho * n)), seed=11, stream=int(rho * 1000))
+        xb = np.zeros(n, np.uint8)
+        xb[idx] = 1
+        want = oracle.bool_pull(rp, c, xb)
+        y1 = A.spmspv(x_dense=to_dev(xb), kernel=k).cpu().numpy()
+        assert np.array_equal(y1 != 0, want != 0), f"bool dense-in k={k} rho={rho}"
+        y2 = A.spmspv(xidx=to_dev(idx), kernel=k).cpu().numpy()
+        assert np.array_equal(y2 != 0, want != 0), f"bool list-in k={k} rho={rho}"
+        yidx, yval, nnz_y = A.spmspv(xidx=to_dev(idx), kernel=k, sparse_out=True)
+        cnt = int(nnz_y.item())
+        assert np.array_equal(yidx[:cnt].cpu().numpy(), np.flatnonzero(want)), f"bool sparse-out k={k}"
+
+
+@pytest.mark.parametrize("k", ["auto"] + ALL_K)
+def test_int32_wraparound_bit_exact(k):
+    rp, c, _ = gen.random_csr(1500, 1200, 0.01, seed=8)
+    val = gen.uniform(len(c), -2**31, 2**31 - 1, seed=1).astype(np.int64).astype(np.int32)
+    x = gen.uniform(1200, -2**31, 2**31 - 1, seed=2).astype(np.int64).astype(np.int32)
+    x[gen.sample_positions(1200, 900, seed=3)] = 0
+    want = oracle.i32_pull(rp, c, val, x)
+    A = make(1500, 1200, rp, c, val)
+    got = A.spmspv(x_dense=to_dev(x), kernel=k).cpu().numpy()
+    assert np.array_equal(got, want), f"int32 k={k}"
+    idx = np.flatnonzero(x).astype(np.int32)
+    got2 = A.spmspv(xidx=to_dev(idx), xval=to_dev(x[idx]), kernel=k).cpu().numpy()
+    assert np.array_equal(got2, want), f"int32 list k={k}"
+
+
+def test_transpose_bit_exact():
+    for (m, n, seed) in [(5000, 3000, 1), (3000, 5000, 2), (1, 700, 3), (700, 1, 4)]:
+        rp, c, v = gen.random_csr(m, n, 0.01, seed=seed, values="uniform", dtype=np.float32)
+        A = make(m, n, rp, c, v)
+        colptr, rowidx, valc, perm = A.csc()
+        cp_ref, ri_ref, pm_ref = oracle.csr_to_csc(m, n, rp, c)
+        assert np.array_equal(colptr.cpu().numpy(), cp_ref)
+        assert np.array_equal(rowidx.cpu().numpy(), ri_ref)
+        assert np.array_equal(perm.cpu().numpy(), pm_ref)
+        assert np.array_equal(valc.cpu().numpy(), v[pm_ref])
+
+
+def test_matrix_features_match_oracle():
+    for name, m, n, rp, c, v in (mat_laplace(), mat_random(np.float32), mat_skewed(np.float32)):
+        A = make(m, n, rp, c, v)
+        got = A.features()
+        want = oracle.matrix_features(m, n, rp)
+        for key in ("m", "n", "nnz", "max_row", "min_row"):
+            assert got[key] == want[key], (name, key)
+        for key in ("avg_row", "relative_range", "var_nnz_row", "gini"):
+            assert abs(got[key] - want[key]) <= 1e-12 * max(1.0, abs(want[key])), (name, key, got[key], want[key])
+
+
+def test_vector_features_and_selection():
+    name, m, n, rp, c, v = mat_skewed(np.float32)
+    A = make(m, n, rp, c, v)
+    colptr, _, _ = oracle.csr_to_csc(m, n, rp, c)
+    for rho, idx, val in x_cases(n, 5, np.float32):
+        kid, f = A.select(xidx=to_dev(idx), xval=to_dev(val))
+        want = oracle.vector_features(n, len(c), colptr, idx)
+        assert f["nnz_x"] == want["nnz_x"] and f["nnz_s"] == want["nnz_s"]
+        assert f["x_sparsity"] == want["x_sparsity"] and abs(f["m_sparsity"] - want["m_sparsity"]) <= 1e-15
+        assert 0 <= kid < asv.ASV_K_COUNT
+        xd = to_dev(gen.densify(n, idx, val))
+        kid2, f2 = A.select(x_dense=xd)
+        nzi = idx[val != 0]
+        want2 = oracle.vector_features(n, len(c), colptr, nzi)
+        assert f2["nnz_x"] == want2["nnz_x"] and f2["nnz_s"] == want2["nnz_s"]
+        # the auto call runs the kernel the selector names
+        A.spmspv(xidx=to_dev(idx), xval=to_dev(val))
+        assert A.last_kernel() == kid
+
+
+def test_compaction_ieee_bit_exact():
+    n = 70001
+    x = gen.uniform(n, -1, 1, seed=4)
+    x[gen.sample_positions(n, 60000, seed=5)] = 0.0
+    x[10] = -0.0
+    x[11] = np.nan
+    x[12] = np.inf
+    x[13] = 5e-324
+    rp, c, v = gen.random_csr(10, n, 0.001, seed=1, values="uniform")
+    A = make(10, n, rp, c, v)
+    idx = torch.empty(n, dtype=torch.int32, device=DEV)
+    val = torch.empty(n, dtype=torch.float64, device=DEV)
+    cnt = torch.zeros(1, dtype=torch.int64, device=DEV)
+    asv.asv_compact(A.handle, to_dev(x), idx, val, cnt)
+    k = int(cnt.item())
+    ref_idx, ref_val = oracle.compact(x)
+    assert np.array_equal(idx[:k].cpu().numpy(), ref_idx)
+    assert np.array_equal(val[:k].cpu().numpy(), ref_val, equal_nan=True)
+
+
+def test_edge_cases():
+    # empty x (list of length 0), all-zero dense x, empty matrix, single row/column
+    name, m, n, rp, c, v = mat_random(np.float64)
+    A = make(m, n, rp, c, v)
+    for k in ["auto"] + ALL_K:
+        y = A.spmspv(xidx=torch.zeros(0, dtype=torch.int32, device=DEV),
+                     xval=torch.zeros(0, dtype=torch.float64, device=DEV), kernel=k)
+        assert torch.count_nonzero(y).item() == 0, k
+        y = A.spmspv(x_dense=torch.zeros(n, dtype=torch.float64, device=DEV), kernel=k)
+        assert torch.count_nonzero(y).item() == 0, k
+        yidx, yval, nnz_y = A.spmspv(xidx=torch.zeros(0, dtype=torch.int32, device=DEV),
+                                     xval=torch.zeros(0, dtype=torch.float64, device=DEV), kernel=k,
+                                     sparse_out=True)
+        assert int(nnz_y.item()) == 0, k
+    E = make(50, 40, np.zeros(51, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float64))
+    for k in ["auto"] + ALL_K:
+        y = E.spmspv(x_dense=torch.ones(40, dtype=torch.float64, device=DEV), kernel=k)
+        assert torch.count_nonzero(y).item() == 0, k
+    for (mm, nn) in [(1, 900), (900, 1)]:
+        rp, c, v = gen.random_csr(mm, nn, 0.5, seed=2, values="uniform")
+        B = make(mm, nn, rp, c, v)
+        x = gen.uniform(nn, -1, 1, seed=3)
+        y_ref, s = oracle.csr_pull(rp, c, v, x)
+        for k in ["auto"] + ALL_K:
+            assert_rows_close(B.spmspv(x_dense=to_dev(x), kernel=k).cpu().numpy(), y_ref, s, "f64", f"{mm}x{nn} {k}")
+
+
+def test_sparse_output_capacity_is_reported():
+    name, m, n, rp, c, v = mat_random(np.float64)
+    A = make(m, n, rp, c, v)
+    x = torch.ones(n, dtype=torch.float64, device=DEV)
+    _, s, hit = oracle.spmspv_rowmajor(n, rp, c, v, np.arange(n, dtype=np.int32), np.ones(n))
+    assert A.status() == 0
+    for k in ("pull_bal", "push_bal_atom", "push_thread_sort"):
+        yidx, yval, nnz_y = A.spmspv(x_dense=x, kernel=k, sparse_out=True, y_cap=10)
+        assert int(nnz_y.item()) == int(hit.sum())
+        assert A.status() == asv.ASV_ERR_CAPACITY
+        assert A.status() == 0
+
+
+def test_validation_rejects_noncanonical():
+    rp = np.array([0, 2, 3], np.int32)
+    c = np.array([1, 0, 2], np.int32)  # row 0 not ascending
+    with pytest.raises(asv.AsvError) as e:
+        make(2, 3, rp, c, np.ones(3), validate=True)
+    assert e.value.status == asv.ASV_ERR_NONCANONICAL
+    c_ok = np.array([0, 1, 2], np.int32)
+    make(2, 3, rp, c_ok, np.ones(3), validate=True).close()
+    c_bad = np.array([0, 1, 3], np.int32)  # out of range
+    with pytest.raises(asv.AsvError):
+        make(2, 3, rp, c_bad, np.ones(3), validate=True)
+
+
+def test_spmv_entry_point_and_copy_flag():
+    name, m, n, rp, c, v = mat_skewed(np.float32)
+    vt = to_dev(v)
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), vt, copy=True)
+    vt.zero_()  # the handle owns its copy
+    x = gen.uniform(n, -1, 1, seed=6).astype(np.float32)
+    y_ref, s = oracle.csr_pull(rp, c, v.astype(np.float64), x.astype(np.float64))
+    for k in ["auto"] + ALL_K:
+        y = A.spmv(to_dev(x), kernel=k)
+        assert_rows_close(y.cpu().numpy(), y_ref, s, "f32", f"spmv {k}")
