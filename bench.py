@@ -1,0 +1,454 @@
+"""Benchmark of the adaptive SpMV/SpMSpV hot path on GB300.
+
+Default workload (one "step"): the R-MAT scale-22 graph (edge factor 16,
+a,b,c = .57,.19,.19; symmetrised, deduplicated), every BFS frontier of 8
+seeded roots multiplied through the Boolean (OR, AND) semiring with
+selector-driven kernel choice and a sparse (list) output, plus one FP32
+PageRank step y = A x with a dense x. Metric: GB/s of useful bytes (the
+byte model of the selected candidate: touched pointers, indices, values,
+gathered x and written y) and its fraction of the measured HBM roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload rmat22|stencil256] [--sweep]
+
+--impl reference times the CPU oracle (the only other implementation of the
+method) on a bounded sample of the same workload. --sweep prints the
+per-kernel x-density table (stderr) instead of the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SpMV/SpMSpV GB/s and % HBM peak vs x density; batched & backward vs plain"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ byte model
+def useful_bytes(kid, m, n, nnz, nnz_x, nnz_s, nnz_y, s_v, s_x, s_y, x_sparse, sparse_out):
+    """Bytes the selected candidate's pattern must touch (each element once)."""
+    x_in = nnz_x * (4 + s_x) if x_sparse else n * s_x
+    out = (nnz_y * (4 + s_y) + 8) if sparse_out else m * s_y
+    if kid <= 2:  # pull SpMV: every row pointer, index and value, x, y
+        return 4 * (m + 1) + nnz * (4 + s_v) + x_in + out
+    if kid <= 5:  # validated pull: all indices, effective values, bitmap, listed x
+        return 4 * (m + 1) + nnz * 4 + nnz_s * s_v + n / 8 + x_in + out
+    # push: list, column pointer pairs, effective entries, output
+    return x_in + 8 * nnz_x + nnz_s * (4 + s_v) + out
+
+
+def work_bytes(m, n, nnz, nnz_x, nnz_s, nnz_y, s_v, s_x, s_y, x_sparse, sparse_out):
+    """Work of one product, independent of the kernel that runs it: the least
+    useful bytes any correct candidate (pull, validated pull, push) touches."""
+    return min(useful_bytes(k, m, n, nnz, nnz_x, nnz_s, nnz_y, s_v, s_x, s_y, x_sparse, sparse_out)
+               for k in (0, 3, 6))
+
+
+def launches(kid, x_sparse, sparse_out, auto=True):
+    """Kernel launches of one call (mirrors the library's dispatch)."""
+    c = 1 + (1 if auto else 0)  # feature pass (+ selector node)
+    compaction = 3  # block counts, block-offset scan, write
+    scan = 3
+    if kid <= 5:
+        dist = kid % 3
+        c += (2 if dist == 2 else 1)
+        if x_sparse:
+            c += 2
+        if sparse_out:
+            c += compaction
+        return c
+    q = kid - 6
+    dist, wb = q % 3, q // 3
+    if not x_sparse:
+        c += compaction
+    if dist == 2 or wb != 0:
+        c += 1 + scan
+    c += 1  # traversal
+    if wb == 1:
+        c += 3 * (1 + scan + 1) + 1  # 3 radix passes (hist, scan, scatter) + reduce-by-key
+    elif wb == 2:
+        c += 1 + 1 + scan + 1 + 1 + 1  # memset, count, scan, copy, scatter, accumulate
+    c += 1 if not sparse_out else compaction
+    return c
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[2 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ workload
+class Rmat22:
+    """R-MAT scale 22 BFS frontiers (Boolean) + one FP32 PageRank step."""
+    name = "rmat22_bfs8_pagerank"
+
+    def __init__(self, scale=22, edge_factor=16, roots=8):
+        import gen
+        self.scale, self.edge_factor, self.nroots = scale, edge_factor, roots
+        t = time.time()
+        self.rowptr, self.col = gen.rmat(scale, edge_factor, gen.config_seed(2))
+        self.gen_s = time.time() - t
+        self.n = self.m = 1 << scale
+        self.nnz = len(self.col)
+        deg = np.diff(self.rowptr)
+        cand = np.flatnonzero(deg > 0)
+        pick = gen.randint(roots, len(cand), gen.config_seed(2), stream=7)
+        self.roots = [int(cand[i]) for i in pick]
+        r = gen.uniform(self.n, 0.0, 1.0, gen.config_seed(2), stream=8)
+        r /= r.sum()
+        self.pr_x = np.where(deg > 0, r / np.maximum(deg, 1), 0.0).astype(np.float32)
+
+    def setup_gpu(self, asv, torch, dev):
+        self.torch = torch
+        self.rp_d = torch.from_numpy(self.rowptr).to(dev)
+        self.col_d = torch.from_numpy(self.col).to(dev)
+        self.ones_d = torch.ones(self.nnz, dtype=torch.float32, device=dev)
+        self.Ab = asv.Matrix(self.m, self.n, self.rp_d, self.col_d, None)
+        self.Af = asv.Matrix(self.m, self.n, self.rp_d, self.col_d, self.ones_d)
+        self.x_pr = torch.from_numpy(self.pr_x).to(dev)
+        self.y_pr = torch.empty(self.m, dtype=torch.float32, device=dev)
+        self.yidx = torch.empty(self.m, dtype=torch.int32, device=dev)
+        self.yval = torch.empty(self.m, dtype=torch.uint8, device=dev)
+        # BFS frontiers from the library's own Boolean SpMSpV (setup, untimed)
+        self.frontiers = []
+        y = torch.empty(self.m, dtype=torch.uint8, device=dev)
+        for root in self.roots:
+            visited = torch.zeros(self.n, dtype=torch.bool, device=dev)
+            f = torch.tensor([root], dtype=torch.int32, device=dev)
+            visited[root] = True
+            while f.numel() > 0:
+                self.frontiers.append(f)
+                self.Ab.spmspv(xidx=f, y=y)
+                nxt = (y.bool() & ~visited).nonzero().flatten().to(torch.int32)
+                visited[nxt.long()] = True
+                f = nxt
+        self.counts = torch.tensor([[f.numel()] for f in self.frontiers], dtype=torch.int64, device=dev)
+        self.nnz_y = torch.zeros(len(self.frontiers) + 1, dtype=torch.int64, device=dev)
+        # the selector's choice and the byte model of every call
+        self.calls = []
+        for i, f in enumerate(self.frontiers):
+            kid, vf = asv.asv_select(self.Ab.handle, self.counts[i], f)
+            self.calls.append(dict(kind="bfs", kid=kid, nnz_x=vf["nnz_x"], nnz_s=vf["nnz_s"]))
+        kid, vf = asv.asv_select(self.Af.handle, x_dense=self.x_pr)
+        self.calls.append(dict(kind="pagerank", kid=kid, nnz_x=vf["nnz_x"], nnz_s=vf["nnz_s"]))
+        self.asv = asv
+        self.run_step()
+        torch.cuda.synchronize()
+        ny = self.nnz_y.cpu().numpy()
+        for i, c in enumerate(self.calls):
+            if c["kind"] == "bfs":
+                c["nnz_y"] = int(ny[i])
+                args_ = (self.m, self.n, self.nnz, c["nnz_x"], c["nnz_s"], c["nnz_y"], 0, 0, 0, True, True)
+                c["bytes"] = work_bytes(*args_)
+                c["kbytes"] = useful_bytes(c["kid"], *args_)
+                c["launches"] = launches(c["kid"], True, True)
+            else:
+                c["nnz_y"] = self.m
+                args_ = (self.m, self.n, self.nnz, c["nnz_x"], c["nnz_s"], self.m, 4, 4, 4, False, False)
+                c["bytes"] = work_bytes(*args_)
+                c["kbytes"] = useful_bytes(c["kid"], *args_)
+                c["launches"] = launches(c["kid"], False, False)
+
+    def run_step(self, events=None):
+        asv = self.asv
+        h = self.Ab.handle
+        for i, f in enumerate(self.frontiers):
+            if events is not None:
+                events[i][0].record()
+            asv.asv_spmspv(h, self.counts[i], f, None, None, asv.ASV_OUT_SPARSE, None, self.yidx, self.yval,
+                           self.nnz_y[i:i + 1], self.m, "auto")
+            if events is not None:
+                events[i][1].record()
+        j = len(self.frontiers)
+        if events is not None:
+            events[j][0].record()
+        asv.asv_spmv(self.Af.handle, self.x_pr, self.y_pr, "auto")
+        if events is not None:
+            events[j][1].record()
+
+    def e2e_setup(self, torch):
+        self.h_front = [f.cpu().pin_memory() for f in self.frontiers]
+        self.h_counts = self.counts.cpu().pin_memory()
+        self.h_prx = torch.from_numpy(self.pr_x).pin_memory()
+        self.h_ypr = torch.empty(self.m, dtype=torch.float32).pin_memory()
+        self.h_nnzy = torch.empty(len(self.frontiers) + 1, dtype=torch.int64).pin_memory()
+        self.d_front = [torch.empty_like(f) for f in self.frontiers]
+        self.d_counts = torch.empty_like(self.counts)
+        self.d_prx = torch.empty_like(self.x_pr)
+        h2d = sum(f.numel() * 4 for f in self.h_front) + self.h_counts.numel() * 8 + self.h_prx.numel() * 4
+        d2h = self.h_ypr.numel() * 4 + self.h_nnzy.numel() * 8
+        return h2d, d2h
+
+    def e2e_step(self):
+        asv = self.asv
+        for hf, df in zip(self.h_front, self.d_front):
+            df.copy_(hf, non_blocking=True)
+        self.d_counts.copy_(self.h_counts, non_blocking=True)
+        self.d_prx.copy_(self.h_prx, non_blocking=True)
+        for i, f in enumerate(self.d_front):
+            asv.asv_spmspv(self.Ab.handle, self.d_counts[i], f, None, None, asv.ASV_OUT_SPARSE, None, self.yidx,
+                           self.yval, self.nnz_y[i:i + 1], self.m, "auto")
+        asv.asv_spmv(self.Af.handle, self.d_prx, self.y_pr, "auto")
+        self.h_ypr.copy_(self.y_pr, non_blocking=True)
+        self.h_nnzy.copy_(self.nnz_y, non_blocking=True)
+
+    def config(self):
+        return {"workload": self.name, "graph": f"rmat scale {self.scale} edge factor {self.edge_factor}",
+                "n": self.n, "nnz": self.nnz, "roots": self.nroots, "bfs_levels": len(self.frontiers),
+                "calls_per_step": len(self.calls), "bfs_output": "sparse list", "pagerank": "fp32 dense x",
+                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "seed": 20061678}
+
+
+def run_cpu_oracle(W, max_bfs_calls, reps=1):
+    """Times the oracle on a bounded sample; returns (bytes, seconds, sample text)."""
+    import oracle
+    n = W.n
+    fr_host = W.frontiers_host if hasattr(W, "frontiers_host") else None
+    xs = W.pr_x.astype(np.float64)
+    t_tot, b_tot = 0.0, 0.0
+    for _ in range(reps):
+        t = time.perf_counter()
+        oracle.csr_pull(W.rowptr, W.col, None, xs)
+        t_tot += time.perf_counter() - t
+        b_tot += W.calls[-1]["bytes"]
+        for i in range(min(max_bfs_calls, len(W.calls) - 1)):
+            xb = np.zeros(n, np.uint8)
+            xb[fr_host[i]] = 1
+            t = time.perf_counter()
+            oracle.bool_pull(W.rowptr, W.col, xb)
+            t_tot += time.perf_counter() - t
+            b_tot += W.calls[i]["bytes"]
+    sample = f"1 PageRank step + first {min(max_bfs_calls, len(W.calls) - 1)} BFS level products, serial FP64 C oracle"
+    return b_tot, t_tot, sample
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return main_reference(args, rank, world)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2006_16767_gb300 as asv
+
+    W = Rmat22()
+    W.setup_gpu(asv, torch, dev)
+    W.frontiers_host = [f.cpu().numpy() for f in W.frontiers]
+    hbm, peak_kind = peaks()
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ncalls = len(W.calls)
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        W.run_step()
+    torch.cuda.synchronize()
+
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    call_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ncalls)]
+               for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_wall = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.nvtx.range_push("timed_step")
+        step_ev[s][0].record()
+        W.run_step(call_ev[s])
+        step_ev[s][1].record()
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    time.sleep(0.2)
+    clk = clocks.stop()
+
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_bytes = sum(c["bytes"] for c in W.calls)
+    value = step_bytes * world / (ms * 1e-3) / 1e9
+
+    # per-kernel durations from the per-call events (same stream as the launches)
+    per_k = {}
+    for s in range(args.steps):
+        for i, c in enumerate(W.calls):
+            d = call_ev[s][i][0].elapsed_time(call_ev[s][i][1])
+            e = per_k.setdefault((c["kind"], c["kid"]), {"ms": 0.0, "bytes": 0.0, "n": 0})
+            e["ms"] += d
+            e["bytes"] += c["kbytes"]
+            e["n"] += 1
+    dom_key = max(per_k, key=lambda k: per_k[k]["ms"])
+    dom = per_k[dom_key]
+    achieved = (dom["bytes"] / dom["n"]) / ((dom["ms"] / dom["n"]) * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": f"{dom_key[0]}:{asv.KERNELS[dom_key[1]]}", "achieved": round(achieved, 1),
+            "peak": hbm, "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None,
+            "share_of_step": round(dom["ms"] / sum(v["ms"] for v in per_k.values()), 3),
+            "note": "duration = auto call (feature pass + selector + kernel), CUDA events on the launch stream"}
+
+    # end to end through the public API with pinned host buffers
+    h2d, d2h = W.e2e_setup(torch)
+    for _ in range(2):
+        W.e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, args.steps // 2)
+    e0.record()
+    for _ in range(e2e_steps):
+        W.e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_val = step_bytes * world / (e2e_ms * 1e-3) / 1e9
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u8 (OR,AND) + f32", "data": "synthetic", "config": W.config(),
+           "frac_of_hbm_roofline": round(value / world / hbm, 4),
+           "roofline": roof,
+           "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "ms_per_step": round(e2e_ms, 4),
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+           "gpu_launches": int(args.steps * sum(c["launches"] for c in W.calls)),
+           "clocks": clk, "wall_s_timed": round(wall, 3),
+           "selected": {asv.KERNELS[k[1]] + ":" + k[0]: v["n"] // args.steps for k, v in per_k.items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        b, t, sample = run_cpu_oracle(W, max_bfs_calls=24)
+        out["cpu_baseline"] = {"value": round(b / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                               "sample": sample, "seconds": round(t, 2)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main_reference(args, rank, world):
+    """The oracle (CPU, serial) on the same workload, metric and unit."""
+    if rank != 0:
+        return
+    import oracle
+    import gen
+    W = Rmat22()
+    # frontiers from the oracle's own queue BFS, the same roots
+    fronts = []
+    for r in W.roots:
+        fronts += oracle.frontiers(W.n, W.rowptr, W.col, r)
+    W.frontiers_host = fronts
+    colptr, _, _ = oracle.csr_to_csc(W.m, W.n, W.rowptr, W.col)
+    W.calls = []
+    for f in fronts:
+        vf = oracle.vector_features(W.n, W.nnz, colptr, f)
+        xb = np.zeros(W.n, np.uint8)
+        xb[f] = 1
+        nnz_y = int(oracle.bool_pull(W.rowptr, W.col, xb).sum())
+        W.calls.append(dict(kind="bfs", kid=0, nnz_x=len(f), nnz_s=vf["nnz_s"],
+                            bytes=work_bytes(W.m, W.n, W.nnz, len(f), vf["nnz_s"], nnz_y, 0, 0, 0, True, True)))
+    W.calls.append(dict(kind="pagerank", kid=0, nnz_x=W.n, nnz_s=W.nnz,
+                        bytes=work_bytes(W.m, W.n, W.nnz, W.n, W.nnz, W.m, 4, 4, 4, False, False)))
+    per_step_calls = 8
+    for _ in range(args.warmup):
+        run_cpu_oracle(W, max_bfs_calls=2)
+    tot_b, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        b, t, sample = run_cpu_oracle(W, max_bfs_calls=per_step_calls)
+        tot_b += b
+        tot_t += t
+    ms = tot_t / args.steps * 1e3
+    val = tot_b / tot_t / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GB/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle)", "data": "synthetic",
+           "config": {"workload": W.name, "n": W.n, "nnz": W.nnz, "roots": W.nroots},
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(val, 4), "unit": "GB/s",
+                            "sample": f"per step: {sample}"},
+           "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -154,8 +154,9 @@ asv_status asv_spmv(asv_matrix A, const void* d_x, void* d_y, int32_t kernel, vo
 /* y = A x for x given either dense (d_x_dense[n], then d_nnz_x/d_xidx/d_xval
  * are ignored and x's nonzeros are those with x_j != 0 by IEEE comparison)
  * or sparse (d_x_dense NULL; *d_nnz_x is a device int64 count, d_xidx[nnz_x]
- * distinct column ids in any order, d_xval[nnz_x] values, NULL for ASV_BOOL
- * or to mean all-ones). Listed entries are structural even when their value
+ * distinct column ids in [0, n) in any order -- NULL allowed only when the
+ * count is 0 -- and d_xval[nnz_x] values, ignored for ASV_BOOL and NULL to
+ * mean all-ones). A list longer than n latches ASV_ERR_ARG and is clamped. Listed entries are structural even when their value
  * is zero. Output (Sec. IV-B write-back):
  *  - ASV_OUT_DENSE: d_y[m] is overwritten with A x;
  *  - ASV_OUT_SPARSE: the structural output set -- rows with at least one

@@ -164,7 +164,7 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     AL(H->carry_row, 4 * (H->ntiles + 1), false);
     AL(H->carry_val, 8 * (H->ntiles + 1), false);
     AL(H->d_trees, sizeof(TreeNode) * kMaxTreeNodes, false);
-    AL(H->d_roots, 4 * 3, false);
+    AL(H->d_roots, 4 * 4, false);
     AL(H->d_desc, sizeof(CallDesc), true);
     AL(H->d_last_kid, 4, true);
     // workspaces
@@ -176,7 +176,7 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     AL(w.xlist_val, vs * n, false);
     AL(w.xscan, 4 * (n + 1), false);
     AL(w.acc, 8 * m, true);
-    AL(w.ytouch, 4 * nw_m, true);
+    AL(w.yflag, (m + 16) & ~(int64_t)15, true);
     AL(w.ywork, vs * m, false);
     const size_t pv = vs == 8 ? 8 : 4;
     AL(w.pkeys[0], 4 * nnz, false);
@@ -199,7 +199,7 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     CKH(build_partition(H, s));
     {
         std::vector<TreeNode> nodes;
-        int32_t roots[3];
+        int32_t roots[4];
         default_trees(nodes, roots);
         CKH(cudaMemcpyAsync(H->d_trees, nodes.data(), sizeof(TreeNode) * nodes.size(), cudaMemcpyHostToDevice, s));
         CKH(cudaMemcpyAsync(H->d_roots, roots, sizeof(roots), cudaMemcpyHostToDevice, s));
@@ -317,7 +317,7 @@ static asv_status prepare_call(asv_matrix_s* H, const int64_t* d_nnz_x, const in
     if (om == ASV_OUT_DENSE && !d_y && H->m > 0) return ASV_ERR_ARG;
     if (om == ASV_OUT_SPARSE && (!d_yidx || !d_nnz_y || y_cap < 0)) return ASV_ERR_ARG;
     const bool xs = d_x_dense == nullptr;
-    if (xs && (!d_nnz_x || !d_xidx)) return ASV_ERR_ARG;
+    if (xs && !d_nnz_x) return ASV_ERR_ARG;  // d_xidx may be NULL when *d_nnz_x == 0
     if (!xs && H->n > 0 && !d_x_dense) return ASV_ERR_ARG;
     memset(&di, 0, sizeof(di));
     di.y = d_y;
@@ -443,8 +443,9 @@ extern "C" asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t
     for (int i = 0; i < 3; ++i)
         if (h_roots[i] < 0 || h_roots[i] >= n_nodes) return ASV_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    const int32_t r4[4] = {h_roots[0], h_roots[1], h_roots[2], n_nodes};
     CK(cudaMemcpyAsync(A->d_trees, nodes.data(), sizeof(TreeNode) * n_nodes, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(A->d_roots, h_roots, 12, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(A->d_roots, r4, 16, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     return ASV_OK;
 }

@@ -100,6 +100,6 @@ void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s
 
 // select.cu
 void launch_select(asv_matrix_s* H, unsigned long long cond_handle, bool set_cond, cudaStream_t s);
-void default_trees(std::vector<TreeNode>& nodes, int32_t roots[3]);
+void default_trees(std::vector<TreeNode>& nodes, int32_t roots[4]);
 
 }  // namespace asv

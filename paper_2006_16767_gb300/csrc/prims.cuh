@@ -171,17 +171,4 @@ __global__ void __launch_bounds__(B) k_radix_scatter(const uint32_t* kin, const 
     }
 }
 
-// ---------------------------------------------------------------- ordered bitmap compaction
-// Count phase: blk[b] = set bits in block b's contiguous word range.
-template <int B>
-__global__ void __launch_bounds__(B) k_bits_count(const uint32_t* bits, int64_t nwords, int32_t* blk) {
-    __shared__ int32_t sm[B / 32 + 1];
-    const int64_t chunk = (nwords + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
-    int32_t s = 0;
-    for (int64_t w = lo + threadIdx.x; w < hi; w += B) s += __popc(bits[w]);
-    s = block_reduce_sum<B>(s, sm);
-    if (threadIdx.x == 0) blk[blockIdx.x] = s;
-}
-
 }  // namespace asv

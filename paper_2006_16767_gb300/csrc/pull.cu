@@ -12,6 +12,8 @@
 #include "internal.h"
 #include "prims.cuh"
 
+#include <type_traits>
+
 namespace asv {
 
 constexpr int kBalB = 256;   // threads per balanced tile
@@ -19,6 +21,12 @@ constexpr int kBalIPT = 8;   // merge items per thread
 constexpr int kBalD = kBalB * kBalIPT;
 
 int64_t pull_tile_items(int32_t) { return kBalD; }
+
+template <class T>
+__device__ __forceinline__ T __int_as_float_t(int v) {
+    if constexpr (sizeof(T) == 4 && std::is_same<T, float>::value) return __int_as_float(v);
+    else return (T)v;
+}
 
 struct PullArg {
     const CallDesc* desc;  // read x/y from the call descriptor when non-null
@@ -40,140 +48,269 @@ __device__ __forceinline__ PullIO resolve(const PullArg& a, void* ywork, bool sp
 template <class T, bool MASK, bool SOUT>
 __global__ void __launch_bounds__(256) k_pull_thread(int64_t m, const int32_t* __restrict__ rowptr,
                                                      const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                     PullArg a, void* ywork, uint32_t* ytouch) {
+                                                     PullArg a, void* ywork, uint8_t* yflag) {
     using S = Sr<T>;
     const PullIO p = resolve(a, ywork, SOUT);
     const T* __restrict__ x = (const T*)p.x;
     T* __restrict__ y = (T*)p.y;
-    for (int64_t base = (int64_t)blockIdx.x * 256; base < m; base += (int64_t)gridDim.x * 256) {
-        const int64_t i = base + threadIdx.x;
-        bool hit = false;
-        if (i < m) {
-            typename S::Acc acc;
-            S::acc_zero(acc);
-            const int32_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
-            for (int32_t k = b; k < e; ++k) {
-                const int32_t c = __ldg(col + k);
-                if (MASK || SOUT) {
-                    const bool bit = test_bit(p.xbits, c);
-                    hit |= bit;
-                    if (MASK && !bit) continue;
-                }
-                S::acc_add(acc, S::mul(load_val(val, k), __ldg(x + c)));
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    bool hit = false;
+    if (i < m) {
+        typename S::Acc acc;
+        S::acc_zero(acc);
+        const int32_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t c = __ldg(col + k);
+            if (MASK || SOUT) {
+                const bool bit = test_bit(p.xbits, c);
+                hit |= bit;
+                if (MASK && !bit) continue;
             }
-            y[i] = S::part_T(S::acc_part(acc));
+            S::acc_add(acc, S::mul(load_val(val, k), __ldg(x + c)));
+            if constexpr (S::kPattern) {
+                if (acc) break;  // OR is settled by the first hit
+            }
         }
-        if (SOUT) {
-            const unsigned w = __ballot_sync(0xffffffffu, hit);
-            if ((threadIdx.x & 31) == 0 && i < m) ytouch[i >> 5] = w;
+        y[i] = S::part_T(S::acc_part(acc));
+    }
+    if (SOUT && hit) yflag[i] = 1;
+}
+
+// ---------------------------------------------------------------- L lanes per row
+// A group of L lanes owns one row; a warp owns RW = (32/L)*U consecutive rows,
+// whose row pointers it reads with one coalesced load. Lane l reads its
+// row's 16-byte-aligned 4-element chunks l, l+L, ... with one 128-bit load of
+// column ids and one of values each (elements outside the row are masked).
+// The first chunk of all U rows of a group is loaded before any x gather, so
+// a warp keeps U*32 bytes per lane in flight. Chunk products are added as a
+// small tree, chunks of a lane with compensated summation, and the group's
+// lanes with shuffles.
+template <class T, bool MASK, bool VEC>
+struct Chunk {
+    int32_t c[4];
+    T v[4];
+    bool in[4];
+};
+
+template <class T, bool MASK, bool VEC>
+__device__ __forceinline__ void chunk_load(Chunk<T, MASK, VEC>& ch, const int32_t* __restrict__ col,
+                                           const T* __restrict__ val, int64_t nnz, int32_t base, int32_t b, int32_t e) {
+    using S = Sr<T>;
+    const bool full = VEC && base < e && (int64_t)base + 4 <= nnz;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ch.in[q] = base + q >= b && base + q < e;
+    if (full) {
+        const int4 cc = __ldg(reinterpret_cast<const int4*>(col + base));
+        ch.c[0] = cc.x; ch.c[1] = cc.y; ch.c[2] = cc.z; ch.c[3] = cc.w;
+        if constexpr (!S::kPattern && !MASK) {
+            if (val != nullptr) {
+                if constexpr (sizeof(T) == 4) {
+                    const int4 vv = __ldg(reinterpret_cast<const int4*>(val + base));
+                    ch.v[0] = __int_as_float_t<T>(vv.x); ch.v[1] = __int_as_float_t<T>(vv.y);
+                    ch.v[2] = __int_as_float_t<T>(vv.z); ch.v[3] = __int_as_float_t<T>(vv.w);
+                } else {
+                    const double2 v01 = __ldg(reinterpret_cast<const double2*>(val + base));
+                    const double2 v23 = __ldg(reinterpret_cast<const double2*>(val + base + 2));
+                    ch.v[0] = (T)v01.x; ch.v[1] = (T)v01.y; ch.v[2] = (T)v23.x; ch.v[3] = (T)v23.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ch.v[q] = S::one();
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ch.c[q] = ch.in[q] ? __ldg(col + base + q) : 0;
+            if constexpr (!S::kPattern && !MASK) ch.v[q] = ch.in[q] ? load_val(val, base + q) : T(0);
         }
     }
 }
 
-// ---------------------------------------------------------------- L lanes per row
-template <class T, bool MASK, bool SOUT, int L>
-__global__ void __launch_bounds__(256) k_pull_warp(int64_t m, const int32_t* __restrict__ rowptr,
-                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                   PullArg a, void* ywork, uint32_t* ytouch) {
+template <class T, bool MASK, bool SOUT, bool VEC>
+__device__ __forceinline__ typename Sr<T>::Part chunk_sum(Chunk<T, MASK, VEC>& ch, const T* __restrict__ val,
+                                                          const T* __restrict__ x, const uint32_t* __restrict__ xbits,
+                                                          int32_t base, bool& hit) {
     using S = Sr<T>;
     using P = typename S::Part;
-    constexpr int GPB = 256 / L;
+    bool eff[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        bool bit = true;
+        if (MASK || SOUT) bit = ch.in[q] && test_bit(xbits, ch.c[q]);
+        if (SOUT) hit |= bit;
+        eff[q] = ch.in[q] && (!MASK || bit);
+    }
+    if constexpr (S::kPattern) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ch.v[q] = S::one();
+    } else if constexpr (MASK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ch.v[q] = eff[q] ? load_val(val, base + q) : T(0);
+    }
+    P pr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pr[q] = eff[q] ? S::mul(ch.v[q], __ldg(x + ch.c[q])) : P(0);
+    return S::part_add(S::part_add(pr[0], pr[1]), S::part_add(pr[2], pr[3]));
+}
+
+template <int L>
+struct WarpRows {
+    static constexpr int U = L >= 4 ? 4 : 2;  // rows per group, loaded together
+    static constexpr int RW = (32 / L) * U;   // rows per warp (<= 32)
+};
+
+template <class T, bool MASK, bool SOUT, int L, bool VEC>
+__global__ void __launch_bounds__(256) k_pull_warp(int64_t m, int64_t nnz, const int32_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                   PullArg a, void* ywork, uint8_t* yflag) {
+    using S = Sr<T>;
+    using P = typename S::Part;
+    constexpr int U = WarpRows<L>::U, RW = WarpRows<L>::RW, RPW = 32 / L;
     const PullIO p = resolve(a, ywork, SOUT);
     const T* __restrict__ x = (const T*)p.x;
     T* __restrict__ y = (T*)p.y;
-    const int g = threadIdx.x / L, l = threadIdx.x % L;
-    for (int64_t i0 = (int64_t)blockIdx.x * GPB; i0 < m; i0 += (int64_t)gridDim.x * GPB) {
-        const int64_t i = i0 + g;
+    const int lane = threadIdx.x & 31, g = lane / L, l = lane % L;
+    const int64_t row0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * RW;
+    if (row0 >= m) return;
+    const int32_t rp = (lane < RW && row0 + lane <= m) ? __ldg(rowptr + row0 + lane) : 0;
+    const int32_t rp_end = __ldg(rowptr + min(row0 + RW, m));
+    int32_t b[U], e[U];
+    bool valid[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int r = u * RPW + g;
+        valid[u] = row0 + r < m;
+        b[u] = __shfl_sync(0xffffffffu, rp, r);
+        const int32_t nx = __shfl_sync(0xffffffffu, rp, (r + 1) & 31);
+        e[u] = (r + 1 == RW) ? rp_end : nx;
+        if (!valid[u]) e[u] = b[u];
+    }
+    Chunk<T, MASK, VEC> ch[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) chunk_load(ch[u], col, val, nnz, (b[u] & ~3) + 4 * l, b[u], e[u]);
+    P vs[U];
+    bool hit[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        hit[u] = false;
         typename S::Acc acc;
         S::acc_zero(acc);
-        bool hit = false;
-        if (i < m) {
-            const int32_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
-            for (int32_t k = b + l; k < e; k += L) {
-                const int32_t c = __ldg(col + k);
-                if (MASK || SOUT) {
-                    const bool bit = test_bit(p.xbits, c);
-                    hit |= bit;
-                    if (MASK && !bit) continue;
-                }
-                S::acc_add(acc, S::mul(load_val(val, k), __ldg(x + c)));
+        const int32_t base0 = (b[u] & ~3) + 4 * l;
+        S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(ch[u], val, x, p.xbits, base0, hit[u]));
+        for (int32_t base = base0 + 4 * L; base < e[u]; base += 4 * L) {
+            if constexpr (S::kPattern) {
+                if (acc) break;  // OR is settled by the first hit
             }
+            Chunk<T, MASK, VEC> c2;
+            chunk_load(c2, col, val, nnz, base, b[u], e[u]);
+            S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(c2, val, x, p.xbits, base, hit[u]));
         }
-        P v = S::acc_part(acc);
+        vs[u] = S::acc_part(acc);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        P v = vs[u];
 #pragma unroll
         for (int o = L / 2; o > 0; o >>= 1) v = S::part_add(v, shfl_xor(v, o, L));
+        bool h = false;
         if (SOUT) {
-            const unsigned bal = __ballot_sync(0xffffffffu, hit);
-            const unsigned gm = (0xffffffffu >> (32 - L)) << ((threadIdx.x & 31) & ~(L - 1));
-            hit = (bal & gm) != 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, hit[u]);
+            const unsigned gm = (0xffffffffu >> (32 - L)) << (lane & ~(L - 1));
+            h = (bal & gm) != 0;
         }
-        if (i < m && l == 0) {
+        if (valid[u] && l == 0) {
+            const int64_t i = row0 + u * RPW + g;
             y[i] = S::part_T(v);
-            if (SOUT && hit) set_bit_once(ytouch, i);
+            if (SOUT && h) yflag[i] = 1;
         }
     }
 }
 
 // ---------------------------------------------------------------- merge-path balanced
 // Stages a tile's products into shared memory. Column ids (and values) are
-// read with 128-bit loads over the 16-byte-aligned span covering [k0, k1).
+// read with 128-bit loads over the 16-byte-aligned span covering [k0, k1);
+// every load of the thread's groups is issued before any of them is used.
 template <class T, bool MASK, bool SOUT, bool VEC>
 __device__ __forceinline__ void stage_products(const int32_t* __restrict__ col, const T* __restrict__ val,
                                                const T* __restrict__ x, const uint32_t* __restrict__ xbits,
                                                int64_t k0, int64_t k1, int64_t nnz, typename Sr<T>::Part* s_prod,
                                                uint32_t* s_eff) {
     using S = Sr<T>;
+    using P = typename S::Part;
+    constexpr int MAXG = (kBalD / 4 + 1 + kBalB - 1) / kBalB;
     const int64_t a0 = k0 & ~(int64_t)3;
     const int ngroups = (int)((k1 - a0 + 3) >> 2);
-    for (int gi = threadIdx.x; gi < ngroups; gi += kBalB) {
+    int32_t c[MAXG][4];
+    T v[MAXG][4];
+    bool eff[MAXG][4], bitv[MAXG][4];
+#pragma unroll
+    for (int j = 0; j < MAXG; ++j) {
+        const int gi = threadIdx.x + j * kBalB;
         const int64_t base = a0 + 4 * (int64_t)gi;
-        int32_t c[4];
-        const bool full = VEC && (base + 4 <= nnz);
-        if (full) {
+        if (gi < ngroups && VEC && base + 4 <= nnz) {
             const int4 cc = __ldg(reinterpret_cast<const int4*>(col + base));
-            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
-        } else {
+            c[j][0] = cc.x; c[j][1] = cc.y; c[j][2] = cc.z; c[j][3] = cc.w;
+            if constexpr (!S::kPattern && !MASK) {
+                if (val != nullptr) {
+                    if constexpr (sizeof(T) == 4) {
+                        const int4 vv = __ldg(reinterpret_cast<const int4*>(val + base));
+                        v[j][0] = __int_as_float_t<T>(vv.x); v[j][1] = __int_as_float_t<T>(vv.y);
+                        v[j][2] = __int_as_float_t<T>(vv.z); v[j][3] = __int_as_float_t<T>(vv.w);
+                    } else {
+                        const double2 v01 = __ldg(reinterpret_cast<const double2*>(val + base));
+                        const double2 v23 = __ldg(reinterpret_cast<const double2*>(val + base + 2));
+                        v[j][0] = (T)v01.x; v[j][1] = (T)v01.y; v[j][2] = (T)v23.x; v[j][3] = (T)v23.y;
+                    }
+                } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) c[e] = (base + e < nnz) ? __ldg(col + base + e) : 0;
-        }
-        bool in[4], bit[4], eff[4];
-        bool any = false;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            in[e] = (base + e >= k0) && (base + e < k1);
-            bit[e] = (MASK || SOUT) && in[e] ? test_bit(xbits, c[e]) : true;
-            eff[e] = in[e] && (!MASK || bit[e]);
-            any |= eff[e];
-        }
-        T v[4];
-        if (!S::kPattern && any) {
-            if (full && val != nullptr && sizeof(T) == 4) {
-                const float4 vv = __ldg(reinterpret_cast<const float4*>(val + base));
-                v[0] = *reinterpret_cast<const T*>(&vv.x);
-                v[1] = *reinterpret_cast<const T*>(&vv.y);
-                v[2] = *reinterpret_cast<const T*>(&vv.z);
-                v[3] = *reinterpret_cast<const T*>(&vv.w);
-            } else if (full && val != nullptr && sizeof(T) == 8) {
-                const double2 v01 = __ldg(reinterpret_cast<const double2*>(val + base));
-                const double2 v23 = __ldg(reinterpret_cast<const double2*>(val + base + 2));
-                v[0] = *reinterpret_cast<const T*>(&v01.x);
-                v[1] = *reinterpret_cast<const T*>(&v01.y);
-                v[2] = *reinterpret_cast<const T*>(&v23.x);
-                v[3] = *reinterpret_cast<const T*>(&v23.y);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v[e] = eff[e] ? load_val(val, base + e) : T(0);
+                    for (int q = 0; q < 4; ++q) v[j][q] = S::one();
+                }
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = S::one();
+            for (int q = 0; q < 4; ++q) {
+                const int64_t k = base + q;
+                const bool in = gi < ngroups && k >= k0 && k < k1;
+                c[j][q] = in ? __ldg(col + k) : 0;
+                if constexpr (!S::kPattern && !MASK) v[j][q] = in ? load_val(val, k) : T(0);
+            }
         }
+    }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if (!in[e]) continue;
-            const int li = (int)(base + e - k0);
-            s_prod[li] = eff[e] ? S::mul(v[e], __ldg(x + c[e])) : typename S::Part(0);
-            if (SOUT && bit[e]) atomicOr(&s_eff[li >> 5], 1u << (li & 31));
+    for (int j = 0; j < MAXG; ++j) {
+        const int gi = threadIdx.x + j * kBalB;
+        const int64_t base = a0 + 4 * (int64_t)gi;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t k = base + q;
+            const bool in = gi < ngroups && k >= k0 && k < k1;
+            bitv[j][q] = (MASK || SOUT) && in ? test_bit(xbits, c[j][q]) : true;
+            eff[j][q] = in && (!MASK || bitv[j][q]);
+        }
+        if constexpr (S::kPattern) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[j][q] = S::one();
+        } else if constexpr (MASK) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[j][q] = eff[j][q] ? load_val(val, base + q) : T(0);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < MAXG; ++j) {
+        const int gi = threadIdx.x + j * kBalB;
+        const int64_t base = a0 + 4 * (int64_t)gi;
+        P pr[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pr[q] = eff[j][q] ? S::mul(v[j][q], __ldg(x + c[j][q])) : P(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t k = base + q;
+            if (gi < ngroups && k >= k0 && k < k1) {
+                const int li = (int)(k - k0);
+                s_prod[li] = pr[q];
+                if (SOUT && bitv[j][q]) atomicOr(&s_eff[li >> 5], 1u << (li & 31));
+            }
         }
     }
 }
@@ -182,7 +319,7 @@ template <class T, bool MASK, bool SOUT, bool VEC>
 __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, const int32_t* __restrict__ rowptr,
                                                     const int32_t* __restrict__ col, const T* __restrict__ val,
                                                     const int32_t* __restrict__ tile_row, PullArg a, void* ywork,
-                                                    uint32_t* ytouch, int32_t* carry_row,
+                                                    uint8_t* yflag, int32_t* carry_row,
                                                     typename Sr<T>::Atom* carry_val) {
     using S = Sr<T>;
     using P = typename S::Part;
@@ -231,7 +368,7 @@ __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, cons
         if (ri < nrows && (int64_t)s_end[ri] <= k0 + ki) {
             s_row[ri] = S::acc_part(acc);
             S::acc_zero(acc);
-            if (SOUT && hit) set_bit_once(ytouch, (int64_t)r0 + ri);
+            if (SOUT && hit) yflag[(int64_t)r0 + ri] = 1;
             hit = false;
             ++ri;
         } else {
@@ -240,7 +377,7 @@ __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, cons
             ++ki;
         }
     }
-    if (SOUT && hit) set_bit_once(ytouch, (int64_t)r0 + ri);
+    if (SOUT && hit) yflag[(int64_t)r0 + ri] = 1;
 
     // segmented inclusive scan of the threads' carries (key = row still open
     // at the thread's end; keys are non-decreasing across threads)
@@ -310,17 +447,22 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     const int64_t m = H->m;
     const T* val = (const T*)H->val;
     void* ywork = H->ws.ywork;
-    uint32_t* yt = H->ws.ytouch;
+    uint8_t* yt = H->ws.yflag;
     const int64_t cap = (int64_t)H->num_sms * 16;
+    const bool vec = ((uintptr_t)H->col % 16 == 0) && ((uintptr_t)H->val % 16 == 0);
     if (dist == 0) {
-        const int64_t g = min(cap, max((int64_t)1, (m + 255) / 256));
-        if (m > 0) k_pull_thread<T, MASK, SOUT><<<(int)g, 256, 0, s>>>(m, H->rowptr, H->col, val, a, ywork, yt);
+        if (m > 0) k_pull_thread<T, MASK, SOUT><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, H->rowptr, H->col, val, a, ywork, yt);
     } else if (dist == 1) {
         const int L = H->pull_lanes;
-        const int64_t gpb = 256 / L;
-        const int64_t g = min(cap, max((int64_t)1, (m + gpb - 1) / gpb));
         if (m == 0) return;
-#define PW(LL) k_pull_warp<T, MASK, SOUT, LL><<<(int)g, 256, 0, s>>>(m, H->rowptr, H->col, val, a, ywork, yt)
+        const int rw = L == 2 ? WarpRows<2>::RW : L == 4 ? WarpRows<4>::RW : L == 8 ? WarpRows<8>::RW
+                     : L == 16 ? WarpRows<16>::RW : WarpRows<32>::RW;
+        const unsigned g = (unsigned)((m + 8 * rw - 1) / (8 * rw));
+#define PW(LL)                                                                                                   \
+    do {                                                                                                         \
+        if (vec) k_pull_warp<T, MASK, SOUT, LL, true><<<g, 256, 0, s>>>(m, H->nnz, H->rowptr, H->col, val, a, ywork, yt);  \
+        else k_pull_warp<T, MASK, SOUT, LL, false><<<g, 256, 0, s>>>(m, H->nnz, H->rowptr, H->col, val, a, ywork, yt); \
+    } while (0)
         switch (L) {
             case 2: PW(2); break;
             case 4: PW(4); break;
@@ -332,7 +474,6 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     } else {
         if (H->ntiles == 0) return;
         using Atom = typename Sr<T>::Atom;
-        const bool vec = ((uintptr_t)H->col % 16 == 0) && ((uintptr_t)H->val % 16 == 0);
         if (vec)
             k_pull_bal<T, MASK, SOUT, true><<<(int)H->ntiles, kBalB, 0, s>>>(
                 m, H->nnz, H->rowptr, H->col, val, H->tile_row, a, ywork, yt, H->carry_row, (Atom*)H->carry_val);

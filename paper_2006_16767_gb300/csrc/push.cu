@@ -29,7 +29,7 @@ __device__ __forceinline__ void emit(const Ws& ws, int32_t r, typename Sr<T>::Pa
     using S = Sr<T>;
     if (WB == WB_ATOM) {
         if constexpr (!S::kPattern) atomicAdd((typename S::Atom*)ws.acc + r, S::to_atom(S::part_T(p)));
-        set_bit_once(ws.ytouch, r);
+        ws.yflag[r] = 1;
     } else {
         ws.pkeys[0][pos] = (uint32_t)r;
         if constexpr (!S::kPattern) {
@@ -159,6 +159,15 @@ __global__ void __launch_bounds__(256) k_reduce_by_key(const uint32_t* __restric
             const int64_t e = r0 + lane;
             const bool valid = e < eend;
             const uint32_t key = valid ? keys[e] : 0xffffffffu;
+            // the segment carried from the previous round ended exactly at
+            // the round boundary: write it out before this round starts
+            if (r0 > e0 && __shfl_sync(0xffffffffu, key, 0) != ckey && lane == 0) {
+                if constexpr (!S::kPattern) {
+                    if (ckey == first_key) atomicAdd(acc + ckey, S::to_atom(S::part_T(cval)));
+                    else acc[ckey] = S::to_atom(S::part_T(cval));
+                }
+                ws.yflag[ckey] = 1;
+            }
             P v = P(0);
             if constexpr (!S::kPattern) v = valid ? S::part_of(vals[e]) : P(0);
             else v = valid ? 1u : 0u;
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(256) k_reduce_by_key(const uint32_t* __restric
                     if (key == first_key) atomicAdd(acc + key, S::to_atom(S::part_T(v)));
                     else acc[key] = S::to_atom(S::part_T(v));
                 }
-                set_bit_once(ws.ytouch, key);
+                ws.yflag[key] = 1;
             }
             // the segment running into the last valid lane carries on
             const int src = (int)min((int64_t)31, eend - 1 - r0);
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(256) k_reduce_by_key(const uint32_t* __restric
         }
         if (lane == 0) {
             if constexpr (!S::kPattern) atomicAdd(acc + ckey, S::to_atom(S::part_T(cval)));
-            set_bit_once(ws.ytouch, ckey);
+            ws.yflag[ckey] = 1;
         }
     }
 }
@@ -248,17 +257,13 @@ __global__ void __launch_bounds__(256) k_priv_accumulate(const uint32_t* __restr
     }
     __syncthreads();
     const int64_t row0 = tile * R;
-    if constexpr (!S::kPattern) {
-        A* acc = (A*)ws.acc;
-        for (int i = threadIdx.x; i < R; i += blockDim.x) {
-            const int64_t r = row0 + i;
-            if (r < m && ((s_flag[i >> 5] >> (i & 31)) & 1u)) acc[r] = s_acc[i];
+    A* acc = (A*)ws.acc;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        const int64_t r = row0 + i;
+        if (r < m && ((s_flag[i >> 5] >> (i & 31)) & 1u)) {
+            if constexpr (!S::kPattern) acc[r] = s_acc[i];
+            ws.yflag[r] = 1;
         }
-    }
-    const int64_t nwords_m = (m + 31) / 32;
-    for (int i = threadIdx.x; i < R / 32; i += blockDim.x) {
-        const int64_t w = (row0 >> 5) + i;
-        if (w < nwords_m && s_flag[i]) ws.ytouch[w] = s_flag[i];
     }
 }
 
@@ -272,7 +277,7 @@ static int bitlen64(int64_t v) {
 template <class T>
 static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s) {
     const T* valc = (const T*)H->val_csc;
-    const int grid = H->num_sms * 8;
+    const int grid = H->num_sms * 32;
     const CallDesc* d = H->d_desc;
     Ws ws = H->ws;
     if (dist == 2 || wb != WB_ATOM) {

@@ -16,9 +16,18 @@ __device__ __forceinline__ int eval_tree(const TreeNode* nodes, int root, const 
     return nodes[node].feature >= 0 ? 0 : nodes[node].leaf;
 }
 
-__global__ void k_select(const MatFeat* __restrict__ mf, CallDesc* desc, const TreeNode* __restrict__ trees,
-                         const int32_t* __restrict__ roots, int32_t* last_kid, unsigned long long cond, int set_cond) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// The block first copies the node table into shared memory (one burst), so
+// the walk down the trees is a chain of shared-memory reads, not of global
+// loads. roots[3] holds the number of nodes.
+__global__ void __launch_bounds__(128) k_select(const MatFeat* __restrict__ mf, CallDesc* desc,
+                                                const TreeNode* __restrict__ trees, const int32_t* __restrict__ roots,
+                                                int32_t* last_kid, unsigned long long cond, int set_cond) {
+    __shared__ TreeNode sn[kMaxTreeNodes];
+    const int cnt = min(__ldg(roots + 3), kMaxTreeNodes);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) sn[i] = trees[i];
+    __syncthreads();
+    trees = sn;
+    if (threadIdx.x != 0) return;
     double f[13];
     f[0] = (double)mf->m;
     f[1] = (double)mf->n;
@@ -51,11 +60,11 @@ __global__ void k_select(const MatFeat* __restrict__ mf, CallDesc* desc, const T
 }
 
 void launch_select(asv_matrix_s* H, unsigned long long cond_handle, bool set_cond, cudaStream_t s) {
-    k_select<<<1, 32, 0, s>>>(H->d_mfeat, H->d_desc, H->d_trees, H->d_roots, H->d_last_kid, cond_handle,
+    k_select<<<1, 128, 0, s>>>(H->d_mfeat, H->d_desc, H->d_trees, H->d_roots, H->d_last_kid, cond_handle,
                               set_cond ? 1 : 0);
 }
 
-void default_trees(std::vector<TreeNode>& nodes, int32_t roots[3]) {
+void default_trees(std::vector<TreeNode>& nodes, int32_t roots[4]) {
     nodes.clear();
     for (int i = 0; i < kDefaultTreeNodes; ++i) {
         TreeNode t;
@@ -67,6 +76,7 @@ void default_trees(std::vector<TreeNode>& nodes, int32_t roots[3]) {
         nodes.push_back(t);
     }
     for (int i = 0; i < 3; ++i) roots[i] = kDefaultTreeRoots[i];
+    roots[3] = (int32_t)nodes.size();
 }
 
 }  // namespace asv

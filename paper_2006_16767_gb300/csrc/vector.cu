@@ -66,28 +66,71 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
     }
 }
 
-// Dense x: one warp per 32-element bitmap word (ballot), degree of every
-// nonzero column from colptr, block totals to the ticketed counters.
-template <class T, int B>
+// Four consecutive elements of x with one 128-bit (or, for bytes, 32-bit) load.
+template <class T>
+__device__ __forceinline__ void load4_nz(const T* __restrict__ x, int64_t j, bool nz[4]) {
+    if constexpr (sizeof(T) == 8) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(x + j));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(x + j + 2));
+        nz[0] = a.x != 0.0; nz[1] = a.y != 0.0; nz[2] = b.x != 0.0; nz[3] = b.y != 0.0;
+    } else if constexpr (sizeof(T) == 4) {
+        const int4 a = __ldg(reinterpret_cast<const int4*>(x + j));
+        nz[0] = Sr<T>::nz(*reinterpret_cast<const T*>(&a.x));
+        nz[1] = Sr<T>::nz(*reinterpret_cast<const T*>(&a.y));
+        nz[2] = Sr<T>::nz(*reinterpret_cast<const T*>(&a.z));
+        nz[3] = Sr<T>::nz(*reinterpret_cast<const T*>(&a.w));
+    } else {
+        const uchar4 a = __ldg(reinterpret_cast<const uchar4*>(x + j));
+        nz[0] = a.x != 0; nz[1] = a.y != 0; nz[2] = a.z != 0; nz[3] = a.w != 0;
+    }
+}
+
+// Dense x: a warp covers 128 elements (four bitmap words) per step, lane l
+// the four elements 4l..4l+3; the nibbles of eight lanes form one word. The
+// degree of every nonzero column comes from colptr; block totals go to the
+// ticketed counters.
+template <class T, int B, bool VEC>
 __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64_t n, const int32_t* __restrict__ colptr,
                                                   uint32_t* xbits, unsigned long long* counters, unsigned int* ticket,
                                                   CallDesc* desc, DescInit di, int64_t nnz, int32_t* status) {
     const int lane = threadIdx.x & 31;
     const int64_t nwords = (n + 31) >> 5;
+    const int64_t nsuper = (n + 127) >> 7;
     const int64_t gw = (int64_t)blockIdx.x * (B / 32) + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * (B / 32);
     unsigned long long cx = 0, cs = 0;
-    for (int64_t w = gw; w < nwords; w += nw) {
-        const int64_t j = w * 32 + lane;
-        bool nz = false;
-        if (j < n) {
-            nz = Sr<T>::nz(__ldg(x + j));
-            if (nz) cs += (unsigned long long)(__ldg(colptr + j + 1) - __ldg(colptr + j));
+    for (int64_t sw = gw; sw < nsuper; sw += nw) {
+        const int64_t j0 = sw * 128 + lane * 4;
+        bool nz[4];
+        if (VEC && j0 + 4 <= n) {
+            load4_nz(x, j0, nz);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nz[q] = (j0 + q < n) && Sr<T>::nz(__ldg(x + j0 + q));
         }
-        const unsigned bits = __ballot_sync(0xffffffffu, nz);
-        if (lane == 0) {
-            xbits[w] = bits;
-            cx += __popc(bits);
+        const unsigned nib = (unsigned)nz[0] | ((unsigned)nz[1] << 1) | ((unsigned)nz[2] << 2) | ((unsigned)nz[3] << 3);
+        if (nib) {
+            if (j0 + 4 <= n) {
+                const int4 cp = __ldg(reinterpret_cast<const int4*>(colptr + j0));
+                const int32_t c4 = __ldg(colptr + j0 + 4);
+                cs += (nz[0] ? cp.y - cp.x : 0) + (nz[1] ? cp.z - cp.y : 0) + (nz[2] ? cp.w - cp.z : 0) +
+                      (nz[3] ? c4 - cp.w : 0);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (nz[q]) cs += (unsigned long long)(__ldg(colptr + j0 + q + 1) - __ldg(colptr + j0 + q));
+            }
+        }
+        unsigned wv = nib << (4 * (lane & 7));
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 4);
+        if ((lane & 7) == 0) {
+            const int64_t w = sw * 4 + (lane >> 3);
+            if (w < nwords) {
+                xbits[w] = wv;
+                cx += __popc(wv);
+            }
         }
     }
     finish_counts<B>(cx, cs, counters, ticket, desc, di, n, nnz, status);
@@ -116,27 +159,26 @@ static int feat_grid(asv_matrix_s* H, int64_t items) {
     return (int)max((int64_t)1, min(g, (int64_t)H->num_sms * 8));
 }
 
+template <class T>
+static void feat_dense_dtype(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
+    const int64_t nsuper = (H->n + 127) / 128;
+    const int g = (int)max((int64_t)1, min((nsuper + 7) / 8, (int64_t)H->num_sms * 32));
+    const T* x = (const T*)di.user_x_dense;
+    const bool vec = ((uintptr_t)x % 16) == 0;
+    if (vec)
+        k_feat_dense<T, 256, true><<<g, 256, 0, s>>>(x, H->n, H->colptr, H->ws.xbits_dense, H->ws.counters,
+                                                     H->ws.ticket, H->d_desc, di, H->nnz, H->ws.status);
+    else
+        k_feat_dense<T, 256, false><<<g, 256, 0, s>>>(x, H->n, H->colptr, H->ws.xbits_dense, H->ws.counters,
+                                                      H->ws.ticket, H->d_desc, di, H->nnz, H->ws.status);
+}
+
 void launch_features_dense(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
-    const int g = feat_grid(H, ((H->n + 31) / 32) * 32);
-    auto* c = H->ws.counters;
-    auto* tk = H->ws.ticket;
     switch (H->dtype) {
-        case ASV_F32:
-            k_feat_dense<float, 256><<<g, 256, 0, s>>>((const float*)di.user_x_dense, H->n, H->colptr, H->ws.xbits_dense,
-                                                       c, tk, H->d_desc, di, H->nnz, H->ws.status);
-            break;
-        case ASV_F64:
-            k_feat_dense<double, 256><<<g, 256, 0, s>>>((const double*)di.user_x_dense, H->n, H->colptr,
-                                                        H->ws.xbits_dense, c, tk, H->d_desc, di, H->nnz, H->ws.status);
-            break;
-        case ASV_I32:
-            k_feat_dense<int32_t, 256><<<g, 256, 0, s>>>((const int32_t*)di.user_x_dense, H->n, H->colptr,
-                                                         H->ws.xbits_dense, c, tk, H->d_desc, di, H->nnz, H->ws.status);
-            break;
-        case ASV_BOOL:
-            k_feat_dense<bool8, 256><<<g, 256, 0, s>>>((const bool8*)di.user_x_dense, H->n, H->colptr, H->ws.xbits_dense,
-                                                       c, tk, H->d_desc, di, H->nnz, H->ws.status);
-            break;
+        case ASV_F32: feat_dense_dtype<float>(H, di, s); break;
+        case ASV_F64: feat_dense_dtype<double>(H, di, s); break;
+        case ASV_I32: feat_dense_dtype<int32_t>(H, di, s); break;
+        case ASV_BOOL: feat_dense_dtype<bool8>(H, di, s); break;
     }
 }
 
@@ -175,12 +217,35 @@ void launch_x_scatter(asv_matrix_s* H, bool set, cudaStream_t s) {
     }
 }
 
-// ---------------------------------------------------------------- ordered compaction of a bitmap
-// Block b owns a contiguous word range; a block scan of the words' popcounts
-// plus the block's offset gives every set bit its ascending output position.
-template <int B, class Policy>
-__global__ void __launch_bounds__(B) k_bits_write(uint32_t* bits, int64_t nwords, const int32_t* __restrict__ blk,
-                                                  Policy pol) {
+// ---------------------------------------------------------------- ordered compaction
+// Over a bitmap (32 items per word) or a byte-flag array (4 items per
+// 32-bit word). Block b owns a contiguous word range; a block scan of the
+// words' item counts plus the block's offset gives every set item its
+// ascending output position.
+template <bool BYTES>
+__device__ __forceinline__ uint32_t item_mask(uint32_t w) {
+    if constexpr (BYTES) {
+        // bit 8q+7 set iff byte q is nonzero
+        return (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;
+    } else {
+        return w;
+    }
+}
+
+template <int B, bool BYTES>
+__global__ void __launch_bounds__(B) k_items_count(const uint32_t* __restrict__ words, int64_t nwords, int32_t* blk) {
+    __shared__ int32_t sm[B / 32 + 1];
+    const int64_t chunk = (nwords + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
+    int32_t s = 0;
+    for (int64_t w = lo + threadIdx.x; w < hi; w += B) s += __popc(item_mask<BYTES>(words[w]));
+    s = block_reduce_sum<B>(s, sm);
+    if (threadIdx.x == 0) blk[blockIdx.x] = s;
+}
+
+template <int B, bool BYTES, class Policy>
+__global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwords, const int32_t* __restrict__ blk,
+                                                   Policy pol) {
     __shared__ int32_t sm[B / 32 + 1];
     const int64_t chunk = (nwords + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
@@ -188,15 +253,16 @@ __global__ void __launch_bounds__(B) k_bits_write(uint32_t* bits, int64_t nwords
     pol.begin();
     for (int64_t off = lo; off < hi; off += B) {
         const int64_t w = off + threadIdx.x;
-        uint32_t word = w < hi ? bits[w] : 0u;
+        const uint32_t raw = w < hi ? words[w] : 0u;
+        uint32_t mask = item_mask<BYTES>(raw);
         int32_t tot;
-        int32_t pos = base + block_excl_scan<B>((int32_t)__popc(word), sm, &tot);
-        if (w < hi && word) {
-            pol.clear_word(bits, w);
-            while (word) {
-                const int b = __ffs(word) - 1;
-                word &= word - 1;
-                pol.emit(pos++, w * 32 + b);
+        int32_t pos = base + block_excl_scan<B>((int32_t)__popc(mask), sm, &tot);
+        if (mask) {
+            pol.clear_word(words, w);
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                mask &= mask - 1;
+                pol.emit(pos++, BYTES ? w * 4 + (b >> 3) : w * 32 + b);
             }
         }
         base += tot;
@@ -274,19 +340,19 @@ struct OutSparsePolicy {
     }
 };
 
-template <class Policy>
-static void compact_bits(asv_matrix_s* H, uint32_t* bits, int64_t nbits, const Policy& pol, cudaStream_t s) {
-    const int64_t nwords = (nbits + 31) / 32;
+template <bool BYTES, class Policy>
+static void compact_items(asv_matrix_s* H, uint32_t* words, int64_t nitems, const Policy& pol, cudaStream_t s) {
+    const int64_t nwords = BYTES ? (nitems + 3) / 4 : (nitems + 31) / 32;
     const int G = H->G;
-    k_bits_count<256><<<G, 256, 0, s>>>(bits, nwords, H->ws.blk);
+    k_items_count<256, BYTES><<<G, 256, 0, s>>>(words, nwords, H->ws.blk);
     k_scan_blocks<1024><<<1, 1024, 0, s>>>(H->ws.blk, G);
-    k_bits_write<256, Policy><<<G, 256, 0, s>>>(bits, nwords, H->ws.blk, pol);
+    k_items_write<256, BYTES, Policy><<<G, 256, 0, s>>>(words, nwords, H->ws.blk, pol);
 }
 
 template <class T>
 static void x_list_dtype(asv_matrix_s* H, cudaStream_t s) {
     XListPolicy<T> pol{H->d_desc, H->ws.xlist_idx, (T*)H->ws.xlist_val, nullptr};
-    compact_bits(H, H->ws.xbits_dense, H->n, pol, s);
+    compact_items<false>(H, H->ws.xbits_dense, H->n, pol, s);
 }
 
 void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
@@ -300,40 +366,36 @@ void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
 
 // ---------------------------------------------------------------- dense write-out of the push accumulators
 template <class T>
-__global__ void k_finalize_dense(int64_t m, typename Sr<T>::Atom* acc, uint32_t* ytouch, const CallDesc* __restrict__ desc) {
+__global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, typename Sr<T>::Atom* acc, uint8_t* yflag,
+                                                        const CallDesc* __restrict__ desc) {
     T* __restrict__ y = (T*)desc->y;
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const uint32_t w = (i < m) ? ytouch[i >> 5] : 0u;
-        const bool bit = (w >> (i & 31)) & 1u;
-        if (i < m) {
-            if (Sr<T>::kPattern) {
-                y[i] = bit ? Sr<T>::one() : T(0);
-            } else if (bit) {
-                y[i] = Sr<T>::from_atom(acc[i]);
-                acc[i] = typename Sr<T>::Atom(0);
-            } else {
-                y[i] = T(0);
-            }
-        }
-        __syncwarp();
-        if (lane == 0 && i < m && w) ytouch[i >> 5] = 0u;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= m) return;
+    const bool f = yflag[i] != 0;
+    if (Sr<T>::kPattern) {
+        y[i] = f ? Sr<T>::one() : T(0);
+    } else if (f) {
+        y[i] = Sr<T>::from_atom(acc[i]);
+        acc[i] = typename Sr<T>::Atom(0);
+    } else {
+        y[i] = T(0);
     }
+    if (f) yflag[i] = 0;
 }
 
 template <class T>
 static void finalize_dtype(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s) {
     using Atom = typename Sr<T>::Atom;
     if (out_mode == ASV_OUT_DENSE) {
-        const int64_t g = max((int64_t)1, min((H->m + 255) / 256, (int64_t)H->num_sms * 16));
-        k_finalize_dense<T><<<(int)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.ytouch, H->d_desc);
+        if (H->m > 0)
+            k_finalize_dense<T><<<(unsigned)((H->m + 255) / 256), 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag,
+                                                                            H->d_desc);
     } else if (from_acc) {
         OutSparsePolicy<T, true> pol{H->d_desc, (Atom*)H->ws.acc, nullptr, H->ws.status, nullptr, nullptr, 0};
-        compact_bits(H, H->ws.ytouch, H->m, pol, s);
+        compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s);
     } else {
         OutSparsePolicy<T, false> pol{H->d_desc, nullptr, (const T*)H->ws.ywork, H->ws.status, nullptr, nullptr, 0};
-        compact_bits(H, H->ws.ytouch, H->m, pol, s);
+        compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s);
     }
 }
 
@@ -366,7 +428,7 @@ static void compact_public_dtype(asv_matrix_s* H, const void* x, int32_t* idx, v
     const int g = feat_grid(H, ((H->n + 31) / 32) * 32);
     k_x_bits<T><<<g, 256, 0, s>>>((const T*)x, H->n, H->ws.xbits_dense);
     PublicCompactPolicy<T> pol{(const T*)x, idx, (T*)val, count};
-    compact_bits(H, H->ws.xbits_dense, H->n, pol, s);
+    compact_items<false>(H, H->ws.xbits_dense, H->n, pol, s);
 }
 
 void launch_compact_public(asv_matrix_s* H, const void* x, int32_t* idx, void* val, int64_t* count, cudaStream_t s) {
