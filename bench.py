@@ -135,6 +135,31 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
+def bfs_frontiers(rowptr, col, roots):
+    """Successive BFS frontiers {v : level(v) = l} of each root, ascending.
+    Levels come from scipy's BFS predecessor tree by pointer jumping."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order
+    n = len(rowptr) - 1
+    A = sp.csr_matrix((np.ones(len(col), np.int8), col, rowptr), shape=(n, n))
+    out = []
+    for root in roots:
+        order, pred = breadth_first_order(A, root, directed=True, return_predecessors=True)
+        anc = np.where(pred >= 0, pred, np.arange(n)).astype(np.int64)
+        depth = (pred >= 0).astype(np.int64)
+        while True:  # depth(v) += depth(anc(v)); anc(v) = anc(anc(v)) until every anc is a root
+            nxt = anc[anc]
+            if np.array_equal(nxt, anc):
+                break
+            depth = depth + depth[anc]
+            anc = nxt
+        level = np.full(n, -1, np.int64)
+        level[order] = depth[order]
+        for l in range(int(level.max()) + 1):
+            out.append(np.flatnonzero(level == l).astype(np.int32))
+    return out
+
+
 class Rmat22:
     """R-MAT scale 22 BFS frontiers (Boolean) + one FP32 PageRank step."""
     name = "rmat22_bfs8_pagerank"
@@ -166,19 +191,8 @@ class Rmat22:
         self.y_pr = torch.empty(self.m, dtype=torch.float32, device=dev)
         self.yidx = torch.empty(self.m, dtype=torch.int32, device=dev)
         self.yval = torch.empty(self.m, dtype=torch.uint8, device=dev)
-        # BFS frontiers from the library's own Boolean SpMSpV (setup, untimed)
-        self.frontiers = []
-        y = torch.empty(self.m, dtype=torch.uint8, device=dev)
-        for root in self.roots:
-            visited = torch.zeros(self.n, dtype=torch.bool, device=dev)
-            f = torch.tensor([root], dtype=torch.int32, device=dev)
-            visited[root] = True
-            while f.numel() > 0:
-                self.frontiers.append(f)
-                self.Ab.spmspv(xidx=f, y=y)
-                nxt = (y.bool() & ~visited).nonzero().flatten().to(torch.int32)
-                visited[nxt.long()] = True
-                f = nxt
+        # BFS frontiers (inputs, prepared on the host with scipy's BFS)
+        self.frontiers = [torch.from_numpy(f).to(dev) for f in bfs_frontiers(self.rowptr, self.col, self.roots)]
         self.counts = torch.tensor([[f.numel()] for f in self.frontiers], dtype=torch.int64, device=dev)
         self.nnz_y = torch.zeros(len(self.frontiers) + 1, dtype=torch.int64, device=dev)
         # the selector's choice and the byte model of every call

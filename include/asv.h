@@ -194,8 +194,10 @@ asv_status asv_compact(asv_matrix A, const void* d_x_dense, int32_t* d_idx, void
 
 /* Replace the handle's decision trees (three cascaded CART trees: computing
  * pattern, workload distribution, write-back; Sec. V-B / VI-B). `nodes` holds
- * n_nodes records of 5 doubles {feature, threshold, left, right, leaf_class};
- * feature < 0 marks a leaf. roots[3] are the node indices of the three roots.
+ * n_nodes (<= 1024) records of 5 doubles {feature, threshold, left, right,
+ * leaf_class}; feature < 0 marks a leaf. h_roots[12] holds the roots of the
+ * three trees for each of the four call formats, in the order (x dense,
+ * y dense), (x dense, y list), (x list, y dense), (x list, y list).
  * Feature indices: 0 m, 1 n, 2 nnz, 3 max_row, 4 min_row, 5 avg_row,
  * 6 relative_range, 7 var_nnz_row, 8 gini, 9 nnz_x, 10 x_sparsity, 11 nnz_s,
  * 12 m_sparsity. A node sends x left when feature <= threshold.

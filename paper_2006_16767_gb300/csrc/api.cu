@@ -5,6 +5,7 @@
 // candidates (with their own format conversion), so the chosen kernel runs
 // with no host round-trip.
 #include <cstdio>
+#include <cstdlib>
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -164,7 +165,7 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     AL(H->carry_row, 4 * (H->ntiles + 1), false);
     AL(H->carry_val, 8 * (H->ntiles + 1), false);
     AL(H->d_trees, sizeof(TreeNode) * kMaxTreeNodes, false);
-    AL(H->d_roots, 4 * 4, false);
+    AL(H->d_roots, 4 * kRootsLen, false);
     AL(H->d_desc, sizeof(CallDesc), true);
     AL(H->d_last_kid, 4, true);
     // workspaces
@@ -199,12 +200,17 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     CKH(build_partition(H, s));
     {
         std::vector<TreeNode> nodes;
-        int32_t roots[4];
-        default_trees(nodes, roots);
+        int32_t roots[kRootsLen];
+        default_trees(dtype, nodes, roots);
         CKH(cudaMemcpyAsync(H->d_trees, nodes.data(), sizeof(TreeNode) * nodes.size(), cudaMemcpyHostToDevice, s));
         CKH(cudaMemcpyAsync(H->d_roots, roots, sizeof(roots), cudaMemcpyHostToDevice, s));
     }
     H->pull_lanes = std::min(32, std::max(2, pow2_floor(H->h_mfeat.avg_row / 3.0)));
+    if (const char* e = getenv("ASV_PULL_UNROLL")) H->pull_unroll = atoi(e) >= 4 ? 4 : 2;
+    if (const char* e = getenv("ASV_PULL_LANES")) {
+        const int l = atoi(e);
+        if (l == 2 || l == 4 || l == 8 || l == 16 || l == 32) H->pull_lanes = l;
+    }
     CKH(cudaStreamSynchronize(s));
     CKH(cudaGetLastError());
     *out = H;
@@ -271,7 +277,11 @@ static void enqueue_candidate(asv_matrix_s* H, int k, int x_sparse, int om, cuda
     }
 }
 
-static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om) {
+// The selector-driven graph of one (x format, output mode): a feature-pass
+// node whose last block also walks the trees and sets the SWITCH value, then
+// the SWITCH node with one branch per candidate. The feature node's
+// arguments are replaced before every launch, so one graph serves all calls.
+static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om, const DescInit& di) {
     if (H->gexec[xs][om]) return ASV_OK;
     if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
     cudaStream_t cs = H->cap_stream;
@@ -280,12 +290,12 @@ static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om) {
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, g, ASV_K_PULL_BAL, cudaGraphCondAssignDefault));
     CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    launch_select(H, (unsigned long long)h, true, cs);
+    launch_features(H, di, select_arg(H, (unsigned long long)h), cs);
     cudaGraph_t g2;
     CK(cudaStreamEndCapture(cs, &g2));
-    cudaGraphNode_t sel;
+    cudaGraphNode_t feat;
     size_t nn = 1;
-    CK(cudaGraphGetNodes(g, &sel, &nn));
+    CK(cudaGraphGetNodes(g, &feat, &nn));
     if (nn != 1) return ASV_ERR_CUDA;
     alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
     memset(cp_raw, 0, sizeof(cp_raw));
@@ -295,7 +305,7 @@ static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om) {
     cp.conditional.type = cudaGraphCondTypeSwitch;
     cp.conditional.size = ASV_K_COUNT;
     cudaGraphNode_t cn;
-    CK(cudaGraphAddNode(&cn, g, &sel, nullptr, 1, &cp));
+    CK(cudaGraphAddNode(&cn, g, &feat, nullptr, 1, &cp));
     for (int k = 0; k < ASV_K_COUNT; ++k) {
         CK(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[k], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeRelaxed));
@@ -307,6 +317,27 @@ static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om) {
     CK(cudaGraphInstantiate(&ex, g, 0));
     H->graph[xs][om] = g;
     H->gexec[xs][om] = ex;
+    H->feat_node[xs][om] = feat;
+    H->cond[xs][om] = (unsigned long long)h;
+    return ASV_OK;
+}
+
+static asv_status launch_auto(asv_matrix_s* H, const DescInit& di, int om, cudaStream_t s) {
+    const int xs = di.x_sparse;
+    asv_status st = build_auto_graph(H, xs, om, di);
+    if (st != ASV_OK) return st;
+    FeatLaunch fl;
+    feature_launch(H, di, select_arg(H, H->cond[xs][om]), fl);
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = fl.func;
+    kp.gridDim = fl.grid;
+    kp.blockDim = fl.block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = fl.args;
+    kp.extra = nullptr;
+    CK(cudaGraphExecKernelNodeSetParams(H->gexec[xs][om], H->feat_node[xs][om], &kp));
+    CK(cudaGraphLaunch(H->gexec[xs][om], s));
     return ASV_OK;
 }
 
@@ -345,11 +376,6 @@ static asv_status prepare_call(asv_matrix_s* H, const int64_t* d_nnz_x, const in
     return ASV_OK;
 }
 
-static void launch_features(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
-    if (di.x_sparse) launch_features_sparse(H, di, s);
-    else launch_features_dense(H, di, s);
-}
-
 extern "C" asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx, const void* d_xval,
                                  const void* d_x_dense, int32_t out_mode, void* d_y, int32_t* d_yidx, void* d_yval,
                                  int64_t* d_nnz_y, int64_t y_cap, int32_t kernel, void* stream) {
@@ -359,12 +385,13 @@ extern "C" asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int
     DescInit di;
     asv_status st = prepare_call(A, d_nnz_x, d_xidx, d_xval, d_x_dense, out_mode, d_y, d_yidx, d_yval, d_nnz_y, y_cap, di);
     if (st != ASV_OK) return st;
-    launch_features(A, di, s);
     if (kernel == ASV_K_AUTO) {
-        st = build_auto_graph(A, di.x_sparse, out_mode);
+        st = launch_auto(A, di, out_mode, s);
         if (st != ASV_OK) return st;
-        CK(cudaGraphLaunch(A->gexec[di.x_sparse][out_mode], s));
     } else {
+        SelectArg none = select_arg(A, 0ull);
+        none.enabled = 0;
+        launch_features(A, di, none, s);
         enqueue_candidate(A, kernel, di.x_sparse, out_mode, s);
     }
     CK(cudaGetLastError());
@@ -393,8 +420,7 @@ extern "C" asv_status asv_select(asv_matrix A, const int64_t* d_nnz_x, const int
     asv_status st = prepare_call(A, d_nnz_x, d_xidx, d_xval, d_x_dense, ASV_OUT_DENSE, A->ws.ywork, nullptr,
                                  nullptr, nullptr, 0, di);
     if (st != ASV_OK) return st;
-    launch_features(A, di, s);
-    launch_select(A, 0ull, false, s);
+    launch_features(A, di, select_arg(A, 0ull), s);
     CallDesc hd;
     CK(cudaMemcpyAsync(&hd, A->d_desc, sizeof(hd), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -440,12 +466,15 @@ extern "C" asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t
         if (t.feature >= 0 && (t.left < 0 || t.left >= n_nodes || t.right < 0 || t.right >= n_nodes)) return ASV_ERR_ARG;
         if (t.feature < 0 && (t.leaf < 0 || t.leaf > 2)) return ASV_ERR_ARG;
     }
-    for (int i = 0; i < 3; ++i)
+    int32_t r[kRootsLen];
+    for (int i = 0; i < kRootsLen - 1; ++i) {
         if (h_roots[i] < 0 || h_roots[i] >= n_nodes) return ASV_ERR_ARG;
+        r[i] = h_roots[i];
+    }
+    r[kRootsLen - 1] = n_nodes;
     cudaStream_t s = (cudaStream_t)stream;
-    const int32_t r4[4] = {h_roots[0], h_roots[1], h_roots[2], n_nodes};
     CK(cudaMemcpyAsync(A->d_trees, nodes.data(), sizeof(TreeNode) * n_nodes, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(A->d_roots, r4, 16, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(A->d_roots, r, sizeof(r), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     return ASV_OK;
 }

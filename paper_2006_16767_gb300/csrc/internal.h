@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "selector.cuh"
 
 struct asv_matrix_s {
     int dev = 0;
@@ -28,7 +29,8 @@ struct asv_matrix_s {
     int64_t ntiles = 0;
     int32_t* carry_row = nullptr;
     void* carry_val = nullptr;
-    int pull_lanes = 8;  // lanes per row of the (sub-)warp pull kernels
+    int pull_lanes = 8;   // lanes per row of the (sub-)warp pull kernels
+    int pull_unroll = 4;  // rows per lane group loaded together (2: more resident warps)
     // selector tables
     asv::TreeNode* d_trees = nullptr;
     int32_t* d_roots = nullptr;
@@ -39,6 +41,8 @@ struct asv_matrix_s {
     // graphs of the selector-driven path, one per (x format, output mode)
     cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphNode_t feat_node[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    unsigned long long cond[2][2] = {{0, 0}, {0, 0}};
     cudaStream_t cap_stream = nullptr;
     int G = 0;  // fixed grid of the scan / sort / compaction primitives
     std::vector<void*> allocs;
@@ -78,8 +82,26 @@ struct DescInit {
     int32_t out_mode;
     int32_t x_sparse;
 };
-void launch_features_dense(asv_matrix_s* H, const DescInit& di, cudaStream_t s);
-void launch_features_sparse(asv_matrix_s* H, const DescInit& di, cudaStream_t s);
+// A feature-pass launch whose argument storage lives in the struct.
+struct FeatLaunch {
+    void* func;
+    dim3 grid, block;
+    void* args[11];
+    const void* xptr;
+    const int64_t* nnz_x_dev;
+    const int32_t* xidx;
+    int64_t n, nnz;
+    const int32_t* colptr;
+    uint32_t* xbits;
+    unsigned long long* counters;
+    unsigned int* ticket;
+    CallDesc* desc;
+    DescInit di;
+    int32_t* status;
+    SelectArg sa;
+};
+void feature_launch(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, FeatLaunch& fl);
+void launch_features(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, cudaStream_t s);
 void launch_x_scatter(asv_matrix_s* H, bool set, cudaStream_t s);
 void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s);
 void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s);
@@ -99,7 +121,7 @@ void launch_pull(asv_matrix_s* H, int dist, bool masked, bool sparse_out, const 
 void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s);
 
 // select.cu
-void launch_select(asv_matrix_s* H, unsigned long long cond_handle, bool set_cond, cudaStream_t s);
-void default_trees(std::vector<TreeNode>& nodes, int32_t roots[4]);
+SelectArg select_arg(asv_matrix_s* H, unsigned long long cond);
+void default_trees(int32_t dtype, std::vector<TreeNode>& nodes, int32_t roots[kRootsLen]);
 
 }  // namespace asv

@@ -1,0 +1,197 @@
+// The (sub-)warp row-major kernel: its template and launcher, instantiated
+// per value type in pull_warp_fp.cu and pull_warp_int.cu.
+#pragma once
+#include "pull_common.cuh"
+
+namespace asv {
+
+// ---------------------------------------------------------------- L lanes per row
+// A group of L lanes owns one row; a warp owns RW = (32/L)*U consecutive rows,
+// whose row pointers it reads with one coalesced load. Lane l reads its
+// row's 16-byte-aligned 4-element chunks l, l+L, ... with one 128-bit load of
+// column ids and one of values each (elements outside the row are masked).
+// The first chunk of all U rows of a group is loaded before any x gather, so
+// a warp keeps U*32 bytes per lane in flight. Chunk products are added as a
+// small tree, chunks of a lane with compensated summation, and the group's
+// lanes with shuffles.
+template <class T, bool MASK, bool VEC>
+struct Chunk {
+    int32_t c[4];
+    T v[4];
+    bool in[4];
+};
+
+template <class T, bool MASK, bool VEC>
+__device__ __forceinline__ void chunk_load(Chunk<T, MASK, VEC>& ch, const int32_t* __restrict__ col,
+                                           const T* __restrict__ val, int64_t nnz, int32_t base, int32_t b, int32_t e) {
+    using S = Sr<T>;
+    const bool full = VEC && base < e && (int64_t)base + 4 <= nnz;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ch.in[q] = base + q >= b && base + q < e;
+    if (full) {
+        const int4 cc = __ldg(reinterpret_cast<const int4*>(col + base));
+        ch.c[0] = cc.x; ch.c[1] = cc.y; ch.c[2] = cc.z; ch.c[3] = cc.w;
+        if constexpr (!S::kPattern && !MASK) {
+            if (val != nullptr) {
+                if constexpr (sizeof(T) == 4) {
+                    const int4 vv = __ldg(reinterpret_cast<const int4*>(val + base));
+                    ch.v[0] = __int_as_float_t<T>(vv.x); ch.v[1] = __int_as_float_t<T>(vv.y);
+                    ch.v[2] = __int_as_float_t<T>(vv.z); ch.v[3] = __int_as_float_t<T>(vv.w);
+                } else {
+                    const double2 v01 = __ldg(reinterpret_cast<const double2*>(val + base));
+                    const double2 v23 = __ldg(reinterpret_cast<const double2*>(val + base + 2));
+                    ch.v[0] = (T)v01.x; ch.v[1] = (T)v01.y; ch.v[2] = (T)v23.x; ch.v[3] = (T)v23.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ch.v[q] = S::one();
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ch.c[q] = ch.in[q] ? __ldg(col + base + q) : 0;
+            if constexpr (!S::kPattern && !MASK) ch.v[q] = ch.in[q] ? load_val(val, base + q) : T(0);
+        }
+    }
+}
+
+template <class T, bool MASK, bool SOUT, bool VEC>
+__device__ __forceinline__ typename Sr<T>::Part chunk_sum(Chunk<T, MASK, VEC>& ch, const T* __restrict__ val,
+                                                          const T* __restrict__ x, const uint32_t* __restrict__ xbits,
+                                                          int32_t base, bool& hit) {
+    using S = Sr<T>;
+    using P = typename S::Part;
+    bool eff[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        bool bit = true;
+        if (MASK || SOUT) bit = ch.in[q] && test_bit(xbits, ch.c[q]);
+        if (SOUT) hit |= bit;
+        eff[q] = ch.in[q] && (!MASK || bit);
+    }
+    if constexpr (S::kPattern) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ch.v[q] = S::one();
+    } else if constexpr (MASK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ch.v[q] = eff[q] ? load_val(val, base + q) : T(0);
+    }
+    P pr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pr[q] = eff[q] ? S::mul(ch.v[q], __ldg(x + ch.c[q])) : P(0);
+    return S::part_add(S::part_add(pr[0], pr[1]), S::part_add(pr[2], pr[3]));
+}
+
+template <int L, int UU>
+struct WarpRows {
+    static constexpr int U = (L == 2 && UU > 2) ? 2 : UU;  // rows per group, loaded together
+    static constexpr int RW = (32 / L) * U;                 // rows per warp (<= 32)
+};
+
+template <class T, bool MASK, bool SOUT, int L, bool VEC, int UU>
+__global__ void __launch_bounds__(256, UU >= 4 ? 4 : 6) k_pull_warp(int64_t m, int64_t nnz, const int32_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                   PullArg a, void* ywork, uint8_t* yflag) {
+    using S = Sr<T>;
+    using P = typename S::Part;
+    constexpr int U = WarpRows<L, UU>::U, RW = WarpRows<L, UU>::RW, RPW = 32 / L;
+    const PullIO p = resolve(a, ywork, SOUT);
+    const T* __restrict__ x = (const T*)p.x;
+    T* __restrict__ y = (T*)p.y;
+    const int lane = threadIdx.x & 31, g = lane / L, l = lane % L;
+    const int64_t row0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * RW;
+    if (row0 >= m) return;
+    const int32_t rp = (lane < RW && row0 + lane <= m) ? __ldg(rowptr + row0 + lane) : 0;
+    const int32_t rp_end = __ldg(rowptr + min(row0 + RW, m));
+    int32_t b[U], e[U];
+    bool valid[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int r = u * RPW + g;
+        valid[u] = row0 + r < m;
+        b[u] = __shfl_sync(0xffffffffu, rp, r);
+        const int32_t nx = __shfl_sync(0xffffffffu, rp, (r + 1) & 31);
+        e[u] = (r + 1 == RW) ? rp_end : nx;
+        if (!valid[u]) e[u] = b[u];
+    }
+    Chunk<T, MASK, VEC> ch[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) chunk_load(ch[u], col, val, nnz, (b[u] & ~3) + 4 * l, b[u], e[u]);
+    P vs[U];
+    bool hit[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        hit[u] = false;
+        typename S::Acc acc;
+        S::acc_zero(acc);
+        const int32_t base0 = (b[u] & ~3) + 4 * l;
+        S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(ch[u], val, x, p.xbits, base0, hit[u]));
+        for (int32_t base = base0 + 4 * L; base < e[u]; base += 4 * L) {
+            if constexpr (S::kPattern) {
+                if (acc) break;  // OR is settled by the first hit
+            }
+            Chunk<T, MASK, VEC> c2;
+            chunk_load(c2, col, val, nnz, base, b[u], e[u]);
+            S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(c2, val, x, p.xbits, base, hit[u]));
+        }
+        vs[u] = S::acc_part(acc);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        P v = vs[u];
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) v = S::part_add(v, shfl_xor(v, o, L));
+        bool h = false;
+        if (SOUT) {
+            const unsigned bal = __ballot_sync(0xffffffffu, hit[u]);
+            const unsigned gm = (0xffffffffu >> (32 - L)) << (lane & ~(L - 1));
+            h = (bal & gm) != 0;
+        }
+        if (valid[u] && l == 0) {
+            const int64_t i = row0 + u * RPW + g;
+            y[i] = S::part_T(v);
+            if (SOUT && h) yflag[i] = 1;
+        }
+    }
+}
+
+
+template <class T, bool MASK, bool SOUT>
+void launch_pull_warp_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStream_t s) {
+    const int64_t m = H->m;
+    const T* val = (const T*)H->val;
+    void* ywork = H->ws.ywork;
+    uint8_t* yt = H->ws.yflag;
+        const int L = H->pull_lanes;
+        if (m == 0) return;
+        const int uu = H->pull_unroll >= 4 ? 4 : 2;
+        const int rw = (32 / L) * ((L == 2) ? 2 : uu);
+        const unsigned g = (unsigned)((m + 8 * rw - 1) / (8 * rw));
+#define PW(LL)                                                                                                   \
+    do {                                                                                                         \
+        if (uu == 4) {                                                                                           \
+            if (vec) k_pull_warp<T, MASK, SOUT, LL, true, 4><<<g, 256, 0, s>>>(m, H->nnz, H->rowptr, H->col, val, a, ywork, yt);  \
+            else k_pull_warp<T, MASK, SOUT, LL, false, 4><<<g, 256, 0, s>>>(m, H->nnz, H->rowptr, H->col, val, a, ywork, yt); \
+        } else {                                                                                                 \
+            if (vec) k_pull_warp<T, MASK, SOUT, LL, true, 2><<<g, 256, 0, s>>>(m, H->nnz, H->rowptr, H->col, val, a, ywork, yt);  \
+            else k_pull_warp<T, MASK, SOUT, LL, false, 2><<<g, 256, 0, s>>>(m, H->nnz, H->rowptr, H->col, val, a, ywork, yt); \
+        }                                                                                                        \
+    } while (0)
+        switch (L) {
+            case 2: PW(2); break;
+            case 4: PW(4); break;
+            case 8: PW(8); break;
+            case 16: PW(16); break;
+            default: PW(32); break;
+        }
+#undef PW
+}
+
+#define ASV_INSTANTIATE_PULL_WARP(T)                                                                   \
+    template void launch_pull_warp_dtype<T, false, false>(asv_matrix_s*, const PullArg&, bool, cudaStream_t); \
+    template void launch_pull_warp_dtype<T, false, true>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);  \
+    template void launch_pull_warp_dtype<T, true, false>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);  \
+    template void launch_pull_warp_dtype<T, true, true>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);
+
+}  // namespace asv

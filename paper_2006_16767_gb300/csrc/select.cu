@@ -1,82 +1,45 @@
 // Kernel selector (Sec. V and Sec. VI-B): three cascaded decision trees over
 // the Table 1 features -- computing pattern first, then workload
-// distribution, then (for the push pattern) write-back -- evaluated by one
-// device thread right after the vector-feature pass, with no host round-trip.
-// Inside the selector-driven CUDA graph the chosen id becomes the value of a
-// SWITCH conditional node whose branches are the candidate kernels.
+// distribution, then (for the push pattern) write-back. In the
+// selector-driven path the trees are walked by the last block of the
+// vector-feature pass, inside the CUDA graph whose SWITCH node runs the
+// chosen candidate (selector.cuh); this file holds the host-side tables.
 #include "internal.h"
+#include "selector.cuh"
 #include "trees_default.h"
 
 namespace asv {
 
-__device__ __forceinline__ int eval_tree(const TreeNode* nodes, int root, const double* f) {
-    int node = root;
-    for (int depth = 0; depth < 64 && nodes[node].feature >= 0; ++depth)
-        node = (f[nodes[node].feature] <= nodes[node].thr) ? nodes[node].left : nodes[node].right;
-    return nodes[node].feature >= 0 ? 0 : nodes[node].leaf;
+SelectArg select_arg(asv_matrix_s* H, unsigned long long cond) {
+    SelectArg sa;
+    sa.mf = H->d_mfeat;
+    sa.trees = H->d_trees;
+    sa.roots = H->d_roots;
+    sa.last_kid = H->d_last_kid;
+    sa.cond = cond;
+    sa.enabled = 1;
+    return sa;
 }
 
-// The block first copies the node table into shared memory (one burst), so
-// the walk down the trees is a chain of shared-memory reads, not of global
-// loads. roots[3] holds the number of nodes.
-__global__ void __launch_bounds__(128) k_select(const MatFeat* __restrict__ mf, CallDesc* desc,
-                                                const TreeNode* __restrict__ trees, const int32_t* __restrict__ roots,
-                                                int32_t* last_kid, unsigned long long cond, int set_cond) {
-    __shared__ TreeNode sn[kMaxTreeNodes];
-    const int cnt = min(__ldg(roots + 3), kMaxTreeNodes);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) sn[i] = trees[i];
-    __syncthreads();
-    trees = sn;
-    if (threadIdx.x != 0) return;
-    double f[13];
-    f[0] = (double)mf->m;
-    f[1] = (double)mf->n;
-    f[2] = (double)mf->nnz;
-    f[3] = (double)mf->max_row;
-    f[4] = (double)mf->min_row;
-    f[5] = mf->avg_row;
-    f[6] = mf->relative_range;
-    f[7] = mf->var_nnz_row;
-    f[8] = mf->gini;
-    f[9] = desc->vfeat[0];
-    f[10] = desc->vfeat[1];
-    f[11] = desc->vfeat[2];
-    f[12] = desc->vfeat[3];
-    const int pattern = eval_tree(trees, roots[0], f);  // 0 push, 1 masked pull, 2 pull
-    const int dist = eval_tree(trees, roots[1], f);     // 0 thread, 1 warp, 2 balanced
-    int kid;
-    if (pattern == 2) {
-        kid = ASV_K_PULL_THREAD + dist;
-    } else if (pattern == 1) {
-        kid = ASV_K_MPULL_THREAD + dist;
-    } else {
-        const int wb = eval_tree(trees, roots[2], f);  // 0 atomic, 1 sort, 2 privatised
-        kid = ASV_K_PUSH_THREAD_ATOM + 3 * wb + dist;
-    }
-    if (kid < 0 || kid >= ASV_K_COUNT) kid = ASV_K_PULL_BAL;
-    desc->kid = kid;
-    *last_kid = kid;
-    if (set_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, (unsigned)kid);
-}
-
-void launch_select(asv_matrix_s* H, unsigned long long cond_handle, bool set_cond, cudaStream_t s) {
-    k_select<<<1, 128, 0, s>>>(H->d_mfeat, H->d_desc, H->d_trees, H->d_roots, H->d_last_kid, cond_handle,
-                              set_cond ? 1 : 0);
-}
-
-void default_trees(std::vector<TreeNode>& nodes, int32_t roots[4]) {
+// The compiled-in trees of a value type: the Boolean table for ASV_BOOL, the
+// FP32 table for every arithmetic type.
+void default_trees(int32_t dtype, std::vector<TreeNode>& nodes, int32_t roots[kRootsLen]) {
+    const bool b = dtype == ASV_BOOL;
+    const int cnt = b ? kTreeNodesBool : kTreeNodesF32;
+    const double (*tab)[5] = b ? kTreesBool : kTreesF32;
+    const int* rt = b ? kTreeRootsBool : kTreeRootsF32;
     nodes.clear();
-    for (int i = 0; i < kDefaultTreeNodes; ++i) {
+    for (int i = 0; i < cnt; ++i) {
         TreeNode t;
-        t.feature = (int32_t)kDefaultTrees[i][0];
-        t.thr = kDefaultTrees[i][1];
-        t.left = (int32_t)kDefaultTrees[i][2];
-        t.right = (int32_t)kDefaultTrees[i][3];
-        t.leaf = (int32_t)kDefaultTrees[i][4];
+        t.feature = (int32_t)tab[i][0];
+        t.thr = tab[i][1];
+        t.left = (int32_t)tab[i][2];
+        t.right = (int32_t)tab[i][3];
+        t.leaf = (int32_t)tab[i][4];
         nodes.push_back(t);
     }
-    for (int i = 0; i < 3; ++i) roots[i] = kDefaultTreeRoots[i];
-    roots[3] = (int32_t)nodes.size();
+    for (int i = 0; i < kRootsLen - 1; ++i) roots[i] = rt[i];
+    roots[kRootsLen - 1] = cnt;
 }
 
 }  // namespace asv

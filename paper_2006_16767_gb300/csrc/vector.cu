@@ -37,9 +37,10 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
 template <int B>
 __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long* counters,
                                               unsigned int* ticket, CallDesc* desc, const DescInit& di, int64_t n,
-                                              int64_t nnz, int32_t* status) {
+                                              int64_t nnz, int32_t* status, const SelectArg& sa) {
     __shared__ unsigned long long sm[B / 32 + 1];
     __shared__ bool last;
+    __shared__ TreeNode sn[kMaxTreeNodes];
     cx = block_reduce_sum<B>(cx, sm);
     cs = block_reduce_sum<B>(cs, sm);
     if (threadIdx.x == 0) {
@@ -63,6 +64,12 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
         publish_desc(desc, di, nx, ns, n, nnz);
         __threadfence();
         atomicExch(ticket, 0u);
+    }
+    // the last block also walks the selector's trees (Sec. VI-B), so the
+    // choice is ready when the feature pass ends
+    if (last && sa.enabled) {
+        __syncthreads();
+        run_selector(sa, desc, sn);
     }
 }
 
@@ -89,10 +96,12 @@ __device__ __forceinline__ void load4_nz(const T* __restrict__ x, int64_t j, boo
 // the four elements 4l..4l+3; the nibbles of eight lanes form one word. The
 // degree of every nonzero column comes from colptr; block totals go to the
 // ticketed counters.
-template <class T, int B, bool VEC>
+template <class T, int B>
 __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64_t n, const int32_t* __restrict__ colptr,
                                                   uint32_t* xbits, unsigned long long* counters, unsigned int* ticket,
-                                                  CallDesc* desc, DescInit di, int64_t nnz, int32_t* status) {
+                                                  CallDesc* desc, DescInit di, int64_t nnz, int32_t* status,
+                                                  SelectArg sa) {
+    const bool VEC = ((uintptr_t)x & 15) == 0;
     const int lane = threadIdx.x & 31;
     const int64_t nwords = (n + 31) >> 5;
     const int64_t nsuper = (n + 127) >> 7;
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
             }
         }
     }
-    finish_counts<B>(cx, cs, counters, ticket, desc, di, n, nnz, status);
+    finish_counts<B>(cx, cs, counters, ticket, desc, di, n, nnz, status, sa);
 }
 
 // Sparse x: nnz_s = sum of the listed columns' lengths.
@@ -141,7 +150,7 @@ template <int B>
 __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ nnz_x_dev, const int32_t* __restrict__ xidx,
                                                    const int32_t* __restrict__ colptr, unsigned long long* counters,
                                                    unsigned int* ticket, CallDesc* desc, DescInit di, int64_t n,
-                                                   int64_t nnz, int32_t* status) {
+                                                   int64_t nnz, int32_t* status, SelectArg sa) {
     int64_t nx = *nnz_x_dev;
     if (nx < 0) nx = 0;
     if (nx > n) nx = n + 1;  // reported and clamped when the totals are published
@@ -151,7 +160,7 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
         cs += (unsigned long long)(__ldg(colptr + j + 1) - __ldg(colptr + j));
     }
     finish_counts<B>(blockIdx.x == 0 && threadIdx.x == 0 ? (unsigned long long)nx : 0ull, cs, counters, ticket, desc,
-                     di, n, nnz, status);
+                     di, n, nnz, status, sa);
 }
 
 static int feat_grid(asv_matrix_s* H, int64_t items) {
@@ -160,33 +169,53 @@ static int feat_grid(asv_matrix_s* H, int64_t items) {
 }
 
 template <class T>
-static void feat_dense_dtype(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
-    const int64_t nsuper = (H->n + 127) / 128;
-    const int g = (int)max((int64_t)1, min((nsuper + 7) / 8, (int64_t)H->num_sms * 32));
-    const T* x = (const T*)di.user_x_dense;
-    const bool vec = ((uintptr_t)x % 16) == 0;
-    if (vec)
-        k_feat_dense<T, 256, true><<<g, 256, 0, s>>>(x, H->n, H->colptr, H->ws.xbits_dense, H->ws.counters,
-                                                     H->ws.ticket, H->d_desc, di, H->nnz, H->ws.status);
-    else
-        k_feat_dense<T, 256, false><<<g, 256, 0, s>>>(x, H->n, H->colptr, H->ws.xbits_dense, H->ws.counters,
-                                                      H->ws.ticket, H->d_desc, di, H->nnz, H->ws.status);
+static void* feat_dense_func() {
+    return (void*)k_feat_dense<T, 256>;
 }
 
-void launch_features_dense(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
-    switch (H->dtype) {
-        case ASV_F32: feat_dense_dtype<float>(H, di, s); break;
-        case ASV_F64: feat_dense_dtype<double>(H, di, s); break;
-        case ASV_I32: feat_dense_dtype<int32_t>(H, di, s); break;
-        case ASV_BOOL: feat_dense_dtype<bool8>(H, di, s); break;
+// Fills the launch of this call's feature pass (function, grid, argument
+// values and the pointer array), for a direct launch or for updating the
+// feature node of the selector-driven graph.
+void feature_launch(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, FeatLaunch& fl) {
+    fl.di = di;
+    fl.sa = sa;
+    fl.colptr = H->colptr;
+    fl.counters = H->ws.counters;
+    fl.ticket = H->ws.ticket;
+    fl.desc = H->d_desc;
+    fl.n = H->n;
+    fl.nnz = H->nnz;
+    fl.status = H->ws.status;
+    fl.block = dim3(256);
+    if (!di.x_sparse) {
+        switch (H->dtype) {
+            case ASV_F32: fl.func = feat_dense_func<float>(); break;
+            case ASV_F64: fl.func = feat_dense_func<double>(); break;
+            case ASV_I32: fl.func = feat_dense_func<int32_t>(); break;
+            default: fl.func = feat_dense_func<bool8>(); break;
+        }
+        const int64_t nsuper = (H->n + 127) / 128;
+        fl.grid = dim3((unsigned)max((int64_t)1, min((nsuper + 7) / 8, (int64_t)H->num_sms * 32)));
+        fl.xptr = di.user_x_dense;
+        fl.xbits = H->ws.xbits_dense;
+        void* a[11] = {&fl.xptr, &fl.n, &fl.colptr, &fl.xbits, &fl.counters, &fl.ticket, &fl.desc, &fl.di,
+                       &fl.nnz, &fl.status, &fl.sa};
+        for (int i = 0; i < 11; ++i) fl.args[i] = a[i];
+    } else {
+        fl.func = (void*)k_feat_sparse<256>;
+        fl.grid = dim3((unsigned)feat_grid(H, H->n));
+        fl.nnz_x_dev = di.user_nnz_x;
+        fl.xidx = di.user_xidx;
+        void* a[11] = {&fl.nnz_x_dev, &fl.xidx, &fl.colptr, &fl.counters, &fl.ticket, &fl.desc, &fl.di,
+                       &fl.n, &fl.nnz, &fl.status, &fl.sa};
+        for (int i = 0; i < 11; ++i) fl.args[i] = a[i];
     }
 }
 
-void launch_features_sparse(asv_matrix_s* H, const DescInit& di, cudaStream_t s) {
-    // the list length lives on the device, so size the grid for the worst case
-    const int g = feat_grid(H, H->n);
-    k_feat_sparse<256><<<g, 256, 0, s>>>(di.user_nnz_x, di.user_xidx, H->colptr, H->ws.counters, H->ws.ticket,
-                                         H->d_desc, di, H->n, H->nnz, H->ws.status);
+void launch_features(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, cudaStream_t s) {
+    FeatLaunch fl;
+    feature_launch(H, di, sa, fl);
+    cudaLaunchKernel(fl.func, fl.grid, fl.block, fl.args, 0, s);
 }
 
 // ---------------------------------------------------------------- sparse x -> dense x + bitmap

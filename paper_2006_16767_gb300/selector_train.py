@@ -1,0 +1,310 @@
+"""Training of the kernel selector for the GPU at hand (Sec. V-B).
+
+The paper labels every (matrix, vector) sample with the fastest candidate,
+trains three decision trees -- computing pattern, workload distribution,
+write-back -- on the Table 1 features, and retrains per hardware because the
+switch points move between GPUs. This module does the same on synthetic
+matrices:
+
+  collect(path)   on a GPU: for every corpus matrix, value type, call format
+                  (x dense or a list; y dense or a list) and x density, time
+                  every candidate through the C ABI and append one JSON row
+                  {features, times} to `path`;
+  fit(path)       on any host with scikit-learn: grid-searched CART per
+                  (value type, format, model) as in Sec. V-B, labels as in
+                  the design notes (pattern of the fastest kernel; fastest
+                  distribution inside that pattern; fastest write-back inside
+                  push at the best push distribution; ties within 2% go to the
+                  lower kernel id);
+  emit(trees)     the C table compiled into the library (csrc/trees_default.h);
+  regret(path, trees)  selected-kernel time over best-candidate time.
+
+Usage:  python -m paper_2006_16767_gb300.selector_train collect out.jsonl
+        python -m paper_2006_16767_gb300.selector_train fit out.jsonl
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+FEATURES = ("m", "n", "nnz", "max_row", "min_row", "avg_row", "relative_range", "var_nnz_row", "gini",
+            "nnz_x", "x_sparsity", "nnz_s", "m_sparsity")
+# Table 1: model 1 sees every feature, model 2 the matrix ones, model 3 the sizes and vector ones
+MODEL_FEATURES = (tuple(range(13)), tuple(range(9)), (0, 1, 2, 9, 10, 11, 12))
+NK = 15
+TIE = 1.02
+
+
+def kernel_parts(k):
+    """(pattern, distribution, write-back) of kernel id k; pattern 0 push, 1 masked pull, 2 pull."""
+    if k < 3:
+        return 2, k, 0
+    if k < 6:
+        return 1, k - 3, 0
+    q = k - 6
+    return 0, q % 3, q // 3
+
+
+def kernel_id(pattern, dist, wb):
+    if pattern == 2:
+        return dist
+    if pattern == 1:
+        return 3 + dist
+    return 6 + 3 * wb + dist
+
+
+# ------------------------------------------------------------------ corpus
+def corpus(scale=1.0):
+    """Synthetic training matrices (none of them is a benchmark matrix)."""
+    import gen
+    s = 7919
+    items = []
+    for g in (64, 128, 192):
+        items.append((f"stencil27_{g}", lambda g=g: gen.stencil27(g, s + g)[:3]))
+    for g in (512, 2048):
+        items.append((f"laplace2d_{g}", lambda g=g: gen.laplace2d(g)))
+    for sc, ef in ((16, 16), (18, 8), (20, 16), (21, 16)):
+        items.append((f"rmat_{sc}_{ef}", lambda sc=sc, ef=ef: rmat_vals(sc, ef, s + sc)))
+    items.append(("zipf_200k", lambda: gen.lognormal_zipf(200_000, 131_072, np.log(40), 1.0, 1.2, s + 1)))
+    items.append(("zipf_1m_64k", lambda: gen.lognormal_zipf(1_000_000, 65_536, np.log(20), 1.0, 1.1, s + 2)))
+    items.append(("bern_8192_1pct", lambda: gen.bernoulli(8192, 8192, 0.01, 0.02, s + 3)))
+    items.append(("bern_4096_5pct", lambda: gen.bernoulli(4096, 4096, 0.05, 0.02, s + 4)))
+    return items
+
+
+def rmat_vals(scale, ef, seed):
+    import gen
+    rp, c = gen.rmat(scale, ef, seed)
+    return rp, c, gen.uniform(len(c), 0.5, 1.5, seed, 3, np.float32)
+
+
+def densities(n):
+    rhos = sorted(set([10.0 ** e for e in np.arange(-6, 0.01, 0.5)] + [0.2, 0.4, 0.6, 0.8]))
+    out = []
+    for r in rhos:
+        k = int(round(r * n))
+        if k >= 1 and (not out or k > out[-1][1]):
+            out.append((r, min(k, n)))
+    return out
+
+
+# ------------------------------------------------------------------ collection (GPU)
+def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
+    import torch
+
+    import gen
+    import paper_2006_16767_gb300 as asv
+    dev = torch.device("cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    t_start = time.time()
+    out = open(path, "a")
+    for name, make in corpus():
+        if time.time() - t_start > budget_s:
+            break
+        rp, c, v = make()
+        m, n = len(rp) - 1, int(c.max()) + 1 if len(c) else 1
+        n = max(n, {"zipf_200k": 131_072, "zipf_1m_64k": 65_536}.get(name, n))
+        rpt, ct = torch.from_numpy(rp).to(dev), torch.from_numpy(c).to(dev)
+        for dt in dtypes:
+            vt = torch.from_numpy(np.asarray(v, np.float32)).to(dev) if dt == "f32" else None
+            A = asv.Matrix(m, n, rpt, ct, vt)
+            tdt = A.tdtype
+            y = torch.empty(m, dtype=tdt, device=dev)
+            yidx = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+            yval = torch.empty(max(m, 1), dtype=tdt, device=dev)
+            nnz_y = torch.zeros(1, dtype=torch.int64, device=dev)
+            for rho, k in densities(n):
+                if time.time() - t_start > budget_s:
+                    break
+                idx = gen.sample_positions(n, k, seed=hash((name, k)) & 0xFFFF, stream=1)
+                it = torch.from_numpy(idx).to(dev)
+                if dt == "f32":
+                    xv = torch.from_numpy(gen.uniform(len(idx), -1, 1, 5, 2, np.float32)).to(dev)
+                    xd = torch.zeros(n, dtype=tdt, device=dev)
+                    xd[it.long()] = xv
+                else:
+                    xv = None
+                    xd = torch.zeros(n, dtype=tdt, device=dev)
+                    xd[it.long()] = 1
+                cnt = torch.tensor([len(idx)], dtype=torch.int64, device=dev)
+                for xs in (0, 1):
+                    kid, vf = asv.asv_select(A.handle, cnt, it, xv, None if xs else xd)
+                    feats = [float(A.features()[f]) for f in FEATURES[:9]] + [
+                        float(vf["nnz_x"]), float(vf["x_sparsity"]), float(vf["nnz_s"]), float(vf["m_sparsity"])]
+                    for om in (0, 1):
+                        times = [None] * NK
+                        best = float("inf")
+                        for kk in range(NK):
+                            def call():
+                                if om == 0:
+                                    asv.asv_spmspv(A.handle, cnt, it, xv, None if xs else xd, 0, y, kernel=kk)
+                                else:
+                                    asv.asv_spmspv(A.handle, cnt, it, xv, None if xs else xd, 1, None, yidx,
+                                                   yval, nnz_y, m, kernel=kk)
+                            call()
+                            ts = []
+                            for r in range(reps):
+                                flush.zero_()
+                                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                                e0.record()
+                                call()
+                                e1.record()
+                                torch.cuda.synchronize()
+                                ts.append(e0.elapsed_time(e1))
+                                if ts[-1] > 30 * best:
+                                    break
+                            times[kk] = float(np.median(ts))
+                            best = min(best, times[kk])
+                        out.write(json.dumps({"matrix": name, "dtype": dt, "fmt": 2 * xs + om, "rho": rho,
+                                              "feat": feats, "t": times, "auto": kid}) + "\n")
+                out.flush()
+            A.close()
+    out.close()
+
+
+# ------------------------------------------------------------------ labels and fitting (host)
+def labels(times):
+    """Per-model labels of one sample (Sec. V-B readings)."""
+    t = np.asarray([x if x is not None else np.inf for x in times])
+
+    def pick(cands):
+        best = min(t[k] for k in cands)
+        for k in sorted(cands):
+            if t[k] <= best * TIE:
+                return k
+        return min(cands, key=lambda k: t[k])
+
+    kbest = pick(range(NK))
+    pat = kernel_parts(kbest)[0]
+    in_pat = [k for k in range(NK) if kernel_parts(k)[0] == pat]
+    dist = kernel_parts(pick(in_pat))[1]
+    push_best = {d: min(t[kernel_id(0, d, w)] for w in range(3)) for d in range(3)}
+    dpush = min(range(3), key=lambda d: (push_best[d], d))
+    wb = kernel_parts(pick([kernel_id(0, dpush, w) for w in range(3)]))[2]
+    return pat, dist, wb
+
+
+def load(path):
+    rows = [json.loads(l) for l in open(path) if l.strip()]
+    return [r for r in rows if all(x is not None for x in r["t"])]
+
+
+def fit(path, seed=0):
+    from sklearn.model_selection import GridSearchCV, train_test_split
+    from sklearn.tree import DecisionTreeClassifier
+    rows = load(path)
+    result = {}
+    report = {}
+    for dt in sorted({r["dtype"] for r in rows}):
+        nodes, roots = [], []
+        for fmt in range(4):
+            sub = [r for r in rows if r["dtype"] == dt and r["fmt"] == fmt]
+            X = np.asarray([r["feat"] for r in sub], np.float64)
+            Y = np.asarray([labels(r["t"]) for r in sub], np.int64)
+            for model in range(3):
+                cols = MODEL_FEATURES[model]
+                y = Y[:, model]
+                Xm = X[:, cols]
+                if len(set(y.tolist())) < 2 or len(sub) < 10:
+                    nodes_m = [(-1, 0.0, 0, 0, int(np.bincount(y).argmax()) if len(y) else 0)]
+                    acc = 1.0
+                else:
+                    Xtr, Xte, ytr, yte = train_test_split(Xm, y, test_size=0.3, random_state=seed, stratify=None)
+                    gs = GridSearchCV(DecisionTreeClassifier(random_state=seed),
+                                      {"max_depth": list(range(1, 11)), "class_weight": [None, "balanced"]},
+                                      cv=min(5, max(2, len(ytr) // 5)))
+                    gs.fit(Xtr, ytr)
+                    acc = float(gs.score(Xte, yte))
+                    clf = DecisionTreeClassifier(random_state=seed, **gs.best_params_).fit(Xm, y)
+                    nodes_m = export_tree(clf, cols)
+                base = len(nodes)
+                for (f, thr, l, r, leaf) in nodes_m:
+                    nodes.append((f, thr, l + base if f >= 0 else 0, r + base if f >= 0 else 0, leaf))
+                roots.append(base)
+                report[f"{dt}/fmt{fmt}/model{model + 1}"] = {"test_accuracy": round(acc, 4), "samples": len(sub),
+                                                             "nodes": len(nodes_m)}
+        result[dt] = {"nodes": nodes, "roots": roots}
+    return result, report
+
+
+def export_tree(clf, cols):
+    t = clf.tree_
+    out = []
+    for i in range(t.node_count):
+        if t.children_left[i] == -1:
+            out.append((-1, 0.0, 0, 0, int(clf.classes_[int(np.argmax(t.value[i][0]))])))
+        else:
+            out.append((int(cols[t.feature[i]]), float(t.threshold[i]), int(t.children_left[i]),
+                        int(t.children_right[i]), 0))
+    return out
+
+
+def predict(trees, dt, fmt, feat):
+    T = trees[dt if dt in trees else "f32"]
+    nodes, roots = T["nodes"], T["roots"]
+
+    def walk(root):
+        i = root
+        while nodes[i][0] >= 0:
+            f, thr, l, r, _ = nodes[i]
+            i = l if feat[f] <= thr else r
+        return nodes[i][4]
+    pat = walk(roots[3 * fmt])
+    dist = walk(roots[3 * fmt + 1])
+    wb = walk(roots[3 * fmt + 2]) if pat == 0 else 0
+    return kernel_id(pat, dist, wb)
+
+
+def regret(path, trees):
+    rows = load(path)
+    out = {}
+    for r in rows:
+        k = predict(trees, r["dtype"], r["fmt"], r["feat"])
+        best = min(r["t"])
+        out.setdefault((r["dtype"], r["fmt"]), []).append(r["t"][k] / best)
+    return {f"{dt}/fmt{f}": {"mean": round(float(np.mean(v)), 4), "p90": round(float(np.percentile(v, 90)), 4),
+                             "max": round(float(np.max(v)), 4), "samples": len(v)}
+            for (dt, f), v in sorted(out.items())}
+
+
+def emit(trees, path=None):
+    """C header with one node table and 12 roots per value type."""
+    path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "trees_default.h")
+    lines = ["// Decision trees compiled into the library as its default selector,",
+             "// trained on this GPU by paper_2006_16767_gb300/selector_train.py (do not edit).",
+             "// Records: {feature, threshold, left, right, leaf_class}; feature < 0 = leaf.",
+             "// Feature ids: 0 m, 1 n, 2 nnz, 3 max_row, 4 min_row, 5 avg_row,",
+             "// 6 relative_range, 7 var_nnz_row, 8 gini, 9 nnz_x, 10 x_sparsity,",
+             "// 11 nnz_s, 12 m_sparsity. Roots: (pattern, distribution, write-back) for",
+             "// (x dense, y dense), (x dense, y list), (x list, y dense), (x list, y list).",
+             "#pragma once", "", "namespace asv {", ""]
+    for dt in ("f32", "bool"):
+        T = trees.get(dt) or trees["f32"]
+        name = "F32" if dt == "f32" else "Bool"
+        lines.append(f"static const int kTreeNodes{name} = {len(T['nodes'])};")
+        lines.append(f"static const double kTrees{name}[][5] = {{")
+        for (f, thr, l, r, leaf) in T["nodes"]:
+            lines.append(f"    {{{f}, {thr!r}, {l}, {r}, {leaf}}},")
+        lines.append("};")
+        lines.append(f"static const int kTreeRoots{name}[12] = {{{', '.join(str(x) for x in T['roots'])}}};")
+        lines.append("")
+    lines += ["}  // namespace asv", ""]
+    open(path, "w").write("\n".join(lines))
+    return path
+
+
+if __name__ == "__main__":
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    cmd = sys.argv[1]
+    if cmd == "collect":
+        collect(sys.argv[2], budget_s=float(sys.argv[3]) if len(sys.argv) > 3 else 900.0)
+    elif cmd == "fit":
+        trees, rep = fit(sys.argv[2])
+        print(json.dumps(rep, indent=1))
+        print(json.dumps(regret(sys.argv[2], trees), indent=1))
+        if "--emit" in sys.argv:
+            print(emit(trees))

@@ -271,3 +271,26 @@ def test_spmv_entry_point_and_copy_flag():
     for k in ["auto"] + ALL_K:
         y = A.spmv(to_dev(x), kernel=k)
         assert_rows_close(y.cpu().numpy(), y_ref, s, "f32", f"spmv {k}")
+
+
+def test_set_trees_drives_the_switch_branch():
+    name, m, n, rp, c, v = mat_random(np.float32)
+    A = make(m, n, rp, c, v)
+    x = gen.uniform(n, -1, 1, seed=12).astype(np.float32)
+    y_ref, s = oracle.csr_pull(rp, c, v.astype(np.float64), x.astype(np.float64))
+    for pat, dist, wb in [(0, 2, 1), (1, 0, 0), (2, 1, 0), (0, 0, 2), (0, 1, 0)]:
+        nodes = [(-1, 0, 0, 0, pat), (-1, 0, 0, 0, dist), (-1, 0, 0, 0, wb)]
+        A.set_trees(nodes, [0, 1, 2] * 4)
+        want = {2: dist, 1: 3 + dist, 0: 6 + 3 * wb + dist}[pat]
+        for dense_in in (True, False):
+            if dense_in:
+                y = A.spmspv(x_dense=to_dev(x))
+            else:
+                idx = np.flatnonzero(x).astype(np.int32)
+                y = A.spmspv(xidx=to_dev(idx), xval=to_dev(x[idx]))
+            assert A.last_kernel() == want
+            assert_rows_close(y.cpu().numpy(), y_ref, s, "f32", f"trees -> {asv.KERNELS[want]}")
+        kid, _ = A.select(x_dense=to_dev(x))
+        assert kid == want
+    with pytest.raises(asv.AsvError):
+        A.set_trees([(0, 1.0, 5, 6, 0)], [0] * 12)  # child index out of range
