@@ -270,6 +270,109 @@ class Rmat22:
                 "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "seed": 20061678}
 
 
+def _time(torch, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_batched(asv, torch, dev, reps=3):
+    """4096 Zipf-row vectors through a 1M x 131072 lognormal/Zipf matrix: one
+    batched call versus 4096 plain selector-driven calls into the same Y."""
+    import gen
+    m, n, B = 1_000_000, 131_072, 4096
+    rp, c, v = gen.lognormal_zipf(m, n, np.log(40), 1.0, 1.2, gen.config_seed(3))
+    xrp_all, xc_all, xv_all = gen.lognormal_zipf(65_536, n, np.log(40), 1.0, 1.2, gen.config_seed(3) + 100)
+    pick = gen.randint(B, 65_536, gen.config_seed(3), 1)
+    lens = (xrp_all[pick + 1] - xrp_all[pick]).astype(np.int64)
+    xptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    xc = np.concatenate([xc_all[xrp_all[p]:xrp_all[p + 1]] for p in pick]).astype(np.int32)
+    xv = np.concatenate([xv_all[xrp_all[p]:xrp_all[p + 1]] for p in pick]).astype(np.float32)
+    A = asv.Matrix(m, n, torch.from_numpy(rp).to(dev), torch.from_numpy(c).to(dev), torch.from_numpy(v).to(dev))
+    colptr_nnz = np.bincount(c, minlength=n)
+    nnz_s = int(colptr_nnz[xc].sum())
+    d_ptr, d_idx, d_val = (torch.from_numpy(a).to(dev) for a in (xptr, xc, xv))
+    Y = torch.empty((B, m), dtype=torch.float32, device=dev)
+    tune = A.autotune_batched(d_ptr, d_idx, d_val)
+    A.spmspv_batched(d_ptr, d_idx, d_val, Y=Y)
+    t_b = _time(torch, lambda: A.spmspv_batched(d_ptr, d_idx, d_val, Y=Y), reps)
+    Yl = torch.empty_like(Y)
+    cnts = [torch.tensor([int(lens[b])], dtype=torch.int64, device=dev) for b in range(B)]
+    slices = [(d_idx[xptr[b]:xptr[b + 1]], d_val[xptr[b]:xptr[b + 1]]) for b in range(B)]
+
+    def looped():
+        for b in range(B):
+            asv.asv_spmspv(A.handle, cnts[b], slices[b][0], slices[b][1], None, asv.ASV_OUT_DENSE, Yl[b])
+    looped()
+    t_l = _time(torch, looped, 1)
+    diff = float(((Y - Yl).abs().max() / Yl.abs().max().clamp_min(1e-30)).item())
+    ybytes = B * m * 4
+    abytes = (m + 1) * 4 + len(c) * 8
+    out = {"workload": "zipf 1M x 131072 (lognormal ln40/1.0, Zipf 1.2), 4096 vectors", "nnz": len(c),
+           "entries": int(xptr[-1]), "multiply_adds": nnz_s, "tune": list(tune),
+           "batched_ms": round(t_b, 3), "looped_ms": round(t_l, 3), "speedup_vs_looped": round(t_l / t_b, 2),
+           "batched_GBs": round((abytes + ybytes + xptr[-1] * 8) / (t_b * 1e-3) / 1e9, 1),
+           "batched_Gmadds": round(nnz_s / (t_b * 1e-3) / 1e9, 1),
+           "max_rel_diff_vs_looped": diff}
+    del Y, Yl, A
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_backward(asv, torch, dev, reps=5):
+    """16384^2 5%-dense layer, 64 activation vectors (5..50% dense): batched
+    forward + fused backward versus 64 plain calls of each."""
+    import gen
+    m = n = 16384
+    B = 64
+    rp, c, v = gen.bernoulli(m, n, 0.05, 0.02, gen.config_seed(4))
+    dens = gen.uniform(B, 0.05, 0.5, gen.config_seed(4), 1)
+    X = gen.halfnormal(B * n, 1.0, gen.config_seed(4), 2).reshape(B, n)
+    X = np.where(gen.uniform(B * n, 0, 1, gen.config_seed(4), 3).reshape(B, n) < dens[:, None], X, 0).astype(np.float32)
+    dY = gen.uniform(B * m, -1, 1, gen.config_seed(4), 4, np.float32).reshape(B, m)
+    A = asv.Matrix(m, n, torch.from_numpy(rp).to(dev), torch.from_numpy(c).to(dev), torch.from_numpy(v).to(dev))
+    Xd, dYd = torch.from_numpy(X).to(dev), torch.from_numpy(dY).to(dev)
+    Y = torch.empty((B, m), dtype=torch.float32, device=dev)
+    dX = torch.empty((B, n), dtype=torch.float32, device=dev)
+    dA = torch.empty(len(c), dtype=torch.float32, device=dev)
+    A.autotune_batched(X_dense=Xd)
+    t_fb = _time(torch, lambda: A.spmspv_batched(X_dense=Xd, Y=Y), reps)
+    t_bb = _time(torch, lambda: asv.asv_spmspv_backward(A.handle, B, Xd, dYd, dX, dA), reps)
+    Yl = torch.empty_like(Y)
+    dXl = torch.empty_like(dX)
+    dAl = torch.empty_like(dA)
+    dA1 = torch.empty_like(dA)
+
+    def fwd_loop():
+        for b in range(B):
+            asv.asv_spmspv(A.handle, None, None, None, Xd[b], asv.ASV_OUT_DENSE, Yl[b])
+
+    def bwd_loop():
+        dAl.zero_()
+        for b in range(B):
+            asv.asv_spmspv_backward(A.handle, 1, Xd[b], dYd[b], dXl[b], dA1)
+            dAl.add_(dA1)
+    fwd_loop()
+    bwd_loop()
+    t_fl = _time(torch, fwd_loop, 2)
+    t_bl = _time(torch, bwd_loop, 2)
+    rel = lambda a, b: float(((a - b).abs().max() / b.abs().max().clamp_min(1e-30)).item())
+    out = {"workload": "16384^2 5% N(0,0.02) layer, 64 vectors 5-50% dense", "nnz": len(c),
+           "forward_batched_ms": round(t_fb, 3), "forward_looped_ms": round(t_fl, 3),
+           "forward_speedup": round(t_fl / t_fb, 2),
+           "backward_fused_ms": round(t_bb, 3), "backward_looped_ms": round(t_bl, 3),
+           "backward_speedup": round(t_bl / t_bb, 2),
+           "max_rel_diff_vs_looped": {"y": rel(Y, Yl), "dx": rel(dX, dXl), "dA": rel(dA, dAl)}}
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_cpu_oracle(W, max_bfs_calls, reps=1):
     """Times the oracle on a bounded sample; returns (bytes, seconds, sample text)."""
     import oracle
@@ -302,6 +405,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and backward sections")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -411,6 +515,9 @@ def main():
            "gpu_launches": int(args.steps * sum(c["launches"] for c in W.calls)),
            "clocks": clk, "wall_s_timed": round(wall, 3),
            "selected": {asv.KERNELS[k[1]] + ":" + k[0]: v["n"] // args.steps for k, v in per_k.items()}}
+    if not args.no_extra:
+        out["batched"] = bench_batched(asv, torch, dev)
+        out["backward"] = bench_backward(asv, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b, t, sample = run_cpu_oracle(W, max_bfs_calls=24)
         out["cpu_baseline"] = {"value": round(b / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",

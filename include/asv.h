@@ -142,6 +142,13 @@ asv_status asv_matrix_arrays(asv_matrix A, const int32_t** d_rowptr, const int32
 asv_status asv_matrix_copy_csc(asv_matrix A, int32_t* d_colptr, int32_t* d_rowidx, void* d_val_csc,
                                int32_t* d_perm, void* stream);
 
+/* The stored values changed (same pattern): refresh the handle's CSC copy
+ * of them. With d_val NULL, or equal to the array a borrowed handle reads,
+ * the current CSR values are re-gathered; a handle created with ASV_COPY
+ * first copies d_val[nnz] into its own array. Not for ASV_BOOL handles or
+ * handles created without values (ASV_ERR_UNSUPPORTED). Enqueued on `stream`. */
+asv_status asv_matrix_update_values(asv_matrix A, const void* d_val, void* stream);
+
 /* ---------------------------------------------------------------- products */
 
 /* y = A x with x dense (d_x[n]) and y dense (d_y[m]), overwritten
@@ -189,6 +196,48 @@ asv_status asv_last_kernel(asv_matrix A, int32_t* h_kernel, void* stream);
  * entries. Uses the handle's workspaces (x has length A's n). */
 asv_status asv_compact(asv_matrix A, const void* d_x_dense, int32_t* d_idx, void* d_val,
                        int64_t* d_count, void* stream);
+
+/* ---------------------------------------------------------------- batched */
+
+/* Tiling of the batched product: rows of A per work item (4, 8 or 16) and
+ * vectors per group (rows * vectors * 4 bytes of shared memory, <= 200 KB). */
+typedef struct {
+    int32_t rows_per_tile;
+    int32_t vectors_per_group;
+} asv_tune;
+
+/* Y[b,:] = A x_b for B vectors at once (FP32 handles; a batched form of the
+ * SpMSpV of Sec. II). The batch is a CSR of vectors -- d_xptr[B+1] device
+ * int64 offsets (relative to d_xptr[0]), d_xidx column ids in [0, n),
+ * distinct within a vector, d_xval values (NULL = ones) -- or, when
+ * d_X_dense is not NULL, a dense row-major [B][n] array whose nonzeros are
+ * taken. d_Y is a dense row-major [B][m] output, fully overwritten. max_entries
+ * bounds the total number of listed entries (ignored for dense input); a
+ * batch with more entries latches ASV_ERR_CAPACITY. `tune` may be NULL (use
+ * the handle's setting, see asv_autotune_batched). One call is one CUDA-graph
+ * launch of the captured pipeline (regroup by column with a radix sort, then
+ * a persistent kernel over row-tile x vector-group work items); the first call
+ * with a new B or tiling, or one that needs larger workspaces, allocates and
+ * captures, so it should not itself be inside a stream capture. */
+asv_status asv_spmspv_batched(asv_matrix A, int32_t B, int64_t max_entries, const int64_t* d_xptr,
+                              const int32_t* d_xidx, const void* d_xval, const void* d_X_dense,
+                              void* d_Y, const asv_tune* tune, void* stream);
+
+/* Times the candidate tilings on this batch (same arguments as
+ * asv_spmspv_batched), keeps the fastest in the handle and returns it in
+ * *h_best (may be NULL). With cache_path, a line "<gpu>|<matrix>|B=..\tR\tGB"
+ * is read if present (no timing) or appended. Synchronises `stream`. */
+asv_status asv_autotune_batched(asv_matrix A, int32_t B, int64_t max_entries, const int64_t* d_xptr,
+                                const int32_t* d_xidx, const void* d_xval, const void* d_X_dense,
+                                void* d_Y, const char* cache_path, asv_tune* h_best, void* stream);
+
+/* Backward pass of Y[b,:] = A x_b (FP32 handles, 1 <= B <= 128): given dense
+ * row-major d_dY[B][m] (and d_X[B][n], needed for dA), writes
+ * d_dX[B][n] = dY A (dx_b = A^T dy_b, read through the CSC view) and
+ * d_dA[nnz] (CSR order) with dA_k = sum_b dy_b[row(k)] * x_b[col(k)], the
+ * gradient of the stored values on A's pattern. Either output may be NULL. */
+asv_status asv_spmspv_backward(asv_matrix A, int32_t B, const void* d_X, const void* d_dY, void* d_dX,
+                               void* d_dA, void* stream);
 
 /* ---------------------------------------------------------------- selector */
 

@@ -49,6 +49,10 @@ class AsvError(RuntimeError):
                          f"cuda error {lib().asv_last_cuda_error()})")
 
 
+class AsvTune(ctypes.Structure):
+    _fields_ = [("rows_per_tile", ctypes.c_int32), ("vectors_per_group", ctypes.c_int32)]
+
+
 class _MFeat(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("max_row", ctypes.c_int64), ("min_row", ctypes.c_int64),
@@ -81,6 +85,10 @@ def lib():
             L.asv_matrix_arrays.argtypes = [vp] + [P(vp)] * 7
             L.asv_matrix_copy_csc.argtypes = [vp, vp, vp, vp, vp, vp]
             L.asv_spmv.argtypes = [vp, vp, vp, i32, vp]
+            L.asv_matrix_update_values.argtypes = [vp, vp, vp]
+            L.asv_spmspv_batched.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, P(AsvTune), vp]
+            L.asv_autotune_batched.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, ctypes.c_char_p, P(AsvTune), vp]
+            L.asv_spmspv_backward.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             L.asv_spmspv.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, i32, vp]
             L.asv_select.argtypes = [vp, vp, vp, vp, vp, P(i32), P(_VFeat), vp]
             L.asv_last_kernel.argtypes = [vp, P(i32), vp]
@@ -94,7 +102,8 @@ def lib():
             for name in ("asv_matrix_create_csr", "asv_matrix_destroy", "asv_matrix_features",
                          "asv_matrix_arrays", "asv_matrix_copy_csc", "asv_spmv", "asv_spmspv", "asv_select", "asv_last_kernel",
                          "asv_compact", "asv_set_trees", "asv_get_status", "asv_last_cuda_error",
-                         "asv_version"):
+                         "asv_version", "asv_matrix_update_values", "asv_spmspv_batched", "asv_autotune_batched",
+                         "asv_spmspv_backward"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -176,6 +185,32 @@ def asv_matrix_arrays(h) -> dict:
 def asv_matrix_copy_csc(h, colptr=None, rowidx=None, val_csc=None, perm=None, stream=None):
     _check(lib().asv_matrix_copy_csc(h, _ptr(colptr), _ptr(rowidx), _ptr(val_csc), _ptr(perm), _stream(stream)),
            "asv_matrix_copy_csc")
+
+
+def asv_matrix_update_values(h, val=None, stream=None):
+    _check(lib().asv_matrix_update_values(h, _ptr(val), _stream(stream)), "asv_matrix_update_values")
+
+
+def asv_spmspv_batched(h, B, max_entries=0, xptr=None, xidx=None, xval=None, X_dense=None, Y=None, tune=None,
+                       stream=None):
+    t = None if tune is None else ctypes.byref(AsvTune(int(tune[0]), int(tune[1])))
+    _check(lib().asv_spmspv_batched(h, int(B), int(max_entries), _ptr(xptr), _ptr(xidx), _ptr(xval), _ptr(X_dense),
+                                    _ptr(Y), t, _stream(stream)), "asv_spmspv_batched")
+
+
+def asv_autotune_batched(h, B, max_entries=0, xptr=None, xidx=None, xval=None, X_dense=None, Y=None,
+                         cache_path=None, stream=None):
+    best = AsvTune()
+    cp = None if cache_path is None else str(cache_path).encode()
+    _check(lib().asv_autotune_batched(h, int(B), int(max_entries), _ptr(xptr), _ptr(xidx), _ptr(xval),
+                                      _ptr(X_dense), _ptr(Y), cp, ctypes.byref(best), _stream(stream)),
+           "asv_autotune_batched")
+    return best.rows_per_tile, best.vectors_per_group
+
+
+def asv_spmspv_backward(h, B, X, dY, dX=None, dA=None, stream=None):
+    _check(lib().asv_spmspv_backward(h, int(B), _ptr(X), _ptr(dY), _ptr(dX), _ptr(dA), _stream(stream)),
+           "asv_spmspv_backward")
 
 
 def asv_spmv(h, x, y, kernel="auto", stream=None):
@@ -303,6 +338,38 @@ class Matrix:
             nnz_x = torch.tensor([xidx.numel()], dtype=torch.int64, device=dev)
         return asv_select(self.handle, nnz_x, xidx, xval, x_dense, stream)
 
+    def update_values(self, val=None, stream=None):
+        asv_matrix_update_values(self.handle, val, stream)
+
+    def spmspv_batched(self, xptr=None, xidx=None, xval=None, X_dense=None, Y=None, tune=None, stream=None):
+        """Y[b,:] = A x_b. The batch is a CSR of vectors (xptr int64[B+1], xidx, xval) or dense [B][n]."""
+        if X_dense is not None:
+            B = X_dense.shape[0]
+            dev = X_dense.device
+        else:
+            B = xptr.numel() - 1
+            dev = xptr.device
+        if Y is None:
+            Y = torch.empty((B, self.m), dtype=torch.float32, device=dev)
+        cap = 0 if xidx is None else xidx.numel()
+        asv_spmspv_batched(self.handle, B, cap, xptr, xidx, xval, X_dense, Y, tune, stream)
+        return Y
+
+    def autotune_batched(self, xptr=None, xidx=None, xval=None, X_dense=None, cache_path=None, stream=None):
+        B = X_dense.shape[0] if X_dense is not None else xptr.numel() - 1
+        dev = (X_dense if X_dense is not None else xptr).device
+        Y = torch.empty((B, self.m), dtype=torch.float32, device=dev)
+        cap = 0 if xidx is None else xidx.numel()
+        return asv_autotune_batched(self.handle, B, cap, xptr, xidx, xval, X_dense, Y, cache_path, stream)
+
+    def backward(self, X, dY, need_dx=True, need_da=True, stream=None):
+        """(dX [B][n] or None, dA [nnz] or None) for Y = X A^T row by row."""
+        B = dY.shape[0]
+        dX = torch.empty((B, self.n), dtype=torch.float32, device=dY.device) if need_dx else None
+        dA = torch.empty(self.nnz, dtype=torch.float32, device=dY.device) if need_da else None
+        asv_spmspv_backward(self.handle, B, X, dY, dX, dA, stream)
+        return dX, dA
+
     def last_kernel(self, stream=None) -> int:
         return asv_last_kernel(self.handle, stream)
 
@@ -311,3 +378,31 @@ class Matrix:
 
     def set_trees(self, nodes, roots, stream=None):
         asv_set_trees(self.handle, nodes, roots, stream)
+
+
+class SpMSpVFunction(torch.autograd.Function):
+    """Differentiable y_b = A x_b for a batch X [B][n] (FP32), A given by its
+    pattern (a Matrix handle) and its stored values `values` [nnz] (CSR order).
+
+    forward:  Y [B][m] through the batched product;
+    backward: dX = dY A (dx_b = A^T dy_b) and dvalues_k = sum_b dy_b[row(k)] x_b[col(k)],
+              the gradient on A's pattern, from one fused pass per view.
+    The handle must read `values` in place (created with ASV_BORROW on it);
+    its CSC copy is refreshed at every forward.
+    """
+
+    @staticmethod
+    def forward(ctx, values, X, A):
+        A.update_values()
+        Xc = X.contiguous()
+        Y = A.spmspv_batched(X_dense=Xc)
+        ctx.save_for_backward(Xc)
+        ctx.A = A
+        return Y
+
+    @staticmethod
+    def backward(ctx, dY):
+        (X,) = ctx.saved_tensors
+        need_dv, need_dx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        dX, dA = ctx.A.backward(X, dY.contiguous(), need_dx=need_dx, need_da=need_dv)
+        return dA, dX, None

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "internal.h"
 
@@ -82,6 +83,7 @@ static void destroy_handle(asv_matrix_s* H) {
             if (H->gexec[a][b]) cudaGraphExecDestroy(H->gexec[a][b]);
             if (H->graph[a][b]) cudaGraphDestroy(H->graph[a][b]);
         }
+    batch_release(H);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
     for (void* p : H->allocs) cudaFree(p);
     delete H;
@@ -132,6 +134,7 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
         H->rowptr = rp;
         H->col = ci;
         H->val = v;
+        H->owns_val = true;
     } else {
         H->rowptr = d_rowptr;
         H->col = d_colidx;
@@ -253,6 +256,18 @@ extern "C" asv_status asv_matrix_copy_csc(asv_matrix A, int32_t* d_colptr, int32
         if (d_val_csc && A->val_csc)
             CK(cudaMemcpyAsync(d_val_csc, A->val_csc, vsize(A->dtype) * A->nnz, cudaMemcpyDeviceToDevice, s));
     }
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_matrix_update_values(asv_matrix A, const void* d_val, void* stream) {
+    if (!A) return ASV_ERR_ARG;
+    if (A->dtype == ASV_BOOL || !A->val) return ASV_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_val && d_val != A->val) {
+        if (!A->owns_val) return ASV_ERR_ARG;  // a borrowed handle reads the caller's array in place
+        if (A->nnz) CK(cudaMemcpyAsync((void*)A->val, d_val, vsize(A->dtype) * A->nnz, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(regather_values(A, s));
     return ASV_OK;
 }
 
@@ -476,6 +491,127 @@ extern "C" asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t
     CK(cudaMemcpyAsync(A->d_trees, nodes.data(), sizeof(TreeNode) * n_nodes, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(A->d_roots, r, sizeof(r), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+    return ASV_OK;
+}
+
+// ---------------------------------------------------------------- batched forms
+static asv_status batched_args(asv_matrix A, int32_t B, int64_t max_entries, const int64_t* d_xptr,
+                               const void* d_X_dense, void* d_Y) {
+    if (!A || B < 0 || !d_Y) return ASV_ERR_ARG;
+    if (A->dtype != ASV_F32) return ASV_ERR_UNSUPPORTED;
+    if (!d_X_dense && (!d_xptr || max_entries < 0)) return ASV_ERR_ARG;
+    if ((int64_t)B * A->m >= ((int64_t)1 << 40)) return ASV_ERR_OVERFLOW;
+    if (d_X_dense && (int64_t)B * A->n >= INT32_MAX) return ASV_ERR_OVERFLOW;
+    if (max_entries >= INT32_MAX) return ASV_ERR_OVERFLOW;
+    return ASV_OK;
+}
+
+static bool tune_ok(const asv_tune& t, int32_t B) {
+    const bool r_ok = t.rows_per_tile == 4 || t.rows_per_tile == 8 || t.rows_per_tile == 16;
+    return r_ok && t.vectors_per_group >= 1 && (int64_t)t.rows_per_tile * t.vectors_per_group * 4 <= 200 * 1024 &&
+           B >= 0;
+}
+
+extern "C" asv_status asv_spmspv_batched(asv_matrix A, int32_t B, int64_t max_entries, const int64_t* d_xptr,
+                                         const int32_t* d_xidx, const void* d_xval, const void* d_X_dense, void* d_Y,
+                                         const asv_tune* tune, void* stream) {
+    asv_status st = batched_args(A, B, max_entries, d_xptr, d_X_dense, d_Y);
+    if (st != ASV_OK) return st;
+    if (B == 0 || A->m == 0) return ASV_OK;
+    asv_tune t{A->tune_R, A->tune_GB};
+    if (tune) t = *tune;
+    if (!tune_ok(t, B)) return ASV_ERR_ARG;
+    t.vectors_per_group = std::min(t.vectors_per_group, B);
+    CK(batched_forward(A, B, max_entries, d_xptr, d_xidx, (const float*)d_xval, (const float*)d_X_dense,
+                       (float*)d_Y, t.rows_per_tile, t.vectors_per_group, (cudaStream_t)stream));
+    return ASV_OK;
+}
+
+static std::string tune_key(asv_matrix A, int32_t B) {
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, A->dev);
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s|m=%lld|n=%lld|nnz=%lld|max_row=%lld|B=%d", p.name, (long long)A->m,
+             (long long)A->n, (long long)A->nnz, (long long)A->h_mfeat.max_row, B);
+    return buf;
+}
+
+extern "C" asv_status asv_autotune_batched(asv_matrix A, int32_t B, int64_t max_entries, const int64_t* d_xptr,
+                                           const int32_t* d_xidx, const void* d_xval, const void* d_X_dense,
+                                           void* d_Y, const char* cache_path, asv_tune* h_best, void* stream) {
+    asv_status st = batched_args(A, B, max_entries, d_xptr, d_X_dense, d_Y);
+    if (st != ASV_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const std::string key = tune_key(A, B);
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[1024];
+            while (fgets(line, sizeof(line), f)) {
+                int r = 0, g = 0;
+                char k[600];
+                if (sscanf(line, "%599[^\t]\t%d\t%d", k, &r, &g) == 3 && key == k) {
+                    asv_tune t{r, g};
+                    if (tune_ok(t, B)) {
+                        A->tune_R = r;
+                        A->tune_GB = g;
+                        if (h_best) *h_best = t;
+                        fclose(f);
+                        return ASV_OK;
+                    }
+                }
+            }
+            fclose(f);
+        }
+    }
+    const asv_tune cands[] = {{4, 4096}, {4, 2048}, {8, 512}, {8, 1024}, {8, 2048}, {8, 4096}, {16, 256},
+                              {16, 512}, {16, 1024}, {16, 2048}};
+    float best = 1e30f;
+    asv_tune bt{A->tune_R, A->tune_GB};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (const asv_tune& c : cands) {
+        if (!tune_ok(c, B) || (c.vectors_per_group > 2 * std::max(B, 1) && c.vectors_per_group > 256)) continue;
+        st = asv_spmspv_batched(A, B, max_entries, d_xptr, d_xidx, d_xval, d_X_dense, d_Y, &c, stream);
+        if (st != ASV_OK) break;
+        float tsum = 0.f;
+        for (int r = 0; r < 3; ++r) {
+            CK(cudaEventRecord(e0, s));
+            st = asv_spmspv_batched(A, B, max_entries, d_xptr, d_xidx, d_xval, d_X_dense, d_Y, &c, stream);
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tsum += ms;
+        }
+        if (tsum < best) {
+            best = tsum;
+            bt = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != ASV_OK) return st;
+    A->tune_R = bt.rows_per_tile;
+    A->tune_GB = bt.vectors_per_group;
+    if (h_best) *h_best = bt;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s\t%d\t%d\n", key.c_str(), bt.rows_per_tile, bt.vectors_per_group);
+            fclose(f);
+        }
+    }
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_spmspv_backward(asv_matrix A, int32_t B, const void* d_X, const void* d_dY, void* d_dX,
+                                          void* d_dA, void* stream) {
+    if (!A || B < 0 || !d_dY || (d_dA && !d_X)) return ASV_ERR_ARG;
+    if (A->dtype != ASV_F32) return ASV_ERR_UNSUPPORTED;
+    if (B > 128) return ASV_ERR_UNSUPPORTED;
+    if (B == 0) return ASV_OK;
+    CK(batched_backward(A, B, (const float*)d_X, (const float*)d_dY, (float*)d_dX, (float*)d_dA,
+                        (cudaStream_t)stream));
     return ASV_OK;
 }
 

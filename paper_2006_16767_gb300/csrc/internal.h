@@ -2,10 +2,28 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <vector>
 
 #include "common.cuh"
 #include "selector.cuh"
+
+// Workspaces of the batched forward/backward forms, grown on demand.
+struct BatchWs {
+    uint32_t* keys[2] = {nullptr, nullptr};
+    uint64_t* pay[2] = {nullptr, nullptr};
+    int64_t* xptr = nullptr;  // [cap_B+1] offsets, then the entry count
+    int32_t* cptr = nullptr;  // [n+1] column pointers of the regrouped batch
+    void* desc = nullptr;     // device BatchDesc
+    unsigned long long* queue = nullptr;  // work queue + ticket (zero-invariant)
+    int64_t cap_entries = 0;
+    int32_t cap_B = 0;
+    std::map<long long, cudaGraphExec_t> graphs;  // captured pipelines by (B, R, GB)
+    void* dYt = nullptr;
+    void* Xt = nullptr;
+    void* dXt = nullptr;
+    int32_t bwd_B = 0;
+};
 
 struct asv_matrix_s {
     int dev = 0;
@@ -17,6 +35,7 @@ struct asv_matrix_s {
     const int32_t* rowptr = nullptr;
     const int32_t* col = nullptr;
     const void* val = nullptr;
+    bool owns_val = false;
     int32_t* colptr = nullptr;
     int32_t* rowidx = nullptr;
     void* val_csc = nullptr;
@@ -45,6 +64,8 @@ struct asv_matrix_s {
     unsigned long long cond[2][2] = {{0, 0}, {0, 0}};
     cudaStream_t cap_stream = nullptr;
     int G = 0;  // fixed grid of the scan / sort / compaction primitives
+    BatchWs bws;
+    int32_t tune_R = 8, tune_GB = 1024;  // batched tiling chosen by the autotuner
     std::vector<void*> allocs;
 };
 
@@ -59,6 +80,7 @@ cudaError_t build_features(asv_matrix_s* H, cudaStream_t s);
 cudaError_t build_partition(asv_matrix_s* H, cudaStream_t s);
 int64_t pull_tile_items(int32_t dtype);
 cudaError_t validate_csr(asv_matrix_s* H, cudaStream_t s, int32_t* d_flag);
+cudaError_t regather_values(asv_matrix_s* H, cudaStream_t s);
 
 // shared scan launcher (device-side count allowed)
 void scan_excl(const int32_t* in, int32_t* out, int64_t n_h, const int64_t* n_d, int32_t* blk, int G,
@@ -119,6 +141,13 @@ void launch_pull(asv_matrix_s* H, int dist, bool masked, bool sparse_out, const 
 
 // push.cu
 void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s);
+
+// batched.cu
+cudaError_t batched_forward(asv_matrix_s* H, int32_t B, int64_t max_entries, const int64_t* xptr, const int32_t* xidx,
+                            const float* xval, const float* Xdense, float* Y, int R, int GB, cudaStream_t s);
+cudaError_t batched_backward(asv_matrix_s* H, int32_t B, const float* X, const float* dY, float* dX, float* dA,
+                             cudaStream_t s);
+void batch_release(asv_matrix_s* H);
 
 // select.cu
 SelectArg select_arg(asv_matrix_s* H, unsigned long long cond);

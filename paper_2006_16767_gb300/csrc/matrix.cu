@@ -261,6 +261,23 @@ cudaError_t build_partition(asv_matrix_s* H, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- value refresh
+template <class V>
+__global__ void k_regather(const int32_t* __restrict__ perm, const V* __restrict__ val, int64_t nnz, V* val_csc) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        val_csc[p] = val[perm[p]];
+}
+
+cudaError_t regather_values(asv_matrix_s* H, cudaStream_t s) {
+    if (H->nnz == 0 || !H->val || !H->val_csc) return cudaSuccess;
+    const int grid = H->num_sms * 8;
+    if (vsize(H->dtype) == 8)
+        k_regather<<<grid, 256, 0, s>>>(H->perm, (const double*)H->val, H->nnz, (double*)H->val_csc);
+    else
+        k_regather<<<grid, 256, 0, s>>>(H->perm, (const uint32_t*)H->val, H->nnz, (uint32_t*)H->val_csc);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- validation
 __global__ void k_validate(const int32_t* rowptr, const int32_t* col, int64_t m, int64_t n, int64_t nnz,
                            int32_t* flag) {

@@ -1,0 +1,180 @@
+"""Batched and differentiable forms against the oracle (through the C ABI).
+
+Row b of a batched product equals the single-vector oracle product of x_b;
+dx_b = A^T dy_b and dA = sum_b dy_b x_b^T on A's pattern equal the oracle's
+adjoint and value gradient; the autograd layer's gradients equal FP64
+central differences of a linear loss on a 256 x 256 slice. FP32 tolerance
+2e-6 of the sum of the magnitudes of the terms."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+from tests._util import assert_rows_close
+
+pytestmark = pytest.mark.gpu
+asv = pytest.importorskip("paper_2006_16767_gb300")
+DEV = "cuda"
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def zipf_problem(m=20000, n=8192, B=300, seed=3):
+    rp, c, v = gen.lognormal_zipf(m, n, np.log(10), 1.0, 1.2, seed)
+    xrp, xc, xv = gen.lognormal_zipf(B, n, np.log(10), 1.0, 1.2, seed + 1)
+    xv = gen.uniform(len(xv), -1, 1, seed, 9, np.float32)
+    return m, n, rp, c, v, xrp.astype(np.int64), xc, xv
+
+
+def check_batch(Y, m, n, rp, c, v, xrp, xc, xv, what):
+    Y = Y.cpu().numpy()
+    for b in range(len(xrp) - 1):
+        lo, hi = xrp[b], xrp[b + 1]
+        y_ref, s, _ = oracle.spmspv_rowmajor(n, rp, c, v.astype(np.float64), xc[lo:hi], xv[lo:hi].astype(np.float64))
+        assert_rows_close(Y[b], y_ref, s, "f32", f"{what} vector {b}")
+
+
+@pytest.mark.parametrize("tune", [None, (4, 4096), (8, 64), (8, 1024), (16, 128), (16, 2048)])
+def test_batched_matches_oracle_per_vector(tune):
+    m, n, rp, c, v, xrp, xc, xv = zipf_problem()
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), to_dev(v))
+    Y = A.spmspv_batched(to_dev(xrp), to_dev(xc), to_dev(xv), tune=tune)
+    check_batch(Y, m, n, rp, c, v, xrp, xc, xv, f"tune={tune}")
+    # a second call reuses the captured pipeline
+    Y2 = A.spmspv_batched(to_dev(xrp), to_dev(xc), to_dev(xv), tune=tune)
+    assert torch.equal(Y, Y2)
+
+
+def test_batched_dense_input_and_edges():
+    m, n, rp, c, v, xrp, xc, xv = zipf_problem(m=3000, n=2000, B=37, seed=5)
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), to_dev(v))
+    Xd = np.zeros((len(xrp) - 1, n), np.float32)
+    for b in range(len(xrp) - 1):
+        Xd[b, xc[xrp[b]:xrp[b + 1]]] = xv[xrp[b]:xrp[b + 1]]
+    Y = A.spmspv_batched(X_dense=to_dev(Xd))
+    check_batch(Y, m, n, rp, c, v, xrp, xc, xv, "dense X")
+    # empty vectors inside the batch, and a batch of one
+    xrp2 = np.array([0, 0, 3, 3, 5], np.int64)
+    xc2 = np.array([1, 7, 9, 0, 1999], np.int32)
+    xv2 = np.array([1, -2, 3, 4, 5], np.float32)
+    Y = A.spmspv_batched(to_dev(xrp2), to_dev(xc2), to_dev(xv2))
+    check_batch(Y, m, n, rp, c, v, xrp2, xc2, xv2, "empty vectors")
+    Y = A.spmspv_batched(to_dev(xrp2[:2]), to_dev(xc2), to_dev(xv2))
+    assert torch.count_nonzero(Y).item() == 0
+
+
+def test_autotune_batched_and_cache(tmp_path):
+    m, n, rp, c, v, xrp, xc, xv = zipf_problem(m=5000, n=4096, B=128, seed=7)
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), to_dev(v))
+    cache = tmp_path / "tune.tsv"
+    t1 = A.autotune_batched(to_dev(xrp), to_dev(xc), to_dev(xv), cache_path=cache)
+    assert t1[0] in (4, 8, 16) and t1[1] >= 1
+    assert cache.exists() and cache.read_text().strip()
+    t2 = A.autotune_batched(to_dev(xrp), to_dev(xc), to_dev(xv), cache_path=cache)
+    assert t2 == t1
+    Y = A.spmspv_batched(to_dev(xrp), to_dev(xc), to_dev(xv))
+    check_batch(Y, m, n, rp, c, v, xrp, xc, xv, "autotuned")
+
+
+def test_backward_matches_oracle():
+    m, n, B = 700, 500, 64
+    rp, c, v = gen.bernoulli(m, n, 0.05, 0.02, 11)
+    X = gen.halfnormal(B * n, 1.0, 12).reshape(B, n)
+    keep = gen.uniform(B * n, 0, 1, 13, 0, np.float64).reshape(B, n) < np.linspace(0.05, 0.5, B)[:, None]
+    X = np.where(keep, X, 0).astype(np.float32)
+    dY = gen.uniform(B * m, -1, 1, 14, 0, np.float32).reshape(B, m)
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), to_dev(v))
+    dX, dA = A.backward(to_dev(X), to_dev(dY))
+    dX, dA = dX.cpu().numpy(), dA.cpu().numpy()
+    colptr, rowidx, perm = oracle.csr_to_csc(m, n, rp, c)
+    vv = v.astype(np.float64)
+    for b in range(B):
+        ref, s = oracle.csc_pull(colptr, rowidx, vv[perm], dY[b].astype(np.float64))
+        assert_rows_close(dX[b], ref, s, "f32", f"dx vector {b}")
+    ref = np.zeros(len(c))
+    scale = np.zeros(len(c))
+    for b in range(B):
+        g = oracle.grad_values(rp, c, dY[b].astype(np.float64), X[b].astype(np.float64))
+        ref += g
+        scale += np.abs(g)
+    assert_rows_close(dA, ref, scale, "f32", "dA")
+
+
+def test_autograd_layer_against_fp64_finite_differences():
+    # the leading 256 x 256 block of a 16384^2, 5%-dense N(0, 0.02) layer
+    m = n = 256
+    rp_full, c_full, v_full = gen.bernoulli(1024, 1024, 0.05, 0.02, gen.config_seed(4))
+    rows = []
+    for i in range(m):
+        lo, hi = rp_full[i], rp_full[i + 1]
+        keep = c_full[lo:hi] < n
+        rows.append((c_full[lo:hi][keep], v_full[lo:hi][keep]))
+    rp = np.concatenate([[0], np.cumsum([len(r[0]) for r in rows])]).astype(np.int32)
+    c = np.concatenate([r[0] for r in rows]).astype(np.int32)
+    v = np.concatenate([r[1] for r in rows]).astype(np.float32)
+    B = 8
+    X = gen.halfnormal(B * n, 1.0, 21).reshape(B, n)
+    X = np.where(gen.uniform(B * n, 0, 1, 22).reshape(B, n) < 0.3, X, 0).astype(np.float32)
+    W = gen.uniform(B * m, -1, 1, 23, 0, np.float64).reshape(B, m)
+
+    vals = to_dev(v).requires_grad_(True)
+    Xt = to_dev(X).requires_grad_(True)
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), vals.detach())
+    # the handle reads vals' storage in place
+    A.val = vals
+    Y = asv.SpMSpVFunction.apply(vals, Xt, A)
+    L = (Y * to_dev(W.astype(np.float32))).sum()
+    L.backward()
+    g_vals = vals.grad.cpu().numpy().astype(np.float64)
+    g_X = Xt.grad.cpu().numpy().astype(np.float64)
+
+    def loss64(vv, XX):
+        tot = 0.0
+        for b in range(B):
+            y, _ = oracle.csr_pull(rp, c, vv, XX[b])
+            tot += float(W[b] @ y)
+        return tot
+
+    v64, X64 = v.astype(np.float64), X.astype(np.float64)
+    h = 1e-3
+    picks = gen.randint(40, len(c), 31)
+    for k in picks:
+        vp, vm = v64.copy(), v64.copy()
+        vp[k] += h
+        vm[k] -= h
+        fd = (loss64(vp, X64) - loss64(vm, X64)) / (2 * h)
+        i = int(np.searchsorted(rp, k, "right") - 1)
+        scale = float(np.sum(np.abs(W[:, i] * X64[:, c[k]])))
+        assert abs(g_vals[k] - fd) <= 2e-6 * scale + 1e-9, (k, g_vals[k], fd)
+    for (b, j) in zip(gen.randint(20, B, 32), gen.randint(20, n, 33)):
+        Xp, Xm = X64.copy(), X64.copy()
+        Xp[b, j] += h
+        Xm[b, j] -= h
+        fd = (loss64(v64, Xp) - loss64(v64, Xm)) / (2 * h)
+        colk = np.flatnonzero(c == j)
+        rowk = np.searchsorted(rp, colk, "right") - 1
+        scale = float(np.sum(np.abs(W[b, rowk] * v64[colk])))
+        assert abs(g_X[b, j] - fd) <= 2e-6 * scale + 1e-9, (b, j, g_X[b, j], fd)
+
+
+def test_update_values_refreshes_the_csc_view():
+    m, n = 900, 700
+    rp, c, v = gen.random_csr(m, n, 0.02, seed=41, values="uniform", dtype=np.float32)
+    vt = to_dev(v)
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), vt)
+    x = gen.uniform(n, -1, 1, 42).astype(np.float32)
+    idx = np.flatnonzero(x).astype(np.int32)
+    v2 = (v * 3 - 1).astype(np.float32)
+    vt.copy_(to_dev(v2))
+    A.update_values()
+    y_ref, s = oracle.csr_pull(rp, c, v2.astype(np.float64), x.astype(np.float64))
+    for k in ("push_bal_atom", "pull_bal", "push_warp_sort"):
+        y = A.spmspv(xidx=to_dev(idx), xval=to_dev(x[idx]), kernel=k)
+        assert_rows_close(y.cpu().numpy(), y_ref, s, "f32", f"updated values {k}")
+    C = asv.Matrix(m, n, to_dev(rp), to_dev(c), to_dev(v), copy=True)
+    C.update_values(to_dev(v2))
+    y = C.spmspv(xidx=to_dev(idx), xval=to_dev(x[idx]), kernel="push_warp_atom")
+    assert_rows_close(y.cpu().numpy(), y_ref, s, "f32", "copied handle")
