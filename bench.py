@@ -220,20 +220,24 @@ class Rmat22:
                 c["kbytes"] = useful_bytes(c["kid"], *args_)
                 c["launches"] = launches(c["kid"], False, False)
 
-    def run_step(self, events=None):
+    def run_step(self, events=None, direct=False):
+        """One step. direct=True replays the selector's recorded choices as
+        direct launches (the profiler cannot see kernels inside graphs with
+        conditional nodes); the timed steps always run the selector."""
         asv = self.asv
         h = self.Ab.handle
         for i, f in enumerate(self.frontiers):
             if events is not None:
                 events[i][0].record()
+            k = self.calls[i]["kid"] if direct else "auto"
             asv.asv_spmspv(h, self.counts[i], f, None, None, asv.ASV_OUT_SPARSE, None, self.yidx, self.yval,
-                           self.nnz_y[i:i + 1], self.m, "auto")
+                           self.nnz_y[i:i + 1], self.m, k)
             if events is not None:
                 events[i][1].record()
         j = len(self.frontiers)
         if events is not None:
             events[j][0].record()
-        asv.asv_spmv(self.Af.handle, self.x_pr, self.y_pr, "auto")
+        asv.asv_spmv(self.Af.handle, self.x_pr, self.y_pr, self.calls[j]["kid"] if direct else "auto")
         if events is not None:
             events[j][1].record()
 
@@ -406,6 +410,9 @@ def main():
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and backward sections")
+    ap.add_argument("--direct", action="store_true",
+                    help="profiling aid: run the recorded kernel choices as direct launches instead of the "
+                         "selector graph (ncu cannot profile kernels inside conditional graphs)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -436,7 +443,7 @@ def main():
     ncalls = len(W.calls)
     for _ in range(max(3, args.warmup)):
         flush.zero_()
-        W.run_step()
+        W.run_step(direct=args.direct)
     torch.cuda.synchronize()
 
     step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -453,7 +460,7 @@ def main():
         flush.zero_()
         torch.cuda.nvtx.range_push("timed_step")
         step_ev[s][0].record()
-        W.run_step(call_ev[s])
+        W.run_step(call_ev[s], direct=args.direct)
         step_ev[s][1].record()
         torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()

@@ -241,12 +241,14 @@ asv_status asv_spmspv_backward(asv_matrix A, int32_t B, const void* d_X, const v
 
 /* ---------------------------------------------------------------- selector */
 
-/* Replace the handle's decision trees (three cascaded CART trees: computing
- * pattern, workload distribution, write-back; Sec. V-B / VI-B). `nodes` holds
- * n_nodes (<= 1024) records of 5 doubles {feature, threshold, left, right,
- * leaf_class}; feature < 0 marks a leaf. h_roots[12] holds the roots of the
- * three trees for each of the four call formats, in the order (x dense,
- * y dense), (x dense, y list), (x list, y dense), (x list, y list).
+/* Replace the handle's decision trees (cascaded CART trees: computing
+ * pattern, then workload distribution given the pattern, then write-back for
+ * the push pattern; Sec. V-B / VI-B). `nodes` holds n_nodes (<= 1024) records
+ * of 5 doubles {feature, threshold, left, right, leaf_class}; feature < 0
+ * marks a leaf. h_roots[20] holds five roots for each of the four call
+ * formats (x dense, y dense), (x dense, y list), (x list, y dense),
+ * (x list, y list): the pattern tree, the distribution trees applied after
+ * pattern 0 (push), 1 (masked pull) and 2 (pull), and the write-back tree.
  * Feature indices: 0 m, 1 n, 2 nnz, 3 max_row, 4 min_row, 5 avg_row,
  * 6 relative_range, 7 var_nnz_row, 8 gini, 9 nnz_x, 10 x_sparsity, 11 nnz_s,
  * 12 m_sparsity. A node sends x left when feature <= threshold.

@@ -245,12 +245,13 @@ def asv_compact(h, x_dense, idx, val, count, stream=None):
 
 
 def asv_set_trees(h, nodes, roots, stream=None):
-    """nodes: sequence of (feature, threshold, left, right, leaf) records; roots: 12 node indices
-    (pattern, distribution, write-back roots for each of the four x/y formats)."""
+    """nodes: (feature, threshold, left, right, leaf) records; roots: 20 node indices, five per
+    call format (pattern; distribution after push / masked pull / pull; write-back). Five
+    roots are repeated for all four formats."""
     import numpy as np
     arr = np.ascontiguousarray(np.asarray(nodes, np.float64).reshape(-1, 5))
     r = np.ascontiguousarray(np.asarray(roots, np.int32).reshape(-1))
-    if r.size == 3:
+    if r.size == 5:
         r = np.tile(r, 4)
     _check(lib().asv_set_trees(h, arr.ctypes.data_as(ctypes.c_void_p), len(arr),
                                r.ctypes.data_as(ctypes.c_void_p), _stream(stream)), "asv_set_trees")

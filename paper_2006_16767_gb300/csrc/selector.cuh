@@ -6,10 +6,12 @@
 
 namespace asv {
 
-// roots[3*f + t]: root of tree t (0 pattern, 1 distribution, 2 write-back)
-// for format f = 2*(x arrives as a list) + (sparse output); roots[12] holds
-// the number of nodes in the shared node table.
-constexpr int kRootsLen = 13;
+// roots[5*f + t] for format f = 2*(x arrives as a list) + (sparse output):
+// t = 0 the pattern tree, t = 1 + p the distribution tree used once pattern p
+// (0 push, 1 masked pull, 2 pull) is chosen, t = 4 the write-back tree;
+// roots[20] holds the number of nodes in the shared node table.
+constexpr int kRootsPerFormat = 5;
+constexpr int kRootsLen = 4 * kRootsPerFormat + 1;
 
 // What the selector needs besides the call descriptor. cond is the SWITCH
 // node's conditional handle (0 = none).
@@ -52,16 +54,16 @@ __device__ __forceinline__ void run_selector(const SelectArg& sa, CallDesc* desc
     f[10] = desc->vfeat[1];
     f[11] = desc->vfeat[2];
     f[12] = desc->vfeat[3];
-    const int* r = sa.roots + 3 * (desc->x_sparse * 2 + desc->out_mode);
-    const int pattern = eval_tree(sn, r[0], f);  // 0 push, 1 masked pull, 2 pull
-    const int dist = eval_tree(sn, r[1], f);     // 0 thread, 1 warp, 2 balanced
+    const int* r = sa.roots + kRootsPerFormat * (desc->x_sparse * 2 + desc->out_mode);
+    const int pattern = min(max(eval_tree(sn, r[0], f), 0), 2);  // 0 push, 1 masked pull, 2 pull
+    const int dist = eval_tree(sn, r[1 + pattern], f);            // 0 thread, 1 warp, 2 balanced
     int kid;
     if (pattern == 2) {
         kid = ASV_K_PULL_THREAD + dist;
     } else if (pattern == 1) {
         kid = ASV_K_MPULL_THREAD + dist;
     } else {
-        const int wb = eval_tree(sn, r[2], f);  // 0 atomic, 1 sort, 2 privatised
+        const int wb = eval_tree(sn, r[4], f);  // 0 atomic, 1 sort, 2 privatised
         kid = ASV_K_PUSH_THREAD_ATOM + 3 * wb + dist;
     }
     if (kid < 0 || kid >= ASV_K_COUNT) kid = ASV_K_PULL_BAL;

@@ -118,7 +118,11 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
             for (int q = 0; q < 4; ++q) nz[q] = (j0 + q < n) && Sr<T>::nz(__ldg(x + j0 + q));
         }
         const unsigned nib = (unsigned)nz[0] | ((unsigned)nz[1] << 1) | ((unsigned)nz[2] << 2) | ((unsigned)nz[3] << 3);
-        if (nib) {
+        // a fully nonzero stretch of 128 columns: two boundary reads give its
+        // degree sum, so a dense x does not stream all of colptr
+        if (__all_sync(0xffffffffu, nib == 0xFu && j0 + 4 <= n)) {
+            if (lane == 0) cs += (unsigned long long)(__ldg(colptr + sw * 128 + 128) - __ldg(colptr + sw * 128));
+        } else if (nib) {
             if (j0 + 4 <= n) {
                 const int4 cp = __ldg(reinterpret_cast<const int4*>(colptr + j0));
                 const int32_t c4 = __ldg(colptr + j0 + 4);

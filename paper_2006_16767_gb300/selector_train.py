@@ -28,6 +28,7 @@ import json
 import os
 import sys
 import time
+import zlib
 
 import numpy as np
 
@@ -58,32 +59,39 @@ def kernel_id(pattern, dist, wb):
 
 
 # ------------------------------------------------------------------ corpus
-def corpus(scale=1.0):
+def corpus():
     """Synthetic training matrices (none of them is a benchmark matrix)."""
     import gen
     s = 7919
     items = []
-    for g in (64, 128, 192):
-        items.append((f"stencil27_{g}", lambda g=g: gen.stencil27(g, s + g)[:3]))
-    for g in (512, 2048):
-        items.append((f"laplace2d_{g}", lambda g=g: gen.laplace2d(g)))
-    for sc, ef in ((16, 16), (18, 8), (20, 16), (21, 16)):
-        items.append((f"rmat_{sc}_{ef}", lambda sc=sc, ef=ef: rmat_vals(sc, ef, s + sc)))
-    items.append(("zipf_200k", lambda: gen.lognormal_zipf(200_000, 131_072, np.log(40), 1.0, 1.2, s + 1)))
-    items.append(("zipf_1m_64k", lambda: gen.lognormal_zipf(1_000_000, 65_536, np.log(20), 1.0, 1.1, s + 2)))
-    items.append(("bern_8192_1pct", lambda: gen.bernoulli(8192, 8192, 0.01, 0.02, s + 3)))
-    items.append(("bern_4096_5pct", lambda: gen.bernoulli(4096, 4096, 0.05, 0.02, s + 4)))
+    for g in (48, 96, 128, 160, 192):
+        items.append((f"stencil27_{g}", lambda g=g: gen.stencil27(g, s + g)[:3] + (g ** 3,)))
+    for g in (256, 512, 1024, 2048):
+        items.append((f"laplace2d_{g}", lambda g=g: gen.laplace2d(g) + (g * g,)))
+    for sc, ef in ((14, 16), (16, 8), (16, 16), (17, 32), (18, 8), (19, 16), (20, 8), (20, 16), (21, 16)):
+        items.append((f"rmat_{sc}_{ef}", lambda sc=sc, ef=ef: rmat_vals(sc, ef, s + sc * 7 + ef)))
+    items.append(("rmat_er_18", lambda: rmat_vals(18, 16, s + 5, a=0.25, b=0.25, c=0.25)))
+    items.append(("rmat_mild_19", lambda: rmat_vals(19, 16, s + 6, a=0.45, b=0.22, c=0.22)))
+    for name, m, n, mu, sg, zs, sd in (("zipf_200k", 200_000, 131_072, np.log(40), 1.0, 1.2, 1),
+                                       ("zipf_1m_64k", 1_000_000, 65_536, np.log(20), 1.0, 1.1, 2),
+                                       ("zipf_500k_256k", 500_000, 262_144, np.log(30), 0.8, 1.3, 7),
+                                       ("zipf_100k_32k", 100_000, 32_768, np.log(80), 1.2, 1.0, 8)):
+        items.append((name, lambda m=m, n=n, mu=mu, sg=sg, zs=zs, sd=sd:
+                      gen.lognormal_zipf(m, n, mu, sg, zs, s + sd) + (n,)))
+    for name, k, p, sd in (("bern_8192_1pct", 8192, 0.01, 3), ("bern_4096_5pct", 4096, 0.05, 4),
+                           ("bern_16384_02pct", 16384, 0.002, 9)):
+        items.append((name, lambda k=k, p=p, sd=sd: gen.bernoulli(k, k, p, 0.02, s + sd) + (k,)))
     return items
 
 
-def rmat_vals(scale, ef, seed):
+def rmat_vals(scale, ef, seed, a=0.57, b=0.19, c=0.19):
     import gen
-    rp, c = gen.rmat(scale, ef, seed)
-    return rp, c, gen.uniform(len(c), 0.5, 1.5, seed, 3, np.float32)
+    rp, c = gen.rmat(scale, ef, seed, a, b, c)
+    return rp, c, gen.uniform(len(c), 0.5, 1.5, seed, 3, np.float32), 1 << scale
 
 
 def densities(n):
-    rhos = sorted(set([10.0 ** e for e in np.arange(-6, 0.01, 0.5)] + [0.2, 0.4, 0.6, 0.8]))
+    rhos = sorted(set([10.0 ** e for e in np.arange(-6, 0.01, 0.25)] + [0.15, 0.2, 0.3, 0.4, 0.5, 0.6, 0.8]))
     out = []
     for r in rhos:
         k = int(round(r * n))
@@ -105,9 +113,8 @@ def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
     for name, make in corpus():
         if time.time() - t_start > budget_s:
             break
-        rp, c, v = make()
-        m, n = len(rp) - 1, int(c.max()) + 1 if len(c) else 1
-        n = max(n, {"zipf_200k": 131_072, "zipf_1m_64k": 65_536}.get(name, n))
+        rp, c, v, n = make()
+        m = len(rp) - 1
         rpt, ct = torch.from_numpy(rp).to(dev), torch.from_numpy(c).to(dev)
         for dt in dtypes:
             vt = torch.from_numpy(np.asarray(v, np.float32)).to(dev) if dt == "f32" else None
@@ -120,7 +127,7 @@ def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
             for rho, k in densities(n):
                 if time.time() - t_start > budget_s:
                     break
-                idx = gen.sample_positions(n, k, seed=hash((name, k)) & 0xFFFF, stream=1)
+                idx = gen.sample_positions(n, k, seed=zlib.crc32(f"{name}/{k}".encode()), stream=1)
                 it = torch.from_numpy(idx).to(dev)
                 if dt == "f32":
                     xv = torch.from_numpy(gen.uniform(len(idx), -1, 1, 5, 2, np.float32)).to(dev)
@@ -168,7 +175,9 @@ def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
 
 # ------------------------------------------------------------------ labels and fitting (host)
 def labels(times):
-    """Per-model labels of one sample (Sec. V-B readings)."""
+    """Per-model labels of one sample (Sec. V-B readings): the pattern of the
+    fastest kernel; for each pattern, its fastest distribution (for push at
+    its best write-back); the fastest write-back at the best push distribution."""
     t = np.asarray([x if x is not None else np.inf for x in times])
 
     def pick(cands):
@@ -178,14 +187,13 @@ def labels(times):
                 return k
         return min(cands, key=lambda k: t[k])
 
-    kbest = pick(range(NK))
-    pat = kernel_parts(kbest)[0]
-    in_pat = [k for k in range(NK) if kernel_parts(k)[0] == pat]
-    dist = kernel_parts(pick(in_pat))[1]
-    push_best = {d: min(t[kernel_id(0, d, w)] for w in range(3)) for d in range(3)}
-    dpush = min(range(3), key=lambda d: (push_best[d], d))
-    wb = kernel_parts(pick([kernel_id(0, dpush, w) for w in range(3)]))[2]
-    return pat, dist, wb
+    pat = kernel_parts(pick(range(NK)))[0]
+    dists = []
+    for p in range(3):
+        in_p = [k for k in range(NK) if kernel_parts(k)[0] == p]
+        dists.append(kernel_parts(pick(in_p))[1])
+    wb = kernel_parts(pick([kernel_id(0, dists[0], w) for w in range(3)]))[2]
+    return pat, dists[0], dists[1], dists[2], wb
 
 
 def load(path):
@@ -193,40 +201,49 @@ def load(path):
     return [r for r in rows if all(x is not None for x in r["t"])]
 
 
-def fit(path, seed=0):
+# feature columns of the five trees of a format: pattern (Table 1 model 1),
+# distribution after push / masked pull / pull (model 2, here with the vector
+# features too: which split is best for push depends on x), write-back (model 3)
+TREE_FEATURES = (MODEL_FEATURES[0], tuple(range(13)), tuple(range(13)), tuple(range(13)), MODEL_FEATURES[2])
+
+
+def _fit_one(X, y, seed):
     from sklearn.model_selection import GridSearchCV, train_test_split
     from sklearn.tree import DecisionTreeClassifier
-    rows = load(path)
-    result = {}
-    report = {}
+    if len(set(y.tolist())) < 2 or len(y) < 10:
+        leaf = int(np.bincount(y).argmax()) if len(y) else 0
+        return None, leaf, 1.0
+    Xtr, Xte, ytr, yte = train_test_split(X, y, test_size=0.3, random_state=seed)
+    folds = max(2, min(5, int(np.bincount(ytr).min()) if len(set(ytr.tolist())) > 1 else 2))
+    gs = GridSearchCV(DecisionTreeClassifier(random_state=seed),
+                      {"max_depth": list(range(1, 11)), "class_weight": [None, "balanced"]}, cv=folds)
+    gs.fit(Xtr, ytr)
+    acc = float(gs.score(Xte, yte))
+    clf = DecisionTreeClassifier(random_state=seed, **gs.best_params_).fit(X, y)
+    return clf, None, acc
+
+
+def fit(path, seed=0, rows=None):
+    import warnings
+    warnings.filterwarnings("ignore")
+    rows = rows if rows is not None else load(path)
+    result, report = {}, {}
     for dt in sorted({r["dtype"] for r in rows}):
         nodes, roots = [], []
         for fmt in range(4):
             sub = [r for r in rows if r["dtype"] == dt and r["fmt"] == fmt]
             X = np.asarray([r["feat"] for r in sub], np.float64)
-            Y = np.asarray([labels(r["t"]) for r in sub], np.int64)
-            for model in range(3):
-                cols = MODEL_FEATURES[model]
-                y = Y[:, model]
-                Xm = X[:, cols]
-                if len(set(y.tolist())) < 2 or len(sub) < 10:
-                    nodes_m = [(-1, 0.0, 0, 0, int(np.bincount(y).argmax()) if len(y) else 0)]
-                    acc = 1.0
-                else:
-                    Xtr, Xte, ytr, yte = train_test_split(Xm, y, test_size=0.3, random_state=seed, stratify=None)
-                    gs = GridSearchCV(DecisionTreeClassifier(random_state=seed),
-                                      {"max_depth": list(range(1, 11)), "class_weight": [None, "balanced"]},
-                                      cv=min(5, max(2, len(ytr) // 5)))
-                    gs.fit(Xtr, ytr)
-                    acc = float(gs.score(Xte, yte))
-                    clf = DecisionTreeClassifier(random_state=seed, **gs.best_params_).fit(Xm, y)
-                    nodes_m = export_tree(clf, cols)
+            Y = np.asarray([labels(r["t"]) for r in sub], np.int64).reshape(-1, 5)
+            for tree in range(5):
+                cols = TREE_FEATURES[tree]
+                clf, leaf, acc = _fit_one(X[:, cols] if len(sub) else X, Y[:, tree], seed)
+                nodes_m = export_tree(clf, cols) if clf is not None else [(-1, 0.0, 0, 0, leaf)]
                 base = len(nodes)
-                for (f, thr, l, r, leaf) in nodes_m:
-                    nodes.append((f, thr, l + base if f >= 0 else 0, r + base if f >= 0 else 0, leaf))
+                for (f, thr, l, r, lf) in nodes_m:
+                    nodes.append((f, thr, l + base if f >= 0 else 0, r + base if f >= 0 else 0, lf))
                 roots.append(base)
-                report[f"{dt}/fmt{fmt}/model{model + 1}"] = {"test_accuracy": round(acc, 4), "samples": len(sub),
-                                                             "nodes": len(nodes_m)}
+                report[f"{dt}/fmt{fmt}/tree{tree}"] = {"test_accuracy": round(acc, 4), "samples": len(sub),
+                                                        "nodes": len(nodes_m)}
         result[dt] = {"nodes": nodes, "roots": roots}
     return result, report
 
@@ -253,14 +270,15 @@ def predict(trees, dt, fmt, feat):
             f, thr, l, r, _ = nodes[i]
             i = l if feat[f] <= thr else r
         return nodes[i][4]
-    pat = walk(roots[3 * fmt])
-    dist = walk(roots[3 * fmt + 1])
-    wb = walk(roots[3 * fmt + 2]) if pat == 0 else 0
+    r = roots[5 * fmt: 5 * fmt + 5]
+    pat = min(max(walk(r[0]), 0), 2)
+    dist = walk(r[1 + pat])
+    wb = walk(r[4]) if pat == 0 else 0
     return kernel_id(pat, dist, wb)
 
 
-def regret(path, trees):
-    rows = load(path)
+def regret(path, trees, rows=None):
+    rows = rows if rows is not None else load(path)
     out = {}
     for r in rows:
         k = predict(trees, r["dtype"], r["fmt"], r["feat"])
@@ -271,6 +289,19 @@ def regret(path, trees):
             for (dt, f), v in sorted(out.items())}
 
 
+def held_out(path, seed=0):
+    """Regret on each corpus matrix with the trees fitted on the others."""
+    rows = load(path)
+    out = {}
+    for mname in sorted({r["matrix"] for r in rows}):
+        train = [r for r in rows if r["matrix"] != mname]
+        test = [r for r in rows if r["matrix"] == mname]
+        trees, _ = fit(None, seed, rows=train)
+        reg = [r["t"][predict(trees, r["dtype"], r["fmt"], r["feat"])] / min(r["t"]) for r in test]
+        out[mname] = {"mean": round(float(np.mean(reg)), 3), "max": round(float(np.max(reg)), 3)}
+    return out
+
+
 def emit(trees, path=None):
     """C header with one node table and 12 roots per value type."""
     path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "trees_default.h")
@@ -279,8 +310,9 @@ def emit(trees, path=None):
              "// Records: {feature, threshold, left, right, leaf_class}; feature < 0 = leaf.",
              "// Feature ids: 0 m, 1 n, 2 nnz, 3 max_row, 4 min_row, 5 avg_row,",
              "// 6 relative_range, 7 var_nnz_row, 8 gini, 9 nnz_x, 10 x_sparsity,",
-             "// 11 nnz_s, 12 m_sparsity. Roots: (pattern, distribution, write-back) for",
-             "// (x dense, y dense), (x dense, y list), (x list, y dense), (x list, y list).",
+             "// 11 nnz_s, 12 m_sparsity. Roots, five per call format -- pattern, distribution",
+             "// after push / masked pull / pull, write-back -- for (x dense, y dense),",
+             "// (x dense, y list), (x list, y dense), (x list, y list).",
              "#pragma once", "", "namespace asv {", ""]
     for dt in ("f32", "bool"):
         T = trees.get(dt) or trees["f32"]
@@ -290,7 +322,7 @@ def emit(trees, path=None):
         for (f, thr, l, r, leaf) in T["nodes"]:
             lines.append(f"    {{{f}, {thr!r}, {l}, {r}, {leaf}}},")
         lines.append("};")
-        lines.append(f"static const int kTreeRoots{name}[12] = {{{', '.join(str(x) for x in T['roots'])}}};")
+        lines.append(f"static const int kTreeRoots{name}[20] = {{{', '.join(str(x) for x in T['roots'])}}};")
         lines.append("")
     lines += ["}  // namespace asv", ""]
     open(path, "w").write("\n".join(lines))
@@ -306,5 +338,7 @@ if __name__ == "__main__":
         trees, rep = fit(sys.argv[2])
         print(json.dumps(rep, indent=1))
         print(json.dumps(regret(sys.argv[2], trees), indent=1))
+        if "--held-out" in sys.argv:
+            print(json.dumps(held_out(sys.argv[2]), indent=1))
         if "--emit" in sys.argv:
             print(emit(trees))

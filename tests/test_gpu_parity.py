@@ -280,7 +280,7 @@ def test_set_trees_drives_the_switch_branch():
     y_ref, s = oracle.csr_pull(rp, c, v.astype(np.float64), x.astype(np.float64))
     for pat, dist, wb in [(0, 2, 1), (1, 0, 0), (2, 1, 0), (0, 0, 2), (0, 1, 0)]:
         nodes = [(-1, 0, 0, 0, pat), (-1, 0, 0, 0, dist), (-1, 0, 0, 0, wb)]
-        A.set_trees(nodes, [0, 1, 2] * 4)
+        A.set_trees(nodes, [0, 1, 1, 1, 2] * 4)
         want = {2: dist, 1: 3 + dist, 0: 6 + 3 * wb + dist}[pat]
         for dense_in in (True, False):
             if dense_in:
@@ -293,4 +293,4 @@ def test_set_trees_drives_the_switch_branch():
         kid, _ = A.select(x_dense=to_dev(x))
         assert kid == want
     with pytest.raises(asv.AsvError):
-        A.set_trees([(0, 1.0, 5, 6, 0)], [0] * 12)  # child index out of range
+        A.set_trees([(0, 1.0, 5, 6, 0)], [0] * 20)  # child index out of range
