@@ -258,6 +258,30 @@ asv_status asv_spmspv_backward(asv_matrix A, int32_t B, const void* d_X, const v
 asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t n_nodes,
                          const int32_t* h_roots, void* stream);
 
+/* ---------------------------------------------------------------- allocation-free */
+
+/* y = A x (FP32, x and y dense) for caller-owned CSR arrays d_rowptr[m+1],
+ * d_colidx[nnz], d_val[nnz] (NULL = all ones), without allocating device
+ * memory and without a handle. The paper has no counterpart: this is for
+ * callers that must not allocate on their call path -- real-time loops in
+ * which cudaMalloc or cudaFree would synchronise the device, runtimes that
+ * give all device memory to their own pool at start-up, and one-off products
+ * on borrowed arrays that cannot afford a handle (which allocates the CSC view
+ * and workspaces). It runs the balanced (merge-path) candidate, whose scratch
+ * -- the tile table and the carries of rows that span tiles -- lives in one
+ * fixed 4 MB device array inside the library, held by every GPU that loads
+ * the library until the process exits. Limit: m + nnz <= 2^29 (2^18 tiles of
+ * 2048 items); larger sizes return ASV_ERR_CAPACITY before anything runs.
+ * The first call on a device looks up the array's device address (once per
+ * device), so make that first call before any stream capture. All calls
+ * share the array: calls whose work overlaps on the GPU (different streams,
+ * or different host threads, without ordering) race on it. Each call
+ * rewrites every scratch entry it reads, so nothing needs clearing between
+ * calls. Enqueued on `stream`; no synchronisation. */
+asv_status asv_spmv_noalloc_f32(int64_t m, int64_t n, int64_t nnz, const int32_t* d_rowptr,
+                                const int32_t* d_colidx, const float* d_val, const float* d_x,
+                                float* d_y, void* stream);
+
 /* ---------------------------------------------------------------- status */
 
 /* Latched device status of the handle (synchronises `stream`); clears it. */

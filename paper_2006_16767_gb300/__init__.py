@@ -89,6 +89,7 @@ def lib():
             L.asv_spmspv_batched.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, P(AsvTune), vp]
             L.asv_autotune_batched.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, ctypes.c_char_p, P(AsvTune), vp]
             L.asv_spmspv_backward.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+            L.asv_spmv_noalloc_f32.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp]
             L.asv_spmspv.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, i32, vp]
             L.asv_select.argtypes = [vp, vp, vp, vp, vp, P(i32), P(_VFeat), vp]
             L.asv_last_kernel.argtypes = [vp, P(i32), vp]
@@ -103,7 +104,7 @@ def lib():
                          "asv_matrix_arrays", "asv_matrix_copy_csc", "asv_spmv", "asv_spmspv", "asv_select", "asv_last_kernel",
                          "asv_compact", "asv_set_trees", "asv_get_status", "asv_last_cuda_error",
                          "asv_version", "asv_matrix_update_values", "asv_spmspv_batched", "asv_autotune_batched",
-                         "asv_spmspv_backward"):
+                         "asv_spmspv_backward", "asv_spmv_noalloc_f32"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -211,6 +212,13 @@ def asv_autotune_batched(h, B, max_entries=0, xptr=None, xidx=None, xval=None, X
 def asv_spmspv_backward(h, B, X, dY, dX=None, dA=None, stream=None):
     _check(lib().asv_spmspv_backward(h, int(B), _ptr(X), _ptr(dY), _ptr(dX), _ptr(dA), _stream(stream)),
            "asv_spmspv_backward")
+
+
+def asv_spmv_noalloc_f32(m, n, rowptr, col, val, x, y, stream=None):
+    """y = A x (FP32) on caller-owned CSR tensors with no device allocation and
+    no handle (for callers that cannot allocate on their call path)."""
+    _check(lib().asv_spmv_noalloc_f32(int(m), int(n), int(col.numel()), _ptr(rowptr), _ptr(col), _ptr(val),
+                                      _ptr(x), _ptr(y), _stream(stream)), "asv_spmv_noalloc_f32")
 
 
 def asv_spmv(h, x, y, kernel="auto", stream=None):

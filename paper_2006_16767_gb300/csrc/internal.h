@@ -139,6 +139,12 @@ struct PullIO {
 void launch_pull(asv_matrix_s* H, int dist, bool masked, bool sparse_out, const PullIO* direct,
                  cudaStream_t s);
 
+void launch_pull_bal_f32_raw(int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col, const float* val,
+                             const float* x, float* y, const int32_t* tile_row, int32_t* carry_row, double* carry_val,
+                             int64_t ntiles, cudaStream_t s);
+void launch_partition_raw(const int32_t* rowptr, int64_t m, int64_t nnz, int64_t ntiles, int32_t* tile_row,
+                          cudaStream_t s);
+
 // push.cu
 void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s);
 

@@ -261,6 +261,14 @@ cudaError_t build_partition(asv_matrix_s* H, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Tile table of the balanced pull for caller-owned arrays (used by the
+// allocation-free entry point).
+void launch_partition_raw(const int32_t* rowptr, int64_t m, int64_t nnz, int64_t ntiles, int32_t* tile_row,
+                          cudaStream_t s) {
+    const int64_t D = pull_tile_items(ASV_F32);
+    k_partition<<<(int)((ntiles + 256) / 256), 256, 0, s>>>(rowptr, m, nnz, ntiles, D, tile_row);
+}
+
 // ---------------------------------------------------------------- value refresh
 template <class V>
 __global__ void k_regather(const int32_t* __restrict__ perm, const V* __restrict__ val, int64_t nnz, V* val_csc) {

@@ -297,6 +297,26 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     }
 }
 
+// The FP32 balanced pull on caller-owned arrays and caller-provided scratch
+// (tile table, carries); used by the allocation-free entry point.
+void launch_pull_bal_f32_raw(int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col, const float* val,
+                             const float* x, float* y, const int32_t* tile_row, int32_t* carry_row, double* carry_val,
+                             int64_t ntiles, cudaStream_t s) {
+    if (ntiles == 0) return;
+    PullArg a;
+    a.desc = nullptr;
+    a.io = PullIO{x, nullptr, y};
+    const bool vec = ((uintptr_t)col % 16 == 0) && ((uintptr_t)val % 16 == 0);
+    if (vec)
+        k_pull_bal<float, false, false, true><<<(int)ntiles, kBalB, 0, s>>>(m, nnz, rowptr, col, val, tile_row, a,
+                                                                            nullptr, nullptr, carry_row, carry_val);
+    else
+        k_pull_bal<float, false, false, false><<<(int)ntiles, kBalB, 0, s>>>(m, nnz, rowptr, col, val, tile_row, a,
+                                                                             nullptr, nullptr, carry_row, carry_val);
+    k_pull_bal_fixup<float><<<(int)((ntiles + 255) / 256), 256, 0, s>>>(ntiles, carry_row, carry_val, nullptr, y,
+                                                                        nullptr, 0);
+}
+
 template <class T>
 static void pull_dtype(asv_matrix_s* H, int dist, bool masked, bool sout, const PullIO* direct, cudaStream_t s) {
     if (masked) {
