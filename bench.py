@@ -377,6 +377,118 @@ def bench_backward(asv, torch, dev, reps=5):
     return out
 
 
+def ncu_case(case, kernel):
+    """Small inputs (larger than L2, a few GB at most) for one-kernel profiles."""
+    import torch
+
+    import __graft_entry__ as ge
+    import gen
+    ge.build()
+    import paper_2006_16767_gb300 as asv
+    dev = torch.device("cuda")
+    if case in ("stencil128", "rmat20"):
+        if case == "stencil128":
+            rp, c, v, _ = gen.stencil27(128, gen.config_seed(5))
+            m = n = 128 ** 3
+        else:
+            rp, c = gen.rmat(20, 16, gen.config_seed(2))
+            m = n = 1 << 20
+            v = np.ones(len(c), np.float32)
+        A = asv.Matrix(m, n, *[torch.from_numpy(a).to(dev) for a in (rp, c, v)])
+        x = torch.from_numpy(gen.uniform(n, -1, 1, 1, 0, np.float32)).to(dev)
+        y = torch.empty(m, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            A.spmv(x, y, kernel=kernel)
+    elif case == "zipf_batched":
+        m, n, B = 200_000, 131_072, 1024
+        rp, c, v = gen.lognormal_zipf(m, n, np.log(40), 1.0, 1.2, gen.config_seed(3))
+        xrp, xc, xv = gen.lognormal_zipf(B, n, np.log(40), 1.0, 1.2, gen.config_seed(3) + 100)
+        A = asv.Matrix(m, n, *[torch.from_numpy(a).to(dev) for a in (rp, c, v)])
+        args_ = [torch.from_numpy(a).to(dev) for a in (xrp.astype(np.int64), xc, xv)]
+        for _ in range(3):
+            A.spmspv_batched(*args_)
+    elif case == "bernoulli_backward":
+        m = n = 8192
+        B = 64
+        rp, c, v = gen.bernoulli(m, n, 0.05, 0.02, gen.config_seed(4))
+        A = asv.Matrix(m, n, *[torch.from_numpy(a).to(dev) for a in (rp, c, v)])
+        X = torch.from_numpy(gen.halfnormal(B * n, 1.0, 5).reshape(B, n)).to(dev)
+        dY = torch.from_numpy(gen.uniform(B * m, -1, 1, 6, 0, np.float32).reshape(B, m)).to(dev)
+        for _ in range(3):
+            A.backward(X, dY)
+    torch.cuda.synchronize()
+    print("ok", case, kernel)
+
+
+def density_sweep(which, out_path, reps=5):
+    """Every candidate and the selector over x densities (x as a list with a
+    dense y, and x dense with a dense y); L2 flushed before every timing."""
+    import torch
+
+    import __graft_entry__ as ge
+    import gen
+    ge.build()
+    import paper_2006_16767_gb300 as asv
+    dev = torch.device("cuda")
+    if which == "stencil256":
+        rp, c, v, _ = gen.stencil27(256, gen.config_seed(5))
+        m = n = 256 ** 3
+        rhos = [1e-5, 1e-4, 1e-3, 1e-2, 1e-1, 1.0]
+    else:
+        rp, c = gen.rmat(22, 16, gen.config_seed(2))
+        m = n = 1 << 22
+        v = np.ones(len(c), np.float32)
+        rhos = [1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1, 0.3, 1.0]
+    nnz = len(c)
+    colcount = np.bincount(c, minlength=n)
+    A = asv.Matrix(m, n, *[torch.from_numpy(a).to(dev) for a in (rp, c, v)])
+    y = torch.empty(m, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    hbm, _ = peaks()
+    out = open(out_path, "w")
+    for rho in rhos:
+        k = max(1, int(round(rho * n)))
+        idx, val = gen.sparse_x(n, k, gen.config_seed(5), 11, np.float32)
+        it, vt = torch.from_numpy(idx).to(dev), torch.from_numpy(val).to(dev)
+        cnt = torch.tensor([len(idx)], dtype=torch.int64, device=dev)
+        xd = torch.zeros(n, dtype=torch.float32, device=dev)
+        xd[it.long()] = vt
+        nnz_s = int(colcount[idx].sum())
+        for fmt, dense_x in (("list_x", False), ("dense_x", True)):
+            def call(kk):
+                asv.asv_spmspv(A.handle, cnt, it, vt, xd if dense_x else None, asv.ASV_OUT_DENSE, y, kernel=kk)
+            times = {}
+            for kk in ["auto"] + list(asv.KERNELS):
+                call(kk)
+                ts = []
+                for _ in range(reps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    call(kk)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                    if ts[-1] > 50 * min(times.values(), default=1e9):
+                        break
+                times[kk] = float(np.median(ts))
+            kid, _ = asv.asv_select(A.handle, cnt, it, vt, xd if dense_x else None)
+            best_k = min(asv.KERNELS, key=lambda q: times[q])
+            work = work_bytes(m, n, nnz, k, nnz_s, m, 4, 4, 4, not dense_x, False)
+            rec = {"matrix": which, "format": fmt, "rho": rho, "nnz_x": k, "nnz_s": nnz_s,
+                   "selected": asv.KERNELS[kid], "auto_ms": round(times["auto"], 4),
+                   "best": best_k, "best_ms": round(times[best_k], 4),
+                   "regret": round(times["auto"] / times[best_k], 3),
+                   "auto_GBs": round(work / (times["auto"] * 1e-3) / 1e9, 1),
+                   "auto_frac": round(work / (times["auto"] * 1e-3) / 1e9 / hbm, 4),
+                   "ms": {q: round(times[q], 4) for q in asv.KERNELS}}
+            out.write(json.dumps(rec) + "\n")
+            out.flush()
+            print(json.dumps({k2: rec[k2] for k2 in ("matrix", "format", "rho", "selected", "auto_ms", "best",
+                                                     "best_ms", "regret", "auto_frac")}), flush=True)
+    out.close()
+
+
 def run_cpu_oracle(W, max_bfs_calls, reps=1):
     """Times the oracle on a bounded sample; returns (bytes, seconds, sample text)."""
     import oracle
@@ -410,6 +522,14 @@ def main():
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and backward sections")
+    ap.add_argument("--ncu-case", default=None,
+                    help="profiling aid: run one small case (stencil128, rmat20, zipf_batched, bernoulli_backward) "
+                         "with --kernel three times and exit")
+    ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--sweep", default=None,
+                    help="x-density sweep of every candidate and the selector on stencil256 or rmat22; "
+                         "writes JSON lines to --sweep-out")
+    ap.add_argument("--sweep-out", default="sweep.jsonl")
     ap.add_argument("--direct", action="store_true",
                     help="profiling aid: run the recorded kernel choices as direct launches instead of the "
                          "selector graph (ncu cannot profile kernels inside conditional graphs)")
@@ -421,6 +541,10 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, rank, world)
+    if args.ncu_case:
+        return ncu_case(args.ncu_case, args.kernel)
+    if args.sweep:
+        return density_sweep(args.sweep, args.sweep_out)
 
     import torch
     dist = None

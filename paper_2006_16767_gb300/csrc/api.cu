@@ -208,8 +208,12 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
         CKH(cudaMemcpyAsync(H->d_trees, nodes.data(), sizeof(TreeNode) * nodes.size(), cudaMemcpyHostToDevice, s));
         CKH(cudaMemcpyAsync(H->d_roots, roots, sizeof(roots), cudaMemcpyHostToDevice, s));
     }
-    H->pull_lanes = std::min(32, std::max(2, pow2_floor(H->h_mfeat.avg_row / 3.0)));
+    // lanes per row for the sub-warp pull: about six entries per lane; fewer
+    // lanes also want two rows per group rather than four (measured on GB300)
+    H->pull_lanes = std::min(32, std::max(2, pow2_floor(H->h_mfeat.avg_row / 6.0)));
+    H->pull_unroll = H->pull_lanes <= 4 ? 2 : 4;
     if (const char* e = getenv("ASV_PULL_UNROLL")) H->pull_unroll = atoi(e) >= 4 ? 4 : 2;
+    if (const char* e = getenv("ASV_PULL_TMA")) H->pull_tma = atoi(e) != 0;
     if (const char* e = getenv("ASV_PULL_LANES")) {
         const int l = atoi(e);
         if (l == 2 || l == 4 || l == 8 || l == 16 || l == 32) H->pull_lanes = l;

@@ -50,6 +50,7 @@ struct asv_matrix_s {
     void* carry_val = nullptr;
     int pull_lanes = 8;   // lanes per row of the (sub-)warp pull kernels
     int pull_unroll = 4;  // rows per lane group loaded together (2: more resident warps)
+    bool pull_tma = true; // one-row-per-thread pull stages its spans with TMA bulk copies
     // selector tables
     asv::TreeNode* d_trees = nullptr;
     int32_t* d_roots = nullptr;

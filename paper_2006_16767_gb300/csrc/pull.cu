@@ -10,6 +10,7 @@
 // zero-invariant structural-set bitmap, which a compaction pass turns into
 // the ascending output list.
 #include "pull_common.cuh"
+#include "tma.cuh"
 
 namespace asv {
 
@@ -23,35 +24,182 @@ constexpr int kBalD = kBalB * kBalIPT;
 int64_t pull_tile_items(int32_t) { return kBalD; }
 
 // ---------------------------------------------------------------- one row per thread
+// Rows too long to stage (or a warp whose 32 rows do not fit the stage) are
+// summed straight from global memory, one row per thread.
 template <class T, bool MASK, bool SOUT>
-__global__ void __launch_bounds__(256) k_pull_thread(int64_t m, const int32_t* __restrict__ rowptr,
-                                                     const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                     PullArg a, void* ywork, uint8_t* yflag) {
+__device__ __forceinline__ typename Sr<T>::Acc row_direct(const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                          const T* __restrict__ x, const uint32_t* __restrict__ xbits,
+                                                          int32_t b, int32_t e, bool& hit) {
     using S = Sr<T>;
+    typename S::Acc acc;
+    S::acc_zero(acc);
+    for (int32_t k = b; k < e; ++k) {
+        const int32_t c = __ldg(col + k);
+        if (MASK || SOUT) {
+            const bool bit = test_bit(xbits, c);
+            hit |= bit;
+            if (MASK && !bit) continue;
+        }
+        S::acc_add(acc, S::mul(load_val(val, k), __ldg(x + c)));
+        if constexpr (S::kPattern) {
+            if (acc) break;  // OR is settled by the first hit
+        }
+    }
+    return acc;
+}
+
+// One row per thread (the paper's direct distribution). A warp owns 32
+// consecutive rows; their contiguous span of column ids (and values, unless
+// validation makes most of them unnecessary) is copied into shared memory
+// with coalesced 128-bit loads, then every lane walks its own row there.
+// With lanes on consecutive rows, the x gathers of one step land on
+// neighbouring columns for banded and mesh-like matrices, so a warp's gather
+// touches one or two cache lines instead of one per lane.
+constexpr int kStageCap = 1024;  // entries staged per warp
+constexpr int kStageWarps = 4;
+
+template <class T, bool MASK, bool SOUT, bool VEC, bool TMA>
+__global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int64_t nnz,
+                                                                  const int32_t* __restrict__ rowptr,
+                                                                  const int32_t* __restrict__ col,
+                                                                  const T* __restrict__ val, PullArg a, void* ywork,
+                                                                  uint8_t* yflag, int32_t* status) {
+    using S = Sr<T>;
+    constexpr bool kStageVals = !S::kPattern && !MASK;
+    __shared__ __align__(16) int32_t s_col[kStageWarps][kStageCap];
+    __shared__ __align__(16) T s_val[kStageVals ? kStageWarps : 1][kStageVals ? kStageCap : 1];
+    __shared__ __align__(8) uint64_t s_bar[kStageWarps];
     const PullIO p = resolve(a, ywork, SOUT);
     const T* __restrict__ x = (const T*)p.x;
     T* __restrict__ y = (T*)p.y;
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t r0 = ((int64_t)blockIdx.x * kStageWarps + w) * 32;
+    if (r0 >= m) return;
+    const int64_t i = r0 + lane;
+    const int32_t rb = __ldg(rowptr + min(i, m));
+    const int32_t span_end = __ldg(rowptr + min(r0 + 32, m));
+    const int32_t re_n = __shfl_down_sync(0xffffffffu, rb, 1);
+    const int32_t re = (lane == 31) ? span_end : re_n;
+    const int32_t s0 = __shfl_sync(0xffffffffu, rb, 0);
+    const int32_t a0 = s0 & ~3;
     bool hit = false;
-    if (i < m) {
-        typename S::Acc acc;
-        S::acc_zero(acc);
-        const int32_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
-        for (int32_t k = b; k < e; ++k) {
-            const int32_t c = __ldg(col + k);
-            if (MASK || SOUT) {
-                const bool bit = test_bit(p.xbits, c);
-                hit |= bit;
-                if (MASK && !bit) continue;
+    typename S::Acc acc;
+    if (span_end - a0 <= kStageCap) {
+        const int nchunks = (span_end - a0 + 3) >> 2;
+        int32_t* sc = s_col[w];
+        T* sv = kStageVals ? s_val[w] : nullptr;
+        // TMA path: the whole 16-byte-aligned span (cut at the last full
+        // 16-byte group of the arrays) in one bulk copy per array; the few
+        // entries after that cut, at the very end of the matrix, by plain loads
+        const int32_t bulk_end = min((int32_t)((span_end + 3) & ~3), (int32_t)(nnz & ~(int64_t)3));
+        const int32_t nbulk = TMA ? max(0, bulk_end - a0) : 0;
+        if (TMA) {
+            if (nbulk > 0 && lane == 0) {
+                mbar_init(&s_bar[w], 1);
+                const uint32_t bytes = (uint32_t)nbulk * 4u * (kStageVals && val != nullptr ? (1u + sizeof(T) / 4u) : 1u);
+                mbar_arrive_expect_tx(&s_bar[w], bytes);
+                bulk_g2s(sc, col + a0, (uint32_t)nbulk * 4u, &s_bar[w]);
+                if constexpr (kStageVals) {
+                    if (val != nullptr) bulk_g2s(sv, val + a0, (uint32_t)nbulk * (uint32_t)sizeof(T), &s_bar[w]);
+                }
             }
-            S::acc_add(acc, S::mul(load_val(val, k), __ldg(x + c)));
-            if constexpr (S::kPattern) {
-                if (acc) break;  // OR is settled by the first hit
+            __syncwarp();
+            for (int32_t k = max(a0 + nbulk, s0) + lane; k < span_end; k += 32) {
+                sc[k - a0] = __ldg(col + k);
+                if constexpr (kStageVals) {
+                    if (val != nullptr) sv[k - a0] = __ldg(val + k);
+                }
+            }
+            if (nbulk > 0 && !mbar_wait(&s_bar[w], 0)) {
+                // the copy did not land within the limit: report, wait once
+                // more (bounded) so no copy is left in flight, and give up
+                latch_status(status, ASV_ERR_TIMEOUT);
+                mbar_wait(&s_bar[w], 0);
+                return;
             }
         }
-        y[i] = S::part_T(S::acc_part(acc));
+        // four chunks per lane in flight at a time: loads first, then stores
+        for (int q0 = 0; q0 < (TMA ? 0 : nchunks); q0 += 128) {
+            int4 cb[4];
+            int4 vb[4];
+            double2 vd[4][2];
+            bool full[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + lane + 32 * u;
+                const int32_t base = a0 + 4 * q;
+                full[u] = VEC && q < nchunks && (int64_t)base + 4 <= nnz;
+                if (full[u]) {
+                    cb[u] = __ldg(reinterpret_cast<const int4*>(col + base));
+                    if constexpr (kStageVals) {
+                        if (val != nullptr) {
+                            if constexpr (sizeof(T) == 4) {
+                                vb[u] = __ldg(reinterpret_cast<const int4*>(val + base));
+                            } else {
+                                vd[u][0] = __ldg(reinterpret_cast<const double2*>(val + base));
+                                vd[u][1] = __ldg(reinterpret_cast<const double2*>(val + base + 2));
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + lane + 32 * u;
+                if (q >= nchunks) continue;
+                const int32_t base = a0 + 4 * q;
+                if (full[u]) {
+                    *reinterpret_cast<int4*>(sc + 4 * q) = cb[u];
+                    if constexpr (kStageVals) {
+                        if (val != nullptr) {
+                            if constexpr (sizeof(T) == 4) {
+                                *reinterpret_cast<int4*>(sv + 4 * q) = vb[u];
+                            } else {
+                                *reinterpret_cast<double2*>(sv + 4 * q) = vd[u][0];
+                                *reinterpret_cast<double2*>(sv + 4 * q + 2) = vd[u][1];
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if ((int64_t)base + t < nnz) {
+                            sc[4 * q + t] = __ldg(col + base + t);
+                            if constexpr (kStageVals) {
+                                if (val != nullptr) sv[4 * q + t] = __ldg(val + base + t);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        S::acc_zero(acc);
+        if (i < m) {
+            for (int32_t k = rb; k < re; ++k) {
+                const int32_t c = sc[k - a0];
+                if (MASK || SOUT) {
+                    const bool bit = test_bit(p.xbits, c);
+                    hit |= bit;
+                    if (MASK && !bit) continue;
+                }
+                T v;
+                if constexpr (kStageVals) v = (val != nullptr) ? sv[k - a0] : S::one();
+                else v = load_val(val, k);
+                S::acc_add(acc, S::mul(v, __ldg(x + c)));
+                if constexpr (S::kPattern) {
+                    if (acc) break;
+                }
+            }
+        }
+    } else {
+        if (i < m) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, re, hit);
+        else S::acc_zero(acc);
     }
-    if (SOUT && hit) yflag[i] = 1;
+    if (i < m) {
+        y[i] = S::part_T(S::acc_part(acc));
+        if (SOUT && hit) yflag[i] = 1;
+    }
 }
 
 // ---------------------------------------------------------------- merge-path balanced
@@ -278,7 +426,19 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     const int64_t cap = (int64_t)H->num_sms * 16;
     const bool vec = ((uintptr_t)H->col % 16 == 0) && ((uintptr_t)H->val % 16 == 0);
     if (dist == 0) {
-        if (m > 0) k_pull_thread<T, MASK, SOUT><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, H->rowptr, H->col, val, a, ywork, yt);
+        const unsigned g = (unsigned)((m + 32 * kStageWarps - 1) / (32 * kStageWarps));
+        int32_t* st = H->ws.status;
+        if (m > 0) {
+            if (vec && H->pull_tma)
+                k_pull_thread<T, MASK, SOUT, true, true><<<g, 32 * kStageWarps, 0, s>>>(m, H->nnz, H->rowptr, H->col,
+                                                                                      val, a, ywork, yt, st);
+            else if (vec)
+                k_pull_thread<T, MASK, SOUT, true, false><<<g, 32 * kStageWarps, 0, s>>>(m, H->nnz, H->rowptr, H->col,
+                                                                                       val, a, ywork, yt, st);
+            else
+                k_pull_thread<T, MASK, SOUT, false, false><<<g, 32 * kStageWarps, 0, s>>>(m, H->nnz, H->rowptr, H->col,
+                                                                                        val, a, ywork, yt, st);
+        }
     } else if (dist == 1) {
         launch_pull_warp_dtype<T, MASK, SOUT>(H, a, vec, s);
     } else {

@@ -10,6 +10,9 @@
 
 namespace asv {
 
+static_assert(kTreeNodesF32 <= kMaxTreeNodes && kTreeNodesBool <= kMaxTreeNodes,
+              "compiled-in trees exceed the selector's node table");
+
 SelectArg select_arg(asv_matrix_s* H, unsigned long long cond) {
     SelectArg sa;
     sa.mf = H->d_mfeat;

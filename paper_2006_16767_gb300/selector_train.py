@@ -215,8 +215,11 @@ def _fit_one(X, y, seed):
         return None, leaf, 1.0
     Xtr, Xte, ytr, yte = train_test_split(X, y, test_size=0.3, random_state=seed)
     folds = max(2, min(5, int(np.bincount(ytr).min()) if len(set(ytr.tolist())) > 1 else 2))
+    # max_leaf_nodes keeps the 20 trees of a value type within the selector's
+    # 1024-node table (at most 47 nodes each)
     gs = GridSearchCV(DecisionTreeClassifier(random_state=seed),
-                      {"max_depth": list(range(1, 11)), "class_weight": [None, "balanced"]}, cv=folds)
+                      {"max_depth": list(range(1, 11)), "class_weight": [None, "balanced"],
+                       "max_leaf_nodes": [8, 16, 24]}, cv=folds)
     gs.fit(Xtr, ytr)
     acc = float(gs.score(Xte, yte))
     clf = DecisionTreeClassifier(random_state=seed, **gs.best_params_).fit(X, y)
