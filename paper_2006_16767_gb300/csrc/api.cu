@@ -345,17 +345,21 @@ static asv_status launch_auto(asv_matrix_s* H, const DescInit& di, int om, cudaS
     const int xs = di.x_sparse;
     asv_status st = build_auto_graph(H, xs, om, di);
     if (st != ASV_OK) return st;
-    FeatLaunch fl;
-    feature_launch(H, di, select_arg(H, H->cond[xs][om]), fl);
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof(kp));
-    kp.func = fl.func;
-    kp.gridDim = fl.grid;
-    kp.blockDim = fl.block;
-    kp.sharedMemBytes = 0;
-    kp.kernelParams = fl.args;
-    kp.extra = nullptr;
-    CK(cudaGraphExecKernelNodeSetParams(H->gexec[xs][om], H->feat_node[xs][om], &kp));
+    // the feature node's arguments change only when the call's pointers do
+    if (memcmp(&H->last_di[xs][om], &di, sizeof(di)) != 0) {
+        FeatLaunch fl;
+        feature_launch(H, di, select_arg(H, H->cond[xs][om]), fl);
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.func = fl.func;
+        kp.gridDim = fl.grid;
+        kp.blockDim = fl.block;
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = fl.args;
+        kp.extra = nullptr;
+        CK(cudaGraphExecKernelNodeSetParams(H->gexec[xs][om], H->feat_node[xs][om], &kp));
+        H->last_di[xs][om] = di;
+    }
     CK(cudaGraphLaunch(H->gexec[xs][om], s));
     return ASV_OK;
 }

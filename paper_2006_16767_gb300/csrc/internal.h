@@ -8,6 +8,27 @@
 #include "common.cuh"
 #include "selector.cuh"
 
+namespace asv {
+// Per-call arguments of the vector-feature pass (written into the call descriptor).
+struct DescInit {
+    const void* x_dense;
+    const uint32_t* xbits;
+    const int32_t* xidx;
+    const void* xval;
+    void* y;
+    int32_t* yidx;
+    void* yval;
+    int64_t* nnz_y;
+    int64_t y_cap;
+    const void* user_x_dense;
+    const int32_t* user_xidx;
+    const void* user_xval;
+    const int64_t* user_nnz_x;
+    int32_t out_mode;
+    int32_t x_sparse;
+};
+}  // namespace asv
+
 // Workspaces of the batched forward/backward forms, grown on demand.
 struct BatchWs {
     uint32_t* keys[2] = {nullptr, nullptr};
@@ -63,6 +84,7 @@ struct asv_matrix_s {
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaGraphNode_t feat_node[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     unsigned long long cond[2][2] = {{0, 0}, {0, 0}};
+    asv::DescInit last_di[2][2];  // arguments the feature node of each graph was last given
     cudaStream_t cap_stream = nullptr;
     int G = 0;  // fixed grid of the scan / sort / compaction primitives
     BatchWs bws;
@@ -88,23 +110,6 @@ void scan_excl(const int32_t* in, int32_t* out, int64_t n_h, const int64_t* n_d,
                bool write_total, cudaStream_t s);
 
 // vector.cu -- per call
-struct DescInit {
-    const void* x_dense;
-    const uint32_t* xbits;
-    const int32_t* xidx;
-    const void* xval;
-    void* y;
-    int32_t* yidx;
-    void* yval;
-    int64_t* nnz_y;
-    int64_t y_cap;
-    const void* user_x_dense;
-    const int32_t* user_xidx;
-    const void* user_xval;
-    const int64_t* user_nnz_x;
-    int32_t out_mode;
-    int32_t x_sparse;
-};
 // A feature-pass launch whose argument storage lives in the struct.
 struct FeatLaunch {
     void* func;

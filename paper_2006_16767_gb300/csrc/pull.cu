@@ -84,7 +84,9 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
     const int32_t a0 = s0 & ~3;
     bool hit = false;
     typename S::Acc acc;
-    if (span_end - a0 <= kStageCap) {
+    // Boolean rows stop at their first hit, so copying whole spans would read
+    // indices the direct walk never touches: they take the direct path
+    if (!S::kPattern && span_end - a0 <= kStageCap) {
         const int nchunks = (span_end - a0 + 3) >> 2;
         int32_t* sc = s_col[w];
         T* sv = kStageVals ? s_val[w] : nullptr;
@@ -176,7 +178,21 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
         __syncwarp();
         S::acc_zero(acc);
         if (i < m) {
-            for (int32_t k = rb; k < re; ++k) {
+            int32_t k = rb;
+            if constexpr (!MASK && !SOUT && kStageVals) {
+                // four gathers in flight per lane before their products are added
+                for (; k + 4 <= re; k += 4) {
+                    const int32_t c0 = sc[k - a0], c1 = sc[k + 1 - a0], c2 = sc[k + 2 - a0], c3 = sc[k + 3 - a0];
+                    const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+                    const T v0 = val ? sv[k - a0] : S::one(), v1 = val ? sv[k + 1 - a0] : S::one();
+                    const T v2 = val ? sv[k + 2 - a0] : S::one(), v3 = val ? sv[k + 3 - a0] : S::one();
+                    S::acc_add(acc, S::mul(v0, x0));
+                    S::acc_add(acc, S::mul(v1, x1));
+                    S::acc_add(acc, S::mul(v2, x2));
+                    S::acc_add(acc, S::mul(v3, x3));
+                }
+            }
+            for (; k < re; ++k) {
                 const int32_t c = sc[k - a0];
                 if (MASK || SOUT) {
                     const bool bit = test_bit(p.xbits, c);

@@ -167,9 +167,11 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
                      di, n, nnz, status, sa);
 }
 
+// Few blocks per SM: every block of the feature pass ends with atomics on
+// the same counters and ticket, so thousands of blocks would serialise there.
 static int feat_grid(asv_matrix_s* H, int64_t items) {
     const int64_t g = (items + 255) / 256;
-    return (int)max((int64_t)1, min(g, (int64_t)H->num_sms * 8));
+    return (int)max((int64_t)1, min(g, (int64_t)H->num_sms * 2));
 }
 
 template <class T>
@@ -199,7 +201,7 @@ void feature_launch(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, Fe
             default: fl.func = feat_dense_func<bool8>(); break;
         }
         const int64_t nsuper = (H->n + 127) / 128;
-        fl.grid = dim3((unsigned)max((int64_t)1, min((nsuper + 7) / 8, (int64_t)H->num_sms * 32)));
+        fl.grid = dim3((unsigned)max((int64_t)1, min((nsuper + 7) / 8, (int64_t)H->num_sms * 4)));
         fl.xptr = di.user_x_dense;
         fl.xbits = H->ws.xbits_dense;
         void* a[11] = {&fl.xptr, &fl.n, &fl.colptr, &fl.xbits, &fl.counters, &fl.ticket, &fl.desc, &fl.di,

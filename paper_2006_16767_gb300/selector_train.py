@@ -64,11 +64,11 @@ def corpus():
     import gen
     s = 7919
     items = []
-    for g in (48, 96, 128, 160, 192):
+    for g in (48, 96, 128, 160, 192, 224):
         items.append((f"stencil27_{g}", lambda g=g: gen.stencil27(g, s + g)[:3] + (g ** 3,)))
     for g in (256, 512, 1024, 2048):
         items.append((f"laplace2d_{g}", lambda g=g: gen.laplace2d(g) + (g * g,)))
-    for sc, ef in ((14, 16), (16, 8), (16, 16), (17, 32), (18, 8), (19, 16), (20, 8), (20, 16), (21, 16)):
+    for sc, ef in ((14, 16), (16, 8), (16, 16), (17, 32), (18, 8), (19, 16), (20, 8), (20, 16), (21, 16), (22, 16)):
         items.append((f"rmat_{sc}_{ef}", lambda sc=sc, ef=ef: rmat_vals(sc, ef, s + sc * 7 + ef)))
     items.append(("rmat_er_18", lambda: rmat_vals(18, 16, s + 5, a=0.25, b=0.25, c=0.25)))
     items.append(("rmat_mild_19", lambda: rmat_vals(19, 16, s + 6, a=0.45, b=0.22, c=0.22)))
