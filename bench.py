@@ -291,7 +291,9 @@ def bench_batched(asv, torch, dev, reps=3):
     import gen
     m, n, B = 1_000_000, 131_072, 4096
     rp, c, v = gen.lognormal_zipf(m, n, np.log(40), 1.0, 1.2, gen.config_seed(3))
-    xrp_all, xc_all, xv_all = gen.lognormal_zipf(65_536, n, np.log(40), 1.0, 1.2, gen.config_seed(3) + 100)
+    # the vectors come from a second matrix over the same feature space (same popular columns)
+    xrp_all, xc_all, xv_all = gen.lognormal_zipf(65_536, n, np.log(40), 1.0, 1.2, gen.config_seed(3) + 100,
+                                                 perm_seed=gen.config_seed(3))
     pick = gen.randint(B, 65_536, gen.config_seed(3), 1)
     lens = (xrp_all[pick + 1] - xrp_all[pick]).astype(np.int64)
     xptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
@@ -402,7 +404,8 @@ def ncu_case(case, kernel):
     elif case == "zipf_batched":
         m, n, B = 200_000, 131_072, 1024
         rp, c, v = gen.lognormal_zipf(m, n, np.log(40), 1.0, 1.2, gen.config_seed(3))
-        xrp, xc, xv = gen.lognormal_zipf(B, n, np.log(40), 1.0, 1.2, gen.config_seed(3) + 100)
+        xrp, xc, xv = gen.lognormal_zipf(B, n, np.log(40), 1.0, 1.2, gen.config_seed(3) + 100,
+                                         perm_seed=gen.config_seed(3))
         A = asv.Matrix(m, n, *[torch.from_numpy(a).to(dev) for a in (rp, c, v)])
         args_ = [torch.from_numpy(a).to(dev) for a in (xrp.astype(np.int64), xc, xv)]
         for _ in range(3):

@@ -87,7 +87,7 @@ def _get():
             lib.gen_stencil27.restype = i64
             lib.gen_rmat.argtypes = [ctypes.c_int32, ctypes.c_int32, d, d, d, u64, i32pp, i32pp]
             lib.gen_rmat.restype = i64
-            lib.gen_lognormal_zipf.argtypes = [i64, i64, d, d, d, u64, i32pp, i32pp, f32pp]
+            lib.gen_lognormal_zipf.argtypes = [i64, i64, d, d, d, u64, u64, i32pp, i32pp, f32pp]
             lib.gen_lognormal_zipf.restype = i64
             lib.gen_bernoulli.argtypes = [i64, i64, d, d, u64, i32pp, i32pp, f32pp]
             lib.gen_bernoulli.restype = i64
@@ -153,13 +153,16 @@ def rmat(scale: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19):
     return _take(rp, n + 1, np.int32), _take(cp, nnz, np.int32)
 
 
-def lognormal_zipf(m: int, n: int, mu: float, sigma: float, s: float, seed: int):
-    """Rows of lognormal length, Zipf(s) column ids: (rowptr, col, val[f32])."""
+def lognormal_zipf(m: int, n: int, mu: float, sigma: float, s: float, seed: int, perm_seed: int | None = None):
+    """Rows of lognormal length, Zipf(s) column ids: (rowptr, col, val[f32]).
+    perm_seed fixes the rank -> column-id map (default: seed); matrices over
+    the same feature space share it."""
     lib = _get()
     rp = ctypes.POINTER(ctypes.c_int32)()
     cp = ctypes.POINTER(ctypes.c_int32)()
     vp = ctypes.POINTER(ctypes.c_float)()
-    nnz = lib.gen_lognormal_zipf(m, n, mu, sigma, s, seed, ctypes.byref(rp), ctypes.byref(cp), ctypes.byref(vp))
+    ps = seed if perm_seed is None else perm_seed
+    nnz = lib.gen_lognormal_zipf(m, n, mu, sigma, s, seed, ps, ctypes.byref(rp), ctypes.byref(cp), ctypes.byref(vp))
     return _take(rp, m + 1, np.int32), _take(cp, nnz, np.int32), _take(vp, nnz, np.float32)
 
 

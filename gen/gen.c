@@ -249,10 +249,12 @@ int64_t gen_rmat(int32_t scale, int32_t edge_factor, double a, double b, double 
  * m rows over n columns. Row length L_i = round(exp(mu + sigma*N(0,1)))
  * clamped to [1, n]; each of the L_i draws picks a column rank r in 1..n with
  * P(r) ~ r^(-s) (inverse CDF on the exact finite Zipf distribution), mapped to
- * a column id by a seeded permutation. Duplicates within a row are dropped.
- * Values are U(0, 1] floats. Output malloc'ed; free with gen_free. Returns nnz. */
+ * a column id by a permutation seeded with perm_seed (matrices sharing a
+ * feature space share it, so their popular columns coincide). Duplicates
+ * within a row are dropped. Values are U(0, 1] floats. Output malloc'ed;
+ * free with gen_free. Returns nnz. */
 int64_t gen_lognormal_zipf(int64_t m, int64_t n, double mu, double sigma, double s,
-                           uint64_t seed, int32_t** rowptr_out, int32_t** col_out,
+                           uint64_t seed, uint64_t perm_seed, int32_t** rowptr_out, int32_t** col_out,
                            float** val_out) {
     double* cdf = (double*)malloc(sizeof(double) * (size_t)n);
     double acc = 0.0;
@@ -260,7 +262,7 @@ int64_t gen_lognormal_zipf(int64_t m, int64_t n, double mu, double sigma, double
     for (int64_t r = 0; r < n; ++r) cdf[r] /= acc;
     cdf[n - 1] = 1.0;
     int32_t* idmap = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-    permutation(n, seed, 5, idmap);
+    permutation(n, perm_seed, 5, idmap);
     int64_t* rp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m + 1));
     rp[0] = 0;
     for (int64_t i = 0; i < m; ++i) {

@@ -200,7 +200,8 @@ asv_status asv_compact(asv_matrix A, const void* d_x_dense, int32_t* d_idx, void
 /* ---------------------------------------------------------------- batched */
 
 /* Tiling of the batched product: rows of A per work item (4, 8 or 16) and
- * vectors per group (rows * vectors * 4 bytes of shared memory, <= 200 KB). */
+ * vectors per group (rows * (vectors + 1) * 8 bytes of shared memory, one
+ * compensated FP32 pair per output, <= 200 KB; larger asks give ASV_ERR_ARG). */
 typedef struct {
     int32_t rows_per_tile;
     int32_t vectors_per_group;

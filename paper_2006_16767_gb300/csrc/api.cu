@@ -516,8 +516,8 @@ static asv_status batched_args(asv_matrix A, int32_t B, int64_t max_entries, con
 
 static bool tune_ok(const asv_tune& t, int32_t B) {
     const bool r_ok = t.rows_per_tile == 4 || t.rows_per_tile == 8 || t.rows_per_tile == 16;
-    return r_ok && t.vectors_per_group >= 1 && (int64_t)t.rows_per_tile * t.vectors_per_group * 4 <= 200 * 1024 &&
-           B >= 0;
+    return r_ok && t.vectors_per_group >= 1 &&
+           (int64_t)t.rows_per_tile * (t.vectors_per_group + 1) * 8 <= 200 * 1024 && B >= 0;
 }
 
 extern "C" asv_status asv_spmspv_batched(asv_matrix A, int32_t B, int64_t max_entries, const int64_t* d_xptr,
@@ -571,8 +571,8 @@ extern "C" asv_status asv_autotune_batched(asv_matrix A, int32_t B, int64_t max_
             fclose(f);
         }
     }
-    const asv_tune cands[] = {{4, 4096}, {4, 2048}, {8, 512}, {8, 1024}, {8, 2048}, {8, 4096}, {16, 256},
-                              {16, 512}, {16, 1024}, {16, 2048}};
+    const asv_tune cands[] = {{4, 4096}, {4, 2048}, {8, 512}, {8, 1024}, {8, 2048}, {4, 1024}, {16, 256},
+                              {16, 512}, {16, 1024}, {16, 1536}};
     float best = 1e30f;
     asv_tune bt{A->tune_R, A->tune_GB};
     cudaEvent_t e0, e1;

@@ -9,9 +9,14 @@
 // items (a tile of R consecutive rows of A) x (a group of GB vectors) from an
 // atomic queue. Warp w owns row i0+w of the tile: for every entry (j, a) of
 // that row it walks the part of column j's list that falls in the vector
-// group and adds a*x_b[j] into a shared-memory tile acc[b][w]. Lanes of one
-// step hold distinct vector ids and a warp's columns are taken in order, so
-// the accumulation needs no atomics and is deterministic. Each column of A
+// group and adds a*x_b[j] into a shared-memory tile acc[w][b] of
+// compensated (Neumaier) sums, one (sum, correction) float pair per output
+// (row stride GB+1 pairs, so that the lanes of one step, which hold
+// ascending vector ids, touch consecutive 8-byte words). An output can sum
+// hundreds of products (the longest rows against the longest vectors of a
+// Zipf batch), so a plain FP32 sum would not keep the 2e-6 relative bound.
+// Lanes of one step hold distinct vector ids and a warp's columns are taken
+// in order, so the accumulation needs no atomics and is deterministic. Each column of A
 // is read once per vector group instead of once per vector, and every
 // element of Y is written exactly once, with R consecutive values per vector.
 //
@@ -138,7 +143,7 @@ __global__ void __launch_bounds__(R * 32) k_batched_fwd(const BatchDesc* __restr
                                                         const int32_t* __restrict__ cptr,
                                                         const uint64_t* __restrict__ pay, unsigned long long* queue,
                                                         unsigned int* ticket) {
-    extern __shared__ float acc[];  // [GB][R]
+    extern __shared__ float2 acc[];  // [R][GB + 1] of (sum, correction)
     __shared__ long long s_item;
     __shared__ bool s_last;
     float* __restrict__ Y = bd->Y;
@@ -155,7 +160,8 @@ __global__ void __launch_bounds__(R * 32) k_batched_fwd(const BatchDesc* __restr
         const int32_t g = (int32_t)(item % ngroups);
         const uint32_t b0 = (uint32_t)g * GB;
         const int32_t nb = min(GB, B - (int32_t)b0);
-        for (int e = threadIdx.x; e < GB * R; e += blockDim.x) acc[e] = 0.0f;
+        const int GBp = GB + 1;
+        for (int e = threadIdx.x; e < GBp * R; e += blockDim.x) acc[e] = make_float2(0.0f, 0.0f);
         __syncthreads();
         const int64_t i = tile * R + w;
         if (i < m) {
@@ -171,7 +177,12 @@ __global__ void __launch_bounds__(R * 32) k_batched_fwd(const BatchDesc* __restr
                 for (int32_t q = lo + lane; q < hi; q += 32) {
                     const uint64_t pv = __ldg(pay + q);
                     const uint32_t b = (uint32_t)(pv >> 32) - b0;
-                    acc[b * R + w] = __fadd_rn(acc[b * R + w], __fmul_rn(a, __uint_as_float((uint32_t)pv)));
+                    KahanF k;
+                    const float2 cur = acc[w * GBp + b];
+                    k.s = cur.x;
+                    k.c = cur.y;
+                    k.add(__fmul_rn(a, __uint_as_float((uint32_t)pv)));
+                    acc[w * GBp + b] = make_float2(k.s, k.c);
                 }
                 __syncwarp();
             }
@@ -182,7 +193,10 @@ __global__ void __launch_bounds__(R * 32) k_batched_fwd(const BatchDesc* __restr
         const int rr = (int)min((int64_t)R, m - r0);
         for (int e = threadIdx.x; e < nb * R; e += blockDim.x) {
             const int b = e / R, r = e % R;
-            if (r < rr) Y[(int64_t)(b0 + b) * m + r0 + r] = acc[b * R + r];
+            if (r < rr) {
+                const float2 sc = acc[r * GBp + b];
+                Y[(int64_t)(b0 + b) * m + r0 + r] = __fadd_rn(sc.x, sc.y);
+            }
         }
         __syncthreads();
     }
@@ -320,7 +334,7 @@ static cudaError_t batch_workspace(asv_matrix_s* H, int64_t entries, int32_t B) 
 
 static void fwd_kernel(asv_matrix_s* H, int32_t B, int R, int GB, const uint64_t* pay, cudaStream_t s) {
     BatchWs& bw = H->bws;
-    const size_t shm = (size_t)R * GB * 4;
+    const size_t shm = (size_t)R * (GB + 1) * sizeof(float2);
     int per_sm = 1;
     unsigned long long* q = (unsigned long long*)bw.queue;
     unsigned int* tk = (unsigned int*)(bw.queue + 1);
