@@ -63,14 +63,25 @@ def work_bytes(m, n, nnz, nnz_x, nnz_s, nnz_y, s_v, s_x, s_y, x_sparse, sparse_o
                for k in (0, 3, 6))
 
 
-def launches(kid, x_sparse, sparse_out, auto=True):
+LONG_ROW, LONG_SEG = 256, 4096  # the library's long-row split (rows > 256 entries, segments of 4096)
+
+
+def long_row_launches(rowptr):
+    """Extra launches of the thread and sub-warp pull kernels on a matrix with
+    long rows: the warp-per-segment pass, plus its fix-up for rows of several
+    segments."""
+    deg = np.diff(rowptr)
+    return int((deg > LONG_ROW).any()) + int((deg > LONG_SEG).any())
+
+
+def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0):
     """Kernel launches of one call (mirrors the library's dispatch)."""
     c = 1 + (1 if auto else 0)  # feature pass (+ selector node)
     compaction = 3  # block counts, block-offset scan, write
     scan = 3
     if kid <= 5:
         dist = kid % 3
-        c += (2 if dist == 2 else 1)
+        c += (2 if dist == 2 else 1 + long_extra)
         if x_sparse:
             c += 2
         if sparse_out:
@@ -172,6 +183,7 @@ class Rmat22:
         self.gen_s = time.time() - t
         self.n = self.m = 1 << scale
         self.nnz = len(self.col)
+        self.long_extra = long_row_launches(self.rowptr)
         deg = np.diff(self.rowptr)
         cand = np.flatnonzero(deg > 0)
         pick = gen.randint(roots, len(cand), gen.config_seed(2), stream=7)
@@ -212,13 +224,13 @@ class Rmat22:
                 args_ = (self.m, self.n, self.nnz, c["nnz_x"], c["nnz_s"], c["nnz_y"], 0, 0, 0, True, True)
                 c["bytes"] = work_bytes(*args_)
                 c["kbytes"] = useful_bytes(c["kid"], *args_)
-                c["launches"] = launches(c["kid"], True, True)
+                c["launches"] = launches(c["kid"], True, True, long_extra=self.long_extra)
             else:
                 c["nnz_y"] = self.m
                 args_ = (self.m, self.n, self.nnz, c["nnz_x"], c["nnz_s"], self.m, 4, 4, 4, False, False)
                 c["bytes"] = work_bytes(*args_)
                 c["kbytes"] = useful_bytes(c["kid"], *args_)
-                c["launches"] = launches(c["kid"], False, False)
+                c["launches"] = launches(c["kid"], False, False, long_extra=self.long_extra)
 
     def run_step(self, events=None, direct=False):
         """One step. direct=True replays the selector's recorded choices as

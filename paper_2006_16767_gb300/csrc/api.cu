@@ -201,6 +201,7 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     CKH(build_csc(H, s));
     CKH(build_features(H, s));  // synchronises
     CKH(build_partition(H, s));
+    CKH(build_long_rows(H, s));  // synchronises
     {
         std::vector<TreeNode> nodes;
         int32_t roots[kRootsLen];

@@ -192,6 +192,13 @@ struct TreeNode {
 };
 constexpr int kMaxTreeNodes = 1024;
 
+// Rows longer than kLongRow entries are taken out of the one-row-per-thread
+// and sub-warp pull kernels and summed by a warp per segment of at most
+// kLongSeg entries (a list built once per matrix): a thread walking a
+// power-law hub row of 10^5 entries alone would serialise the whole call.
+constexpr int kLongRow = 256;
+constexpr int kLongSeg = 4096;
+
 // Handle workspaces, passed by value to the kernels that use them.
 struct Ws {
     uint32_t* xbits_dense;   // n bits, rewritten by every dense-x feature pass

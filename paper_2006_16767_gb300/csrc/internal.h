@@ -69,6 +69,18 @@ struct asv_matrix_s {
     int64_t ntiles = 0;
     int32_t* carry_row = nullptr;
     void* carry_val = nullptr;
+    // rows over kLongRow entries, cut into segments of at most kLongSeg:
+    // segment s covers [seg_beg[s], min(seg_beg[s] + kLongSeg, rowptr[row+1]))
+    // of row seg_row[s]; a row's segments are consecutive and ascending.
+    // Rows with several segments are listed in multi_row with their first
+    // segment in multi_base; their partial sums go to long_part / long_hit.
+    int32_t* seg_row = nullptr;
+    int32_t* seg_beg = nullptr;
+    uint64_t* long_part = nullptr;
+    uint8_t* long_hit = nullptr;
+    int32_t* multi_row = nullptr;
+    int32_t* multi_base = nullptr;
+    int64_t nseg = 0, nmulti = 0;
     int pull_lanes = 8;   // lanes per row of the (sub-)warp pull kernels
     int pull_unroll = 4;  // rows per lane group loaded together (2: more resident warps)
     bool pull_tma = true; // one-row-per-thread pull stages its spans with TMA bulk copies
@@ -101,6 +113,8 @@ const char* kernel_name(int k);
 cudaError_t build_csc(asv_matrix_s* H, cudaStream_t s);
 cudaError_t build_features(asv_matrix_s* H, cudaStream_t s);
 cudaError_t build_partition(asv_matrix_s* H, cudaStream_t s);
+// counts the long rows (synchronises), allocates and fills their segment list
+cudaError_t build_long_rows(asv_matrix_s* H, cudaStream_t s);
 int64_t pull_tile_items(int32_t dtype);
 cudaError_t validate_csr(asv_matrix_s* H, cudaStream_t s, int32_t* d_flag);
 cudaError_t regather_values(asv_matrix_s* H, cudaStream_t s);

@@ -261,6 +261,80 @@ cudaError_t build_partition(asv_matrix_s* H, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- long rows
+// Counts segments and multi-segment rows of the rows longer than kLongRow.
+__global__ void k_long_count(const int32_t* __restrict__ rowptr, int64_t m, unsigned long long* cnt) {
+    __shared__ unsigned long long sm[8 + 1];
+    unsigned long long ns = 0, nm = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t len = rowptr[i + 1] - rowptr[i];
+        if (len > kLongRow) {
+            const int32_t k = (len + kLongSeg - 1) / kLongSeg;
+            ns += (unsigned long long)k;
+            nm += k > 1;
+        }
+    }
+    ns = block_reduce_sum<256>(ns, sm);
+    __syncthreads();
+    nm = block_reduce_sum<256>(nm, sm);
+    if (threadIdx.x == 0) {
+        if (ns) atomicAdd(cnt, ns);
+        if (nm) atomicAdd(cnt + 1, nm);
+    }
+}
+
+// Each long row reserves its consecutive run of segment slots with one atomic,
+// so a row's segments stay together and in order whatever the slot order.
+__global__ void k_long_fill(const int32_t* __restrict__ rowptr, int64_t m, int32_t* seg_row, int32_t* seg_beg,
+                            int32_t* multi_row, int32_t* multi_base, unsigned long long* cursor) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t rb = rowptr[i], len = rowptr[i + 1] - rb;
+        if (len <= kLongRow) continue;
+        const int32_t k = (len + kLongSeg - 1) / kLongSeg;
+        const int32_t base = (int32_t)atomicAdd(cursor, (unsigned long long)k);
+        for (int32_t t = 0; t < k; ++t) {
+            seg_row[base + t] = (int32_t)i;
+            seg_beg[base + t] = rb + t * kLongSeg;
+        }
+        if (k > 1) {
+            const int32_t q = (int32_t)atomicAdd(cursor + 1, 1ull);
+            multi_row[q] = (int32_t)i;
+            multi_base[q] = base;
+        }
+    }
+}
+
+cudaError_t build_long_rows(asv_matrix_s* H, cudaStream_t s) {
+    H->nseg = H->nmulti = 0;
+    if (H->m == 0 || H->nnz <= kLongRow) return cudaSuccess;
+    unsigned long long* d_cnt = (unsigned long long*)H->ws.counters;  // two zeroed words, restored below
+    cudaError_t e;
+    const int grid = H->num_sms * 8;
+    k_long_count<<<grid, 256, 0, s>>>(H->rowptr, H->m, d_cnt);
+    unsigned long long h[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(h), s)) != cudaSuccess) return e;
+    if (h[0] == 0) return cudaSuccess;
+    auto grab = [&](void** p, size_t bytes) -> cudaError_t {
+        cudaError_t r = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+        if (r == cudaSuccess) H->allocs.push_back(*p);
+        return r;
+    };
+    const size_t ns = (size_t)h[0], nm = (size_t)h[1];
+    if ((e = grab((void**)&H->seg_row, 4 * ns)) != cudaSuccess) return e;
+    if ((e = grab((void**)&H->seg_beg, 4 * ns)) != cudaSuccess) return e;
+    if ((e = grab((void**)&H->long_part, 8 * ns)) != cudaSuccess) return e;
+    if ((e = grab((void**)&H->long_hit, ns)) != cudaSuccess) return e;
+    if ((e = grab((void**)&H->multi_row, 4 * nm)) != cudaSuccess) return e;
+    if ((e = grab((void**)&H->multi_base, 4 * nm)) != cudaSuccess) return e;
+    k_long_fill<<<grid, 256, 0, s>>>(H->rowptr, H->m, H->seg_row, H->seg_beg, H->multi_row, H->multi_base, d_cnt);
+    if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(h), s)) != cudaSuccess) return e;
+    H->nseg = (int64_t)ns;
+    H->nmulti = (int64_t)nm;
+    return cudaGetLastError();
+}
+
 // Tile table of the balanced pull for caller-owned arrays (used by the
 // allocation-free entry point).
 void launch_partition_raw(const int32_t* rowptr, int64_t m, int64_t nnz, int64_t ntiles, int32_t* tile_row,

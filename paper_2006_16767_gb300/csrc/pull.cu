@@ -16,6 +16,8 @@ namespace asv {
 
 template <class T, bool MASK, bool SOUT>
 void launch_pull_warp_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStream_t s);
+template <class T, bool MASK, bool SOUT>
+void launch_pull_long_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStream_t s);
 
 constexpr int kBalB = 256;   // threads per balanced tile
 constexpr int kBalIPT = 8;   // merge items per thread
@@ -48,7 +50,8 @@ __device__ __forceinline__ typename Sr<T>::Acc row_direct(const int32_t* __restr
     return acc;
 }
 
-// One row per thread (the paper's direct distribution). A warp owns 32
+// One row per thread (the paper's direct distribution) for rows of at most
+// kLongRow entries; longer rows are left to k_pull_long. A warp owns 32
 // consecutive rows; their contiguous span of column ids (and values, unless
 // validation makes most of them unnecessary) is copied into shared memory
 // with coalesced 128-bit loads, then every lane walks its own row there.
@@ -82,6 +85,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
     const int32_t re = (lane == 31) ? span_end : re_n;
     const int32_t s0 = __shfl_sync(0xffffffffu, rb, 0);
     const int32_t a0 = s0 & ~3;
+    const bool mine = i < m && re - rb <= kLongRow;  // longer rows are summed by k_pull_long
     bool hit = false;
     typename S::Acc acc;
     // Boolean rows stop at their first hit, so copying whole spans would read
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
         }
         __syncwarp();
         S::acc_zero(acc);
-        if (i < m) {
+        if (mine) {
             int32_t k = rb;
             if constexpr (!MASK && !SOUT && kStageVals) {
                 // four gathers in flight per lane before their products are added
@@ -209,10 +213,10 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
             }
         }
     } else {
-        if (i < m) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, re, hit);
+        if (mine) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, re, hit);
         else S::acc_zero(acc);
     }
-    if (i < m) {
+    if (mine) {
         y[i] = S::part_T(S::acc_part(acc));
         if (SOUT && hit) yflag[i] = 1;
     }
@@ -455,8 +459,10 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
                 k_pull_thread<T, MASK, SOUT, false, false><<<g, 32 * kStageWarps, 0, s>>>(m, H->nnz, H->rowptr, H->col,
                                                                                         val, a, ywork, yt, st);
         }
+        launch_pull_long_dtype<T, MASK, SOUT>(H, a, vec, s);
     } else if (dist == 1) {
         launch_pull_warp_dtype<T, MASK, SOUT>(H, a, vec, s);
+        launch_pull_long_dtype<T, MASK, SOUT>(H, a, vec, s);
     } else {
         if (H->ntiles == 0) return;
         using Atom = typename Sr<T>::Atom;

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256, UU >= 4 ? 4 : 6) k_pull_warp(int64_t m, i
         b[u] = __shfl_sync(0xffffffffu, rp, r);
         const int32_t nx = __shfl_sync(0xffffffffu, rp, (r + 1) & 31);
         e[u] = (r + 1 == RW) ? rp_end : nx;
+        if (e[u] - b[u] > kLongRow) valid[u] = false;  // summed by k_pull_long
         if (!valid[u]) e[u] = b[u];
     }
     Chunk<T, MASK, VEC> ch[U];
@@ -157,6 +158,125 @@ __global__ void __launch_bounds__(256, UU >= 4 ? 4 : 6) k_pull_warp(int64_t m, i
 }
 
 
+// ---------------------------------------------------------------- long rows
+// One warp per segment of a long row (at most kLongSeg entries): lane l reads
+// 16-byte chunks l, l+32, ... of the segment with 128-bit loads, the next
+// chunk's loads issued before the current chunk's gathers. Boolean segments
+// stop as soon as any lane has a hit. A row that is one segment is written
+// directly; otherwise the segment's partial goes to part[] in the push-side
+// accumulator type (FP64 for FP32 values) and k_pull_long_fixup adds a row's
+// partials in segment order.
+template <class A>
+__device__ __forceinline__ uint64_t atom_bits(A v) {
+    if constexpr (sizeof(A) == 8) return (uint64_t)__double_as_longlong(v);
+    else return (uint64_t)v;
+}
+
+template <class A>
+__device__ __forceinline__ A atom_from_bits(uint64_t b) {
+    if constexpr (sizeof(A) == 8) return __longlong_as_double((long long)b);
+    else return (A)b;
+}
+
+template <class T>
+__device__ __forceinline__ typename Sr<T>::Atom atom_combine(typename Sr<T>::Atom a, typename Sr<T>::Atom b) {
+    if constexpr (Sr<T>::kPattern) return a | b;
+    else if constexpr (sizeof(typename Sr<T>::Atom) == 8) return __dadd_rn(a, b);
+    else return a + b;
+}
+
+template <class T, bool MASK, bool SOUT, bool VEC>
+__global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, const int32_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                   const int32_t* __restrict__ seg_row,
+                                                   const int32_t* __restrict__ seg_beg, PullArg a, void* ywork,
+                                                   uint8_t* yflag, uint64_t* part, uint8_t* part_hit) {
+    using S = Sr<T>;
+    using P = typename S::Part;
+    const PullIO p = resolve(a, ywork, SOUT);
+    const T* __restrict__ x = (const T*)p.x;
+    T* __restrict__ y = (T*)p.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t sg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (sg >= nseg) return;
+    const int32_t row = __ldg(seg_row + sg);
+    const int32_t rb = __ldg(rowptr + row), re = __ldg(rowptr + row + 1);
+    const int32_t b = __ldg(seg_beg + sg);
+    const int32_t e = min(b + kLongSeg, re);
+    const int32_t a0 = b & ~3;
+    const int nsteps = (e - a0 + 127) >> 7;
+    bool hit = false;
+    typename S::Acc acc;
+    S::acc_zero(acc);
+    Chunk<T, MASK, VEC> cur;
+    chunk_load(cur, col, val, nnz, a0 + 4 * lane, b, e);
+    for (int t = 0; t < nsteps; ++t) {
+        const int32_t base = a0 + 128 * t + 4 * lane;
+        Chunk<T, MASK, VEC> nxt;
+        chunk_load(nxt, col, val, nnz, base + 128, b, e);
+        S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(cur, val, x, p.xbits, base, hit));
+        if constexpr (S::kPattern) {
+            if (__any_sync(0xffffffffu, acc != 0u)) break;  // OR is settled by the first hit
+        }
+        cur = nxt;
+    }
+    P v = S::acc_part(acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = S::part_add(v, shfl_xor(v, o));
+    const bool h = SOUT && __any_sync(0xffffffffu, hit);
+    if (lane != 0) return;
+    if (b == rb && e == re) {
+        y[row] = S::part_T(v);
+        if (SOUT && h) yflag[row] = 1;
+    } else {
+        part[sg] = atom_bits(S::to_atom(v));
+        if (SOUT) part_hit[sg] = h ? 1 : 0;
+    }
+}
+
+template <class T>
+__global__ void k_pull_long_fixup(int64_t nmulti, const int32_t* __restrict__ multi_row,
+                                  const int32_t* __restrict__ multi_base, const int32_t* __restrict__ rowptr,
+                                  const uint64_t* __restrict__ part, const uint8_t* __restrict__ part_hit, PullArg a,
+                                  void* ywork, uint8_t* yflag, int sout) {
+    using S = Sr<T>;
+    using Atom = typename S::Atom;
+    const PullIO p = resolve(a, ywork, sout != 0);
+    T* __restrict__ y = (T*)p.y;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nmulti; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t row = multi_row[q], base = multi_base[q];
+        const int32_t k = (rowptr[row + 1] - rowptr[row] + kLongSeg - 1) / kLongSeg;
+        Atom sum = atom_from_bits<Atom>(part[base]);
+        bool h = sout && part_hit[base];
+        for (int32_t t = 1; t < k; ++t) {
+            sum = atom_combine<T>(sum, atom_from_bits<Atom>(part[base + t]));
+            if (sout) h |= part_hit[base + t] != 0;
+        }
+        y[row] = S::from_atom(sum);
+        if (sout && h) yflag[row] = 1;
+    }
+}
+
+template <class T, bool MASK, bool SOUT>
+void launch_pull_long_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStream_t s) {
+    if (H->nseg == 0) return;
+    const T* val = (const T*)H->val;
+    const unsigned g = (unsigned)((H->nseg + 7) / 8);
+    if (vec)
+        k_pull_long<T, MASK, SOUT, true><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->rowptr, H->col, val, H->seg_row,
+                                                           H->seg_beg, a, H->ws.ywork, H->ws.yflag, H->long_part,
+                                                           H->long_hit);
+    else
+        k_pull_long<T, MASK, SOUT, false><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->rowptr, H->col, val, H->seg_row,
+                                                            H->seg_beg, a, H->ws.ywork, H->ws.yflag, H->long_part,
+                                                            H->long_hit);
+    if (H->nmulti > 0) {
+        const unsigned gf = (unsigned)std::min<int64_t>((H->nmulti + 255) / 256, (int64_t)H->num_sms * 4);
+        k_pull_long_fixup<T><<<gf, 256, 0, s>>>(H->nmulti, H->multi_row, H->multi_base, H->rowptr, H->long_part,
+                                                H->long_hit, a, H->ws.ywork, H->ws.yflag, SOUT ? 1 : 0);
+    }
+}
+
 template <class T, bool MASK, bool SOUT>
 void launch_pull_warp_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStream_t s) {
     const int64_t m = H->m;
@@ -192,6 +312,10 @@ void launch_pull_warp_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStr
     template void launch_pull_warp_dtype<T, false, false>(asv_matrix_s*, const PullArg&, bool, cudaStream_t); \
     template void launch_pull_warp_dtype<T, false, true>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);  \
     template void launch_pull_warp_dtype<T, true, false>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);  \
-    template void launch_pull_warp_dtype<T, true, true>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);
+    template void launch_pull_warp_dtype<T, true, true>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);   \
+    template void launch_pull_long_dtype<T, false, false>(asv_matrix_s*, const PullArg&, bool, cudaStream_t); \
+    template void launch_pull_long_dtype<T, false, true>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);  \
+    template void launch_pull_long_dtype<T, true, false>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);  \
+    template void launch_pull_long_dtype<T, true, true>(asv_matrix_s*, const PullArg&, bool, cudaStream_t);
 
 }  // namespace asv

@@ -46,18 +46,44 @@ __device__ __forceinline__ T list_val(const CallDesc* d, int64_t t) {
 }
 
 // ---------------------------------------------------------------- traversals
+// One listed column per thread for columns of at most kLongCol entries; a
+// longer column (a hub of a power-law graph can hold 10^5 entries) is walked
+// by its whole warp right after, so no thread serialises a hub alone.
+constexpr int kLongCol = 64;
+
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                                      const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
     using S = Sr<T>;
+    const int lane = threadIdx.x & 31;
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nx; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t j = xidx[t];
-        const T xj = list_val<T>(desc, t);
-        const int32_t b = __ldg(colptr + j), e = __ldg(colptr + j + 1);
-        const int64_t pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
-        for (int32_t k = b; k < e; ++k) emit<T, WB>(ws, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t tw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); tw < nx; tw += stride) {
+        const int64_t t = tw + lane;
+        const bool valid = t < nx;
+        T xj = S::one();
+        int32_t b = 0, e = 0;
+        int64_t pos0 = 0;
+        if (valid) {
+            const int32_t j = xidx[t];
+            xj = list_val<T>(desc, t);
+            b = __ldg(colptr + j);
+            e = __ldg(colptr + j + 1);
+            pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
+        }
+        const bool lng = e - b > kLongCol;
+        if (!lng)
+            for (int32_t k = b; k < e; ++k) emit<T, WB>(ws, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
+        for (unsigned pend = __ballot_sync(0xffffffffu, lng); pend; pend &= pend - 1) {
+            const int src = __ffs(pend) - 1;
+            const int32_t bb = __shfl_sync(0xffffffffu, b, src), ee = __shfl_sync(0xffffffffu, e, src);
+            const int64_t p0 = __shfl_sync(0xffffffffu, pos0, src);
+            T xx = S::one();
+            if constexpr (!S::kPattern) xx = __shfl_sync(0xffffffffu, xj, src);
+            for (int32_t k = bb + lane; k < ee; k += 32)
+                emit<T, WB>(ws, __ldg(rowidx + k), S::mul(load_val(valc, k), xx), p0 + k);
+        }
     }
 }
 

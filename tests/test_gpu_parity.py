@@ -52,6 +52,28 @@ def mat_skewed(dtype):
     return "skewed", n, n, rp2, c2, v2
 
 
+LONG_LENS = (0, 1, 255, 256, 257, 300, 1023, 4096, 4097, 8192, 8193, 12289, 20000)
+
+
+def long_rows_pattern(n=20000, short=700, seed=31):
+    """Rows of every length class of the long-row split (at and around 256,
+    one segment, exactly 4096, several segments, a full row) between short
+    random rows."""
+    rows = []
+    for t, L in enumerate(LONG_LENS):
+        rows.append(gen.sample_positions(n, L, seed=seed, stream=100 + t))
+        for q in range(short // len(LONG_LENS)):
+            rows.append(gen.sample_positions(n, q % 9, seed=seed, stream=1000 + 97 * t + q))
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    return len(rows), n, rp, np.concatenate(rows).astype(np.int32)
+
+
+def mat_long(dtype):
+    m, n, rp, c = long_rows_pattern()
+    v = gen.uniform(len(c), -1, 1, seed=13, dtype=np.float64).astype(dtype)
+    return "long_rows", m, n, rp, c, v
+
+
 def x_cases(n, seed, dtype=np.float64):
     out = []
     for rho in (1.0, 0.1, 0.01, 0.001):
@@ -102,7 +124,7 @@ def test_laplace_f64_all_kernels(k):
 @pytest.mark.parametrize("k", ["auto"] + ALL_K)
 @pytest.mark.parametrize("dtype,tag", [(np.float32, "f32"), (np.float64, "f64")])
 def test_random_and_skewed_all_kernels(k, dtype, tag):
-    for maker in (mat_random, mat_skewed):
+    for maker in (mat_random, mat_skewed, mat_long):
         name, m, n, rp, c, v = maker(dtype)
         A = make(m, n, rp, c, v)
         for rho, idx, val in x_cases(n, 123, dtype):
@@ -128,6 +150,33 @@ def test_boolean_bit_exact(k):
         yidx, yval, nnz_y = A.spmspv(xidx=to_dev(idx), kernel=k, sparse_out=True)
         cnt = int(nnz_y.item())
         assert np.array_equal(yidx[:cnt].cpu().numpy(), np.flatnonzero(want)), f"bool sparse-out k={k}"
+
+
+@pytest.mark.parametrize("k", ["auto"] + ALL_K)
+def test_long_rows_boolean_and_int32_bit_exact(k):
+    m, n, rp, c = long_rows_pattern()
+    A = make(m, n, rp, c, None)
+    # x with no column of the long rows (every long row is walked to its end,
+    # as for a BFS frontier past the hubs), then a dense-ish one (early exits)
+    longc = np.unique(np.concatenate([c[rp[i]:rp[i + 1]] for i in range(m) if rp[i + 1] - rp[i] > 256]))
+    free = np.setdiff1d(np.arange(n, dtype=np.int32), longc)
+    for idx in (free[gen.sample_positions(len(free), min(len(free), 40), seed=5)],
+                gen.sample_positions(n, n // 3, seed=6)):
+        idx = idx.astype(np.int32)
+        xb = np.zeros(n, np.uint8)
+        xb[idx] = 1
+        want = oracle.bool_pull(rp, c, xb)
+        y1 = A.spmspv(x_dense=to_dev(xb), kernel=k).cpu().numpy()
+        assert np.array_equal(y1 != 0, want != 0), f"bool long rows dense-in k={k}"
+        yidx, yval, nnz_y = A.spmspv(xidx=to_dev(idx), kernel=k, sparse_out=True)
+        cnt = int(nnz_y.item())
+        assert np.array_equal(yidx[:cnt].cpu().numpy(), np.flatnonzero(want)), f"bool long rows sparse-out k={k}"
+    val = gen.uniform(len(c), -2**31, 2**31 - 1, seed=14).astype(np.int64).astype(np.int32)
+    x = gen.uniform(n, -2**31, 2**31 - 1, seed=15).astype(np.int64).astype(np.int32)
+    x[gen.sample_positions(n, n // 2, seed=16)] = 0
+    Ai = make(m, n, rp, c, val)
+    want = oracle.i32_pull(rp, c, val, x)
+    assert np.array_equal(Ai.spmspv(x_dense=to_dev(x), kernel=k).cpu().numpy(), want), f"int32 long rows k={k}"
 
 
 @pytest.mark.parametrize("k", ["auto"] + ALL_K)
