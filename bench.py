@@ -413,6 +413,22 @@ def ncu_case(case, kernel):
         y = torch.empty(m, dtype=torch.float32, device=dev)
         for _ in range(3):
             A.spmv(x, y, kernel=kernel)
+    elif case == "rmat20_bfs":
+        # the densest BFS frontier of one root, Boolean, list in and list out (a BFS level product)
+        rp, c = gen.rmat(20, 16, gen.config_seed(2))
+        m = n = 1 << 20
+        deg = np.diff(rp)
+        root = int(np.flatnonzero(deg > 0)[0])
+        fronts = bfs_frontiers(rp, c, [root])
+        f = max(fronts, key=len)
+        A = asv.Matrix(m, n, torch.from_numpy(rp).to(dev), torch.from_numpy(c).to(dev), None)
+        fd = torch.from_numpy(f).to(dev)
+        cnt = torch.tensor([len(f)], dtype=torch.int64, device=dev)
+        yidx = torch.empty(m, dtype=torch.int32, device=dev)
+        nnz_y = torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(3):
+            asv.asv_spmspv(A.handle, cnt, fd, None, None, asv.ASV_OUT_SPARSE, None, yidx, None, nnz_y, m, kernel)
+        print("frontier", len(f), "of", n)
     elif case == "zipf_batched":
         m, n, B = 200_000, 131_072, 1024
         rp, c, v = gen.lognormal_zipf(m, n, np.log(40), 1.0, 1.2, gen.config_seed(3))
@@ -496,6 +512,7 @@ def density_sweep(which, out_path, reps=5):
                    "regret": round(times["auto"] / times[best_k], 3),
                    "auto_GBs": round(work / (times["auto"] * 1e-3) / 1e9, 1),
                    "auto_frac": round(work / (times["auto"] * 1e-3) / 1e9 / hbm, 4),
+                   "auto_GFLOPs": round(2 * nnz_s / (times["auto"] * 1e-3) / 1e9, 2),
                    "ms": {q: round(times[q], 4) for q in asv.KERNELS}}
             out.write(json.dumps(rec) + "\n")
             out.flush()
@@ -538,7 +555,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and backward sections")
     ap.add_argument("--ncu-case", default=None,
-                    help="profiling aid: run one small case (stencil128, rmat20, zipf_batched, bernoulli_backward) "
+                    help="profiling aid: run one small case (stencil128, rmat20, rmat20_bfs, zipf_batched, "
+                         "bernoulli_backward) "
                          "with --kernel three times and exit")
     ap.add_argument("--kernel", default="auto")
     ap.add_argument("--sweep", default=None,

@@ -143,6 +143,15 @@ __device__ __forceinline__ bool test_bit(const uint32_t* bits, int64_t j) {
     return (__ldg(bits + (j >> 5)) >> (j & 31)) & 1u;
 }
 
+// The (OR, AND) term of an entry in column c: x_c's truth value. A Boolean x
+// is true exactly where its bitmap bit is set, so with the bitmap at hand one
+// gather (of a bit: the bitmap is 8x smaller than the byte vector) gives both
+// the product and the entry's structural hit, masked or not.
+__device__ __forceinline__ uint32_t bool_gather(const bool8* __restrict__ x, const uint32_t* __restrict__ xbits,
+                                                int64_t c) {
+    return xbits ? (uint32_t)test_bit(xbits, c) : (uint32_t)(__ldg(x + c) != 0);
+}
+
 // Sets bit i of a zero-invariant bitmap; the plain read first avoids the
 // atomic when the bit is already set (the common case for hub rows).
 __device__ __forceinline__ void set_bit_once(uint32_t* bits, int64_t i) {

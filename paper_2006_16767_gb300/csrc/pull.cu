@@ -37,15 +37,20 @@ __device__ __forceinline__ typename Sr<T>::Acc row_direct(const int32_t* __restr
     S::acc_zero(acc);
     for (int32_t k = b; k < e; ++k) {
         const int32_t c = __ldg(col + k);
+        if constexpr (S::kPattern) {
+            if (bool_gather(x, xbits, c)) {  // OR is settled by the first hit
+                acc = 1u;
+                hit = true;
+                break;
+            }
+            continue;
+        }
         if (MASK || SOUT) {
             const bool bit = test_bit(xbits, c);
             hit |= bit;
             if (MASK && !bit) continue;
         }
         S::acc_add(acc, S::mul(load_val(val, k), __ldg(x + c)));
-        if constexpr (S::kPattern) {
-            if (acc) break;  // OR is settled by the first hit
-        }
     }
     return acc;
 }
@@ -184,16 +189,23 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
         if (mine) {
             int32_t k = rb;
             if constexpr (!MASK && !SOUT && kStageVals) {
-                // four gathers in flight per lane before their products are added
-                for (; k + 4 <= re; k += 4) {
-                    const int32_t c0 = sc[k - a0], c1 = sc[k + 1 - a0], c2 = sc[k + 2 - a0], c3 = sc[k + 3 - a0];
-                    const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-                    const T v0 = val ? sv[k - a0] : S::one(), v1 = val ? sv[k + 1 - a0] : S::one();
-                    const T v2 = val ? sv[k + 2 - a0] : S::one(), v3 = val ? sv[k + 3 - a0] : S::one();
-                    S::acc_add(acc, S::mul(v0, x0));
-                    S::acc_add(acc, S::mul(v1, x1));
-                    S::acc_add(acc, S::mul(v2, x2));
-                    S::acc_add(acc, S::mul(v3, x3));
+                // eight gathers in flight per lane before their products are
+                // added (the gathers, not HBM, bound a lane's walk of its row)
+                constexpr int GD = 8;
+                for (; k + GD <= re; k += GD) {
+                    T xg[GD];
+#pragma unroll
+                    for (int u = 0; u < GD; ++u) xg[u] = __ldg(x + sc[k + u - a0]);
+#pragma unroll
+                    for (int u = 0; u < GD; ++u) S::acc_add(acc, S::mul(val ? sv[k + u - a0] : S::one(), xg[u]));
+                }
+                if (k + 4 <= re) {
+                    T xg[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) xg[u] = __ldg(x + sc[k + u - a0]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) S::acc_add(acc, S::mul(val ? sv[k + u - a0] : S::one(), xg[u]));
+                    k += 4;
                 }
             }
             for (; k < re; ++k) {
@@ -280,8 +292,13 @@ __device__ __forceinline__ void stage_products(const int32_t* __restrict__ col, 
         for (int q = 0; q < 4; ++q) {
             const int64_t k = base + q;
             const bool in = gi < ngroups && k >= k0 && k < k1;
-            bitv[j][q] = (MASK || SOUT) && in ? test_bit(xbits, c[j][q]) : true;
-            eff[j][q] = in && (!MASK || bitv[j][q]);
+            if constexpr (S::kPattern) {
+                bitv[j][q] = in && bool_gather(x, xbits, c[j][q]);  // the term itself
+                eff[j][q] = bitv[j][q];
+            } else {
+                bitv[j][q] = (MASK || SOUT) && in ? test_bit(xbits, c[j][q]) : true;
+                eff[j][q] = in && (!MASK || bitv[j][q]);
+            }
         }
         if constexpr (S::kPattern) {
 #pragma unroll
@@ -297,7 +314,10 @@ __device__ __forceinline__ void stage_products(const int32_t* __restrict__ col, 
         const int64_t base = a0 + 4 * (int64_t)gi;
         P pr[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) pr[q] = eff[j][q] ? S::mul(v[j][q], __ldg(x + c[j][q])) : P(0);
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (S::kPattern) pr[q] = eff[j][q] ? P(1) : P(0);
+            else pr[q] = eff[j][q] ? S::mul(v[j][q], __ldg(x + c[j][q])) : P(0);
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t k = base + q;

@@ -62,6 +62,13 @@ __device__ __forceinline__ typename Sr<T>::Part chunk_sum(Chunk<T, MASK, VEC>& c
                                                           int32_t base, bool& hit) {
     using S = Sr<T>;
     using P = typename S::Part;
+    if constexpr (S::kPattern) {
+        uint32_t any = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) any |= ch.in[q] ? bool_gather(x, xbits, ch.c[q]) : 0u;
+        if (SOUT) hit |= any != 0u;
+        return any;
+    }
     bool eff[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {

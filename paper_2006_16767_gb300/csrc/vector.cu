@@ -34,10 +34,12 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
     desc->vfeat[3] = nnz > 0 ? (double)ns / (double)nnz : 0.0;
 }
 
+// `blocks` is the number of blocks that take part (all of them call this);
+// the one that draws the last ticket publishes.
 template <int B>
 __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long* counters,
                                               unsigned int* ticket, CallDesc* desc, const DescInit& di, int64_t n,
-                                              int64_t nnz, int32_t* status, const SelectArg& sa) {
+                                              int64_t nnz, int32_t* status, const SelectArg& sa, unsigned blocks) {
     __shared__ unsigned long long sm[B / 32 + 1];
     __shared__ bool last;
     __shared__ TreeNode sn[kMaxTreeNodes];
@@ -47,7 +49,7 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
         if (cx) atomicAdd(&counters[0], cx);
         if (cs) atomicAdd(&counters[1], cs);
         __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        last = atomicAdd(ticket, 1u) == blocks - 1;
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
             }
         }
     }
-    finish_counts<B>(cx, cs, counters, ticket, desc, di, n, nnz, status, sa);
+    finish_counts<B>(cx, cs, counters, ticket, desc, di, n, nnz, status, sa, gridDim.x);
 }
 
 // Sparse x: nnz_s = sum of the listed columns' lengths.
@@ -158,13 +160,16 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
     int64_t nx = *nnz_x_dev;
     if (nx < 0) nx = 0;
     if (nx > n) nx = n + 1;  // reported and clamped when the totals are published
+    // only the blocks the list reaches take part (a short list costs one block)
+    const unsigned blocks = (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (min(nx, n) + B - 1) / B));
+    if (blockIdx.x >= blocks) return;
     unsigned long long cs = 0;
-    for (int64_t t = blockIdx.x * (int64_t)B + threadIdx.x; t < min(nx, n); t += (int64_t)gridDim.x * B) {
+    for (int64_t t = blockIdx.x * (int64_t)B + threadIdx.x; t < min(nx, n); t += (int64_t)blocks * B) {
         const int32_t j = __ldg(xidx + t);
         cs += (unsigned long long)(__ldg(colptr + j + 1) - __ldg(colptr + j));
     }
     finish_counts<B>(blockIdx.x == 0 && threadIdx.x == 0 ? (unsigned long long)nx : 0ull, cs, counters, ticket, desc,
-                     di, n, nnz, status, sa);
+                     di, n, nnz, status, sa, blocks);
 }
 
 // Few blocks per SM: every block of the feature pass ends with atomics on
