@@ -342,6 +342,29 @@ def bench_batched(asv, torch, dev, reps=3):
     return out
 
 
+def bench_bfs(asv, torch, dev, W):
+    """Whole breadth-first searches on the benchmark graph through the masked
+    product (asv_bfs): the selector per level versus fixed candidates; GTEPS =
+    edges of the reached component / time (Graph500 convention, each
+    undirected edge counted once)."""
+    deg = np.diff(W.rowptr).astype(np.int64)
+    out = {"workload": f"rmat scale {W.scale} edge factor {W.edge_factor}, {W.nroots} roots, Boolean handle"}
+    level = torch.empty(W.n, dtype=torch.int32, device=dev)
+    for k in ("auto", "pull_thread", "push_bal_atom", "mpull_bal"):
+        W.Ab.bfs(W.roots[0], kernel=k, level=level)  # warm-up (graphs, workspaces)
+        torch.cuda.synchronize()
+        tot_ms, edges = 0.0, 0
+        for r in W.roots:
+            t0 = time.perf_counter()
+            _, depth = W.Ab.bfs(r, kernel=k, level=level)
+            torch.cuda.synchronize()
+            tot_ms += (time.perf_counter() - t0) * 1e3
+            lv = level.cpu().numpy()
+            edges += int(deg[lv >= 0].sum()) // 2
+        out[k] = {"ms_per_search": round(tot_ms / len(W.roots), 3), "GTEPS": round(edges / (tot_ms * 1e-3) / 1e9, 2)}
+    return out
+
+
 def bench_backward(asv, torch, dev, reps=5):
     """16384^2 5%-dense layer, 64 activation vectors (5..50% dense): batched
     forward + fused backward versus 64 plain calls of each."""
@@ -680,6 +703,7 @@ def main():
            "clocks": clk, "wall_s_timed": round(wall, 3),
            "selected": {asv.KERNELS[k[1]] + ":" + k[0]: v["n"] // args.steps for k, v in per_k.items()}}
     if not args.no_extra:
+        out["bfs"] = bench_bfs(asv, torch, dev, W)
         out["batched"] = bench_batched(asv, torch, dev)
         out["backward"] = bench_backward(asv, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

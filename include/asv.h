@@ -178,6 +178,34 @@ asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xid
                       void* d_y, int32_t* d_yidx, void* d_yval, int64_t* d_nnz_y,
                       int64_t y_cap, int32_t kernel, void* stream);
 
+/* y = A x restricted by an output mask (an extension for the BFS application
+ * of Sec. VII; the paper's kernels have no mask): d_ymask[(m + 31) / 32] is a
+ * device bitmap, bit i (word i / 32, bit i % 32) set = row i is excluded.
+ * Excluded rows are not computed by the pull kernels (their y_i is 0 in the
+ * dense output) and never enter the sparse output set; the push kernels drop
+ * their entries. Other arguments, errors and formats as asv_spmspv; d_ymask
+ * must not be NULL (ASV_ERR_ARG) and must stay unchanged until the call has
+ * run. The selector does not look at the mask. No synchronisation. */
+asv_status asv_spmspv_masked(asv_matrix A, const uint32_t* d_ymask, const int64_t* d_nnz_x,
+                             const int32_t* d_xidx, const void* d_xval, const void* d_x_dense,
+                             int32_t out_mode, void* d_y, int32_t* d_yidx, void* d_yval,
+                             int64_t* d_nnz_y, int64_t y_cap, int32_t kernel, void* stream);
+
+/* Breadth-first search from vertex `source` over the pattern of a square
+ * handle (any value type; a Boolean handle is the cheap one): d_level[n]
+ * (device int32, caller-owned) receives each vertex's level, 0 for the
+ * source and -1 for vertices not reached. A vertex i is reached from j when
+ * A stores entry (i, j) -- the direction of y = A x; for a symmetric pattern
+ * this is the ordinary undirected search. Each level is one masked product
+ * (frontier in, unvisited rows out, as a sparse list) run by `kernel`
+ * (ASV_K_AUTO: the selector chooses per level). *h_depth (may be NULL)
+ * receives the number of levels including the source's. The first call
+ * allocates the handle's search workspaces (bitmap, two frontier lists);
+ * every call synchronises `stream` once per level. Errors: ASV_ERR_ARG for a
+ * non-square handle, n = 0, a source outside [0, n) or a NULL d_level. */
+asv_status asv_bfs(asv_matrix A, int32_t source, int32_t* d_level, int32_t kernel, int32_t* h_depth,
+                   void* stream);
+
 /* Run the feature pass and the selector for this x (same x arguments as
  * asv_spmspv) and return the chosen kernel id and the vector features
  * (Sec. V-A Table 1, Sec. VI-B cascaded trees). Synchronises `stream`. */

@@ -91,6 +91,8 @@ def lib():
             L.asv_spmspv_backward.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             L.asv_spmv_noalloc_f32.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp]
             L.asv_spmspv.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, i32, vp]
+            L.asv_spmspv_masked.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, i32, vp]
+            L.asv_bfs.argtypes = [vp, i32, vp, i32, P(i32), vp]
             L.asv_select.argtypes = [vp, vp, vp, vp, vp, P(i32), P(_VFeat), vp]
             L.asv_last_kernel.argtypes = [vp, P(i32), vp]
             L.asv_compact.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -104,7 +106,7 @@ def lib():
                          "asv_matrix_arrays", "asv_matrix_copy_csc", "asv_spmv", "asv_spmspv", "asv_select", "asv_last_kernel",
                          "asv_compact", "asv_set_trees", "asv_get_status", "asv_last_cuda_error",
                          "asv_version", "asv_matrix_update_values", "asv_spmspv_batched", "asv_autotune_batched",
-                         "asv_spmspv_backward", "asv_spmv_noalloc_f32"):
+                         "asv_spmspv_backward", "asv_spmv_noalloc_f32", "asv_spmspv_masked", "asv_bfs"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -232,6 +234,20 @@ def asv_spmspv(h, nnz_x=None, xidx=None, xval=None, x_dense=None, out_mode=ASV_O
                             _stream(stream)), "asv_spmspv")
 
 
+def asv_spmspv_masked(h, ymask, nnz_x=None, xidx=None, xval=None, x_dense=None, out_mode=ASV_OUT_DENSE, y=None,
+                      yidx=None, yval=None, nnz_y=None, y_cap=0, kernel="auto", stream=None):
+    _check(lib().asv_spmspv_masked(h, _ptr(ymask), _ptr(nnz_x), _ptr(xidx), _ptr(xval), _ptr(x_dense),
+                                   int(out_mode), _ptr(y), _ptr(yidx), _ptr(yval), _ptr(nnz_y), int(y_cap),
+                                   _kernel_id(kernel), _stream(stream)), "asv_spmspv_masked")
+
+
+def asv_bfs(h, source, level, kernel="auto", stream=None) -> int:
+    depth = ctypes.c_int32()
+    _check(lib().asv_bfs(h, int(source), _ptr(level), _kernel_id(kernel), ctypes.byref(depth), _stream(stream)),
+           "asv_bfs")
+    return depth.value
+
+
 def asv_select(h, nnz_x=None, xidx=None, xval=None, x_dense=None, stream=None):
     k = ctypes.c_int32()
     f = _VFeat()
@@ -322,24 +338,38 @@ class Matrix:
         return y
 
     def spmspv(self, xidx=None, xval=None, nnz_x=None, x_dense=None, sparse_out=False, y=None, y_cap=None,
-               kernel="auto", stream=None):
+               kernel="auto", ymask=None, stream=None):
         """y = A x. x sparse (xidx[, xval]) or dense (x_dense). Returns y (dense) or
-        (yidx, yval, nnz_y) views (sparse output)."""
+        (yidx, yval, nnz_y) views (sparse output). ymask: optional int32 bitmap of
+        (m + 31) // 32 words; rows whose bit is set are excluded from y."""
         dev = (x_dense if x_dense is not None else xidx).device
         if x_dense is None and nnz_x is None:
             nnz_x = torch.tensor([xidx.numel()], dtype=torch.int64, device=dev)
+
+        def call(*a):
+            if ymask is None:
+                asv_spmspv(self.handle, *a)
+            else:
+                asv_spmspv_masked(self.handle, ymask, *a)
         if not sparse_out:
             if y is None:
                 y = torch.empty(self.m, dtype=self.tdtype, device=dev)
-            asv_spmspv(self.handle, nnz_x, xidx, xval, x_dense, ASV_OUT_DENSE, y, kernel=kernel, stream=stream)
+            call(nnz_x, xidx, xval, x_dense, ASV_OUT_DENSE, y, None, None, None, 0, kernel, stream)
             return y
         cap = self.m if y_cap is None else int(y_cap)
         yidx = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
         yval = torch.empty(max(cap, 1), dtype=self.tdtype, device=dev)
         nnz_y = torch.zeros(1, dtype=torch.int64, device=dev)
-        asv_spmspv(self.handle, nnz_x, xidx, xval, x_dense, ASV_OUT_SPARSE, None, yidx, yval, nnz_y, cap,
-                   kernel, stream)
+        call(nnz_x, xidx, xval, x_dense, ASV_OUT_SPARSE, None, yidx, yval, nnz_y, cap, kernel, stream)
         return yidx, yval, nnz_y
+
+    def bfs(self, source, kernel="auto", level=None, stream=None):
+        """Breadth-first search levels from `source` (int32 [n], -1 = unreached)
+        and the number of levels; each level is one masked product."""
+        if level is None:
+            level = torch.empty(self.n, dtype=torch.int32, device=self.rowptr.device)
+        depth = asv_bfs(self.handle, source, level, kernel, stream)
+        return level, depth
 
     def select(self, xidx=None, xval=None, nnz_x=None, x_dense=None, stream=None):
         dev = (x_dense if x_dense is not None else xidx).device

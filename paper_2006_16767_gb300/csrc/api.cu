@@ -84,6 +84,7 @@ static void destroy_handle(asv_matrix_s* H) {
             if (H->graph[a][b]) cudaGraphDestroy(H->graph[a][b]);
         }
     batch_release(H);
+    if (H->bfs_hcount) cudaFreeHost(H->bfs_hcount);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
     for (void* p : H->allocs) cudaFree(p);
     delete H;
@@ -400,15 +401,15 @@ static asv_status prepare_call(asv_matrix_s* H, const int64_t* d_nnz_x, const in
     return ASV_OK;
 }
 
-extern "C" asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx, const void* d_xval,
-                                 const void* d_x_dense, int32_t out_mode, void* d_y, int32_t* d_yidx, void* d_yval,
-                                 int64_t* d_nnz_y, int64_t y_cap, int32_t kernel, void* stream) {
+static asv_status spmspv_impl(asv_matrix A, const uint32_t* d_ymask, const int64_t* d_nnz_x, const int32_t* d_xidx,
+                              const void* d_xval, const void* d_x_dense, int32_t out_mode, void* d_y, int32_t* d_yidx,
+                              void* d_yval, int64_t* d_nnz_y, int64_t y_cap, int32_t kernel, cudaStream_t s) {
     if (!A) return ASV_ERR_ARG;
     if (kernel < ASV_K_AUTO || kernel >= ASV_K_COUNT) return ASV_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
     DescInit di;
     asv_status st = prepare_call(A, d_nnz_x, d_xidx, d_xval, d_x_dense, out_mode, d_y, d_yidx, d_yval, d_nnz_y, y_cap, di);
     if (st != ASV_OK) return st;
+    di.ymask = d_ymask;
     if (kernel == ASV_K_AUTO) {
         st = launch_auto(A, di, out_mode, s);
         if (st != ASV_OK) return st;
@@ -418,6 +419,73 @@ extern "C" asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int
         launch_features(A, di, none, s);
         enqueue_candidate(A, kernel, di.x_sparse, out_mode, s);
     }
+    CK(cudaGetLastError());
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx, const void* d_xval,
+                                 const void* d_x_dense, int32_t out_mode, void* d_y, int32_t* d_yidx, void* d_yval,
+                                 int64_t* d_nnz_y, int64_t y_cap, int32_t kernel, void* stream) {
+    return spmspv_impl(A, nullptr, d_nnz_x, d_xidx, d_xval, d_x_dense, out_mode, d_y, d_yidx, d_yval, d_nnz_y, y_cap,
+                       kernel, (cudaStream_t)stream);
+}
+
+extern "C" asv_status asv_spmspv_masked(asv_matrix A, const uint32_t* d_ymask, const int64_t* d_nnz_x,
+                                        const int32_t* d_xidx, const void* d_xval, const void* d_x_dense,
+                                        int32_t out_mode, void* d_y, int32_t* d_yidx, void* d_yval, int64_t* d_nnz_y,
+                                        int64_t y_cap, int32_t kernel, void* stream) {
+    if (!d_ymask && A && A->m > 0) return ASV_ERR_ARG;
+    return spmspv_impl(A, d_ymask, d_nnz_x, d_xidx, d_xval, d_x_dense, out_mode, d_y, d_yidx, d_yval, d_nnz_y, y_cap,
+                       kernel, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- breadth-first search
+// Level-synchronous BFS through the masked product: frontier_{d+1} =
+// (A frontier_d) restricted to the unvisited rows, as the ascending list the
+// sparse output mode produces; each level is one selector-driven call (or
+// the forced candidate), so the pattern, distribution and write-back adapt
+// from level to level. One stream synchronisation per level reads the size
+// of the new frontier.
+extern "C" asv_status asv_bfs(asv_matrix A, int32_t source, int32_t* d_level, int32_t kernel, int32_t* h_depth,
+                              void* stream) {
+    if (!A || !d_level) return ASV_ERR_ARG;
+    if (A->m != A->n || A->n == 0 || source < 0 || source >= A->n) return ASV_ERR_ARG;
+    if (kernel < ASV_K_AUTO || kernel >= ASV_K_COUNT) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    asv_matrix_s* H = A;
+    if (!H->bfs_hcount) {  // workspaces of the search, allocated on the first call
+        CK(cudaStreamSynchronize(s));
+        void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[4] = {(size_t)4 * ((H->n + 31) / 32), (size_t)4 * H->n, (size_t)4 * H->n, 16};
+        for (int i = 0; i < 4; ++i) {
+            asv_status st = dalloc(H, &p[i], bytes[i], i == 0 || i == 3);
+            if (st != ASV_OK) return st;
+        }
+        H->bfs_visited = (uint32_t*)p[0];
+        H->bfs_front[0] = (int32_t*)p[1];
+        H->bfs_front[1] = (int32_t*)p[2];
+        H->bfs_count = (int64_t*)p[3];
+        CK(cudaMallocHost((void**)&H->bfs_hcount, sizeof(int64_t)));
+    }
+    CK(cudaMemsetAsync(d_level, 0xff, 4 * (size_t)H->n, s));
+    CK(cudaMemsetAsync(H->bfs_visited, 0, 4 * (size_t)((H->n + 31) / 32), s));
+    launch_bfs_init(source, d_level, H->bfs_visited, H->bfs_front[0], H->bfs_count, s);
+    int cur = 0;
+    int32_t depth = 1;
+    for (;;) {
+        asv_status st = spmspv_impl(A, H->bfs_visited, H->bfs_count + cur, H->bfs_front[cur], nullptr, nullptr,
+                                    ASV_OUT_SPARSE, nullptr, H->bfs_front[cur ^ 1], nullptr, H->bfs_count + (cur ^ 1),
+                                    H->n, kernel, s);
+        if (st != ASV_OK) return st;
+        launch_bfs_visit(H->bfs_front[cur ^ 1], H->bfs_count + (cur ^ 1), d_level, H->bfs_visited, depth,
+                         H->num_sms * 4, s);
+        CK(cudaMemcpyAsync(H->bfs_hcount, H->bfs_count + (cur ^ 1), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (*H->bfs_hcount <= 0) break;
+        cur ^= 1;
+        ++depth;
+    }
+    if (h_depth) *h_depth = depth;
     CK(cudaGetLastError());
     return ASV_OK;
 }

@@ -185,7 +185,13 @@ struct CallDesc {
     int32_t kid;             // kernel chosen for this call
     int32_t pad;
     double vfeat[4];         // nnz_x, x_sparsity, nnz_s, m_sparsity
+    const uint32_t* ymask;   // output mask: bit i set = row i excluded from y (NULL = none)
 };
+
+// Row i is excluded by the output mask.
+__device__ __forceinline__ bool row_masked(const uint32_t* __restrict__ ymask, int64_t i) {
+    return ymask != nullptr && ((__ldg(ymask + (i >> 5)) >> (i & 31)) & 1u);
+}
 
 // Device-resident matrix features (Table 1), written once at handle creation.
 struct MatFeat {

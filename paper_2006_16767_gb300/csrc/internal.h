@@ -24,6 +24,7 @@ struct DescInit {
     const int32_t* user_xidx;
     const void* user_xval;
     const int64_t* user_nnz_x;
+    const uint32_t* ymask;  // output mask (NULL = none)
     int32_t out_mode;
     int32_t x_sparse;
 };
@@ -101,6 +102,12 @@ struct asv_matrix_s {
     int G = 0;  // fixed grid of the scan / sort / compaction primitives
     BatchWs bws;
     int32_t tune_R = 8, tune_GB = 1024;  // batched tiling chosen by the autotuner
+    // breadth-first search workspaces (first asv_bfs call): visited bitmap,
+    // two frontier lists, their device counts, a pinned host count
+    uint32_t* bfs_visited = nullptr;
+    int32_t* bfs_front[2] = {nullptr, nullptr};
+    int64_t* bfs_count = nullptr;
+    int64_t* bfs_hcount = nullptr;
     std::vector<void*> allocs;
 };
 
@@ -118,6 +125,12 @@ cudaError_t build_long_rows(asv_matrix_s* H, cudaStream_t s);
 int64_t pull_tile_items(int32_t dtype);
 cudaError_t validate_csr(asv_matrix_s* H, cudaStream_t s, int32_t* d_flag);
 cudaError_t regather_values(asv_matrix_s* H, cudaStream_t s);
+
+// bfs.cu -- level bookkeeping of the breadth-first search
+void launch_bfs_init(int32_t source, int32_t* level, uint32_t* visited, int32_t* front, int64_t* count,
+                     cudaStream_t s);
+void launch_bfs_visit(const int32_t* front, const int64_t* count, int32_t* level, uint32_t* visited, int32_t depth,
+                      int grid, cudaStream_t s);
 
 // shared scan launcher (device-side count allowed)
 void scan_excl(const int32_t* in, int32_t* out, int64_t n_h, const int64_t* n_d, int32_t* blk, int G,
@@ -155,6 +168,7 @@ struct PullIO {
     const void* x;
     const uint32_t* xbits;
     void* y;
+    const uint32_t* ymask = nullptr;  // output mask: rows whose bit is set are not computed (y = 0)
 };
 void launch_pull(asv_matrix_s* H, int dist, bool masked, bool sparse_out, const PullIO* direct,
                  cudaStream_t s);

@@ -35,16 +35,26 @@ __device__ __forceinline__ typename Sr<T>::Acc row_direct(const int32_t* __restr
     using S = Sr<T>;
     typename S::Acc acc;
     S::acc_zero(acc);
-    for (int32_t k = b; k < e; ++k) {
-        const int32_t c = __ldg(col + k);
-        if constexpr (S::kPattern) {
-            if (bool_gather(x, xbits, c)) {  // OR is settled by the first hit
+    if constexpr (S::kPattern) {
+        // four terms per step (their index loads and bit gathers in flight
+        // together); OR is settled by the first true term
+        for (int32_t k = b; k < e; k += 4) {
+            int32_t c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c[u] = k + u < e ? __ldg(col + k + u) : -1;
+            uint32_t t = 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t |= c[u] >= 0 ? bool_gather(x, xbits, c[u]) : 0u;
+            if (t) {
                 acc = 1u;
                 hit = true;
                 break;
             }
-            continue;
         }
+        return acc;
+    }
+    for (int32_t k = b; k < e; ++k) {
+        const int32_t c = __ldg(col + k);
         if (MASK || SOUT) {
             const bool bit = test_bit(xbits, c);
             hit |= bit;
@@ -91,6 +101,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
     const int32_t s0 = __shfl_sync(0xffffffffu, rb, 0);
     const int32_t a0 = s0 & ~3;
     const bool mine = i < m && re - rb <= kLongRow;  // longer rows are summed by k_pull_long
+    const bool off = mine && row_masked(p.ymask, i);  // excluded by the output mask: y_i = 0
     bool hit = false;
     typename S::Acc acc;
     // Boolean rows stop at their first hit, so copying whole spans would read
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
         }
         __syncwarp();
         S::acc_zero(acc);
-        if (mine) {
+        if (mine && !off) {
             int32_t k = rb;
             if constexpr (!MASK && !SOUT && kStageVals) {
                 // eight gathers in flight per lane before their products are
@@ -225,7 +236,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
             }
         }
     } else {
-        if (mine) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, re, hit);
+        if (mine && !off) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, re, hit);
         else S::acc_zero(acc);
     }
     if (mine) {
@@ -383,7 +394,7 @@ __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, cons
         if (ri < nrows && (int64_t)s_end[ri] <= k0 + ki) {
             s_row[ri] = S::acc_part(acc);
             S::acc_zero(acc);
-            if (SOUT && hit) yflag[(int64_t)r0 + ri] = 1;
+            if (SOUT && hit && !row_masked(p.ymask, (int64_t)r0 + ri)) yflag[(int64_t)r0 + ri] = 1;
             hit = false;
             ++ri;
         } else {
@@ -392,7 +403,7 @@ __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, cons
             ++ki;
         }
     }
-    if (SOUT && hit) yflag[(int64_t)r0 + ri] = 1;
+    if (SOUT && hit && !row_masked(p.ymask, (int64_t)r0 + ri)) yflag[(int64_t)r0 + ri] = 1;
 
     // segmented inclusive scan of the threads' carries (key = row still open
     // at the thread's end; keys are non-decreasing across threads)
@@ -422,7 +433,8 @@ __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, cons
     // threads before it that worked on the same row
     if (threadIdx.x > 0 && ri > ri_start) s_row[ri_start] = S::part_add(s_scan[threadIdx.x - 1], s_row[ri_start]);
     __syncthreads();
-    for (int i = threadIdx.x; i < nrows; i += B) y[r0 + i] = S::part_T(s_row[i]);
+    for (int i = threadIdx.x; i < nrows; i += B)
+        y[r0 + i] = row_masked(p.ymask, (int64_t)r0 + i) ? T(0) : S::part_T(s_row[i]);
     if (threadIdx.x == B - 1) {
         carry_row[t] = (r1 < m) ? r1 : -1;
         carry_val[t] = S::to_atom(S::part_T(v));
@@ -442,6 +454,7 @@ __global__ void k_pull_bal_fixup(int64_t ntiles, const int32_t* __restrict__ car
         const int32_t r = carry_row[t];
         if (r < 0) continue;
         if (t > 0 && carry_row[t - 1] == r) continue;
+        if (desc && row_masked(desc->ymask, r)) continue;  // the completing tile wrote 0
         typename S::Atom s = carry_val[t];
         for (int64_t u = t + 1; u < ntiles && carry_row[u] == r; ++u) {
             if constexpr (S::kPattern) s = s | carry_val[u];

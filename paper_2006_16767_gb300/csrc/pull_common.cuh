@@ -24,6 +24,7 @@ __device__ __forceinline__ PullIO resolve(const PullArg& a, void* ywork, bool sp
         p.x = a.desc->x_dense;
         p.xbits = a.desc->xbits;
         p.y = sparse_out ? ywork : a.desc->y;
+        p.ymask = a.desc->ymask;
         return p;
     }
     return a.io;

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256, UU >= 4 ? 4 : 6) k_pull_warp(int64_t m, i
         const int32_t nx = __shfl_sync(0xffffffffu, rp, (r + 1) & 31);
         e[u] = (r + 1 == RW) ? rp_end : nx;
         if (e[u] - b[u] > kLongRow) valid[u] = false;  // summed by k_pull_long
-        if (!valid[u]) e[u] = b[u];
+        if (!valid[u] || row_masked(p.ymask, row0 + r)) e[u] = b[u];  // masked rows: y = 0
     }
     Chunk<T, MASK, VEC> ch[U];
 #pragma unroll
@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     const int32_t row = __ldg(seg_row + sg);
     const int32_t rb = __ldg(rowptr + row), re = __ldg(rowptr + row + 1);
     const int32_t b = __ldg(seg_beg + sg);
-    const int32_t e = min(b + kLongSeg, re);
+    const int32_t e_full = min(b + kLongSeg, re);
+    const int32_t e = row_masked(p.ymask, row) ? b : e_full;  // a masked row sums nothing (y = 0)
     const int32_t a0 = b & ~3;
     const int nsteps = (e - a0 + 127) >> 7;
     bool hit = false;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     for (int o = 16; o > 0; o >>= 1) v = S::part_add(v, shfl_xor(v, o));
     const bool h = SOUT && __any_sync(0xffffffffu, hit);
     if (lane != 0) return;
-    if (b == rb && e == re) {
+    if (b == rb && e_full == re) {
         y[row] = S::part_T(v);
         if (SOUT && h) yflag[row] = 1;
     } else {

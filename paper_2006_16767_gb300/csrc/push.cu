@@ -25,9 +25,11 @@ using PV = typename std::conditional<sizeof(T) == 8, uint64_t, uint32_t>::type;
 
 // One effective nonzero (row r, product p) at effective index pos.
 template <class T, int WB>
-__device__ __forceinline__ void emit(const Ws& ws, int32_t r, typename Sr<T>::Part p, int64_t pos) {
+__device__ __forceinline__ void emit(const Ws& ws, const uint32_t* ymask, int32_t r, typename Sr<T>::Part p,
+                                     int64_t pos) {
     using S = Sr<T>;
     if (WB == WB_ATOM) {
+        if (row_masked(ymask, r)) return;  // excluded by the output mask (pairs are masked when reduced)
         if constexpr (!S::kPattern) atomicAdd((typename S::Atom*)ws.acc + r, S::to_atom(S::part_T(p)));
         ws.yflag[r] = 1;
     } else {
@@ -55,6 +57,7 @@ template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                                      const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
     using S = Sr<T>;
+    const uint32_t* __restrict__ ym = desc->ymask;
     const int lane = threadIdx.x & 31;
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
         }
         const bool lng = e - b > kLongCol;
         if (!lng)
-            for (int32_t k = b; k < e; ++k) emit<T, WB>(ws, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
+            for (int32_t k = b; k < e; ++k) emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
         for (unsigned pend = __ballot_sync(0xffffffffu, lng); pend; pend &= pend - 1) {
             const int src = __ffs(pend) - 1;
             const int32_t bb = __shfl_sync(0xffffffffu, b, src), ee = __shfl_sync(0xffffffffu, e, src);
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
             T xx = S::one();
             if constexpr (!S::kPattern) xx = __shfl_sync(0xffffffffu, xj, src);
             for (int32_t k = bb + lane; k < ee; k += 32)
-                emit<T, WB>(ws, __ldg(rowidx + k), S::mul(load_val(valc, k), xx), p0 + k);
+                emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xx), p0 + k);
         }
     }
 }
@@ -91,6 +94,7 @@ template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                                    const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
     using S = Sr<T>;
+    const uint32_t* __restrict__ ym = desc->ymask;
     const int lane = threadIdx.x & 31;
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
         const T xj = list_val<T>(desc, t);
         const int32_t b = __ldg(colptr + j), e = __ldg(colptr + j + 1);
         const int64_t pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
-        for (int32_t k = b + lane; k < e; k += 32) emit<T, WB>(ws, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
+        for (int32_t k = b + lane; k < e; k += 32) emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
     }
 }
 
@@ -111,6 +115,7 @@ template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                                   const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
     using S = Sr<T>;
+    const uint32_t* __restrict__ ym = desc->ymask;
     constexpr int CH = 32 * kPushIPT;
     const int lane = threadIdx.x & 31;
     const int64_t nx = desc->nnz_x, ns = desc->nnz_s;
@@ -144,7 +149,7 @@ __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ co
             }
             const int32_t j = xidx[lo];
             const int64_t k = (int64_t)__ldg(colptr + j) + (e - sc[lo]);
-            emit<T, WB>(ws, __ldg(rowidx + k), S::mul(load_val(valc, k), list_val<T>(desc, lo)), e);
+            emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), list_val<T>(desc, lo)), e);
         }
     }
 }
@@ -175,6 +180,7 @@ __global__ void __launch_bounds__(256) k_reduce_by_key(const uint32_t* __restric
     const int64_t ns = desc->nnz_s;
     const int64_t nchunks = (ns + CH - 1) / CH;
     const int64_t wpb = blockDim.x / 32;
+    const uint32_t* __restrict__ ym = desc->ymask;
     A* acc = (A*)ws.acc;
     for (int64_t c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks; c += (int64_t)gridDim.x * wpb) {
         const int64_t e0 = c * CH, eend = min(e0 + CH, ns);
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(256) k_reduce_by_key(const uint32_t* __restric
             const uint32_t key = valid ? keys[e] : 0xffffffffu;
             // the segment carried from the previous round ended exactly at
             // the round boundary: write it out before this round starts
-            if (r0 > e0 && __shfl_sync(0xffffffffu, key, 0) != ckey && lane == 0) {
+            if (r0 > e0 && __shfl_sync(0xffffffffu, key, 0) != ckey && lane == 0 && !row_masked(ym, ckey)) {
                 if constexpr (!S::kPattern) {
                     if (ckey == first_key) atomicAdd(acc + ckey, S::to_atom(S::part_T(cval)));
                     else acc[ckey] = S::to_atom(S::part_T(cval));
@@ -207,7 +213,7 @@ __global__ void __launch_bounds__(256) k_reduce_by_key(const uint32_t* __restric
             const uint32_t nk = __shfl_down_sync(0xffffffffu, key, 1);
             const bool last_lane = (lane == 31) || (r0 + lane + 1 >= eend);
             const bool seg_end = valid && (last_lane ? false : nk != key);
-            if (seg_end) {
+            if (seg_end && !row_masked(ym, key)) {
                 if constexpr (!S::kPattern) {
                     if (key == first_key) atomicAdd(acc + key, S::to_atom(S::part_T(v)));
                     else acc[key] = S::to_atom(S::part_T(v));
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(256) k_reduce_by_key(const uint32_t* __restric
             ckey = __shfl_sync(0xffffffffu, key, src);
             cval = __shfl_sync(0xffffffffu, v, src);
         }
-        if (lane == 0) {
+        if (lane == 0 && !row_masked(ym, ckey)) {
             if constexpr (!S::kPattern) atomicAdd(acc + ckey, S::to_atom(S::part_T(cval)));
             ws.yflag[ckey] = 1;
         }
@@ -264,7 +270,8 @@ __global__ void k_bin_scatter(const uint32_t* __restrict__ kin, const T* __restr
 // then the tile's rows and bitmap words are written with plain stores.
 template <class T>
 __global__ void __launch_bounds__(256) k_priv_accumulate(const uint32_t* __restrict__ keys, const T* __restrict__ vals,
-                                                         const int32_t* __restrict__ binoff, int64_t m, Ws ws) {
+                                                         const int32_t* __restrict__ binoff, int64_t m, Ws ws,
+                                                         const CallDesc* __restrict__ desc) {
     using S = Sr<T>;
     using A = typename S::Atom;
     constexpr int R = 1 << kPrivBits;
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(256) k_priv_accumulate(const uint32_t* __restr
     A* acc = (A*)ws.acc;
     for (int i = threadIdx.x; i < R; i += blockDim.x) {
         const int64_t r = row0 + i;
-        if (r < m && ((s_flag[i >> 5] >> (i & 31)) & 1u)) {
+        if (r < m && ((s_flag[i >> 5] >> (i & 31)) & 1u) && !row_masked(desc->ymask, r)) {
             if constexpr (!S::kPattern) acc[r] = s_acc[i];
             ws.yflag[r] = 1;
         }
@@ -339,7 +346,7 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
         scan_excl(bins, bins, nbins, nullptr, ws.blk, H->G, true, s);
         cudaMemcpyAsync(cursor, bins, sizeof(int32_t) * nbins, cudaMemcpyDeviceToDevice, s);
         k_bin_scatter<T><<<grid, 256, 0, s>>>(ws.pkeys[0], (const T*)ws.pvals[0], ws.pkeys[1], (T*)ws.pvals[1], d, cursor);
-        if (nbins > 0) k_priv_accumulate<T><<<nbins, 256, 0, s>>>(ws.pkeys[1], (const T*)ws.pvals[1], bins, H->m, ws);
+        if (nbins > 0) k_priv_accumulate<T><<<nbins, 256, 0, s>>>(ws.pkeys[1], (const T*)ws.pvals[1], bins, H->m, ws, d);
     }
     launch_finalize(H, true, out_mode, s);
 }

@@ -15,7 +15,10 @@ static_assert(kTreeNodesF32 <= kMaxTreeNodes && kTreeNodesBool <= kMaxTreeNodes,
 
 SelectArg select_arg(asv_matrix_s* H, unsigned long long cond) {
     SelectArg sa;
-    sa.mf = H->d_mfeat;
+    const asv_mfeat& m = H->h_mfeat;
+    const double mf[9] = {(double)m.m, (double)m.n, (double)m.nnz, (double)m.max_row, (double)m.min_row,
+                          m.avg_row, m.relative_range, m.var_nnz_row, m.gini};
+    for (int q = 0; q < 9; ++q) sa.mf[q] = mf[q];
     sa.trees = H->d_trees;
     sa.roots = H->d_roots;
     sa.last_kid = H->d_last_kid;

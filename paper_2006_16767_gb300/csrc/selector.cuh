@@ -16,7 +16,7 @@ constexpr int kRootsLen = 4 * kRootsPerFormat + 1;
 // What the selector needs besides the call descriptor. cond is the SWITCH
 // node's conditional handle (0 = none).
 struct SelectArg {
-    const MatFeat* mf;
+    double mf[9];  // Table 1 matrix features 0..8, by value (no load on the critical path)
     const TreeNode* trees;
     const int32_t* roots;
     int32_t* last_kid;
@@ -24,46 +24,57 @@ struct SelectArg {
     int32_t enabled;
 };
 
-__device__ __forceinline__ int eval_tree(const TreeNode* nodes, int root, const double* f) {
+// Nodes [lo, hi) of the table are staged in shared memory (sn); a node
+// outside that window is read from global memory.
+__device__ __forceinline__ int eval_tree(const TreeNode* sn, int lo, int hi, const TreeNode* nodes, int root,
+                                         const double* f) {
     int node = root;
-    for (int depth = 0; depth < 64 && nodes[node].feature >= 0; ++depth)
-        node = (f[nodes[node].feature] <= nodes[node].thr) ? nodes[node].left : nodes[node].right;
-    return nodes[node].feature >= 0 ? 0 : nodes[node].leaf;
+    for (int depth = 0; depth < 64; ++depth) {
+        const TreeNode nd = (node >= lo && node < hi) ? sn[node - lo] : nodes[node];
+        if (nd.feature < 0) return nd.leaf;
+        node = (f[nd.feature] <= nd.thr) ? nd.left : nd.right;
+    }
+    return 0;
 }
 
-// Called by every thread of one block: stages the node table in shared
-// memory, then thread 0 walks the trees, records the choice and sets the
-// graph's SWITCH value when a handle is given.
+// Called by every thread of one block: stages the call format's trees in
+// shared memory, then thread 0 walks them, records the choice and sets the
+// graph's SWITCH value when a handle is given. The trained tables store the
+// five trees of a format contiguously, so the window from the format's
+// lowest root to the next root above its highest root holds all of them
+// (about a quarter of the table: one load per thread).
 __device__ __forceinline__ void run_selector(const SelectArg& sa, CallDesc* desc, TreeNode* sn) {
     const int cnt = min(sa.roots[kRootsLen - 1], kMaxTreeNodes);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) sn[i] = sa.trees[i];
+    const int* r = sa.roots + kRootsPerFormat * (desc->x_sparse * 2 + desc->out_mode);
+    int lo = cnt, mx = -1;
+    for (int t = 0; t < kRootsPerFormat; ++t) {
+        lo = min(lo, r[t]);
+        mx = max(mx, r[t]);
+    }
+    int hi = cnt;
+    for (int q = 0; q < kRootsLen - 1; ++q)
+        if (sa.roots[q] > mx && sa.roots[q] < hi) hi = sa.roots[q];
+    lo = max(lo, 0);
+    hi = min(hi, lo + kMaxTreeNodes);
+    for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) sn[i - lo] = sa.trees[i];
     __syncthreads();
     if (threadIdx.x != 0) return;
-    const MatFeat* mf = sa.mf;
     double f[13];
-    f[0] = (double)mf->m;
-    f[1] = (double)mf->n;
-    f[2] = (double)mf->nnz;
-    f[3] = (double)mf->max_row;
-    f[4] = (double)mf->min_row;
-    f[5] = mf->avg_row;
-    f[6] = mf->relative_range;
-    f[7] = mf->var_nnz_row;
-    f[8] = mf->gini;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = sa.mf[q];
     f[9] = desc->vfeat[0];
     f[10] = desc->vfeat[1];
     f[11] = desc->vfeat[2];
     f[12] = desc->vfeat[3];
-    const int* r = sa.roots + kRootsPerFormat * (desc->x_sparse * 2 + desc->out_mode);
-    const int pattern = min(max(eval_tree(sn, r[0], f), 0), 2);  // 0 push, 1 masked pull, 2 pull
-    const int dist = eval_tree(sn, r[1 + pattern], f);            // 0 thread, 1 warp, 2 balanced
+    const int pattern = min(max(eval_tree(sn, lo, hi, sa.trees, r[0], f), 0), 2);  // 0 push, 1 masked pull, 2 pull
+    const int dist = eval_tree(sn, lo, hi, sa.trees, r[1 + pattern], f);            // 0 thread, 1 warp, 2 balanced
     int kid;
     if (pattern == 2) {
         kid = ASV_K_PULL_THREAD + dist;
     } else if (pattern == 1) {
         kid = ASV_K_MPULL_THREAD + dist;
     } else {
-        const int wb = eval_tree(sn, r[4], f);  // 0 atomic, 1 sort, 2 privatised
+        const int wb = eval_tree(sn, lo, hi, sa.trees, r[4], f);  // 0 atomic, 1 sort, 2 privatised
         kid = ASV_K_PUSH_THREAD_ATOM + 3 * wb + dist;
     }
     if (kid < 0 || kid >= ASV_K_COUNT) kid = ASV_K_PULL_BAL;

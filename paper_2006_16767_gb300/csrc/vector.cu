@@ -28,6 +28,7 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
     desc->user_xval = di.user_xval;
     desc->out_mode = di.out_mode;
     desc->x_sparse = di.x_sparse;
+    desc->ymask = di.ymask;
     desc->vfeat[0] = (double)nx;
     desc->vfeat[1] = n > 0 ? (double)nx / (double)n : 0.0;
     desc->vfeat[2] = (double)ns;
