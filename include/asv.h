@@ -227,12 +227,20 @@ asv_status asv_compact(asv_matrix A, const void* d_x_dense, int32_t* d_idx, void
 
 /* ---------------------------------------------------------------- batched */
 
-/* Tiling of the batched product: rows of A per work item (4, 8 or 16) and
- * vectors per group (rows * (vectors + 1) * 8 bytes of shared memory, one
- * compensated FP32 pair per output, <= 200 KB; larger asks give ASV_ERR_ARG). */
+/* Tiling of the batched product.
+ * hot_columns = 0: the column-list kernel -- rows of A per work item (4, 8 or
+ *   16) and vectors per group (rows * (vectors + 1) * 8 bytes of shared
+ *   memory, one compensated FP32 pair per output, <= 200 KB).
+ * hot_columns = 64 or 128: the hot-column kernel -- at most that many columns
+ *   shared by many vectors are multiplied as a dense block (rows per item 8 or
+ *   16, vectors per group 128 or 256 = threads per block), the other entries
+ *   are added with FP32 atomics (results within tolerance, not bitwise
+ *   reproducible from call to call).
+ * Other values give ASV_ERR_ARG. */
 typedef struct {
     int32_t rows_per_tile;
     int32_t vectors_per_group;
+    int32_t hot_columns;
 } asv_tune;
 
 /* Y[b,:] = A x_b for B vectors at once (FP32 handles; a batched form of the

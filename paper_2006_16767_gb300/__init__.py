@@ -50,7 +50,8 @@ class AsvError(RuntimeError):
 
 
 class AsvTune(ctypes.Structure):
-    _fields_ = [("rows_per_tile", ctypes.c_int32), ("vectors_per_group", ctypes.c_int32)]
+    _fields_ = [("rows_per_tile", ctypes.c_int32), ("vectors_per_group", ctypes.c_int32),
+                ("hot_columns", ctypes.c_int32)]
 
 
 class _MFeat(ctypes.Structure):
@@ -196,7 +197,8 @@ def asv_matrix_update_values(h, val=None, stream=None):
 
 def asv_spmspv_batched(h, B, max_entries=0, xptr=None, xidx=None, xval=None, X_dense=None, Y=None, tune=None,
                        stream=None):
-    t = None if tune is None else ctypes.byref(AsvTune(int(tune[0]), int(tune[1])))
+    t = None if tune is None else ctypes.byref(AsvTune(int(tune[0]), int(tune[1]),
+                                                      int(tune[2]) if len(tune) > 2 else 0))
     _check(lib().asv_spmspv_batched(h, int(B), int(max_entries), _ptr(xptr), _ptr(xidx), _ptr(xval), _ptr(X_dense),
                                     _ptr(Y), t, _stream(stream)), "asv_spmspv_batched")
 
@@ -208,7 +210,7 @@ def asv_autotune_batched(h, B, max_entries=0, xptr=None, xidx=None, xval=None, X
     _check(lib().asv_autotune_batched(h, int(B), int(max_entries), _ptr(xptr), _ptr(xidx), _ptr(xval),
                                       _ptr(X_dense), _ptr(Y), cp, ctypes.byref(best), _stream(stream)),
            "asv_autotune_batched")
-    return best.rows_per_tile, best.vectors_per_group
+    return best.rows_per_tile, best.vectors_per_group, best.hot_columns
 
 
 def asv_spmspv_backward(h, B, X, dY, dX=None, dA=None, stream=None):

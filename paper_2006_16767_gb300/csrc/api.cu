@@ -197,6 +197,14 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     AL(w.status, 4, true);
     AL(w.counters, 16, true);
     AL(w.ticket, 4, true);
+    w.lcol_cap = (int32_t)std::min<int64_t>(nnz / kLongSeg + 1, (int64_t)1 << 30);
+    AL(w.lcol, sizeof(int2) * (size_t)w.lcol_cap, false);
+    AL(w.lcol_n, 4, true);
+    AL(w.chunk_t0, 4 * (nnz / 256 + 2), false);
+    {
+        std::vector<int2> empty((size_t)w.lcol_cap, make_int2(-1, 0));
+        CKH(cudaMemcpy(w.lcol, empty.data(), sizeof(int2) * empty.size(), cudaMemcpyHostToDevice));
+    }
     CKH(cudaDeviceSynchronize());  // the zero-fills above ran on the legacy stream
 
     CKH(build_csc(H, s));
@@ -584,9 +592,13 @@ static asv_status batched_args(asv_matrix A, int32_t B, int64_t max_entries, con
 }
 
 static bool tune_ok(const asv_tune& t, int32_t B) {
+    if (B < 0) return false;
+    if (t.hot_columns != 0) {
+        return (t.hot_columns == 64 || t.hot_columns == 128) && (t.rows_per_tile == 8 || t.rows_per_tile == 16) &&
+               (t.vectors_per_group == 128 || t.vectors_per_group == 256);
+    }
     const bool r_ok = t.rows_per_tile == 4 || t.rows_per_tile == 8 || t.rows_per_tile == 16;
-    return r_ok && t.vectors_per_group >= 1 &&
-           (int64_t)t.rows_per_tile * (t.vectors_per_group + 1) * 8 <= 200 * 1024 && B >= 0;
+    return r_ok && t.vectors_per_group >= 1 && (int64_t)t.rows_per_tile * (t.vectors_per_group + 1) * 8 <= 200 * 1024;
 }
 
 extern "C" asv_status asv_spmspv_batched(asv_matrix A, int32_t B, int64_t max_entries, const int64_t* d_xptr,
@@ -595,12 +607,12 @@ extern "C" asv_status asv_spmspv_batched(asv_matrix A, int32_t B, int64_t max_en
     asv_status st = batched_args(A, B, max_entries, d_xptr, d_X_dense, d_Y);
     if (st != ASV_OK) return st;
     if (B == 0 || A->m == 0) return ASV_OK;
-    asv_tune t{A->tune_R, A->tune_GB};
+    asv_tune t{A->tune_R, A->tune_GB, A->tune_hot};
     if (tune) t = *tune;
     if (!tune_ok(t, B)) return ASV_ERR_ARG;
-    t.vectors_per_group = std::min(t.vectors_per_group, B);
+    if (t.hot_columns == 0) t.vectors_per_group = std::min(t.vectors_per_group, B);
     CK(batched_forward(A, B, max_entries, d_xptr, d_xidx, (const float*)d_xval, (const float*)d_X_dense,
-                       (float*)d_Y, t.rows_per_tile, t.vectors_per_group, (cudaStream_t)stream));
+                       (float*)d_Y, t.rows_per_tile, t.vectors_per_group, t.hot_columns, (cudaStream_t)stream));
     return ASV_OK;
 }
 
@@ -624,13 +636,15 @@ extern "C" asv_status asv_autotune_batched(asv_matrix A, int32_t B, int64_t max_
         if (FILE* f = fopen(cache_path, "r")) {
             char line[1024];
             while (fgets(line, sizeof(line), f)) {
-                int r = 0, g = 0;
+                int r = 0, g = 0, hc = 0;
                 char k[600];
-                if (sscanf(line, "%599[^\t]\t%d\t%d", k, &r, &g) == 3 && key == k) {
-                    asv_tune t{r, g};
+                const int got = sscanf(line, "%599[^\t]\t%d\t%d\t%d", k, &r, &g, &hc);
+                if (got >= 3 && key == k) {
+                    asv_tune t{r, g, got == 4 ? hc : 0};
                     if (tune_ok(t, B)) {
                         A->tune_R = r;
                         A->tune_GB = g;
+                        A->tune_hot = t.hot_columns;
                         if (h_best) *h_best = t;
                         fclose(f);
                         return ASV_OK;
@@ -640,15 +654,18 @@ extern "C" asv_status asv_autotune_batched(asv_matrix A, int32_t B, int64_t max_
             fclose(f);
         }
     }
-    const asv_tune cands[] = {{4, 4096}, {4, 2048}, {8, 512}, {8, 1024}, {8, 2048}, {4, 1024}, {16, 256},
-                              {16, 512}, {16, 1024}, {16, 1536}};
+    const asv_tune cands[] = {{4, 4096, 0},   {4, 2048, 0},   {8, 512, 0},    {8, 1024, 0},  {8, 2048, 0},
+                              {4, 1024, 0},   {16, 256, 0},   {16, 512, 0},   {16, 1024, 0}, {16, 1536, 0},
+                              {8, 256, 128},  {16, 256, 128}, {16, 128, 128}, {16, 256, 64}};
     float best = 1e30f;
-    asv_tune bt{A->tune_R, A->tune_GB};
+    asv_tune bt{A->tune_R, A->tune_GB, A->tune_hot};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     for (const asv_tune& c : cands) {
-        if (!tune_ok(c, B) || (c.vectors_per_group > 2 * std::max(B, 1) && c.vectors_per_group > 256)) continue;
+        if (!tune_ok(c, B) ||
+            (c.hot_columns == 0 && c.vectors_per_group > 2 * std::max(B, 1) && c.vectors_per_group > 256))
+            continue;
         st = asv_spmspv_batched(A, B, max_entries, d_xptr, d_xidx, d_xval, d_X_dense, d_Y, &c, stream);
         if (st != ASV_OK) break;
         float tsum = 0.f;
@@ -671,10 +688,11 @@ extern "C" asv_status asv_autotune_batched(asv_matrix A, int32_t B, int64_t max_
     if (st != ASV_OK) return st;
     A->tune_R = bt.rows_per_tile;
     A->tune_GB = bt.vectors_per_group;
+    A->tune_hot = bt.hot_columns;
     if (h_best) *h_best = bt;
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "a")) {
-            fprintf(f, "%s\t%d\t%d\n", key.c_str(), bt.rows_per_tile, bt.vectors_per_group);
+            fprintf(f, "%s\t%d\t%d\t%d\n", key.c_str(), bt.rows_per_tile, bt.vectors_per_group, bt.hot_columns);
             fclose(f);
         }
     }

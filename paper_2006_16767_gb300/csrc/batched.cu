@@ -20,6 +20,22 @@
 // is read once per vector group instead of once per vector, and every
 // element of Y is written exactly once, with R consecutive values per vector.
 //
+// Hot columns. When a few columns of A are shared by most vectors of the
+// batch (Zipf-distributed features: the 128 most popular columns of the
+// 1M x 131k benchmark matrix carry 98 % of the batch's multiply-adds), the
+// product restricted to those columns is a dense one: the batch's entries in
+// the hot columns are scattered into a dense [H][B] block Xh (zeros where a
+// vector lacks the column), and a persistent kernel gives each thread one
+// vector and each work item R rows: the item's slice of Xh sits in shared
+// memory, the rows' hot entries (in row order) are read as broadcasts, and
+// every thread sums its R outputs with fused multiply-adds in registers --
+// groups of eight terms in FP32, groups added with compensation -- and
+// writes them, so the kernel writes all of Y. The remaining (cold) entries
+// of the batch are then pushed through A's CSC view with FP32 atomic adds
+// into Y. Hot columns are those present in at least theta vectors, theta
+// the smallest power of two that keeps their number within H (chosen on
+// the device from a histogram of the columns' batch counts).
+//
 // Backward. With dY and X given dense [B][m] and [B][n]: both are
 // transposed to vector-minor layouts (dYt[m][B], Xt[n][B]) so that one
 // matrix entry meets B contiguous values; dX^T[j][:] = sum over column j of
@@ -213,6 +229,184 @@ __global__ void __launch_bounds__(R * 32) k_batched_fwd(const BatchDesc* __restr
     }
 }
 
+// ---------------------------------------------------------------- hot-column path
+constexpr int kHotMinCount = 16;  // a column shared by fewer vectors stays cold
+
+// histogram of the columns' batch counts by bit length (bin b: counts in [2^(b-1), 2^b))
+__global__ void k_hot_hist(const int32_t* __restrict__ cptr, int64_t n, int32_t* hist) {
+    __shared__ int32_t sh[33];
+    for (int i = threadIdx.x; i < 33; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cptr[j + 1] - cptr[j];
+        if (c >= kHotMinCount) atomicAdd(&sh[32 - __clz(c)], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 33; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// theta = the smallest power of two whose columns (counts >= theta) number
+// at most hmax; the histogram is re-zeroed for the next call
+__global__ void k_hot_pick(int32_t* hist, int32_t hmax, int32_t* theta, int32_t* hot_n) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int32_t acc = 0, th = 0x7fffffff;
+    for (int b = 32; b >= 1; --b) {
+        if (acc + hist[b] > hmax) break;
+        acc += hist[b];
+        if (hist[b] > 0 || acc > 0) th = 1 << (b - 1);
+    }
+    *theta = max(th, kHotMinCount);
+    *hot_n = 0;
+    for (int b = 0; b < 33; ++b) hist[b] = 0;
+}
+
+__global__ void k_hot_assign(const int32_t* __restrict__ cptr, int64_t n, const int32_t* __restrict__ theta,
+                             int32_t* hot_id, int32_t* hot_n) {
+    const int32_t th = *theta;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cptr[j + 1] - cptr[j];
+        hot_id[j] = c >= th ? atomicAdd(hot_n, 1) : -1;
+    }
+}
+
+// the batch's entries in hot columns -> Xh[h][b]
+__global__ void k_hot_scatter(const uint32_t* __restrict__ key, const uint64_t* __restrict__ pay,
+                              const int64_t* __restrict__ count, const int32_t* __restrict__ hot_id, int32_t B,
+                              float* Xh) {
+    const int64_t E = *count;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t h = hot_id[key[e]];
+        if (h >= 0) {
+            const uint64_t pv = pay[e];
+            Xh[(int64_t)h * B + (uint32_t)(pv >> 32)] = __uint_as_float((uint32_t)pv);
+        }
+    }
+}
+
+template <int R, int V, int HM>
+__global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__ bd, int64_t m, int32_t B,
+                                                  const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                                  const float* __restrict__ val, const int32_t* __restrict__ hot_id,
+                                                  const int32_t* __restrict__ hot_n, const float* __restrict__ Xh,
+                                                  unsigned long long* queue, unsigned int* ticket) {
+    extern __shared__ float xs[];                 // [HM][V] slice of Xh for the current vector tile
+    __shared__ int32_t s_hid[R][HM];              // each row's hot entries, in row order
+    __shared__ float s_a[R][HM];
+    __shared__ int32_t s_cnt[R];
+    __shared__ long long s_item;
+    __shared__ bool s_last;
+    float* __restrict__ Y = bd->Y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NW = V / 32;
+    const int32_t H = min(*hot_n, HM);
+    const int64_t ntiles = (m + R - 1) / R;
+    const int32_t nvt = (B + V - 1) / V;
+    const long long total = (long long)ntiles * nvt;
+    int32_t cur_vt = -1;
+    while (true) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        const int32_t vt = (int32_t)(item / ntiles);   // vector-tile major: the grid shares one slice
+        const int64_t r0 = (item % ntiles) * R;
+        const int32_t b = vt * V + (int32_t)threadIdx.x;
+        if (vt != cur_vt) {
+            for (int h = 0; h < H; ++h) xs[h * V + threadIdx.x] = b < B ? __ldg(Xh + (int64_t)h * B + b) : 0.0f;
+            cur_vt = vt;
+        }
+        // rows r0 .. r0+R-1: warp w collects rows w, w + NW, ... (ballot keeps row order)
+        for (int r = w; r < R; r += NW) {
+            const int64_t i = r0 + r;
+            int32_t cnt = 0;
+            if (i < m) {
+                const int32_t rb = __ldg(rowptr + i), re = __ldg(rowptr + i + 1);
+                for (int32_t k0 = rb; k0 < re; k0 += 32) {
+                    const int32_t k = k0 + lane;
+                    int32_t h = -1;
+                    float a = 0.0f;
+                    if (k < re) {
+                        h = __ldg(hot_id + __ldg(col + k));
+                        a = val ? __ldg(val + k) : 1.0f;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, h >= 0);
+                    const int pos = cnt + __popc(bal & lanemask_lt());
+                    if (h >= 0 && pos < HM) {
+                        s_hid[r][pos] = h;
+                        s_a[r][pos] = a;
+                    }
+                    cnt += __popc(bal);
+                }
+            }
+            if (lane == 0) s_cnt[r] = min(cnt, HM);
+        }
+        __syncthreads();
+        if (b < B) {
+            float out[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                KahanF acc;
+                acc.zero();
+                const int c = s_cnt[r];
+                int q = 0;
+                for (; q + 8 <= c; q += 8) {
+                    float p = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) p = __fmaf_rn(s_a[r][q + u], xs[s_hid[r][q + u] * V + threadIdx.x], p);
+                    acc.add(p);
+                }
+                float p = 0.0f;
+                for (; q < c; ++q) p = __fmaf_rn(s_a[r][q], xs[s_hid[r][q] * V + threadIdx.x], p);
+                acc.add(p);
+                out[r] = acc.value();
+            }
+            float* yb = Y + (int64_t)b * m + r0;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (r0 + r < m) yb[r] = out[r];
+        }
+        __syncthreads();
+    }
+    // the last block out resets the queue (zero-invariant)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        atomicExch(queue, 0ull);
+        __threadfence();
+        atomicExch(ticket, 0u);
+    }
+}
+
+// the cold entries (b, j, v) of the batch: Y[b][i] += a_ij v over column j of
+// A (CSC), one warp per entry
+__global__ void __launch_bounds__(256) k_batched_cold(const uint32_t* __restrict__ key,
+                                                      const uint64_t* __restrict__ pay,
+                                                      const int64_t* __restrict__ count,
+                                                      const int32_t* __restrict__ hot_id,
+                                                      const int32_t* __restrict__ colptr,
+                                                      const int32_t* __restrict__ rowidx,
+                                                      const float* __restrict__ valc, const BatchDesc* __restrict__ bd,
+                                                      int64_t m) {
+    float* __restrict__ Y = bd->Y;
+    const int lane = threadIdx.x & 31;
+    const int64_t E = *count;
+    const int64_t wpb = blockDim.x / 32;
+    for (int64_t e = blockIdx.x * wpb + (threadIdx.x >> 5); e < E; e += (int64_t)gridDim.x * wpb) {
+        const uint32_t j = key[e];
+        if (hot_id[j] >= 0) continue;
+        const uint64_t pv = pay[e];
+        const float v = __uint_as_float((uint32_t)pv);
+        float* yb = Y + (int64_t)(uint32_t)(pv >> 32) * m;
+        const int32_t kb = __ldg(colptr + j), ke = __ldg(colptr + j + 1);
+        for (int32_t k = kb + lane; k < ke; k += 32)
+            atomicAdd(yb + __ldg(rowidx + k), __fmul_rn(valc ? __ldg(valc + k) : 1.0f, v));
+    }
+}
+
 // ---------------------------------------------------------------- backward kernels
 // out[c][r] = in[r][c] for a rows x cols FP32 matrix (32x32 shared tiles)
 __global__ void k_transpose(const float* __restrict__ in, float* __restrict__ out, int64_t rows, int64_t cols) {
@@ -355,9 +549,60 @@ static void fwd_kernel(asv_matrix_s* H, int32_t B, int R, int GB, const uint64_t
 #undef FWD
 }
 
+static cudaError_t hot_workspace(asv_matrix_s* H, int32_t hot) {
+    BatchWs& bw = H->bws;
+    cudaError_t e;
+    if (!bw.hot_id) {
+        if ((e = cudaMalloc((void**)&bw.hot_id, 4 * std::max<int64_t>(H->n, 1))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&bw.hot_ctl, 4 * 40)) != cudaSuccess) return e;
+        if ((e = cudaMemset(bw.hot_ctl, 0, 4 * 40)) != cudaSuccess) return e;
+    }
+    const int64_t need = (int64_t)hot * bw.cap_B;
+    if (need > bw.xh_cap) {
+        cudaDeviceSynchronize();
+        bfree(bw.xh);
+        if ((e = cudaMalloc(&bw.xh, 4 * need)) != cudaSuccess) return e;
+        bw.xh_cap = need;
+        for (auto& kv : bw.graphs) cudaGraphExecDestroy(kv.second);  // they hold the old block
+        bw.graphs.clear();
+    }
+    return cudaSuccess;
+}
+
+// hot columns -> dense Xh, the persistent kernel that writes Y, then the cold entries
+static void hot_pipeline(asv_matrix_s* H, int32_t B, int R, int V, int hot, const uint32_t* key,
+                         const uint64_t* pay, const int64_t* count, cudaStream_t s) {
+    BatchWs& bw = H->bws;
+    int32_t* hist = bw.hot_ctl;          // [33]
+    int32_t* theta = bw.hot_ctl + 33;
+    int32_t* hot_n = bw.hot_ctl + 34;
+    const int g = H->num_sms * 4;
+    k_hot_hist<<<g, 256, 0, s>>>(bw.cptr, H->n, hist);
+    k_hot_pick<<<1, 32, 0, s>>>(hist, hot, theta, hot_n);
+    k_hot_assign<<<g, 256, 0, s>>>(bw.cptr, H->n, theta, bw.hot_id, hot_n);
+    cudaMemsetAsync(bw.xh, 0, 4 * (size_t)hot * B, s);
+    k_hot_scatter<<<g, 256, 0, s>>>(key, pay, count, bw.hot_id, B, (float*)bw.xh);
+    unsigned long long* q = (unsigned long long*)bw.queue;
+    unsigned int* tk = (unsigned int*)(bw.queue + 1);
+    const float* val = (const float*)H->val;
+    const BatchDesc* bd = (const BatchDesc*)bw.desc;
+    const size_t shm = (size_t)hot * V * 4;
+#define HOT(RR, VV, HH)                                                                                            do {                                                                                                               int per_sm = 1;                                                                                                cudaFuncSetAttribute(k_batched_hot<RR, VV, HH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_hot<RR, VV, HH>, VV, shm);                   const int grid = H->num_sms * std::max(per_sm, 1);                                                             k_batched_hot<RR, VV, HH><<<grid, VV, shm, s>>>(bd, H->m, B, H->rowptr, H->col, val, bw.hot_id, hot_n,                                                         (const float*)bw.xh, q, tk);                               } while (0)
+    if (hot <= 64) {
+        if (R <= 8) { if (V <= 128) HOT(8, 128, 64); else HOT(8, 256, 64); }
+        else { if (V <= 128) HOT(16, 128, 64); else HOT(16, 256, 64); }
+    } else {
+        if (R <= 8) { if (V <= 128) HOT(8, 128, 128); else HOT(8, 256, 128); }
+        else { if (V <= 128) HOT(16, 128, 128); else HOT(16, 256, 128); }
+    }
+#undef HOT
+    k_batched_cold<<<H->num_sms * 8, 256, 0, s>>>(key, pay, count, bw.hot_id, H->colptr, H->rowidx,
+                                                  (const float*)H->val_csc, bd, H->m);
+}
+
 // The batched pipeline: entry count, regrouping by column (radix sort), column
-// pointers, then the persistent forward kernel.
-static void enqueue_batched(asv_matrix_s* H, int32_t B, int R, int GB, cudaStream_t s) {
+// pointers, then the persistent forward kernel (or the hot-column pipeline).
+static void enqueue_batched(asv_matrix_s* H, int32_t B, int R, int GB, int hot, cudaStream_t s) {
     BatchWs& bw = H->bws;
     const BatchDesc* bd = (const BatchDesc*)bw.desc;
     int64_t* count = bw.xptr + (bw.cap_B + 1);
@@ -371,18 +616,21 @@ static void enqueue_batched(asv_matrix_s* H, int32_t B, int R, int GB, cudaStrea
     uint64_t* vb[2] = {bw.pay[0], bw.pay[1]};
     const int cur = radix_sort<uint64_t, true>(kb, vb, 0, count, bitlen(H->n - 1), H->ws.hist, H->ws.blk, H->G, s);
     k_batch_colptr<<<H->num_sms * 8, 256, 0, s>>>(kb[cur], count, H->n, bw.cptr);
-    fwd_kernel(H, B, R, GB, vb[cur], s);
+    if (hot > 0) hot_pipeline(H, B, R, GB, hot, kb[cur], vb[cur], count, s);
+    else fwd_kernel(H, B, R, GB, vb[cur], s);
 }
 
 cudaError_t batched_forward(asv_matrix_s* H, int32_t B, int64_t max_entries, const int64_t* xptr, const int32_t* xidx,
-                            const float* xval, const float* Xdense, float* Y, int R, int GB, cudaStream_t s) {
+                            const float* xval, const float* Xdense, float* Y, int R, int GB, int hot,
+                            cudaStream_t s) {
     const int64_t need = Xdense ? (int64_t)B * H->n : max_entries;
     cudaError_t e = batch_workspace(H, need, B);
     if (e != cudaSuccess) return e;
+    if (hot > 0 && (e = hot_workspace(H, hot)) != cudaSuccess) return e;
     BatchWs& bw = H->bws;
     BatchDesc hd{xptr, xidx, xval, Xdense, Y, bw.cap_entries};
     if ((e = cudaMemcpyAsync(bw.desc, &hd, sizeof(hd), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
-    const long long key = ((long long)B << 20) | ((long long)R << 12) | (long long)GB;
+    const long long key = ((long long)B << 24) | ((long long)hot << 16) | ((long long)R << 12) | (long long)GB;
     auto it = bw.graphs.find(key);
     if (it == bw.graphs.end()) {
         if (!H->cap_stream) {
@@ -390,7 +638,7 @@ cudaError_t batched_forward(asv_matrix_s* H, int32_t B, int64_t max_entries, con
         }
         cudaGraph_t g;
         if ((e = cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
-        enqueue_batched(H, B, R, GB, H->cap_stream);
+        enqueue_batched(H, B, R, GB, hot, H->cap_stream);
         if ((e = cudaStreamEndCapture(H->cap_stream, &g)) != cudaSuccess) return e;
         cudaGraphExec_t ex;
         e = cudaGraphInstantiate(&ex, g, 0);
@@ -463,7 +711,7 @@ void batch_release(asv_matrix_s* H) {
     for (auto& kv : bw.graphs) cudaGraphExecDestroy(kv.second);
     bw.graphs.clear();
     void* ps[] = {bw.keys[0], bw.keys[1], bw.pay[0], bw.pay[1], bw.xptr, bw.cptr, bw.desc, bw.queue, bw.dYt, bw.Xt,
-                  bw.dXt};
+                  bw.dXt, bw.hot_id, bw.hot_ctl, bw.xh};
     for (void* p : ps) if (p) cudaFree(p);
 }
 

@@ -233,6 +233,13 @@ struct Ws {
     int32_t* status;         // latched device status word
     unsigned long long* counters;  // zero-invariant accumulators of the feature pass
     unsigned int* ticket;    // last-block tickets (zero-invariant)
+    // listed columns over kLongSeg entries met by the thread/warp push: list
+    // index and a segment cursor per entry, their count; reset to zero by
+    // the next call's feature pass
+    int2* lcol;
+    unsigned int* lcol_n;
+    int32_t lcol_cap;
+    int32_t* chunk_t0;       // list entry owning the first item of each balanced push chunk
 };
 
 __device__ __forceinline__ void latch_status(int32_t* status, int32_t code) {

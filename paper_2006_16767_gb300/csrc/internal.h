@@ -45,6 +45,12 @@ struct BatchWs {
     void* Xt = nullptr;
     void* dXt = nullptr;
     int32_t bwd_B = 0;
+    // hot-column path: column -> hot slot, control words (histogram, threshold,
+    // count), dense [hot][B] block of the batch's hot entries
+    int32_t* hot_id = nullptr;
+    int32_t* hot_ctl = nullptr;
+    void* xh = nullptr;
+    int64_t xh_cap = 0;
 };
 
 struct asv_matrix_s {
@@ -101,7 +107,7 @@ struct asv_matrix_s {
     cudaStream_t cap_stream = nullptr;
     int G = 0;  // fixed grid of the scan / sort / compaction primitives
     BatchWs bws;
-    int32_t tune_R = 8, tune_GB = 1024;  // batched tiling chosen by the autotuner
+    int32_t tune_R = 8, tune_GB = 1024, tune_hot = 0;  // batched tiling chosen by the autotuner
     // breadth-first search workspaces (first asv_bfs call): visited bitmap,
     // two frontier lists, their device counts, a pinned host count
     uint32_t* bfs_visited = nullptr;
@@ -184,7 +190,8 @@ void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s
 
 // batched.cu
 cudaError_t batched_forward(asv_matrix_s* H, int32_t B, int64_t max_entries, const int64_t* xptr, const int32_t* xidx,
-                            const float* xval, const float* Xdense, float* Y, int R, int GB, cudaStream_t s);
+                            const float* xval, const float* Xdense, float* Y, int R, int GB, int hot,
+                            cudaStream_t s);
 cudaError_t batched_backward(asv_matrix_s* H, int32_t B, const float* X, const float* dY, float* dX, float* dA,
                              cudaStream_t s);
 void batch_release(asv_matrix_s* H);

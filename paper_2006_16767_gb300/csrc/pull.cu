@@ -36,9 +36,14 @@ __device__ __forceinline__ typename Sr<T>::Acc row_direct(const int32_t* __restr
     typename S::Acc acc;
     S::acc_zero(acc);
     if constexpr (S::kPattern) {
-        // four terms per step (their index loads and bit gathers in flight
-        // together); OR is settled by the first true term
-        for (int32_t k = b; k < e; k += 4) {
+        // the first term alone (with a dense frontier most rows stop there),
+        // then four terms per step with their index loads and bit gathers in
+        // flight together; OR is settled by the first true term
+        if (b < e && bool_gather(x, xbits, __ldg(col + b))) {
+            hit = true;
+            return 1u;
+        }
+        for (int32_t k = b + 1; k < e; k += 4) {
             int32_t c[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) c[u] = k + u < e ? __ldg(col + k + u) : -1;

@@ -53,6 +53,64 @@ __device__ __forceinline__ T list_val(const CallDesc* d, int64_t t) {
 // by its whole warp right after, so no thread serialises a hub alone.
 constexpr int kLongCol = 64;
 
+// A listed column of more than kLongSeg entries (a hub) would keep one warp
+// busy long after the rest of the grid is done, so the warp that meets it
+// queues it instead, and every warp, once its own columns are done, takes
+// segments of kLongSeg entries from the queued columns through per-column
+// atomic cursors. The warp that queued a column reaches the queue after
+// queuing it, so every segment is taken; nobody waits.
+template <class T, int WB>
+__device__ __forceinline__ void push_segment(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
+                                             const T* __restrict__ valc, const CallDesc* __restrict__ desc,
+                                             const Ws& ws, const uint32_t* ym, int64_t t, int32_t s, int lane) {
+    using S = Sr<T>;
+    const int32_t j = desc->xidx[t];
+    const T xj = list_val<T>(desc, t);
+    const int32_t b = __ldg(colptr + j), e = __ldg(colptr + j + 1);
+    const int64_t pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
+    const int32_t sb = b + s * kLongSeg, se = min(sb + kLongSeg, e);
+    for (int32_t k = sb + lane; k < se; k += 32)
+        emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
+}
+
+// Queues list entry t (column of `len` entries); returns false when the
+// queue is full (the caller then walks the column itself).
+// An entry reads (-1, 0) until its column is published, so a helper that
+// sees the count before the entry skips it (its owner processes it).
+__device__ __forceinline__ bool queue_long(const Ws& ws, int64_t t) {
+    const unsigned q = atomicAdd(ws.lcol_n, 1u);
+    if ((int32_t)q >= ws.lcol_cap) return false;
+    *(volatile int32_t*)&ws.lcol[q].x = (int32_t)t;
+    return true;
+}
+
+template <class T, int WB>
+__device__ __forceinline__ void help_long(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
+                                          const T* __restrict__ valc, const CallDesc* __restrict__ desc,
+                                          const Ws& ws, const uint32_t* ym, int lane) {
+    const int32_t nq = min((int32_t)*(volatile unsigned int*)ws.lcol_n, ws.lcol_cap);
+    for (int32_t q = 0; q < nq; ++q) {
+        int32_t t = 0, nseg = 0;
+        if (lane == 0) {
+            t = *(volatile int32_t*)&ws.lcol[q].x;
+            if (t >= 0) {
+                const int32_t j = desc->xidx[t];
+                nseg = (__ldg(colptr + j + 1) - __ldg(colptr + j) + kLongSeg - 1) / kLongSeg;
+            }
+        }
+        t = __shfl_sync(0xffffffffu, t, 0);
+        nseg = __shfl_sync(0xffffffffu, nseg, 0);
+        if (t < 0) continue;  // not yet published: its owner will take it
+        for (;;) {
+            int32_t s = 0;
+            if (lane == 0) s = atomicAdd(&ws.lcol[q].y, 1);
+            s = __shfl_sync(0xffffffffu, s, 0);
+            if (s >= nseg) break;
+            push_segment<T, WB>(colptr, rowidx, valc, desc, ws, ym, t, s, lane);
+        }
+    }
+}
+
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                                      const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
@@ -78,7 +136,9 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
         const bool lng = e - b > kLongCol;
         if (!lng)
             for (int32_t k = b; k < e; ++k) emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
-        for (unsigned pend = __ballot_sync(0xffffffffu, lng); pend; pend &= pend - 1) {
+        // hubs go to the shared queue; the rest of the long columns to the warp
+        const bool queued = lng && e - b > kLongSeg && queue_long(ws, t);
+        for (unsigned pend = __ballot_sync(0xffffffffu, lng && !queued); pend; pend &= pend - 1) {
             const int src = __ffs(pend) - 1;
             const int32_t bb = __shfl_sync(0xffffffffu, b, src), ee = __shfl_sync(0xffffffffu, e, src);
             const int64_t p0 = __shfl_sync(0xffffffffu, pos0, src);
@@ -88,6 +148,7 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
                 emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xx), p0 + k);
         }
     }
+    help_long<T, WB>(colptr, rowidx, valc, desc, ws, ym, lane);
 }
 
 template <class T, int WB>
@@ -103,54 +164,120 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
         const int32_t j = xidx[t];
         const T xj = list_val<T>(desc, t);
         const int32_t b = __ldg(colptr + j), e = __ldg(colptr + j + 1);
+        if (e - b > kLongSeg) {
+            bool queued = false;
+            if (lane == 0) queued = queue_long(ws, t);
+            if (__shfl_sync(0xffffffffu, queued, 0)) continue;
+        }
         const int64_t pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
         for (int32_t k = b + lane; k < e; k += 32) emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
     }
+    help_long<T, WB>(colptr, rowidx, valc, desc, ws, ym, lane);
 }
 
 // Even split: warp-chunks of 32*IPT effective nonzeros; the listed column of
-// effective index e is the last t with xscan[t] <= e (binary search inside
-// the chunk's column range).
+// effective index e is the last t with xscan[t] <= e. A warp finds the range
+// [t0, t1] of columns its chunk touches by two binary searches, then (when
+// the range is short, the usual case) resolves every item's column with a
+// load-balanced search in shared memory: each column's start is marked in a
+// per-item table and a running maximum fills the gaps, while the columns'
+// base offsets (colptr[j] - xscan[t]) and x values are staged beside it.
+// Every item then costs one shared-memory read plus its own coalesced loads
+// of the row index and value. Ranges longer than the chunk (runs of empty
+// columns) fall back to one binary search per item.
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                                   const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
     using S = Sr<T>;
-    const uint32_t* __restrict__ ym = desc->ymask;
     constexpr int CH = 32 * kPushIPT;
-    const int lane = threadIdx.x & 31;
+    __shared__ int32_t s_t[8][CH];          // item -> list index of its column
+    __shared__ int32_t s_base[8][CH + 1];   // column t0 + q: colptr[j] - xscan[t]
+    __shared__ T s_xv[8][S::kPattern ? 1 : CH + 1];
+    const uint32_t* __restrict__ ym = desc->ymask;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nx = desc->nnz_x, ns = desc->nnz_s;
     const int32_t* __restrict__ xidx = desc->xidx;
     const int32_t* __restrict__ sc = ws.xscan;
     const int64_t nchunks = (ns + CH - 1) / CH;
     const int64_t wpb = blockDim.x / 32;
-    for (int64_t c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks; c += (int64_t)gridDim.x * wpb) {
+    for (int64_t c = blockIdx.x * wpb + w; c < nchunks; c += (int64_t)gridDim.x * wpb) {
         const int64_t e0 = c * CH, elast = min(e0 + CH, ns) - 1;
-        int64_t bound = 0;
-        if (lane < 2) {
-            const int64_t target = lane == 0 ? e0 : elast;
-            int64_t lo = 0, hi = nx - 1;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if ((int64_t)sc[mid] <= target) lo = mid;
-                else hi = mid - 1;
+        // the chunk's columns lie in [owner of e0, owner of the next chunk's
+        // first item] (columns past elast start beyond the chunk and are skipped)
+        const int64_t t0 = ws.chunk_t0[c];
+        const int64_t t1 = (c + 1 < nchunks) ? (int64_t)ws.chunk_t0[c + 1] : nx - 1;
+        const int nt = (int)(t1 - t0 + 1);
+        if (nt <= CH + 1) {
+            for (int i = lane; i < CH; i += 32) s_t[w][i] = -1;
+            __syncwarp();
+            for (int q = lane; q < nt; q += 32) {
+                const int64_t t = t0 + q;
+                const int32_t st = sc[t];
+                s_base[w][q] = __ldg(colptr + xidx[t]) - st;
+                if constexpr (!S::kPattern) s_xv[w][q] = list_val<T>(desc, t);
+                const int64_t pos = max((int64_t)st - e0, (int64_t)0);
+                if (pos < CH) atomicMax(&s_t[w][pos], (int32_t)q);
             }
-            bound = lo;
-        }
-        const int64_t t0 = __shfl_sync(0xffffffffu, bound, 0), t1 = __shfl_sync(0xffffffffu, bound, 1);
+            __syncwarp();
+            // running maximum over the table: lane l owns entries 8l .. 8l+7
+            int32_t run = -1;
+            int32_t v[kPushIPT];
+#pragma unroll
+            for (int u = 0; u < kPushIPT; ++u) {
+                run = max(run, s_t[w][lane * kPushIPT + u]);
+                v[u] = run;
+            }
+            int32_t pre = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t other = __shfl_up_sync(0xffffffffu, pre, o);
+                if (lane >= o) pre = max(pre, other);
+            }
+            int32_t carry = __shfl_up_sync(0xffffffffu, pre, 1);
+            if (lane == 0) carry = -1;
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < kPushIPT; ++u) s_t[w][lane * kPushIPT + u] = max(v[u], carry);
+            __syncwarp();
+#pragma unroll 4
+            for (int s2 = 0; s2 < kPushIPT; ++s2) {
+                const int64_t e = e0 + s2 * 32 + lane;
+                if (e > elast) break;
+                const int q = s_t[w][s2 * 32 + lane];
+                const int64_t k = (int64_t)s_base[w][q] + e;
+                const T xq = S::kPattern ? S::one() : s_xv[w][S::kPattern ? 0 : q];
+                emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xq), e);
+            }
+            __syncwarp();
+        } else {
 #pragma unroll 2
-        for (int s = 0; s < kPushIPT; ++s) {
-            const int64_t e = e0 + s * 32 + lane;
-            if (e > elast) break;
-            int64_t lo = t0, hi = t1;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if ((int64_t)sc[mid] <= e) lo = mid;
-                else hi = mid - 1;
+            for (int s2 = 0; s2 < kPushIPT; ++s2) {
+                const int64_t e = e0 + s2 * 32 + lane;
+                if (e > elast) break;
+                int64_t lo = t0, hi = t1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) >> 1;
+                    if ((int64_t)sc[mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int32_t j = xidx[lo];
+                const int64_t k = (int64_t)__ldg(colptr + j) + (e - sc[lo]);
+                emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), list_val<T>(desc, lo)), e);
             }
-            const int32_t j = xidx[lo];
-            const int64_t k = (int64_t)__ldg(colptr + j) + (e - sc[lo]);
-            emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), list_val<T>(desc, lo)), e);
         }
+    }
+}
+
+// The list entry owning the first item of every balanced chunk: entry t
+// covers items [xscan[t], xscan[t+1]); each chunk start lies in exactly one
+// non-empty entry, which writes it (no search, no atomics).
+__global__ void k_chunk_owner(const int32_t* __restrict__ sc, const CallDesc* __restrict__ desc, int32_t* chunk_t0) {
+    constexpr int CH = 32 * kPushIPT;
+    const int64_t nx = desc->nnz_x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nx; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = sc[t], e = sc[t + 1];
+        if (e <= b) continue;
+        for (int64_t c = (b + CH - 1) / CH; c * CH < e; ++c) chunk_t0[c] = (int32_t)t;
     }
 }
 
@@ -310,18 +437,22 @@ static int bitlen64(int64_t v) {
 template <class T>
 static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s) {
     const T* valc = (const T*)H->val_csc;
-    const int grid = H->num_sms * 32;
+    // a few blocks per SM for the per-column traversals (they stride over the
+    // list, and a large grid of mostly idle blocks costs launch time on short
+    // lists); more, smaller waves for the balanced one, whose chunks vary in cost
+    const int grid = H->num_sms * 8;
     const CallDesc* d = H->d_desc;
     Ws ws = H->ws;
     if (dist == 2 || wb != WB_ATOM) {
         k_list_deg<<<grid, 256, 0, s>>>(H->colptr, d, ws.xscan);
         scan_excl(ws.xscan, ws.xscan, 0, &H->d_desc->nnz_x, ws.blk, H->G, true, s);
     }
+    if (dist == 2) k_chunk_owner<<<grid, 256, 0, s>>>(ws.xscan, d, ws.chunk_t0);
 #define TRAV(WBV)                                                                                   \
     do {                                                                                            \
         if (dist == 0) k_push_thread<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws); \
         else if (dist == 1) k_push_warp<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws); \
-        else k_push_bal<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws);          \
+        else k_push_bal<T, WBV><<<grid * 4, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws);      \
     } while (0)
     if (wb == WB_ATOM) TRAV(WB_ATOM);
     else TRAV(WB_SORT);

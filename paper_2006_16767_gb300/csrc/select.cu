@@ -24,6 +24,9 @@ SelectArg select_arg(asv_matrix_s* H, unsigned long long cond) {
     sa.last_kid = H->d_last_kid;
     sa.cond = cond;
     sa.enabled = 1;
+    sa.lcol = H->ws.lcol;
+    sa.lcol_n = H->ws.lcol_n;
+    sa.lcol_cap = H->ws.lcol_cap;
     return sa;
 }
 

@@ -22,6 +22,10 @@ struct SelectArg {
     int32_t* last_kid;
     unsigned long long cond;
     int32_t enabled;
+    // the push kernels' hub-column queue, reset by every feature pass
+    int2* lcol;
+    unsigned int* lcol_n;
+    int32_t lcol_cap;
 };
 
 // Nodes [lo, hi) of the table are staged in shared memory (sn); a node

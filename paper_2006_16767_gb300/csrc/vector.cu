@@ -68,6 +68,15 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
         __threadfence();
         atomicExch(ticket, 0u);
     }
+    // the last block returns the push kernels' hub-column queue of the
+    // previous call to its empty state
+    if (last && sa.lcol_n) {
+        __shared__ int32_t s_nq;
+        if (threadIdx.x == 0) s_nq = min((int32_t)*(volatile unsigned int*)sa.lcol_n, sa.lcol_cap);
+        __syncthreads();
+        for (int32_t i = threadIdx.x; i < s_nq; i += B) sa.lcol[i] = make_int2(-1, 0);
+        if (threadIdx.x == 0) *sa.lcol_n = 0u;
+    }
     // the last block also walks the selector's trees (Sec. VI-B), so the
     // choice is ready when the feature pass ends
     if (last && sa.enabled) {

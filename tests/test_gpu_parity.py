@@ -179,6 +179,34 @@ def test_long_rows_boolean_and_int32_bit_exact(k):
     assert np.array_equal(Ai.spmspv(x_dense=to_dev(x), kernel=k).cpu().numpy(), want), f"int32 long rows k={k}"
 
 
+def long_columns_pattern():
+    """The transpose of long_rows_pattern: columns of every length class of the
+    hub-column queue of the thread and warp push (over 64, over 4096, several
+    segments)."""
+    m0, n0, rp, c = long_rows_pattern()
+    colptr, rowidx, _ = oracle.csr_to_csc(m0, n0, rp, c)
+    return n0, m0, colptr.astype(np.int32), rowidx.astype(np.int32)
+
+
+@pytest.mark.parametrize("k", ["auto"] + ALL_K)
+def test_long_columns_all_kernels(k):
+    m, n, rp, c = long_columns_pattern()
+    deg = np.bincount(c, minlength=n)
+    hubs = np.flatnonzero(deg > 64).astype(np.int32)
+    v = gen.uniform(len(c), -1, 1, seed=17, dtype=np.float64).astype(np.float32)
+    A = make(m, n, rp, c, v)
+    Ab = make(m, n, rp, c, None)
+    for idx in (hubs, np.arange(n, dtype=np.int32), gen.sample_positions(n, n // 5, seed=18)):
+        xv = gen.uniform(len(idx), -1, 1, seed=19, dtype=np.float64)
+        for sparse_out in (False, True):
+            check(A, k, "long_columns", n, rp, c, v, idx, xv, np.float32, "f32", False, sparse_out)
+        xb = np.zeros(n, np.uint8)
+        xb[idx] = 1
+        want = oracle.bool_pull(rp, c, xb)
+        y = Ab.spmspv(xidx=to_dev(idx), kernel=k).cpu().numpy()
+        assert np.array_equal(y != 0, want != 0), f"bool long columns k={k}"
+
+
 @pytest.mark.parametrize("k", ["auto"] + ALL_K)
 def test_int32_wraparound_bit_exact(k):
     rp, c, _ = gen.random_csr(1500, 1200, 0.01, seed=8)
