@@ -234,8 +234,9 @@ asv_status asv_compact(asv_matrix A, const void* d_x_dense, int32_t* d_idx, void
  * hot_columns = 64 or 128: the hot-column kernel -- at most that many columns
  *   shared by many vectors are multiplied as a dense block (rows per item 8 or
  *   16, vectors per group 128 or 256 = threads per block), the other entries
- *   are added with FP32 atomics (results within tolerance, not bitwise
- *   reproducible from call to call).
+ *   are added through shared-memory atomics (results within tolerance, not
+ *   bitwise reproducible from call to call). Its workspaces (first use) take
+ *   about 16 bytes per nonzero of A plus 4 * n * (B / vectors + 1) bytes.
  * Other values give ASV_ERR_ARG. */
 typedef struct {
     int32_t rows_per_tile;

@@ -284,21 +284,71 @@ __global__ void k_hot_scatter(const uint32_t* __restrict__ key, const uint64_t* 
     }
 }
 
+// A's entries split once per call into per-row lists, in row order: hot
+// entries (slot, a) and the cold entries (j, a) whose column some vector of
+// the batch holds; entries in columns no vector holds are dropped.
+__global__ void k_split_count(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t m,
+                              const int32_t* __restrict__ hot_id, const int32_t* __restrict__ cptr, int32_t* hcnt,
+                              int32_t* ccnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t h = 0, c = 0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            const int32_t j = __ldg(col + k);
+            if (__ldg(hot_id + j) >= 0) ++h;
+            else if (__ldg(cptr + j + 1) > __ldg(cptr + j)) ++c;
+        }
+        hcnt[i] = h;
+        ccnt[i] = c;
+    }
+}
+
+__global__ void k_split_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const float* __restrict__ val, int64_t m, const int32_t* __restrict__ hot_id,
+                             const int32_t* __restrict__ cptr, const int32_t* __restrict__ hrow,
+                             const int32_t* __restrict__ crow, int2* hent, int2* cent) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t ph = hrow[i], pc = crow[i];
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            const int32_t j = __ldg(col + k);
+            const float a = val ? __ldg(val + k) : 1.0f;
+            const int32_t h = __ldg(hot_id + j);
+            if (h >= 0) hent[ph++] = make_int2(h, __float_as_int(a));
+            else if (__ldg(cptr + j + 1) > __ldg(cptr + j)) cent[pc++] = make_int2(j, __float_as_int(a));
+        }
+    }
+}
+
+// For every cold column j that some vector holds: tb[j*(nvt+1) + t] = first
+// position of its (vector-ascending) list whose vector is in tile t or later.
+__global__ void k_tile_bounds(const int32_t* __restrict__ cptr, const uint64_t* __restrict__ pay, int64_t n,
+                              const int32_t* __restrict__ hot_id, int32_t nvt, int32_t V, int32_t* tb) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t lo = cptr[j], hi = cptr[j + 1];
+        if (hi <= lo || hot_id[j] >= 0) continue;
+        int32_t* t = tb + j * (int64_t)(nvt + 1);
+        int32_t p = lo;
+        for (int32_t u = 0; u <= nvt; ++u) {
+            const uint32_t first_b = (uint32_t)u * (uint32_t)V;
+            while (p < hi && (uint32_t)(pay[p] >> 32) < first_b) ++p;
+            t[u] = p;
+        }
+    }
+}
+
 template <int R, int V, int HM>
 __global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__ bd, int64_t m, int32_t B,
-                                                  const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                                  const float* __restrict__ val, const int32_t* __restrict__ hot_id,
+                                                  const int32_t* __restrict__ hrow, const int2* __restrict__ hent,
+                                                  const int32_t* __restrict__ crow, const int2* __restrict__ cent,
+                                                  const int32_t* __restrict__ tb, const uint64_t* __restrict__ pay,
                                                   const int32_t* __restrict__ hot_n, const float* __restrict__ Xh,
                                                   unsigned long long* queue, unsigned int* ticket) {
     extern __shared__ float xs[];                 // [HM][V] slice of Xh for the current vector tile
-    __shared__ int32_t s_hid[R][HM];              // each row's hot entries, in row order
-    __shared__ float s_a[R][HM];
-    __shared__ int32_t s_cnt[R];
+    __shared__ int2 s_ent[R * HM];                // the item's hot entries: (slot * V, a), rows in order
+    __shared__ float s_cold[R][V];                // cold contributions of the item
+    __shared__ int32_t s_hrow[R + 1], s_crow[R + 1];
     __shared__ long long s_item;
     __shared__ bool s_last;
     float* __restrict__ Y = bd->Y;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    constexpr int NW = V / 32;
     const int32_t H = min(*hot_n, HM);
     const int64_t ntiles = (m + R - 1) / R;
     const int32_t nvt = (B + V - 1) / V;
@@ -311,60 +361,68 @@ __global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__
         if (item >= total) break;
         const int32_t vt = (int32_t)(item / ntiles);   // vector-tile major: the grid shares one slice
         const int64_t r0 = (item % ntiles) * R;
-        const int32_t b = vt * V + (int32_t)threadIdx.x;
+        const int nr = (int)min((int64_t)R, m - r0);
+        const int32_t b0 = vt * V;
+        const int32_t b = b0 + (int32_t)threadIdx.x;
         if (vt != cur_vt) {
             for (int h = 0; h < H; ++h) xs[h * V + threadIdx.x] = b < B ? __ldg(Xh + (int64_t)h * B + b) : 0.0f;
             cur_vt = vt;
         }
-        // rows r0 .. r0+R-1: warp w collects rows w, w + NW, ... (ballot keeps row order)
-        for (int r = w; r < R; r += NW) {
-            const int64_t i = r0 + r;
-            int32_t cnt = 0;
-            if (i < m) {
-                const int32_t rb = __ldg(rowptr + i), re = __ldg(rowptr + i + 1);
-                for (int32_t k0 = rb; k0 < re; k0 += 32) {
-                    const int32_t k = k0 + lane;
-                    int32_t h = -1;
-                    float a = 0.0f;
-                    if (k < re) {
-                        h = __ldg(hot_id + __ldg(col + k));
-                        a = val ? __ldg(val + k) : 1.0f;
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, h >= 0);
-                    const int pos = cnt + __popc(bal & lanemask_lt());
-                    if (h >= 0 && pos < HM) {
-                        s_hid[r][pos] = h;
-                        s_a[r][pos] = a;
-                    }
-                    cnt += __popc(bal);
-                }
+        if (threadIdx.x <= R) {
+            const int64_t i = r0 + min((int)threadIdx.x, nr);
+            s_hrow[threadIdx.x] = __ldg(hrow + i);
+            s_crow[threadIdx.x] = __ldg(crow + i);
+        }
+        for (int e = threadIdx.x; e < R * V; e += V) (&s_cold[0][0])[e] = 0.0f;
+        __syncthreads();
+        // the item's hot entries (contiguous: its rows are consecutive)
+        const int32_t h0 = s_hrow[0], hn = min(s_hrow[nr] - h0, R * HM);
+        for (int e = threadIdx.x; e < hn; e += V) {
+            const int2 en = __ldg(hent + h0 + e);
+            s_ent[e] = make_int2(en.x * V, en.y);
+        }
+        // cold entries: each thread takes entries of the item's rows and adds
+        // a * x_b for the vectors b of this tile that hold the column
+        const int32_t c0 = s_crow[0], cn = s_crow[nr] - c0;
+        for (int e = threadIdx.x; e < cn; e += V) {
+            const int2 en = __ldg(cent + c0 + e);
+            int r = 0;
+            while (r + 1 < nr && s_crow[r + 1] <= c0 + e) ++r;
+            const int32_t* t = tb + (int64_t)en.x * (nvt + 1) + vt;
+            const int32_t lo = __ldg(t), hi = __ldg(t + 1);
+            for (int32_t q = lo; q < hi; ++q) {
+                const uint64_t pv = __ldg(pay + q);
+                atomicAdd(&s_cold[r][(int32_t)(pv >> 32) - b0],
+                          __fmul_rn(__int_as_float(en.y), __uint_as_float((uint32_t)pv)));
             }
-            if (lane == 0) s_cnt[r] = min(cnt, HM);
         }
         __syncthreads();
         if (b < B) {
-            float out[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
+            const float* __restrict__ xt = xs + threadIdx.x;
+            float* yb = Y + (int64_t)b * m + r0;
+            for (int r = 0; r < nr; ++r) {
                 KahanF acc;
                 acc.zero();
-                const int c = s_cnt[r];
-                int q = 0;
-                for (; q + 8 <= c; q += 8) {
+                const int qb = s_hrow[r] - h0, qe = min(s_hrow[r + 1] - h0, R * HM);
+                int q = qb;
+                for (; q + 8 <= qe; q += 8) {
                     float p = 0.0f;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) p = __fmaf_rn(s_a[r][q + u], xs[s_hid[r][q + u] * V + threadIdx.x], p);
+                    for (int u = 0; u < 8; ++u) {
+                        const int2 en = s_ent[q + u];  // one broadcast read per term
+                        p = __fmaf_rn(__int_as_float(en.y), xt[en.x], p);
+                    }
                     acc.add(p);
                 }
                 float p = 0.0f;
-                for (; q < c; ++q) p = __fmaf_rn(s_a[r][q], xs[s_hid[r][q] * V + threadIdx.x], p);
+                for (; q < qe; ++q) {
+                    const int2 en = s_ent[q];
+                    p = __fmaf_rn(__int_as_float(en.y), xt[en.x], p);
+                }
                 acc.add(p);
-                out[r] = acc.value();
+                acc.add(s_cold[r][threadIdx.x]);
+                yb[r] = acc.value();
             }
-            float* yb = Y + (int64_t)b * m + r0;
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (r0 + r < m) yb[r] = out[r];
         }
         __syncthreads();
     }
@@ -378,32 +436,6 @@ __global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__
         atomicExch(queue, 0ull);
         __threadfence();
         atomicExch(ticket, 0u);
-    }
-}
-
-// the cold entries (b, j, v) of the batch: Y[b][i] += a_ij v over column j of
-// A (CSC), one warp per entry
-__global__ void __launch_bounds__(256) k_batched_cold(const uint32_t* __restrict__ key,
-                                                      const uint64_t* __restrict__ pay,
-                                                      const int64_t* __restrict__ count,
-                                                      const int32_t* __restrict__ hot_id,
-                                                      const int32_t* __restrict__ colptr,
-                                                      const int32_t* __restrict__ rowidx,
-                                                      const float* __restrict__ valc, const BatchDesc* __restrict__ bd,
-                                                      int64_t m) {
-    float* __restrict__ Y = bd->Y;
-    const int lane = threadIdx.x & 31;
-    const int64_t E = *count;
-    const int64_t wpb = blockDim.x / 32;
-    for (int64_t e = blockIdx.x * wpb + (threadIdx.x >> 5); e < E; e += (int64_t)gridDim.x * wpb) {
-        const uint32_t j = key[e];
-        if (hot_id[j] >= 0) continue;
-        const uint64_t pv = pay[e];
-        const float v = __uint_as_float((uint32_t)pv);
-        float* yb = Y + (int64_t)(uint32_t)(pv >> 32) * m;
-        const int32_t kb = __ldg(colptr + j), ke = __ldg(colptr + j + 1);
-        for (int32_t k = kb + lane; k < ke; k += 32)
-            atomicAdd(yb + __ldg(rowidx + k), __fmul_rn(valc ? __ldg(valc + k) : 1.0f, v));
     }
 }
 
@@ -549,13 +581,19 @@ static void fwd_kernel(asv_matrix_s* H, int32_t B, int R, int GB, const uint64_t
 #undef FWD
 }
 
-static cudaError_t hot_workspace(asv_matrix_s* H, int32_t hot) {
+static cudaError_t hot_workspace(asv_matrix_s* H, int32_t hot, int32_t V) {
     BatchWs& bw = H->bws;
     cudaError_t e;
+    bool moved = false;
     if (!bw.hot_id) {
+        const int64_t m1 = H->m + 1, nnz = std::max<int64_t>(H->nnz, 1);
         if ((e = cudaMalloc((void**)&bw.hot_id, 4 * std::max<int64_t>(H->n, 1))) != cudaSuccess) return e;
         if ((e = cudaMalloc((void**)&bw.hot_ctl, 4 * 40)) != cudaSuccess) return e;
         if ((e = cudaMemset(bw.hot_ctl, 0, 4 * 40)) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&bw.hrow, 4 * (m1 + 1))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&bw.crow, 4 * (m1 + 1))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&bw.hent, 8 * nnz)) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&bw.cent, 8 * nnz)) != cudaSuccess) return e;
     }
     const int64_t need = (int64_t)hot * bw.cap_B;
     if (need > bw.xh_cap) {
@@ -563,13 +601,25 @@ static cudaError_t hot_workspace(asv_matrix_s* H, int32_t hot) {
         bfree(bw.xh);
         if ((e = cudaMalloc(&bw.xh, 4 * need)) != cudaSuccess) return e;
         bw.xh_cap = need;
-        for (auto& kv : bw.graphs) cudaGraphExecDestroy(kv.second);  // they hold the old block
+        moved = true;
+    }
+    const int64_t tneed = std::max<int64_t>(H->n, 1) * ((bw.cap_B + V - 1) / V + 1);
+    if (tneed > bw.tb_cap) {
+        cudaDeviceSynchronize();
+        bfree(bw.tb);
+        if ((e = cudaMalloc(&bw.tb, 4 * tneed)) != cudaSuccess) return e;
+        bw.tb_cap = tneed;
+        moved = true;
+    }
+    if (moved) {  // captured pipelines hold the old buffers
+        for (auto& kv : bw.graphs) cudaGraphExecDestroy(kv.second);
         bw.graphs.clear();
     }
     return cudaSuccess;
 }
 
-// hot columns -> dense Xh, the persistent kernel that writes Y, then the cold entries
+// hot columns -> dense Xh; A split into per-row hot and cold lists; the cold
+// columns' tile bounds; the persistent kernel that writes Y
 static void hot_pipeline(asv_matrix_s* H, int32_t B, int R, int V, int hot, const uint32_t* key,
                          const uint64_t* pay, const int64_t* count, cudaStream_t s) {
     BatchWs& bw = H->bws;
@@ -582,12 +632,28 @@ static void hot_pipeline(asv_matrix_s* H, int32_t B, int R, int V, int hot, cons
     k_hot_assign<<<g, 256, 0, s>>>(bw.cptr, H->n, theta, bw.hot_id, hot_n);
     cudaMemsetAsync(bw.xh, 0, 4 * (size_t)hot * B, s);
     k_hot_scatter<<<g, 256, 0, s>>>(key, pay, count, bw.hot_id, B, (float*)bw.xh);
+    const float* val = (const float*)H->val;
+    k_split_count<<<H->num_sms * 8, 256, 0, s>>>(H->rowptr, H->col, H->m, bw.hot_id, bw.cptr, bw.hrow, bw.crow);
+    scan_excl(bw.hrow, bw.hrow, H->m, nullptr, H->ws.blk, H->G, true, s);
+    scan_excl(bw.crow, bw.crow, H->m, nullptr, H->ws.blk, H->G, true, s);
+    k_split_fill<<<H->num_sms * 8, 256, 0, s>>>(H->rowptr, H->col, val, H->m, bw.hot_id, bw.cptr, bw.hrow, bw.crow,
+                                                (int2*)bw.hent, (int2*)bw.cent);
+    const int32_t nvt = (B + V - 1) / V;
+    k_tile_bounds<<<g, 256, 0, s>>>(bw.cptr, pay, H->n, bw.hot_id, nvt, V, (int32_t*)bw.tb);
     unsigned long long* q = (unsigned long long*)bw.queue;
     unsigned int* tk = (unsigned int*)(bw.queue + 1);
-    const float* val = (const float*)H->val;
     const BatchDesc* bd = (const BatchDesc*)bw.desc;
     const size_t shm = (size_t)hot * V * 4;
-#define HOT(RR, VV, HH)                                                                                            do {                                                                                                               int per_sm = 1;                                                                                                cudaFuncSetAttribute(k_batched_hot<RR, VV, HH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_hot<RR, VV, HH>, VV, shm);                   const int grid = H->num_sms * std::max(per_sm, 1);                                                             k_batched_hot<RR, VV, HH><<<grid, VV, shm, s>>>(bd, H->m, B, H->rowptr, H->col, val, bw.hot_id, hot_n,                                                         (const float*)bw.xh, q, tk);                               } while (0)
+#define HOT(RR, VV, HH)                                                                                        \
+    do {                                                                                                       \
+        int per_sm = 1;                                                                                        \
+        cudaFuncSetAttribute(k_batched_hot<RR, VV, HH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_hot<RR, VV, HH>, VV, shm);           \
+        const int grid = H->num_sms * std::max(per_sm, 1);                                                     \
+        k_batched_hot<RR, VV, HH><<<grid, VV, shm, s>>>(bd, H->m, B, bw.hrow, (const int2*)bw.hent, bw.crow,   \
+                                                        (const int2*)bw.cent, (const int32_t*)bw.tb, pay, hot_n, \
+                                                        (const float*)bw.xh, q, tk);                           \
+    } while (0)
     if (hot <= 64) {
         if (R <= 8) { if (V <= 128) HOT(8, 128, 64); else HOT(8, 256, 64); }
         else { if (V <= 128) HOT(16, 128, 64); else HOT(16, 256, 64); }
@@ -596,8 +662,6 @@ static void hot_pipeline(asv_matrix_s* H, int32_t B, int R, int V, int hot, cons
         else { if (V <= 128) HOT(16, 128, 128); else HOT(16, 256, 128); }
     }
 #undef HOT
-    k_batched_cold<<<H->num_sms * 8, 256, 0, s>>>(key, pay, count, bw.hot_id, H->colptr, H->rowidx,
-                                                  (const float*)H->val_csc, bd, H->m);
 }
 
 // The batched pipeline: entry count, regrouping by column (radix sort), column
@@ -626,7 +690,7 @@ cudaError_t batched_forward(asv_matrix_s* H, int32_t B, int64_t max_entries, con
     const int64_t need = Xdense ? (int64_t)B * H->n : max_entries;
     cudaError_t e = batch_workspace(H, need, B);
     if (e != cudaSuccess) return e;
-    if (hot > 0 && (e = hot_workspace(H, hot)) != cudaSuccess) return e;
+    if (hot > 0 && (e = hot_workspace(H, hot, GB)) != cudaSuccess) return e;
     BatchWs& bw = H->bws;
     BatchDesc hd{xptr, xidx, xval, Xdense, Y, bw.cap_entries};
     if ((e = cudaMemcpyAsync(bw.desc, &hd, sizeof(hd), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
@@ -711,7 +775,7 @@ void batch_release(asv_matrix_s* H) {
     for (auto& kv : bw.graphs) cudaGraphExecDestroy(kv.second);
     bw.graphs.clear();
     void* ps[] = {bw.keys[0], bw.keys[1], bw.pay[0], bw.pay[1], bw.xptr, bw.cptr, bw.desc, bw.queue, bw.dYt, bw.Xt,
-                  bw.dXt, bw.hot_id, bw.hot_ctl, bw.xh};
+                  bw.dXt, bw.hot_id, bw.hot_ctl, bw.xh, bw.hrow, bw.crow, bw.hent, bw.cent, bw.tb};
     for (void* p : ps) if (p) cudaFree(p);
 }
 

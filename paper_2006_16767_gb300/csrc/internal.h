@@ -51,6 +51,14 @@ struct BatchWs {
     int32_t* hot_ctl = nullptr;
     void* xh = nullptr;
     int64_t xh_cap = 0;
+    // A's entries split per row into hot (slot, a) and cold (column, a) lists,
+    // and the cold columns' vector-tile bounds
+    int32_t* hrow = nullptr;
+    int32_t* crow = nullptr;
+    void* hent = nullptr;
+    void* cent = nullptr;
+    void* tb = nullptr;
+    int64_t tb_cap = 0;
 };
 
 struct asv_matrix_s {
