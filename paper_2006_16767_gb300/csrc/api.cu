@@ -610,6 +610,7 @@ extern "C" asv_status asv_spmspv_batched(asv_matrix A, int32_t B, int64_t max_en
     asv_tune t{A->tune_R, A->tune_GB, A->tune_hot};
     if (tune) t = *tune;
     if (!tune_ok(t, B)) return ASV_ERR_ARG;
+    if (t.hot_columns != 0 && (int64_t)t.hot_columns * B >= INT32_MAX) return ASV_ERR_OVERFLOW;
     if (t.hot_columns == 0) t.vectors_per_group = std::min(t.vectors_per_group, B);
     CK(batched_forward(A, B, max_entries, d_xptr, d_xidx, (const float*)d_xval, (const float*)d_X_dense,
                        (float*)d_Y, t.rows_per_tile, t.vectors_per_group, t.hot_columns, (cudaStream_t)stream));

@@ -342,9 +342,8 @@ __global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__
                                                   const int32_t* __restrict__ tb, const uint64_t* __restrict__ pay,
                                                   const int32_t* __restrict__ hot_n, const float* __restrict__ Xh,
                                                   unsigned long long* queue, unsigned int* ticket) {
-    extern __shared__ float xs[];                 // [HM][V] slice of Xh for the current vector tile
-    __shared__ int2 s_ent[R * HM];                // the item's hot entries: (slot * V, a), rows in order
-    __shared__ float s_cold[R][V];                // cold contributions of the item
+    __shared__ int2 s_ent[R * HM];                // the item's hot entries: (slot * B, a), rows in order
+    __shared__ float s_cold[R][V + 1];            // cold contributions of the item, then its outputs
     __shared__ int32_t s_hrow[R + 1], s_crow[R + 1];
     __shared__ long long s_item;
     __shared__ bool s_last;
@@ -353,7 +352,6 @@ __global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__
     const int64_t ntiles = (m + R - 1) / R;
     const int32_t nvt = (B + V - 1) / V;
     const long long total = (long long)ntiles * nvt;
-    int32_t cur_vt = -1;
     while (true) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
         __syncthreads();
@@ -364,22 +362,18 @@ __global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__
         const int nr = (int)min((int64_t)R, m - r0);
         const int32_t b0 = vt * V;
         const int32_t b = b0 + (int32_t)threadIdx.x;
-        if (vt != cur_vt) {
-            for (int h = 0; h < H; ++h) xs[h * V + threadIdx.x] = b < B ? __ldg(Xh + (int64_t)h * B + b) : 0.0f;
-            cur_vt = vt;
-        }
         if (threadIdx.x <= R) {
             const int64_t i = r0 + min((int)threadIdx.x, nr);
             s_hrow[threadIdx.x] = __ldg(hrow + i);
             s_crow[threadIdx.x] = __ldg(crow + i);
         }
-        for (int e = threadIdx.x; e < R * V; e += V) (&s_cold[0][0])[e] = 0.0f;
+        for (int e = threadIdx.x; e < R * (V + 1); e += V) (&s_cold[0][0])[e] = 0.0f;
         __syncthreads();
         // the item's hot entries (contiguous: its rows are consecutive)
         const int32_t h0 = s_hrow[0], hn = min(s_hrow[nr] - h0, R * HM);
         for (int e = threadIdx.x; e < hn; e += V) {
             const int2 en = __ldg(hent + h0 + e);
-            s_ent[e] = make_int2(en.x * V, en.y);
+            s_ent[e] = make_int2(en.x * B, en.y);
         }
         // cold entries: each thread takes entries of the item's rows and adds
         // a * x_b for the vectors b of this tile that hold the column
@@ -398,8 +392,9 @@ __global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__
         }
         __syncthreads();
         if (b < B) {
-            const float* __restrict__ xt = xs + threadIdx.x;
-            float* yb = Y + (int64_t)b * m + r0;
+            // the tile's slice of Xh (H rows of V floats) stays in L1: every
+            // block of the grid works on the same vector tile at a time
+            const float* __restrict__ xt = Xh + b;
             for (int r = 0; r < nr; ++r) {
                 KahanF acc;
                 acc.zero();
@@ -410,18 +405,31 @@ __global__ void __launch_bounds__(V) k_batched_hot(const BatchDesc* __restrict__
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int2 en = s_ent[q + u];  // one broadcast read per term
-                        p = __fmaf_rn(__int_as_float(en.y), xt[en.x], p);
+                        p = __fmaf_rn(__int_as_float(en.y), __ldg(xt + en.x), p);
                     }
                     acc.add(p);
                 }
                 float p = 0.0f;
                 for (; q < qe; ++q) {
                     const int2 en = s_ent[q];
-                    p = __fmaf_rn(__int_as_float(en.y), xt[en.x], p);
+                    p = __fmaf_rn(__int_as_float(en.y), __ldg(xt + en.x), p);
                 }
                 acc.add(p);
                 acc.add(s_cold[r][threadIdx.x]);
-                yb[r] = acc.value();
+                s_cold[r][threadIdx.x] = acc.value();  // only this thread reads (r, tid)
+            }
+        }
+        __syncthreads();
+        // write-out: a warp instruction covers 32 / R vectors' runs of R
+        // consecutive rows (whole 32-byte sectors of Y), not 32 scattered words
+        {
+            constexpr int VPI = 32 / R;  // vectors per instruction
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+            const int r = lane % R;
+            for (int it = 0; it < R; ++it) {
+                const int v = w * 32 + it * VPI + lane / R;
+                const int32_t bv = b0 + v;
+                if (bv < B && r < nr) Y[(int64_t)bv * m + r0 + r] = s_cold[r][v];
             }
         }
         __syncthreads();
@@ -643,14 +651,12 @@ static void hot_pipeline(asv_matrix_s* H, int32_t B, int R, int V, int hot, cons
     unsigned long long* q = (unsigned long long*)bw.queue;
     unsigned int* tk = (unsigned int*)(bw.queue + 1);
     const BatchDesc* bd = (const BatchDesc*)bw.desc;
-    const size_t shm = (size_t)hot * V * 4;
 #define HOT(RR, VV, HH)                                                                                        \
     do {                                                                                                       \
         int per_sm = 1;                                                                                        \
-        cudaFuncSetAttribute(k_batched_hot<RR, VV, HH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_hot<RR, VV, HH>, VV, shm);           \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_hot<RR, VV, HH>, VV, 0);             \
         const int grid = H->num_sms * std::max(per_sm, 1);                                                     \
-        k_batched_hot<RR, VV, HH><<<grid, VV, shm, s>>>(bd, H->m, B, bw.hrow, (const int2*)bw.hent, bw.crow,   \
+        k_batched_hot<RR, VV, HH><<<grid, VV, 0, s>>>(bd, H->m, B, bw.hrow, (const int2*)bw.hent, bw.crow,     \
                                                         (const int2*)bw.cent, (const int32_t*)bw.tb, pay, hot_n, \
                                                         (const float*)bw.xh, q, tk);                           \
     } while (0)
