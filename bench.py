@@ -65,6 +65,12 @@ def work_bytes(m, n, nnz, nnz_x, nnz_s, nnz_y, s_v, s_x, s_y, x_sparse, sparse_o
 
 LONG_ROW, LONG_SEG = 256, 4096  # the library's long-row split (rows > 256 entries, segments of 4096)
 
+# DRAM bytes (read + write) per call of a call class, from the profiler's
+# launch list of one step of this workload (cold caches, per-call ranges):
+# profiles/rmat22_bfs8_pagerank_step_launches.md. Filled for the classes that
+# list covers and valid for the kernels it was taken with.
+NCU_DRAM_BYTES_PER_CALL = {}
+
 
 def long_row_launches(rowptr):
     """Extra launches of the thread and sub-warp pull kernels on a matrix with
@@ -75,8 +81,10 @@ def long_row_launches(rowptr):
 
 
 def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0):
-    """Kernel launches of one call (mirrors the library's dispatch)."""
-    c = 1 + (1 if auto else 0)  # feature pass (+ selector node)
+    """Kernel launches of one call (mirrors the library's dispatch). The
+    selector runs inside the feature pass and the SWITCH node launches no
+    kernel of its own, so auto and forced calls launch the same kernels."""
+    c = 1  # feature pass
     compaction = 3  # block counts, block-offset scan, write
     scan = 3
     if kid <= 5:
@@ -93,6 +101,8 @@ def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0):
         c += compaction
     if dist == 2 or wb != 0:
         c += 1 + scan
+    if dist == 2:
+        c += 1  # chunk owners of the balanced split
     c += 1  # traversal
     if wb == 1:
         c += 3 * (1 + scan + 1) + 1  # 3 radix passes (hist, scan, scatter) + reduce-by-key
@@ -684,7 +694,10 @@ def main():
     achieved = (dom["bytes"] / dom["n"]) / ((dom["ms"] / dom["n"]) * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": f"{dom_key[0]}:{asv.KERNELS[dom_key[1]]}", "achieved": round(achieved, 1),
             "peak": hbm, "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None,
+            "frac": round(achieved / hbm, 4),
+            "traffic": NCU_DRAM_BYTES_PER_CALL.get(f"{dom_key[0]}:{asv.KERNELS[dom_key[1]]}"),
+            "traffic_unit": "bytes per call (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "algorithmic_bytes_per_call": int(dom["bytes"] / dom["n"]),
             "share_of_step": round(dom["ms"] / sum(v["ms"] for v in per_k.values()), 3),
             "note": "duration = auto call (feature pass + selector + kernel), CUDA events on the launch stream"}
 

@@ -240,6 +240,33 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
                 }
             }
         }
+    } else if constexpr (S::kPattern) {
+        // each lane walks the first 32 entries of its row alone (most rows
+        // stop early); a row still undecided after them would hold the whole
+        // warp for a serial chain of loads, so the warp finishes those rows
+        // together, 64 terms (two coalesced index loads and their bit
+        // gathers) per step
+        constexpr unsigned FULL = 0xffffffffu;
+        constexpr int32_t kAlone = 32;
+        S::acc_zero(acc);
+        if (mine && !off) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, min(re, rb + kAlone), hit);
+        const bool coop = mine && !off && !acc && re - rb > kAlone;
+        for (unsigned pend = __ballot_sync(FULL, coop); pend; pend &= pend - 1) {
+            const int src = __ffs(pend) - 1;
+            const int32_t b = __shfl_sync(FULL, rb, src) + kAlone, e = __shfl_sync(FULL, re, src);
+            bool found = false;
+            for (int32_t k0 = b; k0 < e && !found; k0 += 64) {
+                const int32_t k1 = k0 + lane, k2 = k0 + 32 + lane;
+                const int32_t c1 = k1 < e ? __ldg(col + k1) : -1, c2 = k2 < e ? __ldg(col + k2) : -1;
+                const uint32_t t = (c1 >= 0 ? bool_gather(x, p.xbits, c1) : 0u) |
+                                   (c2 >= 0 ? bool_gather(x, p.xbits, c2) : 0u);
+                found = __any_sync(FULL, t != 0u);
+            }
+            if (lane == src && found) {
+                acc = 1u;
+                hit = true;
+            }
+        }
     } else {
         if (mine && !off) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, re, hit);
         else S::acc_zero(acc);

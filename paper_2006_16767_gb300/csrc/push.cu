@@ -30,8 +30,15 @@ __device__ __forceinline__ void emit(const Ws& ws, const uint32_t* ymask, int32_
     using S = Sr<T>;
     if (WB == WB_ATOM) {
         if (row_masked(ymask, r)) return;  // excluded by the output mask (pairs are masked when reduced)
-        if constexpr (!S::kPattern) atomicAdd((typename S::Atom*)ws.acc + r, S::to_atom(S::part_T(p)));
-        ws.yflag[r] = 1;
+        if constexpr (!S::kPattern) {
+            atomicAdd((typename S::Atom*)ws.acc + r, S::to_atom(S::part_T(p)));
+            ws.yflag[r] = 1;
+        } else {
+            // a Boolean search reaches most rows many times: a (possibly
+            // L1-stale) read that already sees the flag saves the store; a
+            // stale 0 only costs one
+            if (ws.yflag[r] == 0) ws.yflag[r] = 1;
+        }
     } else {
         ws.pkeys[0][pos] = (uint32_t)r;
         if constexpr (!S::kPattern) {

@@ -100,6 +100,42 @@ def densities(n):
     return out
 
 
+def bfs_levels(rp, c, n, root):
+    """Host BFS levels over the pattern (scipy), -1 = unreached."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order
+    A = sp.csr_matrix((np.ones(len(c), np.int8), c, rp), shape=(n, n))
+    order, pred = breadth_first_order(A, root, directed=True, return_predecessors=True)
+    level = np.full(n, -1, np.int64)
+    level[root] = 0
+    for v in order[1:]:  # BFS order: a vertex's predecessor is settled before it
+        level[v] = level[pred[v]] + 1
+    return level
+
+
+def vectors(name, rp, c, n, m, roots=2, max_levels=8):
+    """The x of one training matrix: seeded uniform positions at every
+    density, and -- for square matrices -- BFS frontiers (the inputs of the
+    graph applications, whose structure uniform positions do not have) from
+    a few seeded roots, at most max_levels per root spread over the search."""
+    import gen
+    out = []
+    for rho, k in densities(n):
+        out.append((rho, gen.sample_positions(n, k, seed=zlib.crc32(f"{name}/{k}".encode()), stream=1)))
+    if m == n and n > 1:
+        deg = np.diff(rp)
+        cand = np.flatnonzero(deg > 0)
+        picks = gen.randint(roots, len(cand), zlib.crc32(f"{name}/roots".encode()), 3) if len(cand) else []
+        for r in picks:
+            level = bfs_levels(rp, c, n, int(cand[r]))
+            L = int(level.max()) + 1
+            for l in sorted(set(np.linspace(1, L - 1, num=min(max_levels, max(L - 1, 0))).astype(int).tolist())):
+                f = np.flatnonzero(level == l).astype(np.int32)
+                if len(f):
+                    out.append((len(f) / n, f))
+    return out
+
+
 # ------------------------------------------------------------------ collection (GPU)
 def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
     import torch
@@ -124,10 +160,9 @@ def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
             yidx = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
             yval = torch.empty(max(m, 1), dtype=tdt, device=dev)
             nnz_y = torch.zeros(1, dtype=torch.int64, device=dev)
-            for rho, k in densities(n):
+            for rho, idx in vectors(name, rp, c, n, m):
                 if time.time() - t_start > budget_s:
                     break
-                idx = gen.sample_positions(n, k, seed=zlib.crc32(f"{name}/{k}".encode()), stream=1)
                 it = torch.from_numpy(idx).to(dev)
                 if dt == "f32":
                     xv = torch.from_numpy(gen.uniform(len(idx), -1, 1, 5, 2, np.float32)).to(dev)
