@@ -67,9 +67,15 @@ LONG_ROW, LONG_SEG = 256, 4096  # the library's long-row split (rows > 256 entri
 
 # DRAM bytes (read + write) per call of a call class, from the profiler's
 # launch list of one step of this workload (cold caches, per-call ranges):
-# profiles/rmat22_bfs8_pagerank_step_launches.md. Filled for the classes that
-# list covers and valid for the kernels it was taken with.
-NCU_DRAM_BYTES_PER_CALL = {}
+# profiles/rmat22_bfs8_pagerank_step_launches.md. Valid for the kernels that
+# list was taken with; a class it does not cover reports null.
+NCU_DRAM_BYTES_PER_CALL = {
+    "bfs:pull_thread": 303211559,
+    "bfs:push_bal_atom": 82686379,
+    "bfs:push_thread_atom": 11936081,
+    "bfs:push_warp_atom": 10725376,
+    "pagerank:pull_warp": 1167799040,
+}
 
 
 def long_row_launches(rowptr):
