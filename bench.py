@@ -390,6 +390,46 @@ def bench_bfs(asv, torch, dev, W):
     return out
 
 
+def bench_pagerank(asv, torch, dev, W):
+    """Incremental (delta-form) PageRank to a 1e-4 relative threshold on the
+    benchmark graph through asv_pagerank: the selector per product versus a
+    fixed pull and a fixed push candidate."""
+    eps = 1e-4 * 0.15 / W.n
+    out = {"workload": f"rmat scale {W.scale} edge factor {W.edge_factor}, damping 0.85, eps {eps:.3g}, FP32"}
+    rank = torch.empty(W.n, dtype=torch.float32, device=dev)
+    for k in ("auto", "pull_warp", "push_bal_atom"):
+        W.Af.pagerank(0.85, eps, 100, kernel=k, rank=rank)  # warm-up (graphs, workspaces)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, iters = W.Af.pagerank(0.85, eps, 100, kernel=k, rank=rank)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        out[k] = {"ms": round(ms, 2), "products": iters, "ms_per_product": round(ms / max(iters, 1), 3)}
+    return out
+
+
+def bench_create(asv, torch, dev, W, reps=3):
+    """Handle creation on the benchmark graph (once per matrix, outside the
+    per-call cost): CSC view by radix sort, Table 1 features, merge-path
+    partition, long-row segments. Bytes: CSR read (rowptr, col, values) plus
+    the CSC written (colptr, rowidx, values, perm)."""
+    out = {}
+    for name, val in (("boolean", None), ("fp32", W.ones_d)):
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            A = asv.Matrix(W.m, W.n, W.rp_d, W.col_d, val)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            del A
+        t = min(ts)
+        sv = 0 if val is None else 4
+        byt = 4 * (W.m + 1) + W.nnz * (4 + sv) + 4 * (W.n + 1) + W.nnz * (4 + sv + 4)
+        out[name] = {"ms": round(t * 1e3, 2), "GBs_csr_to_csc": round(byt / t / 1e9, 1)}
+    return out
+
+
 def bench_backward(asv, torch, dev, reps=5):
     """16384^2 5%-dense layer, 64 activation vectors (5..50% dense): batched
     forward + fused backward versus 64 plain calls of each."""
@@ -734,6 +774,8 @@ def main():
            "selected": {asv.KERNELS[k[1]] + ":" + k[0]: v["n"] // args.steps for k, v in per_k.items()}}
     if not args.no_extra:
         out["bfs"] = bench_bfs(asv, torch, dev, W)
+        out["create"] = bench_create(asv, torch, dev, W)
+        out["pagerank_incremental"] = bench_pagerank(asv, torch, dev, W)
         out["batched"] = bench_batched(asv, torch, dev)
         out["backward"] = bench_backward(asv, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -191,6 +191,26 @@ asv_status asv_spmspv_masked(asv_matrix A, const uint32_t* d_ymask, const int64_
                              int32_t out_mode, void* d_y, int32_t* d_yidx, void* d_yval,
                              int64_t* d_nnz_y, int64_t y_cap, int32_t kernel, void* stream);
 
+/* Incremental (delta-form) PageRank over a square FP32 or FP64 handle (the
+ * incremental PageRank application of Sec. VII; the paper gives no formula,
+ * this is the delta iteration of the power method): rank = sum of delta_k,
+ * delta_0 = (1 - damping)/n on every vertex, delta_{k+1} = damping *
+ * A D^{-1} delta_k with D the column counts of A (a column without entries
+ * contributes 0) and A's stored values as edge weights (all ones for the
+ * plain PageRank). After each product the entries with |delta| < eps are
+ * dropped, so the input vector of the product turns sparse as the iteration
+ * converges and the selector (kernel = ASV_K_AUTO) moves from pull to push
+ * kernels on its own; eps = 0 keeps every entry (the exact power series).
+ * d_rank[n] (device, the handle's value type, caller-owned) receives the
+ * rank; *h_iters (may be NULL) the number of products run (at most
+ * max_iter; fewer when the delta list empties). The first call allocates the
+ * handle's driver workspaces; every call synchronises `stream` once per
+ * iteration. Errors: ASV_ERR_ARG (non-square, n = 0, damping outside [0, 1),
+ * eps < 0, max_iter < 0, NULL d_rank), ASV_ERR_UNSUPPORTED (Boolean or int32
+ * handle). */
+asv_status asv_pagerank(asv_matrix A, double damping, double eps, int32_t max_iter, void* d_rank,
+                        int32_t kernel, int32_t* h_iters, void* stream);
+
 /* Breadth-first search from vertex `source` over the pattern of a square
  * handle (any value type; a Boolean handle is the cheap one): d_level[n]
  * (device int32, caller-owned) receives each vertex's level, 0 for the

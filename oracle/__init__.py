@@ -236,6 +236,40 @@ def pagerank_step(N, rowptr, col, colptr, r, d=0.85):
     return x, y, rn
 
 
+def pagerank_delta(n, rowptr, col, val, d, eps, max_iter):
+    """Delta-form (incremental) PageRank, Sec. VII's incremental PageRank
+    application read as: rank = sum of delta_k, delta_0 = (1 - d)/N on every
+    vertex, delta_{k+1} = d A D^{-1} delta_k with D the column counts (a
+    column with none contributes 0), entries with |delta| < eps dropped after
+    each product. Each product is the oracle's row-major SpMSpV; the output
+    set is the structural one. Returns (rank, products run, the smallest
+    | |delta| - eps | / eps met, i.e. how far any keep/drop decision was
+    from the threshold)."""
+    rowptr, col = _i32(rowptr), _i32(col)
+    val = None if val is None else _f64(val)
+    deg = np.bincount(col, minlength=n).astype(np.float64)
+    r = np.full(n, (1.0 - d) / n)
+    idx = np.arange(n, dtype=np.int32)
+    dv = r.copy()
+    margin = np.inf
+    it = 0
+    for it in range(1, max_iter + 1):
+        xv = np.where(deg[idx] > 0, dv / np.maximum(deg[idx], 1.0), 0.0)
+        y, _, hit = spmspv_rowmajor(n, rowptr, col, val, idx, xv)
+        rows = np.flatnonzero(hit).astype(np.int32)
+        dnew = d * y[rows]
+        r[rows] += dnew
+        if eps > 0 and len(dnew):
+            margin = min(margin, float(np.min(np.abs(np.abs(dnew) - eps)) / eps))
+        keep = np.abs(dnew) >= eps
+        idx, dv = rows[keep], dnew[keep]
+        if len(idx) == 0:
+            break
+    else:
+        it = max_iter
+    return r, it, margin
+
+
 def grad_values(rowptr, col, dy, x):
     """dA_k = dy[row(k)] * x[col_k] in CSR order."""
     rowptr, col, dy, x = _i32(rowptr), _i32(col), _f64(dy), _f64(x)

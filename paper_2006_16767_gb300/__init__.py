@@ -94,6 +94,7 @@ def lib():
             L.asv_spmspv.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, i32, vp]
             L.asv_spmspv_masked.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, i32, vp]
             L.asv_bfs.argtypes = [vp, i32, vp, i32, P(i32), vp]
+            L.asv_pagerank.argtypes = [vp, ctypes.c_double, ctypes.c_double, i32, vp, i32, P(i32), vp]
             L.asv_select.argtypes = [vp, vp, vp, vp, vp, P(i32), P(_VFeat), vp]
             L.asv_last_kernel.argtypes = [vp, P(i32), vp]
             L.asv_compact.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -107,7 +108,8 @@ def lib():
                          "asv_matrix_arrays", "asv_matrix_copy_csc", "asv_spmv", "asv_spmspv", "asv_select", "asv_last_kernel",
                          "asv_compact", "asv_set_trees", "asv_get_status", "asv_last_cuda_error",
                          "asv_version", "asv_matrix_update_values", "asv_spmspv_batched", "asv_autotune_batched",
-                         "asv_spmspv_backward", "asv_spmv_noalloc_f32", "asv_spmspv_masked", "asv_bfs"):
+                         "asv_spmspv_backward", "asv_spmv_noalloc_f32", "asv_spmspv_masked", "asv_bfs",
+                         "asv_pagerank"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -250,6 +252,13 @@ def asv_bfs(h, source, level, kernel="auto", stream=None) -> int:
     return depth.value
 
 
+def asv_pagerank(h, damping, eps, max_iter, rank, kernel="auto", stream=None) -> int:
+    iters = ctypes.c_int32()
+    _check(lib().asv_pagerank(h, float(damping), float(eps), int(max_iter), _ptr(rank), _kernel_id(kernel),
+                              ctypes.byref(iters), _stream(stream)), "asv_pagerank")
+    return iters.value
+
+
 def asv_select(h, nnz_x=None, xidx=None, xval=None, x_dense=None, stream=None):
     k = ctypes.c_int32()
     f = _VFeat()
@@ -364,6 +373,14 @@ class Matrix:
         nnz_y = torch.zeros(1, dtype=torch.int64, device=dev)
         call(nnz_x, xidx, xval, x_dense, ASV_OUT_SPARSE, None, yidx, yval, nnz_y, cap, kernel, stream)
         return yidx, yval, nnz_y
+
+    def pagerank(self, damping=0.85, eps=1e-10, max_iter=100, kernel="auto", rank=None, stream=None):
+        """Delta-form PageRank (rank vector of the handle's value type, number of
+        products run); deltas below eps are dropped after every product."""
+        if rank is None:
+            rank = torch.empty(self.n, dtype=self.tdtype, device=self.rowptr.device)
+        iters = asv_pagerank(self.handle, damping, eps, max_iter, rank, kernel, stream)
+        return rank, iters
 
     def bfs(self, source, kernel="auto", level=None, stream=None):
         """Breadth-first search levels from `source` (int32 [n], -1 = unreached)

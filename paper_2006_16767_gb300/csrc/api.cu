@@ -454,6 +454,69 @@ extern "C" asv_status asv_spmspv_masked(asv_matrix A, const uint32_t* d_ymask, c
 // the forced candidate), so the pattern, distribution and write-back adapt
 // from level to level. One stream synchronisation per level reads the size
 // of the new frontier.
+// ---------------------------------------------------------------- incremental PageRank
+// Delta-form PageRank: rank = sum of delta_k, delta_0 = (1 - d)/N on every
+// vertex, delta_{k+1} = d A D^{-1} delta_k with entries below eps dropped.
+// Each iteration scales the delta list by the column degrees, runs one
+// selector-driven product (list in, sparse list out), adds d y to the rank
+// and keeps the entries at or above eps; one stream synchronisation per
+// iteration reads the new list's size.
+extern "C" asv_status asv_pagerank(asv_matrix A, double damping, double eps, int32_t max_iter, void* d_rank,
+                                   int32_t kernel, int32_t* h_iters, void* stream) {
+    if (!A || !d_rank) return ASV_ERR_ARG;
+    if (A->dtype != ASV_F32 && A->dtype != ASV_F64) return ASV_ERR_UNSUPPORTED;
+    if (A->m != A->n || A->n == 0 || max_iter < 0 || !(damping >= 0.0 && damping < 1.0) || !(eps >= 0.0))
+        return ASV_ERR_ARG;
+    if (kernel < ASV_K_AUTO || kernel >= ASV_K_COUNT) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    asv_matrix_s* H = A;
+    const size_t vs = vsize(H->dtype);
+    if (!H->pr_count) {  // workspaces of the driver, allocated on the first call
+        CK(cudaStreamSynchronize(s));
+        void* p[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[8] = {4 * (size_t)H->n, 4 * (size_t)H->n, vs * H->n, vs * H->n, vs * H->n,
+                                 4 * (size_t)H->n, vs * H->n, 32};
+        for (int i = 0; i < 8; ++i) {
+            asv_status st = dalloc(H, &p[i], bytes[i], i == 7);
+            if (st != ASV_OK) return st;
+        }
+        H->pr_idx[0] = (int32_t*)p[0];
+        H->pr_idx[1] = (int32_t*)p[1];
+        H->pr_val[0] = p[2];
+        H->pr_val[1] = p[3];
+        H->pr_x = p[4];
+        H->pr_yidx = (int32_t*)p[5];
+        H->pr_yval = p[6];
+        H->pr_count = (int64_t*)p[7];
+        if (!H->bfs_hcount) CK(cudaMallocHost((void**)&H->bfs_hcount, sizeof(int64_t)));
+    }
+    const int grid = H->num_sms * 4;
+    launch_pr_init(H->dtype, H->n, (1.0 - damping) / (double)H->n, d_rank, H->pr_idx[0], H->pr_val[0], H->pr_count,
+                   grid, s);
+    int cur = 0, it = 0;
+    for (; it < max_iter; ++it) {
+        int64_t* cnt = H->pr_count + cur;
+        int64_t* nxt = H->pr_count + (cur ^ 1);
+        launch_pr_scale(H->dtype, H->pr_idx[cur], H->pr_val[cur], cnt, H->colptr, H->pr_x, grid, s);
+        asv_status st = spmspv_impl(A, nullptr, cnt, H->pr_idx[cur], H->pr_x, nullptr, ASV_OUT_SPARSE, nullptr,
+                                    H->pr_yidx, H->pr_yval, H->pr_count + 2, H->n, kernel, s);
+        if (st != ASV_OK) return st;
+        CK(cudaMemsetAsync(nxt, 0, sizeof(int64_t), s));
+        launch_pr_update(H->dtype, H->pr_yidx, H->pr_yval, H->pr_count + 2, damping, eps, d_rank,
+                         H->pr_idx[cur ^ 1], H->pr_val[cur ^ 1], nxt, grid, s);
+        CK(cudaMemcpyAsync(H->bfs_hcount, nxt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        cur ^= 1;
+        if (*H->bfs_hcount <= 0) {
+            ++it;
+            break;
+        }
+    }
+    if (h_iters) *h_iters = it;
+    CK(cudaGetLastError());
+    return ASV_OK;
+}
+
 extern "C" asv_status asv_bfs(asv_matrix A, int32_t source, int32_t* d_level, int32_t kernel, int32_t* h_depth,
                               void* stream) {
     if (!A || !d_level) return ASV_ERR_ARG;

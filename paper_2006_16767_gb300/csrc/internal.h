@@ -122,6 +122,14 @@ struct asv_matrix_s {
     int32_t* bfs_front[2] = {nullptr, nullptr};
     int64_t* bfs_count = nullptr;
     int64_t* bfs_hcount = nullptr;
+    // incremental PageRank workspaces (first asv_pagerank call): two delta
+    // lists (index, value), the scaled x values, the product's sparse output
+    int32_t* pr_idx[2] = {nullptr, nullptr};
+    void* pr_val[2] = {nullptr, nullptr};
+    void* pr_x = nullptr;
+    int32_t* pr_yidx = nullptr;
+    void* pr_yval = nullptr;
+    int64_t* pr_count = nullptr;  // [0], [1] delta counts, [2] product count
     std::vector<void*> allocs;
 };
 
@@ -145,6 +153,13 @@ void launch_bfs_init(int32_t source, int32_t* level, uint32_t* visited, int32_t*
                      cudaStream_t s);
 void launch_bfs_visit(const int32_t* front, const int64_t* count, int32_t* level, uint32_t* visited, int32_t depth,
                       int grid, cudaStream_t s);
+
+void launch_pr_init(int32_t dtype, int64_t n, double c, void* rank, int32_t* didx, void* dval, int64_t* count,
+                    int grid, cudaStream_t s);
+void launch_pr_scale(int32_t dtype, const int32_t* didx, const void* dval, const int64_t* count,
+                     const int32_t* colptr, void* xval, int grid, cudaStream_t s);
+void launch_pr_update(int32_t dtype, const int32_t* yidx, const void* yval, const int64_t* ycount, double damping,
+                      double eps, void* rank, int32_t* didx, void* dval, int64_t* dcount, int grid, cudaStream_t s);
 
 // shared scan launcher (device-side count allowed)
 void scan_excl(const int32_t* in, int32_t* out, int64_t n_h, const int64_t* n_d, int32_t* blk, int G,

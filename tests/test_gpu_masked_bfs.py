@@ -158,3 +158,40 @@ def test_bfs_on_a_float_handle_and_argument_errors():
     R = asv.Matrix(n, n // 2, to_dev(rp2), to_dev(c2), None)
     with pytest.raises(asv.AsvError):
         R.bfs(0)
+
+
+@pytest.mark.parametrize("k", ["auto", "pull_warp", "push_bal_atom", "push_thread_sort", "mpull_thread"])
+def test_incremental_pagerank_fp64_matches_oracle(k):
+    rp, c = gen.rmat(12, 8, seed=41)
+    n = 1 << 12
+    A = asv.Matrix(n, n, to_dev(rp), to_dev(c), to_dev(np.ones(len(c), np.float64)))
+    for eps in (0.0, 1e-9):
+        want, it, margin = oracle.pagerank_delta(n, rp, c, None, 0.85, eps, 60)
+        assert margin > 1e-6, "a keep/drop decision of the oracle run sits on the threshold"
+        rank, iters = A.pagerank(0.85, eps, 60, kernel=k)
+        got = rank.cpu().numpy()
+        assert iters == it, f"pagerank k={k} eps={eps}: {iters} products vs {it}"
+        assert np.max(np.abs(got - want) / want) <= 1e-11, f"pagerank k={k} eps={eps}"
+
+
+def test_incremental_pagerank_fp32_and_arguments():
+    rp, c = gen.rmat(12, 8, seed=42)
+    n = 1 << 12
+    A = asv.Matrix(n, n, to_dev(rp), to_dev(c), to_dev(np.ones(len(c), np.float32)))
+    want, it, _ = oracle.pagerank_delta(n, rp, c, None, 0.85, 1e-8, 40)
+    rank, iters = A.pagerank(0.85, 1e-8, 40)
+    got = rank.cpu().numpy().astype(np.float64)
+    # FP32 products and FP32 deltas: a few keep/drop decisions may differ
+    # near the threshold, each moving a rank by about eps
+    assert np.max(np.abs(got - want)) <= 1e-4 * want.max() + 40 * 1e-8
+    assert abs(iters - it) <= 2
+    r0, i0 = A.pagerank(0.85, 1e-8, 0)
+    assert i0 == 0 and np.allclose(r0.cpu().numpy(), 0.15 / n)
+    for bad in (dict(damping=1.0), dict(damping=-0.1), dict(eps=-1.0), dict(max_iter=-1)):
+        kw = dict(damping=0.85, eps=1e-8, max_iter=5)
+        kw.update(bad)
+        with pytest.raises(asv.AsvError):
+            A.pagerank(**kw)
+    Ab = asv.Matrix(n, n, to_dev(rp), to_dev(c), None)
+    with pytest.raises(asv.AsvError):
+        Ab.pagerank()

@@ -336,3 +336,32 @@ def test_empty_shapes():
     assert np.array_equal(colptr, np.zeros(3)) and rowidx.size == 0
     y, t = oracle.csc_push(3, colptr, rowidx, np.zeros(0), np.zeros(0, np.int32), np.zeros(0))
     assert np.array_equal(y, np.zeros(3)) and not t.any()
+
+
+def test_pagerank_delta_equals_the_linear_solve_without_threshold():
+    """With eps = 0 the delta iteration sums the Neumann series of
+    (I - d A D^-1)^-1 (1-d)/N; pinned against numpy's dense solve of that
+    system on a small symmetric graph with a dangling (isolated) vertex."""
+    rp, c = gen.rmat(7, 4, seed=12)
+    n = 1 << 7
+    Ad = np.zeros((n, n))
+    for i in range(n):
+        Ad[i, c[rp[i]:rp[i + 1]]] = 1.0
+    deg = Ad.sum(axis=0)
+    assert (deg == 0).any()
+    M = 0.85 * Ad / np.where(deg > 0, deg, 1.0)[None, :]
+    want = np.linalg.solve(np.eye(n) - M, np.full(n, 0.15 / n))
+    r, it, _ = oracle.pagerank_delta(n, rp, c, None, 0.85, 0.0, 400)
+    np.testing.assert_allclose(r, want, rtol=1e-12, atol=1e-15)
+
+
+def test_pagerank_delta_threshold_drops_and_stops():
+    # a large eps stops after the first product, which must equal one plain pull step
+    rp, c = gen.rmat(8, 4, seed=13)
+    n = 1 << 8
+    r1, it1, _ = oracle.pagerank_delta(n, rp, c, None, 0.85, 1.0, 50)
+    assert it1 == 1
+    deg = np.bincount(c, minlength=n)
+    x = np.where(deg > 0, (0.15 / n) / np.maximum(deg, 1), 0.0)
+    y, _ = oracle.csr_pull(rp, c, np.ones(len(c)), x)
+    np.testing.assert_allclose(r1, 0.15 / n + 0.85 * y, rtol=1e-14)
