@@ -367,6 +367,77 @@ def emit(trees, path=None):
     return path
 
 
+def compare(path, seed=0):
+    """The model comparison of Sec. V-B / Table 2 on this corpus: decision
+    trees (what the device walks) against SVM, random forest and gradient
+    boosting, each per (value type, format, model), on the same 7:3 split.
+    Reports test accuracy per model, the selection regret those predictions
+    give on the test samples (time of the predicted kernel / fastest), and the
+    host-side latency of predicting one sample."""
+    import warnings
+    warnings.filterwarnings("ignore")
+    from sklearn.ensemble import GradientBoostingClassifier, RandomForestClassifier
+    from sklearn.model_selection import train_test_split
+    from sklearn.pipeline import make_pipeline
+    from sklearn.preprocessing import FunctionTransformer, StandardScaler
+    from sklearn.svm import SVC
+    from sklearn.tree import DecisionTreeClassifier
+    rows = load(path)
+    log = FunctionTransformer(lambda X: np.log1p(np.abs(X)))
+    families = {
+        "decision_tree": lambda: DecisionTreeClassifier(random_state=seed, max_depth=8, max_leaf_nodes=24),
+        "svm_rbf": lambda: make_pipeline(log, StandardScaler(), SVC(C=10.0, gamma="scale")),
+        "random_forest": lambda: RandomForestClassifier(n_estimators=100, random_state=seed),
+        "gradient_boosting": lambda: GradientBoostingClassifier(random_state=seed),
+    }
+    report = {}
+    for dt in sorted({r["dtype"] for r in rows}):
+        for fmt in range(4):
+            sub = [r for r in rows if r["dtype"] == dt and r["fmt"] == fmt]
+            X = np.asarray([r["feat"] for r in sub], np.float64)
+            Y = np.asarray([labels(r["t"]) for r in sub], np.int64).reshape(-1, 5)
+            T = np.asarray([[x if x is not None else np.inf for x in r["t"]] for r in sub])
+            itr, ite = train_test_split(np.arange(len(sub)), test_size=0.3, random_state=seed)
+            for fam, make in families.items():
+                pred = np.zeros((len(ite), 5), np.int64)
+                accs, lat = [], []
+                for tree in range(5):
+                    cols = list(TREE_FEATURES[tree])
+                    y = Y[:, tree]
+                    if len(set(y[itr].tolist())) < 2:
+                        pred[:, tree] = int(np.bincount(y[itr]).argmax())
+                        accs.append(float(np.mean(pred[:, tree] == y[ite])))
+                        continue
+                    clf = make().fit(X[itr][:, cols], y[itr])
+                    pred[:, tree] = clf.predict(X[ite][:, cols])
+                    accs.append(float(np.mean(pred[:, tree] == y[ite])))
+                    one = X[ite[:1]][:, cols]
+                    t0 = time.perf_counter()
+                    for _ in range(50):
+                        clf.predict(one)
+                    lat.append((time.perf_counter() - t0) / 50)
+                reg = []
+                for q, i in enumerate(ite):
+                    pat = int(pred[q, 0])
+                    dist = int(pred[q, 1 + pat])
+                    k = kernel_id(pat, dist, int(pred[q, 4]) if pat == 0 else 0)
+                    reg.append(T[i, k] / np.min(T[i]))
+                e = report.setdefault(fam, {"accuracy": [], "regret": [], "latency_us": []})
+                e["accuracy"].append(accs)
+                e["regret"] += reg
+                e["latency_us"] += [x * 1e6 for x in lat]
+    out = {}
+    for fam, e in report.items():
+        A = np.asarray(e["accuracy"])
+        out[fam] = {"accuracy_pattern": round(float(A[:, 0].mean()), 4),
+                    "accuracy_distribution": round(float(A[:, 1:4].mean()), 4),
+                    "accuracy_writeback": round(float(A[:, 4].mean()), 4),
+                    "regret_mean": round(float(np.mean(e["regret"])), 4),
+                    "regret_p90": round(float(np.percentile(e["regret"], 90)), 4),
+                    "host_predict_us_per_model": round(float(np.median(e["latency_us"])), 1)}
+    return out
+
+
 if __name__ == "__main__":
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     cmd = sys.argv[1]
@@ -380,3 +451,5 @@ if __name__ == "__main__":
             print(json.dumps(held_out(sys.argv[2]), indent=1))
         if "--emit" in sys.argv:
             print(emit(trees))
+    elif cmd == "compare":
+        print(json.dumps(compare(sys.argv[2]), indent=1))
