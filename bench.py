@@ -91,8 +91,8 @@ def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0):
     selector runs inside the feature pass and the SWITCH node launches no
     kernel of its own, so auto and forced calls launch the same kernels."""
     c = 1  # feature pass
-    compaction = 3  # block counts, block-offset scan, write
-    scan = 3
+    compaction = 2  # block counts, write (each block sums the counts before it)
+    scan = 2
     if kid <= 5:
         dist = kid % 3
         c += (2 if dist == 2 else 1 + long_extra)
@@ -111,7 +111,7 @@ def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0):
         c += 1  # chunk owners of the balanced split
     c += 1  # traversal
     if wb == 1:
-        c += 3 * (1 + scan + 1) + 1  # 3 radix passes (hist, scan, scatter) + reduce-by-key
+        c += 3 * (1 + scan + 1) + 1  # radix passes (hist, scan, scatter) + reduce-by-key
     elif wb == 2:
         c += 1 + 1 + scan + 1 + 1 + 1  # memset, count, scan, copy, scatter, accumulate
     c += 1 if not sparse_out else compaction

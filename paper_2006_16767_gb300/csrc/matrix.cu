@@ -20,7 +20,6 @@ size_t vsize(int32_t dtype) {
 void scan_excl(const int32_t* in, int32_t* out, int64_t n_h, const int64_t* n_d, int32_t* blk, int G,
                bool write_total, cudaStream_t s) {
     k_scan_reduce<256><<<G, 256, 0, s>>>(in, n_h, n_d, blk);
-    k_scan_blocks<1024><<<1, 1024, 0, s>>>(blk, G);
     k_scan_down<256><<<G, 256, 0, s>>>(in, out, n_h, n_d, blk, write_total ? 1 : 0);
 }
 

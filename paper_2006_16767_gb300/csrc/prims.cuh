@@ -79,6 +79,16 @@ __global__ void __launch_bounds__(B) k_scan_reduce(const int32_t* in, int64_t n_
     if (threadIdx.x == 0) blk[blockIdx.x] = s;
 }
 
+// Sum of blk[0 .. b) by the whole block: each block of a scan or compaction
+// finds its own offset among the G (a few hundred) block totals, which saves
+// a separate one-block scan launch between the two passes.
+template <int B>
+__device__ __forceinline__ int32_t block_prefix(const int32_t* __restrict__ blk, int b, int32_t* sm /* >= B/32+1 */) {
+    int32_t s = 0;
+    for (int i = threadIdx.x; i < b; i += B) s += blk[i];
+    return block_reduce_sum<B>(s, sm);
+}
+
 // Exclusive scan of blk[0..G) in place; blk[G] receives the total.
 template <int B>
 __global__ void __launch_bounds__(B) k_scan_blocks(int32_t* blk, int G) {
@@ -101,7 +111,7 @@ __global__ void __launch_bounds__(B) k_scan_down(const int32_t* in, int32_t* out
     const int64_t n = dev_count(n_h, n_d);
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
-    int32_t base = blk[blockIdx.x];
+    int32_t base = block_prefix<B>(blk, blockIdx.x, sm);  // blk holds the raw block sums
     for (int64_t off = lo; off < hi; off += B) {
         const int64_t i = off + threadIdx.x;
         int32_t v = i < hi ? in[i] : 0, tot;
@@ -109,7 +119,7 @@ __global__ void __launch_bounds__(B) k_scan_down(const int32_t* in, int32_t* out
         if (i < hi) out[i] = base + e;
         base += tot;
     }
-    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = blk[gridDim.x];
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = base;
 }
 
 // ---------------------------------------------------------------- radix sort (LSD, 8-bit digits)

@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwor
     __shared__ int32_t sm[B / 32 + 1];
     const int64_t chunk = (nwords + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
-    int32_t base = blk[blockIdx.x];
+    int32_t base = block_prefix<B>(blk, blockIdx.x, sm);  // blk holds the raw block counts
     pol.begin();
     for (int64_t off = lo; off < hi; off += B) {
         const int64_t w = off + threadIdx.x;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwor
         }
         base += tot;
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) pol.count(blk[gridDim.x]);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) pol.count(base);
 }
 
 // dense x -> ascending list (values gathered from x)
@@ -395,7 +395,6 @@ static void compact_items(asv_matrix_s* H, uint32_t* words, int64_t nitems, cons
     const int64_t nwords = BYTES ? (nitems + 3) / 4 : (nitems + 31) / 32;
     const int G = H->G;
     k_items_count<256, BYTES><<<G, 256, 0, s>>>(words, nwords, H->ws.blk);
-    k_scan_blocks<1024><<<1, 1024, 0, s>>>(H->ws.blk, G);
     k_items_write<256, BYTES, Policy><<<G, 256, 0, s>>>(words, nwords, H->ws.blk, pol);
 }
 
