@@ -216,36 +216,19 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     bool hit = false;
     typename S::Acc acc;
     S::acc_zero(acc);
-    if constexpr (S::kPattern) {
-        // Boolean (index-only) segments: two 128-entry chunks per step, the
-        // next two loaded before this step's bit gathers -- four chunks (64
-        // bytes of indices per lane) in flight; stop at the first true term
-        Chunk<T, MASK, VEC> c0, c1;
-        chunk_load(c0, col, val, nnz, a0 + 4 * lane, b, e);
-        chunk_load(c1, col, val, nnz, a0 + 128 + 4 * lane, b, e);
-        for (int t = 0; t < nsteps; t += 2) {
-            const int32_t base = a0 + 128 * t + 4 * lane;
-            Chunk<T, MASK, VEC> n0, n1;
-            chunk_load(n0, col, val, nnz, base + 256, b, e);
-            chunk_load(n1, col, val, nnz, base + 384, b, e);
-            S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(c0, val, x, p.xbits, base, hit));
-            S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(c1, val, x, p.xbits, base + 128, hit));
+    Chunk<T, MASK, VEC> cur;
+    chunk_load(cur, col, val, nnz, a0 + 4 * lane, b, e);
+    for (int t = 0; t < nsteps; ++t) {
+        const int32_t base = a0 + 128 * t + 4 * lane;
+        Chunk<T, MASK, VEC> nxt;
+        chunk_load(nxt, col, val, nnz, base + 128, b, e);
+        S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(cur, val, x, p.xbits, base, hit));
+        if constexpr (S::kPattern) {
+            // OR is settled by the first hit (a deeper prefetch measured slower:
+            // most long rows of a BFS level stop within their first chunks)
             if (__any_sync(0xffffffffu, acc != 0u)) break;
-            c0 = n0;
-            c1 = n1;
         }
-    } else {
-        // value types: one chunk per step, the next one loaded before this
-        // step's gathers (more would cost occupancy in registers)
-        Chunk<T, MASK, VEC> cur;
-        chunk_load(cur, col, val, nnz, a0 + 4 * lane, b, e);
-        for (int t = 0; t < nsteps; ++t) {
-            const int32_t base = a0 + 128 * t + 4 * lane;
-            Chunk<T, MASK, VEC> nxt;
-            chunk_load(nxt, col, val, nnz, base + 128, b, e);
-            S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(cur, val, x, p.xbits, base, hit));
-            cur = nxt;
-        }
+        cur = nxt;
     }
     P v = S::acc_part(acc);
 #pragma unroll
