@@ -372,6 +372,7 @@ def bench_bfs(asv, torch, dev, W):
     product (asv_bfs): the selector per level versus fixed candidates; GTEPS =
     edges of the reached component / time (Graph500 convention, each
     undirected edge counted once)."""
+    import gen
     deg = np.diff(W.rowptr).astype(np.int64)
     out = {"workload": f"rmat scale {W.scale} edge factor {W.edge_factor}, {W.nroots} roots, Boolean handle"}
     level = torch.empty(W.n, dtype=torch.int32, device=dev)
@@ -387,6 +388,23 @@ def bench_bfs(asv, torch, dev, W):
             lv = level.cpu().numpy()
             edges += int(deg[lv >= 0].sum()) // 2
         out[k] = {"ms_per_search": round(tot_ms / len(W.roots), 3), "GTEPS": round(edges / (tot_ms * 1e-3) / 1e9, 2)}
+    # a high-diameter graph: the 5-point mesh 1024 x 1024 searched from a
+    # corner (2047 levels, a thin frontier each), where per-level overheads rule
+    side = 1024
+    rp, c, _ = gen.laplace2d(side)
+    nm = side * side
+    M = asv.Matrix(nm, nm, torch.from_numpy(rp).to(dev), torch.from_numpy(c).to(dev), None)
+    lv = torch.empty(nm, dtype=torch.int32, device=dev)
+    mesh = {"workload": f"5-point mesh {side}x{side}, source at a corner, Boolean handle"}
+    for k in ("auto", "push_warp_atom"):
+        M.bfs(0, kernel=k, level=lv)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, depth = M.bfs(0, kernel=k, level=lv)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        mesh[k] = {"ms_per_search": round(ms, 2), "levels": depth, "us_per_level": round(ms * 1e3 / depth, 2)}
+    out["mesh"] = mesh
     return out
 
 

@@ -203,9 +203,12 @@ asv_status asv_spmspv_masked(asv_matrix A, const uint32_t* d_ymask, const int64_
  * kernels on its own; eps = 0 keeps every entry (the exact power series).
  * d_rank[n] (device, the handle's value type, caller-owned) receives the
  * rank; *h_iters (may be NULL) the number of products run (at most
- * max_iter; fewer when the delta list empties). The first call allocates the
- * handle's driver workspaces; every call synchronises `stream` once per
- * iteration. Errors: ASV_ERR_ARG (non-square, n = 0, damping outside [0, 1),
+ * max_iter; fewer when the delta list empties). The iterations run on the
+ * device as one CUDA graph (a WHILE node over product + update, no host
+ * round trip per iteration); the call synchronises `stream` once, at the
+ * end, only when h_iters is given. The first call allocates the handle's
+ * driver workspaces, the first call with each `kernel` builds its graph.
+ * Errors: ASV_ERR_ARG (non-square, n = 0, damping outside [0, 1),
  * eps < 0, max_iter < 0, NULL d_rank), ASV_ERR_UNSUPPORTED (Boolean or int32
  * handle). */
 asv_status asv_pagerank(asv_matrix A, double damping, double eps, int32_t max_iter, void* d_rank,
@@ -219,9 +222,13 @@ asv_status asv_pagerank(asv_matrix A, double damping, double eps, int32_t max_it
  * this is the ordinary undirected search. Each level is one masked product
  * (frontier in, unvisited rows out, as a sparse list) run by `kernel`
  * (ASV_K_AUTO: the selector chooses per level). *h_depth (may be NULL)
- * receives the number of levels including the source's. The first call
- * allocates the handle's search workspaces (bitmap, two frontier lists);
- * every call synchronises `stream` once per level. Errors: ASV_ERR_ARG for a
+ * receives the number of levels including the source's. The levels run on
+ * the device as one CUDA graph (a WHILE node over product + level step, no
+ * host round trip per level); the call synchronises `stream` once, at the
+ * end, only when h_depth is given. The first call allocates the handle's
+ * search workspaces (bitmap, two frontier lists), the first call with each
+ * `kernel` builds its graph. The workspaces and graphs belong to the handle:
+ * searches on one handle must not overlap in time. Errors: ASV_ERR_ARG for a
  * non-square handle, n = 0, a source outside [0, n) or a NULL d_level. */
 asv_status asv_bfs(asv_matrix A, int32_t source, int32_t* d_level, int32_t kernel, int32_t* h_depth,
                    void* stream);

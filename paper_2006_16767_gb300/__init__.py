@@ -245,18 +245,21 @@ def asv_spmspv_masked(h, ymask, nnz_x=None, xidx=None, xval=None, x_dense=None, 
                                    _kernel_id(kernel), _stream(stream)), "asv_spmspv_masked")
 
 
-def asv_bfs(h, source, level, kernel="auto", stream=None) -> int:
+def asv_bfs(h, source, level, kernel="auto", stream=None, wait=True):
+    """Number of levels (waits for the search), or None with wait=False
+    (the search is only enqueued on `stream`)."""
     depth = ctypes.c_int32()
-    _check(lib().asv_bfs(h, int(source), _ptr(level), _kernel_id(kernel), ctypes.byref(depth), _stream(stream)),
-           "asv_bfs")
-    return depth.value
+    _check(lib().asv_bfs(h, int(source), _ptr(level), _kernel_id(kernel), ctypes.byref(depth) if wait else None,
+                         _stream(stream)), "asv_bfs")
+    return depth.value if wait else None
 
 
-def asv_pagerank(h, damping, eps, max_iter, rank, kernel="auto", stream=None) -> int:
+def asv_pagerank(h, damping, eps, max_iter, rank, kernel="auto", stream=None, wait=True):
+    """Number of products run (waits), or None with wait=False (enqueued only)."""
     iters = ctypes.c_int32()
     _check(lib().asv_pagerank(h, float(damping), float(eps), int(max_iter), _ptr(rank), _kernel_id(kernel),
-                              ctypes.byref(iters), _stream(stream)), "asv_pagerank")
-    return iters.value
+                              ctypes.byref(iters) if wait else None, _stream(stream)), "asv_pagerank")
+    return iters.value if wait else None
 
 
 def asv_select(h, nnz_x=None, xidx=None, xval=None, x_dense=None, stream=None):
@@ -374,20 +377,22 @@ class Matrix:
         call(nnz_x, xidx, xval, x_dense, ASV_OUT_SPARSE, None, yidx, yval, nnz_y, cap, kernel, stream)
         return yidx, yval, nnz_y
 
-    def pagerank(self, damping=0.85, eps=1e-10, max_iter=100, kernel="auto", rank=None, stream=None):
+    def pagerank(self, damping=0.85, eps=1e-10, max_iter=100, kernel="auto", rank=None, stream=None, wait=True):
         """Delta-form PageRank (rank vector of the handle's value type, number of
-        products run); deltas below eps are dropped after every product."""
+        products run -- None with wait=False); deltas below eps are dropped
+        after every product. The iterations run on the device."""
         if rank is None:
             rank = torch.empty(self.n, dtype=self.tdtype, device=self.rowptr.device)
-        iters = asv_pagerank(self.handle, damping, eps, max_iter, rank, kernel, stream)
+        iters = asv_pagerank(self.handle, damping, eps, max_iter, rank, kernel, stream, wait)
         return rank, iters
 
-    def bfs(self, source, kernel="auto", level=None, stream=None):
+    def bfs(self, source, kernel="auto", level=None, stream=None, wait=True):
         """Breadth-first search levels from `source` (int32 [n], -1 = unreached)
-        and the number of levels; each level is one masked product."""
+        and the number of levels (None with wait=False); each level is one
+        masked product, and the levels run on the device."""
         if level is None:
             level = torch.empty(self.n, dtype=torch.int32, device=self.rowptr.device)
-        depth = asv_bfs(self.handle, source, level, kernel, stream)
+        depth = asv_bfs(self.handle, source, level, kernel, stream, wait)
         return level, depth
 
     def select(self, xidx=None, xval=None, nnz_x=None, x_dense=None, stream=None):

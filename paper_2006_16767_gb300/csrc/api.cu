@@ -84,6 +84,12 @@ static void destroy_handle(asv_matrix_s* H) {
             if (H->graph[a][b]) cudaGraphDestroy(H->graph[a][b]);
         }
     batch_release(H);
+    for (int k = 0; k <= ASV_K_COUNT; ++k) {
+        if (H->bfs_exec[k]) cudaGraphExecDestroy(H->bfs_exec[k]);
+        if (H->bfs_graph[k]) cudaGraphDestroy(H->bfs_graph[k]);
+        if (H->pr_exec[k]) cudaGraphExecDestroy(H->pr_exec[k]);
+        if (H->pr_graph[k]) cudaGraphDestroy(H->pr_graph[k]);
+    }
     if (H->bfs_hcount) cudaFreeHost(H->bfs_hcount);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
     for (void* p : H->allocs) cudaFree(p);
@@ -447,20 +453,96 @@ extern "C" asv_status asv_spmspv_masked(asv_matrix A, const uint32_t* d_ymask, c
                        kernel, (cudaStream_t)stream);
 }
 
-// ---------------------------------------------------------------- breadth-first search
-// Level-synchronous BFS through the masked product: frontier_{d+1} =
-// (A frontier_d) restricted to the unvisited rows, as the ascending list the
-// sparse output mode produces; each level is one selector-driven call (or
-// the forced candidate), so the pattern, distribution and write-back adapt
-// from level to level. One stream synchronisation per level reads the size
-// of the new frontier.
-// ---------------------------------------------------------------- incremental PageRank
-// Delta-form PageRank: rank = sum of delta_k, delta_0 = (1 - d)/N on every
-// vertex, delta_{k+1} = d A D^{-1} delta_k with entries below eps dropped.
-// Each iteration scales the delta list by the column degrees, runs one
-// selector-driven product (list in, sparse list out), adds d y to the rank
-// and keeps the entries at or above eps; one stream synchronisation per
-// iteration reads the new list's size.
+// ---------------------------------------------------------------- driver loops
+// BFS and PageRank run their iterations as one CUDA graph each: a WHILE node
+// (condition 1 at every launch) whose body is the product of one iteration
+// -- list x in, sparse y out; the feature pass, then either the SWITCH over
+// all candidates that the feature pass's selector sets (AUTO) or the forced
+// candidate -- followed by the driver's step kernel, whose last block sets
+// the WHILE condition. The graph holds fixed workspace pointers; the
+// per-call arguments live in the driver's device LoopState. `step` enqueues
+// the step kernel given the WHILE handle.
+template <class Step>
+static asv_status build_loop_graph(asv_matrix_s* H, const DescInit& di, int32_t kernel, Step step, cudaGraph_t* g_out,
+                                   cudaGraphExec_t* ex_out) {
+    if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = H->cap_stream;
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = [&]() -> cudaError_t {
+        cudaError_t r;
+#define CKL(expr) if ((r = (expr)) != cudaSuccess) return r
+        cudaGraphConditionalHandle hw;
+        CKL(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault));
+        alignas(cudaGraphNodeParams) unsigned char wp_raw[sizeof(cudaGraphNodeParams)];
+        memset(wp_raw, 0, sizeof(wp_raw));
+        cudaGraphNodeParams& wp = *reinterpret_cast<cudaGraphNodeParams*>(wp_raw);
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = hw;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wn;
+        CKL(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp));
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        if (kernel != ASV_K_AUTO) {
+            SelectArg none = select_arg(H, 0ull);
+            none.enabled = 0;
+            CKL(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            launch_features(H, di, none, cs);
+            enqueue_candidate(H, kernel, 1, ASV_OUT_SPARSE, cs);
+            step(cs, (unsigned long long)hw);
+            cudaGraph_t cap;
+            CKL(cudaStreamEndCapture(cs, &cap));
+        } else {
+            cudaGraphConditionalHandle hs;
+            CKL(cudaGraphConditionalHandleCreate(&hs, body, ASV_K_PULL_BAL, cudaGraphCondAssignDefault));
+            CKL(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            launch_features(H, di, select_arg(H, (unsigned long long)hs), cs);
+            cudaGraph_t cap;
+            CKL(cudaStreamEndCapture(cs, &cap));
+            cudaGraphNode_t feat;
+            size_t nn = 1;
+            CKL(cudaGraphGetNodes(body, &feat, &nn));
+            if (nn != 1) return cudaErrorInvalidValue;
+            alignas(cudaGraphNodeParams) unsigned char sp_raw[sizeof(cudaGraphNodeParams)];
+            memset(sp_raw, 0, sizeof(sp_raw));
+            cudaGraphNodeParams& sp = *reinterpret_cast<cudaGraphNodeParams*>(sp_raw);
+            sp.type = cudaGraphNodeTypeConditional;
+            sp.conditional.handle = hs;
+            sp.conditional.type = cudaGraphCondTypeSwitch;
+            sp.conditional.size = ASV_K_COUNT;
+            cudaGraphNode_t sn;
+            CKL(cudaGraphAddNode(&sn, body, &feat, nullptr, 1, &sp));
+            for (int k = 0; k < ASV_K_COUNT; ++k) {
+                CKL(cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed));
+                enqueue_candidate(H, k, 1, ASV_OUT_SPARSE, cs);
+                CKL(cudaStreamEndCapture(cs, &cap));
+            }
+            CKL(cudaStreamBeginCaptureToGraph(cs, body, &sn, nullptr, 1, cudaStreamCaptureModeRelaxed));
+            step(cs, (unsigned long long)hw);
+            CKL(cudaStreamEndCapture(cs, &cap));
+        }
+        CKL(cudaGraphInstantiate(&ex, g, 0));
+#undef CKL
+        return cudaSuccess;
+    }();
+    if (e != cudaSuccess) {
+        g_last_cuda = (int32_t)e;
+        cudaGraphDestroy(g);
+        return e == cudaErrorMemoryAllocation ? ASV_ERR_NOMEM : ASV_ERR_CUDA;
+    }
+    *g_out = g;
+    *ex_out = ex;
+    return ASV_OK;
+}
+
+// Incremental PageRank, delta form: rank = sum of delta_k, delta_0 = (1 - d)/N
+// on every vertex, delta_{k+1} = d A D^{-1} delta_k with entries below eps
+// dropped. Each iteration is one selector-driven product (list in, sparse
+// list out) and one step kernel that adds d y to the rank and keeps the
+// entries at or above eps, scaled, as the next input list.
 extern "C" asv_status asv_pagerank(asv_matrix A, double damping, double eps, int32_t max_iter, void* d_rank,
                                    int32_t kernel, int32_t* h_iters, void* stream) {
     if (!A || !d_rank) return ASV_ERR_ARG;
@@ -473,50 +555,51 @@ extern "C" asv_status asv_pagerank(asv_matrix A, double damping, double eps, int
     const size_t vs = vsize(H->dtype);
     if (!H->pr_count) {  // workspaces of the driver, allocated on the first call
         CK(cudaStreamSynchronize(s));
-        void* p[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-        const size_t bytes[8] = {4 * (size_t)H->n, 4 * (size_t)H->n, vs * H->n, vs * H->n, vs * H->n,
-                                 4 * (size_t)H->n, vs * H->n, 32};
-        for (int i = 0; i < 8; ++i) {
-            asv_status st = dalloc(H, &p[i], bytes[i], i == 7);
+        void* p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[6] = {4 * (size_t)H->n, vs * H->n, 4 * (size_t)H->n, vs * H->n, 32, sizeof(LoopState)};
+        for (int i = 0; i < 6; ++i) {
+            asv_status st = dalloc(H, &p[i], bytes[i], i >= 4);
             if (st != ASV_OK) return st;
         }
-        H->pr_idx[0] = (int32_t*)p[0];
-        H->pr_idx[1] = (int32_t*)p[1];
-        H->pr_val[0] = p[2];
-        H->pr_val[1] = p[3];
-        H->pr_x = p[4];
-        H->pr_yidx = (int32_t*)p[5];
-        H->pr_yval = p[6];
-        H->pr_count = (int64_t*)p[7];
+        H->pr_xidx = (int32_t*)p[0];
+        H->pr_xval = p[1];
+        H->pr_yidx = (int32_t*)p[2];
+        H->pr_yval = p[3];
+        H->pr_count = (int64_t*)p[4];
+        H->pr_state = (LoopState*)p[5];
         if (!H->bfs_hcount) CK(cudaMallocHost((void**)&H->bfs_hcount, sizeof(int64_t)));
     }
     const int grid = H->num_sms * 4;
-    launch_pr_init(H->dtype, H->n, (1.0 - damping) / (double)H->n, d_rank, H->pr_idx[0], H->pr_val[0], H->pr_count,
-                   grid, s);
-    int cur = 0, it = 0;
-    for (; it < max_iter; ++it) {
-        int64_t* cnt = H->pr_count + cur;
-        int64_t* nxt = H->pr_count + (cur ^ 1);
-        launch_pr_scale(H->dtype, H->pr_idx[cur], H->pr_val[cur], cnt, H->colptr, H->pr_x, grid, s);
-        asv_status st = spmspv_impl(A, nullptr, cnt, H->pr_idx[cur], H->pr_x, nullptr, ASV_OUT_SPARSE, nullptr,
-                                    H->pr_yidx, H->pr_yval, H->pr_count + 2, H->n, kernel, s);
+    const int slot = kernel + 1;
+    if (!H->pr_exec[slot]) {
+        DescInit di;
+        asv_status st = prepare_call(H, H->pr_count, H->pr_xidx, H->pr_xval, nullptr, ASV_OUT_SPARSE, nullptr,
+                                     H->pr_yidx, H->pr_yval, H->pr_count + 2, H->n, di);
         if (st != ASV_OK) return st;
-        CK(cudaMemsetAsync(nxt, 0, sizeof(int64_t), s));
-        launch_pr_update(H->dtype, H->pr_yidx, H->pr_yval, H->pr_count + 2, damping, eps, d_rank,
-                         H->pr_idx[cur ^ 1], H->pr_val[cur ^ 1], nxt, grid, s);
-        CK(cudaMemcpyAsync(H->bfs_hcount, nxt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        cur ^= 1;
-        if (*H->bfs_hcount <= 0) {
-            ++it;
-            break;
-        }
+        auto step = [H, grid](cudaStream_t cs, unsigned long long loop) {
+            launch_pr_step(H->dtype, H->pr_yidx, H->pr_yval, H->pr_count, H->colptr, H->pr_xidx, H->pr_xval,
+                           H->pr_state, loop, grid, cs);
+        };
+        st = build_loop_graph(H, di, kernel, step, &H->pr_graph[slot], &H->pr_exec[slot]);
+        if (st != ASV_OK) return st;
     }
-    if (h_iters) *h_iters = it;
+    launch_pr_init(H->dtype, H->n, damping, eps, max_iter, d_rank, H->colptr, H->pr_xidx, H->pr_xval, H->pr_count,
+                   H->pr_state, grid, s);
+    if (max_iter > 0) CK(cudaGraphLaunch(H->pr_exec[slot], s));
+    if (h_iters) {
+        CK(cudaMemcpyAsync(H->bfs_hcount, &H->pr_state->iter, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *h_iters = (int32_t)*H->bfs_hcount;
+    }
     CK(cudaGetLastError());
     return ASV_OK;
 }
 
+// Level-synchronous BFS through the masked product: frontier_{d+1} =
+// (A frontier_d) restricted to the unvisited rows, as the ascending list the
+// sparse output mode produces; each level is one selector-driven product (or
+// the forced candidate), so the pattern, distribution and write-back adapt
+// from level to level, and one step kernel that records the levels.
 extern "C" asv_status asv_bfs(asv_matrix A, int32_t source, int32_t* d_level, int32_t kernel, int32_t* h_depth,
                               void* stream) {
     if (!A || !d_level) return ASV_ERR_ARG;
@@ -524,39 +607,46 @@ extern "C" asv_status asv_bfs(asv_matrix A, int32_t source, int32_t* d_level, in
     if (kernel < ASV_K_AUTO || kernel >= ASV_K_COUNT) return ASV_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     asv_matrix_s* H = A;
-    if (!H->bfs_hcount) {  // workspaces of the search, allocated on the first call
+    if (!H->bfs_count) {  // workspaces of the search, allocated on the first call
         CK(cudaStreamSynchronize(s));
-        void* p[4] = {nullptr, nullptr, nullptr, nullptr};
-        const size_t bytes[4] = {(size_t)4 * ((H->n + 31) / 32), (size_t)4 * H->n, (size_t)4 * H->n, 16};
-        for (int i = 0; i < 4; ++i) {
-            asv_status st = dalloc(H, &p[i], bytes[i], i == 0 || i == 3);
+        void* p[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[5] = {(size_t)4 * ((H->n + 31) / 32), (size_t)4 * H->n, (size_t)4 * H->n, 16,
+                                 sizeof(LoopState)};
+        for (int i = 0; i < 5; ++i) {
+            asv_status st = dalloc(H, &p[i], bytes[i], i == 0 || i >= 3);
             if (st != ASV_OK) return st;
         }
         H->bfs_visited = (uint32_t*)p[0];
         H->bfs_front[0] = (int32_t*)p[1];
         H->bfs_front[1] = (int32_t*)p[2];
         H->bfs_count = (int64_t*)p[3];
-        CK(cudaMallocHost((void**)&H->bfs_hcount, sizeof(int64_t)));
+        H->bfs_state = (LoopState*)p[4];
+        if (!H->bfs_hcount) CK(cudaMallocHost((void**)&H->bfs_hcount, sizeof(int64_t)));
+    }
+    const int slot = kernel + 1;
+    if (!H->bfs_exec[slot]) {
+        DescInit di;
+        asv_status st = prepare_call(H, H->bfs_count, H->bfs_front[0], nullptr, nullptr, ASV_OUT_SPARSE, nullptr,
+                                     H->bfs_front[1], nullptr, H->bfs_count + 1, H->n, di);
+        if (st != ASV_OK) return st;
+        di.ymask = H->bfs_visited;
+        const int grid = H->num_sms * 4;
+        auto step = [H, grid](cudaStream_t cs, unsigned long long loop) {
+            launch_bfs_step(H->bfs_front[1], H->bfs_count, H->bfs_front[0], H->bfs_visited, H->bfs_state, loop, grid,
+                            cs);
+        };
+        st = build_loop_graph(H, di, kernel, step, &H->bfs_graph[slot], &H->bfs_exec[slot]);
+        if (st != ASV_OK) return st;
     }
     CK(cudaMemsetAsync(d_level, 0xff, 4 * (size_t)H->n, s));
     CK(cudaMemsetAsync(H->bfs_visited, 0, 4 * (size_t)((H->n + 31) / 32), s));
-    launch_bfs_init(source, d_level, H->bfs_visited, H->bfs_front[0], H->bfs_count, s);
-    int cur = 0;
-    int32_t depth = 1;
-    for (;;) {
-        asv_status st = spmspv_impl(A, H->bfs_visited, H->bfs_count + cur, H->bfs_front[cur], nullptr, nullptr,
-                                    ASV_OUT_SPARSE, nullptr, H->bfs_front[cur ^ 1], nullptr, H->bfs_count + (cur ^ 1),
-                                    H->n, kernel, s);
-        if (st != ASV_OK) return st;
-        launch_bfs_visit(H->bfs_front[cur ^ 1], H->bfs_count + (cur ^ 1), d_level, H->bfs_visited, depth,
-                         H->num_sms * 4, s);
-        CK(cudaMemcpyAsync(H->bfs_hcount, H->bfs_count + (cur ^ 1), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    launch_bfs_init(source, H->n, d_level, H->bfs_visited, H->bfs_front[0], H->bfs_count, H->bfs_state, s);
+    CK(cudaGraphLaunch(H->bfs_exec[slot], s));
+    if (h_depth) {
+        CK(cudaMemcpyAsync(H->bfs_hcount, &H->bfs_state->iter, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (*H->bfs_hcount <= 0) break;
-        cur ^= 1;
-        ++depth;
+        *h_depth = (int32_t)*H->bfs_hcount;
     }
-    if (h_depth) *h_depth = depth;
     CK(cudaGetLastError());
     return ASV_OK;
 }

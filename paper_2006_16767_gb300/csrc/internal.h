@@ -28,6 +28,18 @@ struct DescInit {
     int32_t out_mode;
     int32_t x_sparse;
 };
+
+// Device-resident state of a driver loop (BFS, PageRank). The loop graph is
+// built once per handle with fixed pointers, so what changes from call to
+// call -- the caller's output array and the scalar arguments -- is written
+// here by the driver's init kernel and read by its step kernel.
+struct LoopState {
+    void* out;            // BFS: the level array; PageRank: the rank
+    int64_t iter;         // BFS: level the next frontier gets; PageRank: products run
+    int64_t max_iter;     // bound on iter (BFS: n, which no search reaches)
+    double p0, p1;        // PageRank: damping, eps
+    unsigned int ticket;  // last-block ticket of the step kernel, re-zeroed by that block
+};
 }  // namespace asv
 
 // Workspaces of the batched forward/backward forms, grown on demand.
@@ -116,20 +128,27 @@ struct asv_matrix_s {
     int G = 0;  // fixed grid of the scan / sort / compaction primitives
     BatchWs bws;
     int32_t tune_R = 8, tune_GB = 1024, tune_hot = 0;  // batched tiling chosen by the autotuner
-    // breadth-first search workspaces (first asv_bfs call): visited bitmap,
-    // two frontier lists, their device counts, a pinned host count
+    // breadth-first search (first asv_bfs call): visited bitmap, the current
+    // and the next frontier list, their device counts, the loop state, a
+    // pinned host scalar, and one loop graph per kernel id (AUTO first)
     uint32_t* bfs_visited = nullptr;
     int32_t* bfs_front[2] = {nullptr, nullptr};
     int64_t* bfs_count = nullptr;
+    asv::LoopState* bfs_state = nullptr;
     int64_t* bfs_hcount = nullptr;
-    // incremental PageRank workspaces (first asv_pagerank call): two delta
-    // lists (index, value), the scaled x values, the product's sparse output
-    int32_t* pr_idx[2] = {nullptr, nullptr};
-    void* pr_val[2] = {nullptr, nullptr};
-    void* pr_x = nullptr;
+    cudaGraph_t bfs_graph[ASV_K_COUNT + 1] = {};
+    cudaGraphExec_t bfs_exec[ASV_K_COUNT + 1] = {};
+    // incremental PageRank (first asv_pagerank call): the product's input
+    // list (index, scaled delta), its sparse output, the counts ([0] input,
+    // [1] next input being appended, [2] output), the loop state and graphs
+    int32_t* pr_xidx = nullptr;
+    void* pr_xval = nullptr;
     int32_t* pr_yidx = nullptr;
     void* pr_yval = nullptr;
-    int64_t* pr_count = nullptr;  // [0], [1] delta counts, [2] product count
+    int64_t* pr_count = nullptr;
+    asv::LoopState* pr_state = nullptr;
+    cudaGraph_t pr_graph[ASV_K_COUNT + 1] = {};
+    cudaGraphExec_t pr_exec[ASV_K_COUNT + 1] = {};
     std::vector<void*> allocs;
 };
 
@@ -148,18 +167,18 @@ int64_t pull_tile_items(int32_t dtype);
 cudaError_t validate_csr(asv_matrix_s* H, cudaStream_t s, int32_t* d_flag);
 cudaError_t regather_values(asv_matrix_s* H, cudaStream_t s);
 
-// bfs.cu -- level bookkeeping of the breadth-first search
-void launch_bfs_init(int32_t source, int32_t* level, uint32_t* visited, int32_t* front, int64_t* count,
-                     cudaStream_t s);
-void launch_bfs_visit(const int32_t* front, const int64_t* count, int32_t* level, uint32_t* visited, int32_t depth,
-                      int grid, cudaStream_t s);
-
-void launch_pr_init(int32_t dtype, int64_t n, double c, void* rank, int32_t* didx, void* dval, int64_t* count,
-                    int grid, cudaStream_t s);
-void launch_pr_scale(int32_t dtype, const int32_t* didx, const void* dval, const int64_t* count,
-                     const int32_t* colptr, void* xval, int grid, cudaStream_t s);
-void launch_pr_update(int32_t dtype, const int32_t* yidx, const void* yval, const int64_t* ycount, double damping,
-                      double eps, void* rank, int32_t* didx, void* dval, int64_t* dcount, int grid, cudaStream_t s);
+// bfs.cu -- the two driver loops, each run as a CUDA graph WHILE node whose
+// body is one selector-driven product followed by the step kernel below;
+// the step kernel's last block sets the loop condition
+void launch_bfs_init(int32_t source, int64_t n, int32_t* level, uint32_t* visited, int32_t* front, int64_t* count,
+                     LoopState* st, cudaStream_t s);
+void launch_bfs_step(const int32_t* next, int64_t* count, int32_t* front, uint32_t* visited, LoopState* st,
+                     unsigned long long loop, int grid, cudaStream_t s);
+void launch_pr_init(int32_t dtype, int64_t n, double damping, double eps, int32_t max_iter, void* rank,
+                    const int32_t* colptr, int32_t* xidx, void* xval, int64_t* count, LoopState* st, int grid,
+                    cudaStream_t s);
+void launch_pr_step(int32_t dtype, const int32_t* yidx, const void* yval, int64_t* count, const int32_t* colptr,
+                    int32_t* xidx, void* xval, LoopState* st, unsigned long long loop, int grid, cudaStream_t s);
 
 // shared scan launcher (device-side count allowed)
 void scan_excl(const int32_t* in, int32_t* out, int64_t n_h, const int64_t* n_d, int32_t* blk, int G,

@@ -7,7 +7,9 @@ oracle's product with those rows zeroed and removed from the structural set
 within the per-row tolerances, Boolean and int32 bit for bit. BFS: the level
 of every vertex equals the oracle's queue BFS, bit for bit, for the selector
 and for forced candidates of each pattern, on a power-law graph, a mesh and
-a graph with several components."""
+a graph with several components; long paths run thousands of iterations of
+the device-side loop. PageRank: the delta iteration against the oracle's.
+"""
 import numpy as np
 import pytest
 import torch
@@ -158,6 +160,64 @@ def test_bfs_on_a_float_handle_and_argument_errors():
     R = asv.Matrix(n, n // 2, to_dev(rp2), to_dev(c2), None)
     with pytest.raises(asv.AsvError):
         R.bfs(0)
+
+
+def path_graph(n, start=0):
+    """Undirected path start - start+1 - ... - n-1; vertices below start isolated."""
+    rows = [np.array([i + 1], np.int32) if start <= i < n - 1 else np.zeros(0, np.int32) for i in range(n)]
+    return symmetric(n, rows)
+
+
+@pytest.mark.parametrize("k", ["auto", "push_warp_atom", "mpull_thread", "pull_bal"])
+def test_bfs_device_loop_long_paths_and_isolated_source(k):
+    # a 5000-vertex path: 5000 iterations of the device-side loop, one vertex per level
+    n = 5000
+    rp, c = path_graph(n)
+    A = asv.Matrix(n, n, to_dev(rp), to_dev(c), None)
+    for root in (0, n // 2, n - 1):
+        want, L = oracle.bfs(n, rp, c, root)
+        level, depth = A.bfs(root, kernel=k)
+        assert np.array_equal(level.cpu().numpy(), want), f"path root={root} k={k}"
+        assert depth == L, f"path depth root={root} k={k}: {depth} vs {L}"
+    # a source without edges: one (empty) product, every other vertex unreached
+    rp, c = path_graph(64, start=1)
+    A = asv.Matrix(64, 64, to_dev(rp), to_dev(c), None)
+    level, depth = A.bfs(0, kernel=k)
+    want = np.full(64, -1, np.int32)
+    want[0] = 0
+    assert np.array_equal(level.cpu().numpy(), want) and depth == 1, f"isolated source k={k}"
+    level, depth = A.bfs(5, kernel=k)
+    assert np.array_equal(level.cpu().numpy(), oracle.bfs(64, rp, c, 5)[0]) and depth == 59
+
+
+def test_drivers_share_a_handle_and_run_without_host_scalars():
+    rp, c = gen.rmat(12, 8, seed=43)
+    n = 1 << 12
+    A = asv.Matrix(n, n, to_dev(rp), to_dev(c), to_dev(np.ones(len(c), np.float64)))
+    deg = np.diff(rp)
+    r0, r1 = int(np.argmax(deg)), int(np.flatnonzero(deg > 0)[0])
+    # PageRank first, then BFS on the same handle: each driver keeps its own workspaces
+    want_pr, it, _ = oracle.pagerank_delta(n, rp, c, None, 0.85, 1e-9, 50)
+    rank, iters = A.pagerank(0.85, 1e-9, 50)
+    assert iters == it and np.max(np.abs(rank.cpu().numpy() - want_pr) / want_pr) <= 1e-11
+    level, depth = A.bfs(r0)
+    want0, L0 = oracle.bfs(n, rp, c, r0)
+    assert np.array_equal(level.cpu().numpy(), want0) and depth == L0
+    # without host scalars the calls only enqueue; results are read after a synchronisation
+    lv = [torch.empty(n, dtype=torch.int32, device=DEV) for _ in range(2)]
+    rk = torch.empty(n, dtype=torch.float64, device=DEV)
+    assert A.bfs(r1, level=lv[0], wait=False)[1] is None
+    assert A.pagerank(0.85, 1e-9, 50, rank=rk, wait=False)[1] is None
+    assert A.bfs(r0, level=lv[1], kernel="push_bal_atom", wait=False)[1] is None
+    torch.cuda.synchronize()
+    assert np.array_equal(lv[0].cpu().numpy(), oracle.bfs(n, rp, c, r1)[0])
+    assert np.array_equal(lv[1].cpu().numpy(), want0)
+    assert np.max(np.abs(rk.cpu().numpy() - want_pr) / want_pr) <= 1e-11
+    # one product only, and the exact series cut at 3 products
+    for mi in (1, 3):
+        want, it, _ = oracle.pagerank_delta(n, rp, c, None, 0.85, 0.0, mi)
+        rank, iters = A.pagerank(0.85, 0.0, mi)
+        assert iters == it == mi and np.max(np.abs(rank.cpu().numpy() - want) / want) <= 1e-12
 
 
 @pytest.mark.parametrize("k", ["auto", "pull_warp", "push_bal_atom", "push_thread_sort", "mpull_thread"])
