@@ -70,11 +70,11 @@ LONG_ROW, LONG_SEG = 256, 4096  # the library's long-row split (rows > 256 entri
 # profiles/rmat22_bfs8_pagerank_step_launches.md. Valid for the kernels that
 # list was taken with; a class it does not cover reports null.
 NCU_DRAM_BYTES_PER_CALL = {
-    "bfs:pull_thread": 303211559,
-    "bfs:push_bal_atom": 82686379,
-    "bfs:push_thread_atom": 11936081,
-    "bfs:push_warp_atom": 10725376,
-    "pagerank:pull_warp": 1167799040,
+    "bfs:pull_thread": 294869386,
+    "bfs:push_bal_atom": 82690458,
+    "bfs:push_thread_atom": 11933521,
+    "bfs:push_warp_atom": 10724608,
+    "pagerank:pull_warp": 1158579712,
 }
 
 

@@ -97,12 +97,12 @@ struct asv_matrix_s {
     int32_t* carry_row = nullptr;
     void* carry_val = nullptr;
     // rows over kLongRow entries, cut into segments of at most kLongSeg:
-    // segment s covers [seg_beg[s], min(seg_beg[s] + kLongSeg, rowptr[row+1]))
-    // of row seg_row[s]; a row's segments are consecutive and ascending.
-    // Rows with several segments are listed in multi_row with their first
-    // segment in multi_base; their partial sums go to long_part / long_hit.
-    int32_t* seg_row = nullptr;
-    int32_t* seg_beg = nullptr;
+    // segment s = {row, begin, end, 1 if it is the whole row}: entries
+    // [begin, end) of the row, at most kLongSeg of them; a row's segments are
+    // consecutive and ascending. Rows with several segments are listed in
+    // multi_row with their first segment in multi_base; their partial sums
+    // go to long_part / long_hit.
+    int4* seg = nullptr;
     uint64_t* long_part = nullptr;
     uint8_t* long_hit = nullptr;
     int32_t* multi_row = nullptr;
@@ -155,6 +155,7 @@ struct asv_matrix_s {
 namespace asv {
 
 size_t vsize(int32_t dtype);
+
 const char* kernel_name(int k);
 
 // matrix.cu -- run once at handle creation

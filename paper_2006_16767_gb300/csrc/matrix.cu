@@ -284,16 +284,16 @@ __global__ void k_long_count(const int32_t* __restrict__ rowptr, int64_t m, unsi
 
 // Each long row reserves its consecutive run of segment slots with one atomic,
 // so a row's segments stay together and in order whatever the slot order.
-__global__ void k_long_fill(const int32_t* __restrict__ rowptr, int64_t m, int32_t* seg_row, int32_t* seg_beg,
-                            int32_t* multi_row, int32_t* multi_base, unsigned long long* cursor) {
+__global__ void k_long_fill(const int32_t* __restrict__ rowptr, int64_t m, int4* seg, int32_t* multi_row,
+                            int32_t* multi_base, unsigned long long* cursor) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t rb = rowptr[i], len = rowptr[i + 1] - rb;
+        const int32_t rb = rowptr[i], re = rowptr[i + 1], len = re - rb;
         if (len <= kLongRow) continue;
         const int32_t k = (len + kLongSeg - 1) / kLongSeg;
         const int32_t base = (int32_t)atomicAdd(cursor, (unsigned long long)k);
         for (int32_t t = 0; t < k; ++t) {
-            seg_row[base + t] = (int32_t)i;
-            seg_beg[base + t] = rb + t * kLongSeg;
+            const int32_t b = rb + t * kLongSeg;
+            seg[base + t] = make_int4((int32_t)i, b, min(b + kLongSeg, re), k == 1 ? 1 : 0);
         }
         if (k > 1) {
             const int32_t q = (int32_t)atomicAdd(cursor + 1, 1ull);
@@ -321,13 +321,12 @@ cudaError_t build_long_rows(asv_matrix_s* H, cudaStream_t s) {
         return r;
     };
     const size_t ns = (size_t)h[0], nm = (size_t)h[1];
-    if ((e = grab((void**)&H->seg_row, 4 * ns)) != cudaSuccess) return e;
-    if ((e = grab((void**)&H->seg_beg, 4 * ns)) != cudaSuccess) return e;
+    if ((e = grab((void**)&H->seg, 16 * ns)) != cudaSuccess) return e;
     if ((e = grab((void**)&H->long_part, 8 * ns)) != cudaSuccess) return e;
     if ((e = grab((void**)&H->long_hit, ns)) != cudaSuccess) return e;
     if ((e = grab((void**)&H->multi_row, 4 * nm)) != cudaSuccess) return e;
     if ((e = grab((void**)&H->multi_base, 4 * nm)) != cudaSuccess) return e;
-    k_long_fill<<<grid, 256, 0, s>>>(H->rowptr, H->m, H->seg_row, H->seg_beg, H->multi_row, H->multi_base, d_cnt);
+    k_long_fill<<<grid, 256, 0, s>>>(H->rowptr, H->m, H->seg, H->multi_row, H->multi_base, d_cnt);
     if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(h), s)) != cudaSuccess) return e;
     H->nseg = (int64_t)ns;
     H->nmulti = (int64_t)nm;

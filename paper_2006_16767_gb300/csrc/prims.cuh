@@ -63,17 +63,33 @@ __device__ __forceinline__ int64_t dev_count(int64_t host_n, const int64_t* dev_
 }
 
 // ---------------------------------------------------------------- device exclusive scan
-// Three launches over a fixed grid of G blocks, each owning one contiguous
-// range: per-block sums, a one-block scan of the sums, then per-block scans
-// seeded with the block offset. Deterministic; n may live on the device.
+// Items per thread and round in the second pass of a scan or compaction: a
+// thread loads a contiguous run (independent loads, one memory latency) and
+// the block scans the runs' totals once per B * kRun items.
+constexpr int kRun = 8;
+
+// Block b of the grid owns [lo, hi); the chunk is a whole number of runs, so
+// runs start 32-byte aligned relative to the array and never straddle blocks.
+__device__ __forceinline__ void block_range(int64_t n, int64_t& lo, int64_t& hi) {
+    int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    chunk = (chunk + kRun - 1) / kRun * kRun;
+    lo = min(n, (int64_t)blockIdx.x * chunk);
+    hi = min(n, lo + chunk);
+}
+
+// Two launches over a fixed grid of G blocks, each owning one contiguous
+// range: per-block sums, then per-block scans seeded with the block's offset
+// (the sum of the block sums before it). Deterministic; n may live on the
+// device.
 template <int B>
 __global__ void __launch_bounds__(B) k_scan_reduce(const int32_t* in, int64_t n_h, const int64_t* n_d,
                                                    int32_t* blk) {
     __shared__ int32_t sm[B / 32 + 1];
     const int64_t n = dev_count(n_h, n_d);
-    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    int64_t lo, hi;
+    block_range(n, lo, hi);
     int32_t s = 0;
+#pragma unroll 4
     for (int64_t i = lo + threadIdx.x; i < hi; i += B) s += in[i];
     s = block_reduce_sum<B>(s, sm);
     if (threadIdx.x == 0) blk[blockIdx.x] = s;
@@ -89,34 +105,47 @@ __device__ __forceinline__ int32_t block_prefix(const int32_t* __restrict__ blk,
     return block_reduce_sum<B>(s, sm);
 }
 
-// Exclusive scan of blk[0..G) in place; blk[G] receives the total.
-template <int B>
-__global__ void __launch_bounds__(B) k_scan_blocks(int32_t* blk, int G) {
-    __shared__ int32_t sm[B / 32 + 1];
-    int32_t base = 0;
-    for (int off = 0; off < G; off += B) {
-        const int i = off + threadIdx.x;
-        int32_t v = i < G ? blk[i] : 0, tot;
-        int32_t e = block_excl_scan<B>(v, sm, &tot);
-        if (i < G) blk[i] = base + e;
-        base += tot;
-    }
-    if (threadIdx.x == 0) blk[G] = base;
-}
-
 template <int B>
 __global__ void __launch_bounds__(B) k_scan_down(const int32_t* in, int32_t* out, int64_t n_h,
                                                  const int64_t* n_d, const int32_t* blk, int write_total) {
     __shared__ int32_t sm[B / 32 + 1];
     const int64_t n = dev_count(n_h, n_d);
-    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    int64_t lo, hi;
+    block_range(n, lo, hi);
+    const bool vec = (((uintptr_t)in | (uintptr_t)out) & 15) == 0;
     int32_t base = block_prefix<B>(blk, blockIdx.x, sm);  // blk holds the raw block sums
-    for (int64_t off = lo; off < hi; off += B) {
-        const int64_t i = off + threadIdx.x;
-        int32_t v = i < hi ? in[i] : 0, tot;
-        int32_t e = block_excl_scan<B>(v, sm, &tot);
-        if (i < hi) out[i] = base + e;
+    for (int64_t off = lo; off < hi; off += (int64_t)B * kRun) {
+        const int64_t i0 = off + (int64_t)threadIdx.x * kRun;
+        const bool full = vec && i0 + kRun <= hi;
+        int32_t v[kRun];
+        if (full) {
+            const int4 a = *reinterpret_cast<const int4*>(in + i0);
+            const int4 b = *reinterpret_cast<const int4*>(in + i0 + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < kRun; ++q) v[q] = i0 + q < hi ? in[i0 + q] : 0;
+        }
+        int32_t c = 0;
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) c += v[q];
+        int32_t tot;
+        int32_t e = base + block_excl_scan<B>(c, sm, &tot);
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) {
+            const int32_t x = v[q];
+            v[q] = e;
+            e += x;
+        }
+        if (full) {
+            *reinterpret_cast<int4*>(out + i0) = make_int4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<int4*>(out + i0 + 4) = make_int4(v[4], v[5], v[6], v[7]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kRun; ++q)
+                if (i0 + q < hi) out[i0 + q] = v[q];
+        }
         base += tot;
     }
     if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = base;

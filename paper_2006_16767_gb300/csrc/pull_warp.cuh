@@ -54,6 +54,13 @@ __device__ __forceinline__ void chunk_load(Chunk<T, MASK, VEC>& ch, const int32_
             if constexpr (!S::kPattern && !MASK) ch.v[q] = ch.in[q] ? load_val(val, base + q) : T(0);
         }
     }
+    // a pattern chunk marks entries outside the row with column -1 (column
+    // ids are non-negative), so it carries no separate in-range flags
+    if constexpr (S::kPattern) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (!ch.in[q]) ch.c[q] = -1;
+    }
 }
 
 template <class T, bool MASK, bool SOUT, bool VEC>
@@ -65,7 +72,7 @@ __device__ __forceinline__ typename Sr<T>::Part chunk_sum(Chunk<T, MASK, VEC>& c
     if constexpr (S::kPattern) {
         uint32_t any = 0u;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) any |= ch.in[q] ? bool_gather(x, xbits, ch.c[q]) : 0u;
+        for (int q = 0; q < 4; ++q) any |= ch.c[q] >= 0 ? bool_gather(x, xbits, ch.c[q]) : 0u;
         if (SOUT) hit |= any != 0u;
         return any;
     }
@@ -166,7 +173,8 @@ __global__ void __launch_bounds__(256, UU >= 4 ? 4 : 6) k_pull_warp(int64_t m, i
 
 
 // ---------------------------------------------------------------- long rows
-// One warp per segment of a long row (at most kLongSeg entries): lane l reads
+// One warp per segment of a long row (at most kLongSeg entries, from a
+// 16-byte descriptor built once per matrix): lane l reads
 // 16-byte chunks l, l+32, ... of the segment with 128-bit loads, the next
 // chunk's loads issued before the current chunk's gathers. Boolean segments
 // stop as soon as any lane has a hit. A row that is one segment is written
@@ -193,11 +201,10 @@ __device__ __forceinline__ typename Sr<T>::Atom atom_combine(typename Sr<T>::Ato
 }
 
 template <class T, bool MASK, bool SOUT, bool VEC>
-__global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, const int32_t* __restrict__ rowptr,
+__global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, const int4* __restrict__ seg,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                   const int32_t* __restrict__ seg_row,
-                                                   const int32_t* __restrict__ seg_beg, PullArg a, void* ywork,
-                                                   uint8_t* yflag, uint64_t* part, uint8_t* part_hit) {
+                                                   PullArg a, void* ywork, uint8_t* yflag, uint64_t* part,
+                                                   uint8_t* part_hit) {
     using S = Sr<T>;
     using P = typename S::Part;
     const PullIO p = resolve(a, ywork, SOUT);
@@ -206,11 +213,9 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     const int lane = threadIdx.x & 31;
     const int64_t sg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (sg >= nseg) return;
-    const int32_t row = __ldg(seg_row + sg);
-    const int32_t rb = __ldg(rowptr + row), re = __ldg(rowptr + row + 1);
-    const int32_t b = __ldg(seg_beg + sg);
-    const int32_t e_full = min(b + kLongSeg, re);
-    const int32_t e = row_masked(p.ymask, row) ? b : e_full;  // a masked row sums nothing (y = 0)
+    const int4 d = __ldg(seg + sg);  // {row, begin, end, whole row}
+    const int32_t row = d.x, b = d.y;
+    const int32_t e = row_masked(p.ymask, row) ? b : d.z;  // a masked row sums nothing (y = 0)
     const int32_t a0 = b & ~3;
     const int nsteps = (e - a0 + 127) >> 7;
     bool hit = false;
@@ -224,8 +229,10 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
         chunk_load(nxt, col, val, nnz, base + 128, b, e);
         S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(cur, val, x, p.xbits, base, hit));
         if constexpr (S::kPattern) {
-            // OR is settled by the first hit (a deeper prefetch measured slower:
-            // most long rows of a BFS level stop within their first chunks)
+            // OR is settled by the first hit (a deeper prefetch, and warps
+            // that keep the next segment's first chunk in flight, measured
+            // slower: most long rows of a BFS level stop within their first
+            // chunks)
             if (__any_sync(0xffffffffu, acc != 0u)) break;
         }
         cur = nxt;
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     for (int o = 16; o > 0; o >>= 1) v = S::part_add(v, shfl_xor(v, o));
     const bool h = SOUT && __any_sync(0xffffffffu, hit);
     if (lane != 0) return;
-    if (b == rb && e_full == re) {
+    if (d.w) {
         y[row] = S::part_T(v);
         if (SOUT && h) yflag[row] = 1;
     } else {
@@ -273,13 +280,11 @@ void launch_pull_long_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStr
     const T* val = (const T*)H->val;
     const unsigned g = (unsigned)((H->nseg + 7) / 8);
     if (vec)
-        k_pull_long<T, MASK, SOUT, true><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->rowptr, H->col, val, H->seg_row,
-                                                           H->seg_beg, a, H->ws.ywork, H->ws.yflag, H->long_part,
-                                                           H->long_hit);
+        k_pull_long<T, MASK, SOUT, true><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->seg, H->col, val, a, H->ws.ywork,
+                                                           H->ws.yflag, H->long_part, H->long_hit);
     else
-        k_pull_long<T, MASK, SOUT, false><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->rowptr, H->col, val, H->seg_row,
-                                                            H->seg_beg, a, H->ws.ywork, H->ws.yflag, H->long_part,
-                                                            H->long_hit);
+        k_pull_long<T, MASK, SOUT, false><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->seg, H->col, val, a, H->ws.ywork,
+                                                            H->ws.yflag, H->long_part, H->long_hit);
     if (H->nmulti > 0) {
         const unsigned gf = (unsigned)std::min<int64_t>((H->nmulti + 255) / 256, (int64_t)H->num_sms * 4);
         k_pull_long_fixup<T><<<gf, 256, 0, s>>>(H->nmulti, H->multi_row, H->multi_base, H->rowptr, H->long_part,

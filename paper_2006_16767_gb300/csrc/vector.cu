@@ -173,8 +173,20 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
     // only the blocks the list reaches take part (a short list costs one block)
     const unsigned blocks = (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (min(nx, n) + B - 1) / B));
     if (blockIdx.x >= blocks) return;
+    // four list entries per thread in flight: their column lengths are
+    // independent gathers
+    const int64_t nl = min(nx, n);
+    const int64_t stride = (int64_t)blocks * B;
     unsigned long long cs = 0;
-    for (int64_t t = blockIdx.x * (int64_t)B + threadIdx.x; t < min(nx, n); t += (int64_t)blocks * B) {
+    int64_t t = blockIdx.x * (int64_t)B + threadIdx.x;
+    for (; t + 3 * stride < nl; t += 4 * stride) {
+        int32_t j[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) j[q] = __ldg(xidx + t + q * stride);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cs += (unsigned long long)(__ldg(colptr + j[q] + 1) - __ldg(colptr + j[q]));
+    }
+    for (; t < nl; t += stride) {
         const int32_t j = __ldg(xidx + t);
         cs += (unsigned long long)(__ldg(colptr + j + 1) - __ldg(colptr + j));
     }
@@ -186,7 +198,7 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
 // the same counters and ticket, so thousands of blocks would serialise there.
 static int feat_grid(asv_matrix_s* H, int64_t items) {
     const int64_t g = (items + 255) / 256;
-    return (int)max((int64_t)1, min(g, (int64_t)H->num_sms * 2));
+    return (int)max((int64_t)1, min(g, (int64_t)H->num_sms * 4));
 }
 
 template <class T>
@@ -245,10 +257,31 @@ __global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
     const T* __restrict__ xval = (const T*)desc->xval;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nx; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const bool vals = xval && !Sr<T>::kPattern;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // four entries per thread in flight (independent index and value loads)
+    for (; t + 3 * stride < nx; t += 4 * stride) {
+        int32_t j[4];
+        T v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            j[q] = xidx[t + q * stride];
+            v[q] = (set && vals) ? xval[t + q * stride] : (set ? Sr<T>::one() : T(0));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            xdense[j[q]] = v[q];
+            if (set)
+                atomicOr(&xbits[j[q] >> 5], 1u << (j[q] & 31));
+            else
+                xbits[j[q] >> 5] = 0u;
+        }
+    }
+    for (; t < nx; t += stride) {
         const int32_t j = xidx[t];
         if (set) {
-            xdense[j] = (xval && !Sr<T>::kPattern) ? xval[t] : Sr<T>::one();
+            xdense[j] = vals ? xval[t] : Sr<T>::one();
             atomicOr(&xbits[j >> 5], 1u << (j & 31));
         } else {
             xdense[j] = T(0);
@@ -285,34 +318,59 @@ __device__ __forceinline__ uint32_t item_mask(uint32_t w) {
 template <int B, bool BYTES>
 __global__ void __launch_bounds__(B) k_items_count(const uint32_t* __restrict__ words, int64_t nwords, int32_t* blk) {
     __shared__ int32_t sm[B / 32 + 1];
-    const int64_t chunk = (nwords + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
+    int64_t lo, hi;
+    block_range(nwords, lo, hi);
     int32_t s = 0;
+#pragma unroll 4
     for (int64_t w = lo + threadIdx.x; w < hi; w += B) s += __popc(item_mask<BYTES>(words[w]));
     s = block_reduce_sum<B>(s, sm);
     if (threadIdx.x == 0) blk[blockIdx.x] = s;
 }
 
+// Each thread takes a run of kRun consecutive words per round: all its loads
+// are issued before the one block scan of the round, and its items are
+// emitted in order from its scanned offset.
 template <int B, bool BYTES, class Policy>
 __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwords, const int32_t* __restrict__ blk,
                                                    Policy pol) {
     __shared__ int32_t sm[B / 32 + 1];
-    const int64_t chunk = (nwords + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
+    int64_t lo, hi;
+    block_range(nwords, lo, hi);
+    const bool vec = ((uintptr_t)words & 15) == 0;
     int32_t base = block_prefix<B>(blk, blockIdx.x, sm);  // blk holds the raw block counts
     pol.begin();
-    for (int64_t off = lo; off < hi; off += B) {
-        const int64_t w = off + threadIdx.x;
-        const uint32_t raw = w < hi ? words[w] : 0u;
-        uint32_t mask = item_mask<BYTES>(raw);
+    for (int64_t off = lo; off < hi; off += (int64_t)B * kRun) {
+        const int64_t w0 = off + (int64_t)threadIdx.x * kRun;
+        uint32_t m[kRun];
+        if (vec && w0 + kRun <= hi) {
+            const uint4 a = *reinterpret_cast<const uint4*>(words + w0);
+            const uint4 b = *reinterpret_cast<const uint4*>(words + w0 + 4);
+            m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
+            m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < kRun; ++q) m[q] = w0 + q < hi ? words[w0 + q] : 0u;
+        }
+        int32_t c = 0;
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) {
+            m[q] = item_mask<BYTES>(m[q]);
+            c += __popc(m[q]);
+        }
         int32_t tot;
-        int32_t pos = base + block_excl_scan<B>((int32_t)__popc(mask), sm, &tot);
-        if (mask) {
-            pol.clear_word(words, w);
-            while (mask) {
-                const int b = __ffs(mask) - 1;
-                mask &= mask - 1;
-                pol.emit(pos++, BYTES ? w * 4 + (b >> 3) : w * 32 + b);
+        int32_t pos = base + block_excl_scan<B>(c, sm, &tot);
+        if (c) {
+#pragma unroll
+            for (int q = 0; q < kRun; ++q) {
+                uint32_t mask = m[q];
+                if (!mask) continue;
+                const int64_t w = w0 + q;
+                pol.clear_word(words, w);
+                while (mask) {
+                    const int b = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    pol.emit(pos++, BYTES ? w * 4 + (b >> 3) : w * 32 + b);
+                }
             }
         }
         base += tot;

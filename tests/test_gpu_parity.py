@@ -52,7 +52,7 @@ def mat_skewed(dtype):
     return "skewed", n, n, rp2, c2, v2
 
 
-LONG_LENS = (0, 1, 255, 256, 257, 300, 1023, 4096, 4097, 8192, 8193, 12289, 20000)
+LONG_LENS = (0, 1, 255, 256, 257, 300, 1023, 1024, 1025, 2049, 4096, 4097, 8192, 8193, 12289, 20000)
 
 
 def long_rows_pattern(n=20000, short=700, seed=31):
