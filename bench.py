@@ -106,9 +106,7 @@ def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0):
     if not x_sparse:
         c += compaction
     if dist == 2 or wb != 0:
-        c += 1 + scan
-    if dist == 2:
-        c += 1  # chunk owners of the balanced split
+        c += 2  # list lengths + block sums, then their scan (and the balanced split's chunk owners)
     c += 1  # traversal
     if wb == 1:
         c += 3 * (1 + scan + 1) + 1  # radix passes (hist, scan, scatter) + reduce-by-key

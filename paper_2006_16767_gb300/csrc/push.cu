@@ -275,27 +275,65 @@ __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ co
     }
 }
 
-// The list entry owning the first item of every balanced chunk: entry t
-// covers items [xscan[t], xscan[t+1]); each chunk start lies in exactly one
-// non-empty entry, which writes it (no search, no atomics).
-__global__ void k_chunk_owner(const int32_t* __restrict__ sc, const CallDesc* __restrict__ desc, int32_t* chunk_t0) {
-    constexpr int CH = 32 * kPushIPT;
+// Exclusive scan of the listed columns' lengths, xscan[0..nnz_x], in two
+// launches. Pass 1: each block writes its entries' lengths and their sum.
+template <int B>
+__global__ void __launch_bounds__(B) k_list_deg(const int32_t* __restrict__ colptr, const CallDesc* __restrict__ desc,
+                                                int32_t* deg, int32_t* blk) {
+    __shared__ int32_t sm[B / 32 + 1];
     const int64_t nx = desc->nnz_x;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nx; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = sc[t], e = sc[t + 1];
-        if (e <= b) continue;
-        for (int64_t c = (b + CH - 1) / CH; c * CH < e; ++c) chunk_t0[c] = (int32_t)t;
+    const int32_t* __restrict__ xidx = desc->xidx;
+    int64_t lo, hi;
+    block_range(nx, lo, hi);
+    int32_t s = 0;
+#pragma unroll 4
+    for (int64_t t = lo + threadIdx.x; t < hi; t += B) {
+        const int32_t j = __ldg(xidx + t);
+        const int32_t d = __ldg(colptr + j + 1) - __ldg(colptr + j);
+        deg[t] = d;
+        s += d;
     }
+    s = block_reduce_sum<B>(s, sm);
+    if (threadIdx.x == 0) blk[blockIdx.x] = s;
 }
 
-// degree of each listed column, then an exclusive scan gives xscan[0..nnz_x]
-__global__ void k_list_deg(const int32_t* __restrict__ colptr, const CallDesc* __restrict__ desc, int32_t* deg) {
+// Pass 2: the lengths become their exclusive scan in place (runs of kRun per
+// thread, one block scan per round, seeded with the sums of the blocks
+// before). With OWNERS, entry t -- covering items [xscan[t], xscan[t] +
+// len) -- also records itself as the owner of every balanced chunk whose
+// first item it covers: each chunk start lies in exactly one non-empty
+// entry, so no search and no atomics.
+template <int B, bool OWNERS>
+__global__ void __launch_bounds__(B) k_list_scan(int32_t* xscan, const CallDesc* __restrict__ desc,
+                                                 const int32_t* __restrict__ blk, int32_t* chunk_t0) {
+    constexpr int CH = 32 * kPushIPT;
+    __shared__ int32_t sm[B / 32 + 1];
     const int64_t nx = desc->nnz_x;
-    const int32_t* xidx = desc->xidx;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nx; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t j = xidx[t];
-        deg[t] = __ldg(colptr + j + 1) - __ldg(colptr + j);
+    int64_t lo, hi;
+    block_range(nx, lo, hi);
+    int32_t base = block_prefix<B>(blk, blockIdx.x, sm);
+    for (int64_t off = lo; off < hi; off += (int64_t)B * kRun) {
+        const int64_t t0 = off + (int64_t)threadIdx.x * kRun;
+        int32_t v[kRun];
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) v[q] = t0 + q < hi ? xscan[t0 + q] : 0;
+        int32_t c = 0;
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) c += v[q];
+        int32_t tot;
+        int32_t e = base + block_excl_scan<B>(c, sm, &tot);
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) {
+            if (t0 + q >= hi) break;
+            xscan[t0 + q] = e;
+            if (OWNERS)
+                for (int64_t ch = ((int64_t)e + CH - 1) / CH; ch * CH < (int64_t)e + v[q]; ++ch)
+                    chunk_t0[ch] = (int32_t)(t0 + q);
+            e += v[q];
+        }
+        base += tot;
     }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) xscan[nx] = base;
 }
 
 // ---------------------------------------------------------------- sort write-back: reduce-by-key
@@ -451,10 +489,12 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
     const CallDesc* d = H->d_desc;
     Ws ws = H->ws;
     if (dist == 2 || wb != WB_ATOM) {
-        k_list_deg<<<grid, 256, 0, s>>>(H->colptr, d, ws.xscan);
-        scan_excl(ws.xscan, ws.xscan, 0, &H->d_desc->nnz_x, ws.blk, H->G, true, s);
+        k_list_deg<256><<<H->G, 256, 0, s>>>(H->colptr, d, ws.xscan, ws.blk);
+        if (dist == 2)
+            k_list_scan<256, true><<<H->G, 256, 0, s>>>(ws.xscan, d, ws.blk, ws.chunk_t0);
+        else
+            k_list_scan<256, false><<<H->G, 256, 0, s>>>(ws.xscan, d, ws.blk, ws.chunk_t0);
     }
-    if (dist == 2) k_chunk_owner<<<grid, 256, 0, s>>>(ws.xscan, d, ws.chunk_t0);
 #define TRAV(WBV)                                                                                   \
     do {                                                                                            \
         if (dist == 0) k_push_thread<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws); \

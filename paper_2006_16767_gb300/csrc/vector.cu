@@ -315,64 +315,87 @@ __device__ __forceinline__ uint32_t item_mask(uint32_t w) {
     }
 }
 
+template <bool BYTES>
+__device__ __forceinline__ void load_run(const uint32_t* __restrict__ words, int64_t w0, int64_t hi, bool vec,
+                                         uint32_t (&m)[kRun]) {
+    if (vec && w0 + kRun <= hi) {
+        const uint4 a = *reinterpret_cast<const uint4*>(words + w0);
+        const uint4 b = *reinterpret_cast<const uint4*>(words + w0 + 4);
+        m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
+        m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) m[q] = w0 + q < hi ? words[w0 + q] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kRun; ++q) m[q] = item_mask<BYTES>(m[q]);
+}
+
+// Items of each block's range, one run of kRun words (two 16-byte loads) per
+// thread and round.
 template <int B, bool BYTES>
 __global__ void __launch_bounds__(B) k_items_count(const uint32_t* __restrict__ words, int64_t nwords, int32_t* blk) {
     __shared__ int32_t sm[B / 32 + 1];
     int64_t lo, hi;
     block_range(nwords, lo, hi);
+    const bool vec = ((uintptr_t)words & 15) == 0;
     int32_t s = 0;
-#pragma unroll 4
-    for (int64_t w = lo + threadIdx.x; w < hi; w += B) s += __popc(item_mask<BYTES>(words[w]));
+    for (int64_t w0 = lo + (int64_t)threadIdx.x * kRun; w0 < hi; w0 += (int64_t)B * kRun) {
+        uint32_t m[kRun];
+        load_run<BYTES>(words, w0, hi, vec, m);
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) s += __popc(m[q]);
+    }
     s = block_reduce_sum<B>(s, sm);
     if (threadIdx.x == 0) blk[blockIdx.x] = s;
 }
 
-// Each thread takes a run of kRun consecutive words per round: all its loads
-// are issued before the one block scan of the round, and its items are
-// emitted in order from its scanned offset.
+// Per round a thread takes a run of consecutive words (kRun byte-flag words,
+// or one bitmap word -- at most 32 items either way), all its loads issued
+// before the round's one block scan. The items' indices are staged in shared
+// memory at their offsets within the round and written out by consecutive
+// threads to consecutive output positions, so the stores of a warp are
+// contiguous rather than one scattered word per thread.
 template <int B, bool BYTES, class Policy>
 __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwords, const int32_t* __restrict__ blk,
                                                    Policy pol) {
+    constexpr int RUN = BYTES ? kRun : 1;  // words per thread and round
+    constexpr int CAP = B * 32;            // items per round at most
     __shared__ int32_t sm[B / 32 + 1];
+    __shared__ int32_t stage[CAP];
     int64_t lo, hi;
     block_range(nwords, lo, hi);
     const bool vec = ((uintptr_t)words & 15) == 0;
     int32_t base = block_prefix<B>(blk, blockIdx.x, sm);  // blk holds the raw block counts
     pol.begin();
-    for (int64_t off = lo; off < hi; off += (int64_t)B * kRun) {
-        const int64_t w0 = off + (int64_t)threadIdx.x * kRun;
+    for (int64_t off = lo; off < hi; off += (int64_t)B * RUN) {
+        const int64_t w0 = off + (int64_t)threadIdx.x * RUN;
         uint32_t m[kRun];
-        if (vec && w0 + kRun <= hi) {
-            const uint4 a = *reinterpret_cast<const uint4*>(words + w0);
-            const uint4 b = *reinterpret_cast<const uint4*>(words + w0 + 4);
-            m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
-            m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+        if constexpr (BYTES) {
+            load_run<BYTES>(words, w0, hi, vec, m);
         } else {
-#pragma unroll
-            for (int q = 0; q < kRun; ++q) m[q] = w0 + q < hi ? words[w0 + q] : 0u;
+            m[0] = w0 < hi ? words[w0] : 0u;
         }
         int32_t c = 0;
 #pragma unroll
-        for (int q = 0; q < kRun; ++q) {
-            m[q] = item_mask<BYTES>(m[q]);
-            c += __popc(m[q]);
-        }
+        for (int q = 0; q < RUN; ++q) c += __popc(m[q]);
         int32_t tot;
-        int32_t pos = base + block_excl_scan<B>(c, sm, &tot);
-        if (c) {
+        int32_t p = block_excl_scan<B>(c, sm, &tot);
 #pragma unroll
-            for (int q = 0; q < kRun; ++q) {
-                uint32_t mask = m[q];
-                if (!mask) continue;
-                const int64_t w = w0 + q;
-                pol.clear_word(words, w);
-                while (mask) {
-                    const int b = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    pol.emit(pos++, BYTES ? w * 4 + (b >> 3) : w * 32 + b);
-                }
+        for (int q = 0; q < RUN; ++q) {
+            uint32_t mask = m[q];
+            if (!mask) continue;
+            const int64_t w = w0 + q;
+            pol.clear_word(words, w);
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                mask &= mask - 1;
+                stage[p++] = (int32_t)(BYTES ? w * 4 + (b >> 3) : w * 32 + b);
             }
         }
+        __syncthreads();
+        for (int32_t k = threadIdx.x; k < tot; k += B) pol.emit(base + k, stage[k]);
+        __syncthreads();
         base += tot;
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) pol.count(base);
