@@ -92,6 +92,9 @@ static void destroy_handle(asv_matrix_s* H) {
     }
     if (H->bfs_hcount) cudaFreeHost(H->bfs_hcount);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    if (H->side_stream) cudaStreamDestroy(H->side_stream);
+    if (H->ev_fork) cudaEventDestroy(H->ev_fork);
+    if (H->ev_join) cudaEventDestroy(H->ev_join);
     for (void* p : H->allocs) cudaFree(p);
     delete H;
 }
@@ -122,6 +125,9 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     H->flags = flags;
     CKH(cudaGetDevice(&H->dev));
     CKH(cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, H->dev));
+    CKH(cudaStreamCreateWithFlags(&H->side_stream, cudaStreamNonBlocking));
+    CKH(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming));
+    CKH(cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming));
     H->G = H->num_sms * 4;
     const size_t vs = vsize(dtype);
     const bool has_val = (dtype != ASV_BOOL) && d_val != nullptr;

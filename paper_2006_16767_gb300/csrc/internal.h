@@ -125,6 +125,11 @@ struct asv_matrix_s {
     unsigned long long cond[2][2] = {{0, 0}, {0, 0}};
     asv::DescInit last_di[2][2];  // arguments the feature node of each graph was last given
     cudaStream_t cap_stream = nullptr;
+    // the long-row pass of the thread and sub-warp pulls runs beside the
+    // short-row kernel: a side stream joined by two events (in a graph
+    // capture they become a fork and a join of the captured graph)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int G = 0;  // fixed grid of the scan / sort / compaction primitives
     BatchWs bws;
     int32_t tune_R = 8, tune_GB = 1024, tune_hot = 0;  // batched tiling chosen by the autotuner

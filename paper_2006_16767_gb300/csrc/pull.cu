@@ -510,6 +510,17 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     uint8_t* yt = H->ws.yflag;
     const int64_t cap = (int64_t)H->num_sms * 16;
     const bool vec = ((uintptr_t)H->col % 16 == 0) && ((uintptr_t)H->val % 16 == 0);
+    // rows over kLongRow entries: their warp-per-segment pass (and fix-up)
+    // goes first, on the side stream; the short-row kernel then fills the SMs
+    // that the pass's tail -- segments walked to their end -- leaves idle.
+    // The two write disjoint rows.
+    const bool fork = dist != 2 && H->nseg > 0;
+    if (fork) {
+        cudaEventRecord(H->ev_fork, s);
+        cudaStreamWaitEvent(H->side_stream, H->ev_fork, 0);
+        launch_pull_long_dtype<T, MASK, SOUT>(H, a, vec, H->side_stream);
+        cudaEventRecord(H->ev_join, H->side_stream);
+    }
     if (dist == 0) {
         const unsigned g = (unsigned)((m + 32 * kStageWarps - 1) / (32 * kStageWarps));
         int32_t* st = H->ws.status;
@@ -524,10 +535,8 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
                 k_pull_thread<T, MASK, SOUT, false, false><<<g, 32 * kStageWarps, 0, s>>>(m, H->nnz, H->rowptr, H->col,
                                                                                         val, a, ywork, yt, st);
         }
-        launch_pull_long_dtype<T, MASK, SOUT>(H, a, vec, s);
     } else if (dist == 1) {
         launch_pull_warp_dtype<T, MASK, SOUT>(H, a, vec, s);
-        launch_pull_long_dtype<T, MASK, SOUT>(H, a, vec, s);
     } else {
         if (H->ntiles == 0) return;
         using Atom = typename Sr<T>::Atom;
@@ -542,6 +551,7 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
                                                    direct ? nullptr : H->d_desc, direct ? direct->y : nullptr,
                                                    ywork, SOUT ? 1 : 0);
     }
+    if (fork) cudaStreamWaitEvent(s, H->ev_join, 0);
 }
 
 // The FP32 balanced pull on caller-owned arrays and caller-provided scratch
