@@ -70,11 +70,11 @@ LONG_ROW, LONG_SEG = 256, 4096  # the library's long-row split (rows > 256 entri
 # profiles/rmat22_bfs8_pagerank_step_launches.md. Valid for the kernels that
 # list was taken with; a class it does not cover reports null.
 NCU_DRAM_BYTES_PER_CALL = {
-    "bfs:pull_thread": 294869386,
-    "bfs:push_bal_atom": 82690458,
-    "bfs:push_thread_atom": 11933521,
-    "bfs:push_warp_atom": 10724608,
-    "pagerank:pull_warp": 1158579712,
+    "bfs:pull_thread": 293882939,
+    "bfs:push_bal_atom": 79034914,
+    "bfs:push_thread_atom": 11930054,
+    "bfs:push_warp_atom": 10721493,
+    "pagerank:pull_warp": 1158448128,
 }
 
 
@@ -762,6 +762,8 @@ def main():
             "algorithmic_bytes_per_call": int(dom["bytes"] / dom["n"]),
             "share_of_step": round(dom["ms"] / sum(v["ms"] for v in per_k.values()), 3),
             "note": "duration = auto call (feature pass + selector + kernel), CUDA events on the launch stream"}
+    class_ms = {f"{k[0]}:{asv.KERNELS[k[1]]}": round(v["ms"] / args.steps, 4)
+                for k, v in sorted(per_k.items(), key=lambda kv: -kv[1]["ms"])}
 
     # end to end through the public API with pinned host buffers
     h2d, d2h = W.e2e_setup(torch)
@@ -787,7 +789,8 @@ def main():
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": int(args.steps * sum(c["launches"] for c in W.calls)),
            "clocks": clk, "wall_s_timed": round(wall, 3),
-           "selected": {asv.KERNELS[k[1]] + ":" + k[0]: v["n"] // args.steps for k, v in per_k.items()}}
+           "selected": {asv.KERNELS[k[1]] + ":" + k[0]: v["n"] // args.steps for k, v in per_k.items()},
+           "class_ms_per_step": class_ms}
     if not args.no_extra:
         out["bfs"] = bench_bfs(asv, torch, dev, W)
         out["create"] = bench_create(asv, torch, dev, W)
