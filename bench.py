@@ -198,6 +198,7 @@ class Rmat22:
         self.n = self.m = 1 << scale
         self.nnz = len(self.col)
         self.long_extra = long_row_launches(self.rowptr)
+        self.long_extra_flags = min(self.long_extra, 1)  # a Boolean sparse output needs no fix-up
         deg = np.diff(self.rowptr)
         cand = np.flatnonzero(deg > 0)
         pick = gen.randint(roots, len(cand), gen.config_seed(2), stream=7)
@@ -238,7 +239,7 @@ class Rmat22:
                 args_ = (self.m, self.n, self.nnz, c["nnz_x"], c["nnz_s"], c["nnz_y"], 0, 0, 0, True, True)
                 c["bytes"] = work_bytes(*args_)
                 c["kbytes"] = useful_bytes(c["kid"], *args_)
-                c["launches"] = launches(c["kid"], True, True, long_extra=self.long_extra)
+                c["launches"] = launches(c["kid"], True, True, long_extra=self.long_extra_flags)
             else:
                 c["nnz_y"] = self.m
                 args_ = (self.m, self.n, self.nnz, c["nnz_x"], c["nnz_s"], self.m, 4, 4, 4, False, False)

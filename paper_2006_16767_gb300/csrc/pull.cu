@@ -272,7 +272,8 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
         else S::acc_zero(acc);
     }
     if (mine) {
-        y[i] = S::part_T(S::acc_part(acc));
+        // a Boolean sparse output is its flags (the emitted values are one)
+        if (!(S::kPattern && SOUT)) y[i] = S::part_T(S::acc_part(acc));
         if (SOUT && hit) yflag[i] = 1;
     }
 }

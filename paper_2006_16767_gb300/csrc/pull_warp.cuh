@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256, UU >= 4 ? 4 : 6) k_pull_warp(int64_t m, i
         }
         if (valid[u] && l == 0) {
             const int64_t i = row0 + u * RPW + g;
-            y[i] = S::part_T(v);
+            if (!(S::kPattern && SOUT)) y[i] = S::part_T(v);  // a Boolean sparse output is its flags
             if (SOUT && h) yflag[i] = 1;
         }
     }
@@ -177,10 +177,11 @@ __global__ void __launch_bounds__(256, UU >= 4 ? 4 : 6) k_pull_warp(int64_t m, i
 // 16-byte descriptor built once per matrix): lane l reads
 // 16-byte chunks l, l+32, ... of the segment with 128-bit loads, the next
 // chunk's loads issued before the current chunk's gathers. Boolean segments
-// stop as soon as any lane has a hit. A row that is one segment is written
-// directly; otherwise the segment's partial goes to part[] in the push-side
-// accumulator type (FP64 for FP32 values) and k_pull_long_fixup adds a row's
-// partials in segment order.
+// stop as soon as any lane has a hit; for a Boolean sparse output a segment
+// with a hit sets its row's flag and nothing else. Otherwise a row that is
+// one segment is written directly, and the segments of a longer row leave
+// their partials in part[] in the push-side accumulator type (FP64 for FP32
+// values) for k_pull_long_fixup to add in segment order.
 template <class A>
 __device__ __forceinline__ uint64_t atom_bits(A v) {
     if constexpr (sizeof(A) == 8) return (uint64_t)__double_as_longlong(v);
@@ -242,6 +243,12 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     for (int o = 16; o > 0; o >>= 1) v = S::part_add(v, shfl_xor(v, o));
     const bool h = SOUT && __any_sync(0xffffffffu, hit);
     if (lane != 0) return;
+    if constexpr (S::kPattern && SOUT) {
+        // a Boolean sparse output is its flags: any segment with a true term
+        // settles its row, so no partials and no fix-up
+        if (h) yflag[row] = 1;
+        return;
+    }
     if (d.w) {
         y[row] = S::part_T(v);
         if (SOUT && h) yflag[row] = 1;
@@ -285,7 +292,7 @@ void launch_pull_long_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStr
     else
         k_pull_long<T, MASK, SOUT, false><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->seg, H->col, val, a, H->ws.ywork,
                                                             H->ws.yflag, H->long_part, H->long_hit);
-    if (H->nmulti > 0) {
+    if (H->nmulti > 0 && !(Sr<T>::kPattern && SOUT)) {
         const unsigned gf = (unsigned)std::min<int64_t>((H->nmulti + 255) / 256, (int64_t)H->num_sms * 4);
         k_pull_long_fixup<T><<<gf, 256, 0, s>>>(H->nmulti, H->multi_row, H->multi_base, H->rowptr, H->long_part,
                                                 H->long_hit, a, H->ws.ywork, H->ws.yflag, SOUT ? 1 : 0);
