@@ -70,11 +70,11 @@ LONG_ROW, LONG_SEG = 256, 4096  # the library's long-row split (rows > 256 entri
 # profiles/rmat22_bfs8_pagerank_step_launches.md. Valid for the kernels that
 # list was taken with; a class it does not cover reports null.
 NCU_DRAM_BYTES_PER_CALL = {
-    "bfs:pull_thread": 293882939,
-    "bfs:push_bal_atom": 79034914,
-    "bfs:push_thread_atom": 11930054,
-    "bfs:push_warp_atom": 10721493,
-    "pagerank:pull_warp": 1158448128,
+    "bfs:pull_thread": 289718134,
+    "bfs:push_bal_atom": 79034812,
+    "bfs:push_thread_atom": 11930065,
+    "bfs:push_warp_atom": 10720811,
+    "pagerank:pull_warp": 1159331584,
 }
 
 
