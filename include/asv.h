@@ -120,7 +120,25 @@ asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t n, int64_t 
                                  const void* d_val, int32_t dtype, uint32_t flags,
                                  void* stream);
 
-/* Release the handle and everything it owns (synchronises its device). */
+/* Transposed view (Sec. II: row-major access reads A in CSR, column-major
+ * access in CSC, and A's CSC arrays are exactly the CSR arrays of A^T):
+ * *At becomes an n x m handle for A^T whose
+ * CSR is A's CSC and whose CSC is A's CSR, borrowed from A with no copy of
+ * any pointer, index or value array. The view computes its own Table 1
+ * features (A^T's row lengths are A's column lengths), nnz-balanced
+ * partition, long-row segments and per-call workspaces, and its CSC -> CSR
+ * map (the inverse of A's), so every entry point taking a handle computes
+ * with A^T: y = A^T x through asv_spmv / asv_spmspv with the selector or a
+ * forced candidate. Lifetime: A must outlive At -- asv_matrix_destroy(A)
+ * returns ASV_ERR_ARG while A has live views. Values: the view reads A's
+ * arrays in place, so asv_matrix_update_values(A, ...) updates both, and
+ * asv_matrix_update_values on the view returns ASV_ERR_UNSUPPORTED. The
+ * current device must be A's (else ASV_ERR_ARG). Synchronises `stream`. */
+asv_status asv_matrix_transpose_view(asv_matrix A, asv_matrix* At, void* stream);
+
+/* Release the handle and everything it owns (synchronises its device).
+ * Returns ASV_ERR_ARG, and releases nothing, while transposed views of A
+ * are alive. */
 asv_status asv_matrix_destroy(asv_matrix A);
 
 /* Copy the Table 1 matrix features to *h_out (synchronises). */

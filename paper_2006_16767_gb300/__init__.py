@@ -82,6 +82,7 @@ def lib():
             P = ctypes.POINTER
             L.asv_matrix_create_csr.argtypes = [P(vp), i64, i64, i64, vp, vp, vp, i32, ctypes.c_uint32, vp]
             L.asv_matrix_destroy.argtypes = [vp]
+            L.asv_matrix_transpose_view.argtypes = [vp, P(vp), vp]
             L.asv_matrix_features.argtypes = [vp, P(_MFeat)]
             L.asv_matrix_arrays.argtypes = [vp] + [P(vp)] * 7
             L.asv_matrix_copy_csc.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -169,6 +170,13 @@ def asv_matrix_create_csr(m, n, rowptr, col, val, dtype=None, flags=ASV_BORROW, 
                                        _ptr(val), int(dtype), int(flags), _stream(stream)),
            "asv_matrix_create_csr")
     return h
+
+
+def asv_matrix_transpose_view(h, stream=None):
+    """Raw handle of A^T borrowing A's arrays; A must be destroyed after it."""
+    t = ctypes.c_void_p()
+    _check(lib().asv_matrix_transpose_view(h, ctypes.byref(t), _stream(stream)), "asv_matrix_transpose_view")
+    return t
 
 
 def asv_matrix_destroy(h):
@@ -314,6 +322,8 @@ class Matrix:
     def __init__(self, m, n, rowptr, col, val=None, dtype=None, validate=False, copy=False, stream=None):
         self.m, self.n = int(m), int(n)
         self.rowptr, self.col, self.val = rowptr, col, val
+        self.device = rowptr.device
+        self.parent = None
         self.dtype = (ASV_BOOL if val is None else _DT[val.dtype]) if dtype is None else dtype
         flags = (ASV_VALIDATE if validate else 0) | (ASV_COPY if copy else 0)
         self.handle = asv_matrix_create_csr(m, n, rowptr, col, val, self.dtype, flags, stream)
@@ -331,12 +341,25 @@ class Matrix:
         except Exception:
             pass
 
+    def transpose_view(self, stream=None) -> "Matrix":
+        """A^T as an n x m handle over this matrix's CSC and CSR (nothing copied).
+
+        The view keeps this matrix alive; its ``rowptr``/``col``/``val`` are
+        None because the arrays belong to this matrix's handle."""
+        t = Matrix.__new__(Matrix)
+        t.m, t.n, t.nnz = self.n, self.m, self.nnz
+        t.dtype, t.tdtype, t.device = self.dtype, self.tdtype, self.device
+        t.rowptr = t.col = t.val = None
+        t.parent = self
+        t.handle = asv_matrix_transpose_view(self.handle, stream)
+        return t
+
     def features(self) -> dict:
         return asv_matrix_features(self.handle)
 
     def csc(self):
         """(colptr, rowidx, val_csc, perm) as CUDA tensors (copies of the handle's arrays)."""
-        dev = self.rowptr.device
+        dev = self.device
         colptr = torch.empty(self.n + 1, dtype=torch.int32, device=dev)
         rowidx = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=dev)
         perm = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=dev)
@@ -382,7 +405,7 @@ class Matrix:
         products run -- None with wait=False); deltas below eps are dropped
         after every product. The iterations run on the device."""
         if rank is None:
-            rank = torch.empty(self.n, dtype=self.tdtype, device=self.rowptr.device)
+            rank = torch.empty(self.n, dtype=self.tdtype, device=self.device)
         iters = asv_pagerank(self.handle, damping, eps, max_iter, rank, kernel, stream, wait)
         return rank, iters
 
@@ -391,7 +414,7 @@ class Matrix:
         and the number of levels (None with wait=False); each level is one
         masked product, and the levels run on the device."""
         if level is None:
-            level = torch.empty(self.n, dtype=torch.int32, device=self.rowptr.device)
+            level = torch.empty(self.n, dtype=torch.int32, device=self.device)
         depth = asv_bfs(self.handle, source, level, kernel, stream, wait)
         return level, depth
 

@@ -99,6 +99,19 @@ static void destroy_handle(asv_matrix_s* H) {
     delete H;
 }
 
+// Device, stream and events every handle needs; on failure H is released.
+static asv_status init_handle(asv_matrix_s* H) {
+    CKH(cudaGetDevice(&H->dev));
+    CKH(cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, H->dev));
+    CKH(cudaStreamCreateWithFlags(&H->side_stream, cudaStreamNonBlocking));
+    CKH(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming));
+    CKH(cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming));
+    H->G = H->num_sms * 4;
+    return ASV_OK;
+}
+
+static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s, const asv_matrix_s* P);
+
 static int pow2_floor(double v) {
     int p = 1;
     while (p * 2 <= v) p *= 2;
@@ -123,12 +136,7 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     H->n = n;
     H->nnz = nnz;
     H->flags = flags;
-    CKH(cudaGetDevice(&H->dev));
-    CKH(cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, H->dev));
-    CKH(cudaStreamCreateWithFlags(&H->side_stream, cudaStreamNonBlocking));
-    CKH(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming));
-    CKH(cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming));
-    H->G = H->num_sms * 4;
+    if (asv_status st = init_handle(H)) return st;
     const size_t vs = vsize(dtype);
     const bool has_val = (dtype != ASV_BOOL) && d_val != nullptr;
 
@@ -166,14 +174,32 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
             return ASV_ERR_NONCANONICAL;
         }
     }
+    return finish_handle(out, H, s, nullptr);
+}
 
-    const int64_t nw_n = (n + 31) / 32, nw_m = (m + 31) / 32;
+// Everything of a handle after its CSR arrays are set: the CSC view, the
+// Table 1 features, the pull partition and long-row segments, the selector
+// tables and the per-call workspaces. With a parent P the handle is P's
+// transposed view: its CSC is P's CSR (borrowed, never written) and its
+// CSC -> CSR position map is the inverse of P's.
+static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s, const asv_matrix_s* P) {
+    const int64_t m = H->m, n = H->n, nnz = H->nnz;
+    const int32_t dtype = H->dtype;
+    const size_t vs = vsize(dtype);
+    const bool has_val = H->val != nullptr;
+    const int64_t nw_n = (n + 31) / 32;
     const int G = H->G;
     // CSC view
-    AL(H->colptr, 4 * (n + 1), false);
-    AL(H->rowidx, 4 * nnz, false);
+    if (P) {
+        H->colptr = const_cast<int32_t*>(P->rowptr);
+        H->rowidx = const_cast<int32_t*>(P->col);
+        H->val_csc = const_cast<void*>(P->val);
+    } else {
+        AL(H->colptr, 4 * (n + 1), false);
+        AL(H->rowidx, 4 * nnz, false);
+        if (has_val) AL(H->val_csc, vs * nnz, false);
+    }
     AL(H->perm, 4 * nnz, false);
-    if (has_val) AL(H->val_csc, vs * nnz, false);
     // features / partition / selector
     AL(H->d_mfeat, sizeof(MatFeat), true);
     H->ntiles = (m + nnz + pull_tile_items(dtype) - 1) / pull_tile_items(dtype);
@@ -219,7 +245,7 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     }
     CKH(cudaDeviceSynchronize());  // the zero-fills above ran on the legacy stream
 
-    CKH(build_csc(H, s));
+    CKH(P ? invert_perm(P->perm, nnz, H->perm, s) : build_csc(H, s));
     CKH(build_features(H, s));  // synchronises
     CKH(build_partition(H, s));
     CKH(build_long_rows(H, s));  // synchronises
@@ -246,8 +272,37 @@ extern "C" asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t 
     return ASV_OK;
 }
 
+extern "C" asv_status asv_matrix_transpose_view(asv_matrix A, asv_matrix* out, void* stream) {
+    if (!out) return ASV_ERR_ARG;
+    *out = nullptr;
+    if (!A) return ASV_ERR_ARG;
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != A->dev) return ASV_ERR_ARG;
+    asv_matrix_s* H = new (std::nothrow) asv_matrix_s();
+    if (!H) return ASV_ERR_NOMEM;
+    H->dtype = A->dtype;
+    H->m = A->n;
+    H->n = A->m;
+    H->nnz = A->nnz;
+    H->flags = ASV_BORROW;
+    if (asv_status st = init_handle(H)) return st;
+    // the CSR of A^T is A's CSC (rows of A^T = columns of A, ascending)
+    H->rowptr = A->colptr;
+    H->col = A->rowidx;
+    H->val = A->val_csc;
+    const asv_status st = finish_handle(out, H, (cudaStream_t)stream, A);
+    if (st == ASV_OK) {
+        H->parent = A;
+        ++A->views;
+    }
+    return st;
+}
+
 extern "C" asv_status asv_matrix_destroy(asv_matrix A) {
     if (!A) return ASV_ERR_ARG;
+    if (A->views > 0) return ASV_ERR_ARG;  // its transposed views read its arrays
+    if (A->parent) --A->parent->views;
     destroy_handle(A);
     return ASV_OK;
 }
@@ -287,7 +342,7 @@ extern "C" asv_status asv_matrix_copy_csc(asv_matrix A, int32_t* d_colptr, int32
 
 extern "C" asv_status asv_matrix_update_values(asv_matrix A, const void* d_val, void* stream) {
     if (!A) return ASV_ERR_ARG;
-    if (A->dtype == ASV_BOOL || !A->val) return ASV_ERR_UNSUPPORTED;
+    if (A->dtype == ASV_BOOL || !A->val || A->parent) return ASV_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (d_val && d_val != A->val) {
         if (!A->owns_val) return ASV_ERR_ARG;  // a borrowed handle reads the caller's array in place

@@ -155,6 +155,10 @@ struct asv_matrix_s {
     cudaGraph_t pr_graph[ASV_K_COUNT + 1] = {};
     cudaGraphExec_t pr_exec[ASV_K_COUNT + 1] = {};
     std::vector<void*> allocs;
+    // transposed views: a view borrows its parent's CSR and CSC arrays, so
+    // the parent counts its live views and is not destroyed before them
+    asv_matrix_s* parent = nullptr;
+    int views = 0;
 };
 
 namespace asv {
@@ -172,6 +176,8 @@ cudaError_t build_long_rows(asv_matrix_s* H, cudaStream_t s);
 int64_t pull_tile_items(int32_t dtype);
 cudaError_t validate_csr(asv_matrix_s* H, cudaStream_t s, int32_t* d_flag);
 cudaError_t regather_values(asv_matrix_s* H, cudaStream_t s);
+// inv[perm[p]] = p for p < nnz
+cudaError_t invert_perm(const int32_t* perm, int64_t nnz, int32_t* inv, cudaStream_t s);
 
 // bfs.cu -- the two driver loops, each run as a CUDA graph WHILE node whose
 // body is one selector-driven product followed by the step kernel below;

@@ -358,6 +358,21 @@ cudaError_t regather_values(asv_matrix_s* H, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- transposed view
+// The CSC -> CSR position map of A^T: entry p of A's CSC is entry p of A^T's
+// CSR and sits at A^T's CSC position perm[p] (A's CSR position).
+__global__ void k_invert_perm(const int32_t* __restrict__ perm, int64_t nnz, int32_t* __restrict__ inv) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[p]] = (int32_t)p;
+}
+
+cudaError_t invert_perm(const int32_t* perm, int64_t nnz, int32_t* inv, cudaStream_t s) {
+    if (nnz == 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 4096);  // grid-stride beyond
+    k_invert_perm<<<grid, 256, 0, s>>>(perm, nnz, inv);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- validation
 __global__ void k_validate(const int32_t* rowptr, const int32_t* col, int64_t m, int64_t n, int64_t nnz,
                            int32_t* flag) {

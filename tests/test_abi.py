@@ -67,6 +67,10 @@ def test_argument_errors_are_caught_on_the_host(libpath):
     assert L.asv_spmv(None, None, None, 0, None) == asv.ASV_ERR_ARG
     assert L.asv_spmspv(None, None, None, None, None, 0, None, None, None, None, 0, 0, None) == asv.ASV_ERR_ARG
     assert L.asv_matrix_destroy(None) == asv.ASV_ERR_ARG
+    h.value = 1
+    assert L.asv_matrix_transpose_view(None, ctypes.byref(h), None) == asv.ASV_ERR_ARG
+    assert h.value is None  # the out-handle is cleared before the argument check fails
+    assert L.asv_matrix_transpose_view(None, None, None) == asv.ASV_ERR_ARG
 
 
 def test_no_cpu_fallback_without_the_library(tmp_path, monkeypatch):
