@@ -70,11 +70,11 @@ LONG_ROW, LONG_SEG = 256, 4096  # the library's long-row split (rows > 256 entri
 # profiles/rmat22_bfs8_pagerank_step_launches.md. Valid for the kernels that
 # list was taken with; a class it does not cover reports null.
 NCU_DRAM_BYTES_PER_CALL = {
-    "bfs:pull_thread": 289718134,
-    "bfs:push_bal_atom": 79034812,
-    "bfs:push_thread_atom": 11930065,
-    "bfs:push_warp_atom": 10720811,
-    "pagerank:pull_warp": 1159331584,
+    "bfs:pull_thread": 289735562,
+    "bfs:push_bal_atom": 79029009,
+    "bfs:push_thread_atom": 11932183,
+    "bfs:push_warp_atom": 10722432,
+    "pagerank:pull_warp": 1159183616,
 }
 
 
@@ -347,9 +347,16 @@ def bench_batched(asv, torch, dev, reps=3):
     cnts = [torch.tensor([int(lens[b])], dtype=torch.int64, device=dev) for b in range(B)]
     slices = [(d_idx[xptr[b]:xptr[b + 1]], d_val[xptr[b]:xptr[b + 1]]) for b in range(B)]
 
-    def looped():
+    def looped(kernel="auto"):
         for b in range(B):
-            asv.asv_spmspv(A.handle, cnts[b], slices[b][0], slices[b][1], None, asv.ASV_OUT_DENSE, Yl[b])
+            asv.asv_spmspv(A.handle, cnts[b], slices[b][0], slices[b][1], None, asv.ASV_OUT_DENSE, Yl[b],
+                           kernel=kernel)
+    # the same loop with each of the candidates that compete here forced, so
+    # the batched form is also compared with the best fixed plain kernel
+    fixed = {}
+    for k in ("pull_warp", "push_warp_atom", "push_bal_atom"):
+        looped(k)
+        fixed[k] = round(_time(torch, lambda: looped(k), 1), 3)
     looped()
     t_l = _time(torch, looped, 1)
     diff = float(((Y - Yl).abs().max() / Yl.abs().max().clamp_min(1e-30)).item())
@@ -358,6 +365,7 @@ def bench_batched(asv, torch, dev, reps=3):
     out = {"workload": "zipf 1M x 131072 (lognormal ln40/1.0, Zipf 1.2), 4096 vectors", "nnz": len(c),
            "entries": int(xptr[-1]), "multiply_adds": nnz_s, "tune": list(tune),
            "batched_ms": round(t_b, 3), "looped_ms": round(t_l, 3), "speedup_vs_looped": round(t_l / t_b, 2),
+           "looped_fixed_ms": fixed, "speedup_vs_best_fixed_looped": round(min(fixed.values()) / t_b, 2),
            "batched_GBs": round((abytes + ybytes + xptr[-1] * 8) / (t_b * 1e-3) / 1e9, 1),
            "batched_Gmadds": round(nnz_s / (t_b * 1e-3) / 1e9, 1),
            "max_rel_diff_vs_looped": diff}

@@ -133,7 +133,10 @@ asv_status asv_matrix_create_csr(asv_matrix* out, int64_t m, int64_t n, int64_t 
  * returns ASV_ERR_ARG while A has live views. Values: the view reads A's
  * arrays in place, so asv_matrix_update_values(A, ...) updates both, and
  * asv_matrix_update_values on the view returns ASV_ERR_UNSUPPORTED. The
- * current device must be A's (else ASV_ERR_ARG). Synchronises `stream`. */
+ * current device must be A's (else ASV_ERR_ARG), and A's CSR arrays must
+ * start on 16-byte boundaries (every cudaMalloc or torch allocation does,
+ * as do ASV_COPY handles; else ASV_ERR_UNSUPPORTED), because the view's
+ * column-major kernels read them with 16-byte loads. Synchronises `stream`. */
 asv_status asv_matrix_transpose_view(asv_matrix A, asv_matrix* At, void* stream);
 
 /* Release the handle and everything it owns (synchronises its device).

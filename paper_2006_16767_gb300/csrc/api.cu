@@ -233,7 +233,7 @@ static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s
     AL(w.hist, 4 * hist_n, false);
     AL(w.blk, 4 * (G + 1), false);
     AL(w.status, 4, true);
-    AL(w.counters, 16, true);
+    AL(w.counters, 24, true);
     AL(w.ticket, 4, true);
     w.lcol_cap = (int32_t)std::min<int64_t>(nnz / kLongSeg + 1, (int64_t)1 << 30);
     AL(w.lcol, sizeof(int2) * (size_t)w.lcol_cap, false);
@@ -279,6 +279,10 @@ extern "C" asv_status asv_matrix_transpose_view(asv_matrix A, asv_matrix* out, v
     int dev = -1;
     CK(cudaGetDevice(&dev));
     if (dev != A->dev) return ASV_ERR_ARG;
+    // the view reads A's CSR as its CSC, whose kernels take 16-byte loads
+    // of the column pointers
+    auto misaligned = [](const void* p) { return ((uintptr_t)p & 15) != 0; };
+    if (misaligned(A->rowptr) || misaligned(A->col) || misaligned(A->val)) return ASV_ERR_UNSUPPORTED;
     asv_matrix_s* H = new (std::nothrow) asv_matrix_s();
     if (!H) return ASV_ERR_NOMEM;
     H->dtype = A->dtype;

@@ -186,6 +186,7 @@ struct CallDesc {
     int32_t pad;
     double vfeat[4];         // nnz_x, x_sparsity, nnz_s, m_sparsity
     const uint32_t* ymask;   // output mask: bit i set = row i excluded from y (NULL = none)
+    int64_t nhub;            // listed columns longer than kLongSeg (hubs of the thread/warp push)
 };
 
 // Row i is excluded by the output mask.

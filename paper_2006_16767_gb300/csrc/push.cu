@@ -65,7 +65,19 @@ constexpr int kLongCol = 64;
 // queues it instead, and every warp, once its own columns are done, takes
 // segments of kLongSeg entries from the queued columns through per-column
 // atomic cursors. The warp that queued a column reaches the queue after
-// queuing it, so every segment is taken; nobody waits.
+// queuing it, so every segment is taken whatever the other warps do. The
+// feature pass counted the list's hubs (desc->nhub), so in the thread push,
+// where a short list of hubs leaves nearly the whole grid without columns of
+// its own, a warp first waits, for a bounded time, until that many are
+// queued; without the wait it would find the queue still empty and leave the
+// hubs to the one or two warps that own them (37 hub columns of 6.8M entries:
+// 36 ms instead of 0.6 ms). The warp push does not wait: there every listed
+// column has its own warp, and on the same list its 37 owner warps sweeping
+// the queued columns together (0.25 ms) beat the whole grid joining them
+// (0.58 ms): the owners take the queued columns one after the other, so the
+// segments in flight at a time are consecutive ones of one column, on
+// disjoint rows. The wait only decides who helps, never what is done.
+constexpr int kHubWaitIters = 256;  // x ~128 ns of sleep: a few tens of microseconds at most
 template <class T, int WB>
 __device__ __forceinline__ void push_segment(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                              const T* __restrict__ valc, const CallDesc* __restrict__ desc,
@@ -91,15 +103,28 @@ __device__ __forceinline__ bool queue_long(const Ws& ws, int64_t t) {
     return true;
 }
 
-template <class T, int WB>
+template <class T, int WB, bool WAIT>
 __device__ __forceinline__ void help_long(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                           const T* __restrict__ valc, const CallDesc* __restrict__ desc,
                                           const Ws& ws, const uint32_t* ym, int lane) {
-    const int32_t nq = min((int32_t)*(volatile unsigned int*)ws.lcol_n, ws.lcol_cap);
+    int32_t nq = 0;
+    if (lane == 0) {
+        const int64_t want = WAIT ? min(desc->nhub, (int64_t)ws.lcol_cap) : 0;
+        nq = min((int32_t)*(volatile unsigned int*)ws.lcol_n, ws.lcol_cap);
+        for (int it = 0; nq < want && it < kHubWaitIters; ++it) {
+            __nanosleep(128);
+            nq = min((int32_t)*(volatile unsigned int*)ws.lcol_n, ws.lcol_cap);
+        }
+    }
+    nq = __shfl_sync(0xffffffffu, nq, 0);
     for (int32_t q = 0; q < nq; ++q) {
         int32_t t = 0, nseg = 0;
         if (lane == 0) {
             t = *(volatile int32_t*)&ws.lcol[q].x;
+            for (int it = 0; WAIT && t < 0 && it < kHubWaitIters; ++it) {  // counted, not yet published
+                __nanosleep(64);
+                t = *(volatile int32_t*)&ws.lcol[q].x;
+            }
             if (t >= 0) {
                 const int32_t j = desc->xidx[t];
                 nseg = (__ldg(colptr + j + 1) - __ldg(colptr + j) + kLongSeg - 1) / kLongSeg;
@@ -155,7 +180,7 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
                 emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xx), p0 + k);
         }
     }
-    help_long<T, WB>(colptr, rowidx, valc, desc, ws, ym, lane);
+    help_long<T, WB, true>(colptr, rowidx, valc, desc, ws, ym, lane);
 }
 
 template <class T, int WB>
@@ -179,7 +204,7 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
         const int64_t pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
         for (int32_t k = b + lane; k < e; k += 32) emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
     }
-    help_long<T, WB>(colptr, rowidx, valc, desc, ws, ym, lane);
+    help_long<T, WB, false>(colptr, rowidx, valc, desc, ws, ym, lane);
 }
 
 // Even split: warp-chunks of 32*IPT effective nonzeros; the listed column of

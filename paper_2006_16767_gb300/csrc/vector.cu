@@ -11,7 +11,7 @@ namespace asv {
 // Block totals of the feature pass go to zero-invariant counters; the last
 // block to finish (ticket) publishes them to the descriptor and re-zeroes.
 __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di, unsigned long long nx,
-                                             unsigned long long ns, int64_t n, int64_t nnz) {
+                                             unsigned long long ns, unsigned long long nh, int64_t n, int64_t nnz) {
     desc->x_dense = di.x_dense;
     desc->xbits = di.xbits;
     desc->xidx = di.xidx;
@@ -29,6 +29,7 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
     desc->out_mode = di.out_mode;
     desc->x_sparse = di.x_sparse;
     desc->ymask = di.ymask;
+    desc->nhub = (int64_t)nh;
     desc->vfeat[0] = (double)nx;
     desc->vfeat[1] = n > 0 ? (double)nx / (double)n : 0.0;
     desc->vfeat[2] = (double)ns;
@@ -36,19 +37,23 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
 }
 
 // `blocks` is the number of blocks that take part (all of them call this);
-// the one that draws the last ticket publishes.
+// the one that draws the last ticket publishes. ch counts the listed columns
+// longer than kLongSeg.
 template <int B>
-__device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long* counters,
-                                              unsigned int* ticket, CallDesc* desc, const DescInit& di, int64_t n,
-                                              int64_t nnz, int32_t* status, const SelectArg& sa, unsigned blocks) {
+__device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long ch,
+                                              unsigned long long* counters, unsigned int* ticket, CallDesc* desc,
+                                              const DescInit& di, int64_t n, int64_t nnz, int32_t* status,
+                                              const SelectArg& sa, unsigned blocks) {
     __shared__ unsigned long long sm[B / 32 + 1];
     __shared__ bool last;
     __shared__ TreeNode sn[kMaxTreeNodes];
     cx = block_reduce_sum<B>(cx, sm);
     cs = block_reduce_sum<B>(cs, sm);
+    ch = block_reduce_sum<B>(ch, sm);
     if (threadIdx.x == 0) {
         if (cx) atomicAdd(&counters[0], cx);
         if (cs) atomicAdd(&counters[1], cs);
+        if (ch) atomicAdd(&counters[2], ch);
         __threadfence();
         last = atomicAdd(ticket, 1u) == blocks - 1;
     }
@@ -57,6 +62,7 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
         __threadfence();
         unsigned long long nx = atomicExch(&counters[0], 0ull);
         unsigned long long ns = atomicExch(&counters[1], 0ull);
+        unsigned long long nh = atomicExch(&counters[2], 0ull);
         // a list with repeated or out-of-range entries could exceed the
         // workspaces sized for nnz_x <= n and nnz_s <= nnz: clamp and report
         if (nx > (unsigned long long)n || ns > (unsigned long long)nnz) {
@@ -64,7 +70,7 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
             nx = nx > (unsigned long long)n ? (unsigned long long)n : nx;
             ns = ns > (unsigned long long)nnz ? (unsigned long long)nnz : ns;
         }
-        publish_desc(desc, di, nx, ns, n, nnz);
+        publish_desc(desc, di, nx, ns, nh < nx ? nh : nx, n, nnz);
         __threadfence();
         atomicExch(ticket, 0u);
     }
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
     const int64_t nsuper = (n + 127) >> 7;
     const int64_t gw = (int64_t)blockIdx.x * (B / 32) + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * (B / 32);
-    unsigned long long cx = 0, cs = 0;
+    unsigned long long cx = 0, cs = 0, ch = 0;
     for (int64_t sw = gw; sw < nsuper; sw += nw) {
         const int64_t j0 = sw * 128 + lane * 4;
         bool nz[4];
@@ -133,17 +139,35 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
         // a fully nonzero stretch of 128 columns: two boundary reads give its
         // degree sum, so a dense x does not stream all of colptr
         if (__all_sync(0xffffffffu, nib == 0xFu && j0 + 4 <= n)) {
-            if (lane == 0) cs += (unsigned long long)(__ldg(colptr + sw * 128 + 128) - __ldg(colptr + sw * 128));
+            int32_t span = 0;
+            if (lane == 0) span = __ldg(colptr + sw * 128 + 128) - __ldg(colptr + sw * 128);
+            if (lane == 0) cs += (unsigned long long)span;
+            // a stretch longer than one hub may hold hubs: count them
+            if (__shfl_sync(0xffffffffu, span, 0) > kLongSeg) {
+                const int4 cp = __ldg(reinterpret_cast<const int4*>(colptr + j0));
+                const int32_t c4 = __ldg(colptr + j0 + 4);
+                ch += (cp.y - cp.x > kLongSeg) + (cp.z - cp.y > kLongSeg) + (cp.w - cp.z > kLongSeg) +
+                      (c4 - cp.w > kLongSeg);
+            }
         } else if (nib) {
             if (j0 + 4 <= n) {
                 const int4 cp = __ldg(reinterpret_cast<const int4*>(colptr + j0));
                 const int32_t c4 = __ldg(colptr + j0 + 4);
-                cs += (nz[0] ? cp.y - cp.x : 0) + (nz[1] ? cp.z - cp.y : 0) + (nz[2] ? cp.w - cp.z : 0) +
-                      (nz[3] ? c4 - cp.w : 0);
+                const int32_t d[4] = {cp.y - cp.x, cp.z - cp.y, cp.w - cp.z, c4 - cp.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (nz[q]) {
+                        cs += (unsigned long long)d[q];
+                        ch += d[q] > kLongSeg;
+                    }
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (nz[q]) cs += (unsigned long long)(__ldg(colptr + j0 + q + 1) - __ldg(colptr + j0 + q));
+                    if (nz[q]) {
+                        const int32_t d = __ldg(colptr + j0 + q + 1) - __ldg(colptr + j0 + q);
+                        cs += (unsigned long long)d;
+                        ch += d > kLongSeg;
+                    }
             }
         }
         unsigned wv = nib << (4 * (lane & 7));
@@ -158,7 +182,7 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
             }
         }
     }
-    finish_counts<B>(cx, cs, counters, ticket, desc, di, n, nnz, status, sa, gridDim.x);
+    finish_counts<B>(cx, cs, ch, counters, ticket, desc, di, n, nnz, status, sa, gridDim.x);
 }
 
 // Sparse x: nnz_s = sum of the listed columns' lengths.
@@ -177,21 +201,27 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
     // independent gathers
     const int64_t nl = min(nx, n);
     const int64_t stride = (int64_t)blocks * B;
-    unsigned long long cs = 0;
+    unsigned long long cs = 0, ch = 0;
     int64_t t = blockIdx.x * (int64_t)B + threadIdx.x;
     for (; t + 3 * stride < nl; t += 4 * stride) {
         int32_t j[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) j[q] = __ldg(xidx + t + q * stride);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cs += (unsigned long long)(__ldg(colptr + j[q] + 1) - __ldg(colptr + j[q]));
+        for (int q = 0; q < 4; ++q) {
+            const int32_t d = __ldg(colptr + j[q] + 1) - __ldg(colptr + j[q]);
+            cs += (unsigned long long)d;
+            ch += d > kLongSeg;
+        }
     }
     for (; t < nl; t += stride) {
         const int32_t j = __ldg(xidx + t);
-        cs += (unsigned long long)(__ldg(colptr + j + 1) - __ldg(colptr + j));
+        const int32_t d = __ldg(colptr + j + 1) - __ldg(colptr + j);
+        cs += (unsigned long long)d;
+        ch += d > kLongSeg;
     }
-    finish_counts<B>(blockIdx.x == 0 && threadIdx.x == 0 ? (unsigned long long)nx : 0ull, cs, counters, ticket, desc,
-                     di, n, nnz, status, sa, blocks);
+    finish_counts<B>(blockIdx.x == 0 && threadIdx.x == 0 ? (unsigned long long)nx : 0ull, cs, ch, counters, ticket,
+                     desc, di, n, nnz, status, sa, blocks);
 }
 
 // Few blocks per SM: every block of the feature pass ends with atomics on
