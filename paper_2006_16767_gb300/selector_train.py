@@ -59,10 +59,19 @@ def kernel_id(pattern, dist, wb):
 
 
 # ------------------------------------------------------------------ corpus
+CORPUS_SEED = 7919
+# lognormal-row / Zipf-column matrices of the corpus: (m, n, ln of the median
+# row length, its sigma, Zipf exponent, seed offset)
+ZIPF = {"zipf_200k": (200_000, 131_072, np.log(40), 1.0, 1.2, 1),
+        "zipf_1m_64k": (1_000_000, 65_536, np.log(20), 1.0, 1.1, 2),
+        "zipf_500k_256k": (500_000, 262_144, np.log(30), 0.8, 1.3, 7),
+        "zipf_100k_32k": (100_000, 32_768, np.log(80), 1.2, 1.0, 8)}
+
+
 def corpus():
     """Synthetic training matrices (none of them is a benchmark matrix)."""
     import gen
-    s = 7919
+    s = CORPUS_SEED
     items = []
     for g in (48, 96, 128, 160, 192, 224):
         items.append((f"stencil27_{g}", lambda g=g: gen.stencil27(g, s + g)[:3] + (g ** 3,)))
@@ -72,12 +81,9 @@ def corpus():
         items.append((f"rmat_{sc}_{ef}", lambda sc=sc, ef=ef: rmat_vals(sc, ef, s + sc * 7 + ef)))
     items.append(("rmat_er_18", lambda: rmat_vals(18, 16, s + 5, a=0.25, b=0.25, c=0.25)))
     items.append(("rmat_mild_19", lambda: rmat_vals(19, 16, s + 6, a=0.45, b=0.22, c=0.22)))
-    for name, m, n, mu, sg, zs, sd in (("zipf_200k", 200_000, 131_072, np.log(40), 1.0, 1.2, 1),
-                                       ("zipf_1m_64k", 1_000_000, 65_536, np.log(20), 1.0, 1.1, 2),
-                                       ("zipf_500k_256k", 500_000, 262_144, np.log(30), 0.8, 1.3, 7),
-                                       ("zipf_100k_32k", 100_000, 32_768, np.log(80), 1.2, 1.0, 8)):
+    for name, (m, n, mu, sg, zs, sd) in ZIPF.items():
         items.append((name, lambda m=m, n=n, mu=mu, sg=sg, zs=zs, sd=sd:
-                      gen.lognormal_zipf(m, n, mu, sg, zs, s + sd) + (n,)))
+                      gen.lognormal_zipf(m, n, mu, sg, zs, CORPUS_SEED + sd) + (n,)))
     for name, k, p, sd in (("bern_8192_1pct", 8192, 0.01, 3), ("bern_4096_5pct", 4096, 0.05, 4),
                            ("bern_16384_02pct", 16384, 0.002, 9)):
         items.append((name, lambda k=k, p=p, sd=sd: gen.bernoulli(k, k, p, 0.02, s + sd) + (k,)))
@@ -113,15 +119,34 @@ def bfs_levels(rp, c, n, root):
     return level
 
 
+def feature_rows(name, count=24):
+    """x drawn as rows of a second matrix over the same feature space as the
+    Zipf corpus matrix `name` (same rank -> column map, so the same popular
+    columns): a few dozen entries that reach the hub columns, so nnz_s / nnz
+    is far above nnz_x / n -- the sparse-data inputs that uniform positions
+    do not produce. Rows picked at spread-out length quantiles."""
+    import gen
+    m, n, mu, sg, zs, sd = ZIPF[name]
+    xrp, xc, _ = gen.lognormal_zipf(4096, n, mu, sg, zs, CORPUS_SEED + sd + 100, perm_seed=CORPUS_SEED + sd)
+    lens = np.diff(xrp)
+    order = np.argsort(lens, kind="stable")
+    picks = order[np.linspace(0, len(order) - 1, num=count).astype(np.int64)]
+    return [(float(lens[r]) / n, np.unique(xc[xrp[r]:xrp[r + 1]]).astype(np.int32)) for r in picks if lens[r] > 0]
+
+
 def vectors(name, rp, c, n, m, roots=2, max_levels=8):
     """The x of one training matrix: seeded uniform positions at every
-    density, and -- for square matrices -- BFS frontiers (the inputs of the
-    graph applications, whose structure uniform positions do not have) from
-    a few seeded roots, at most max_levels per root spread over the search."""
+    density; for the Zipf matrices, rows of a second matrix over the same
+    feature space; and -- for square matrices -- BFS frontiers (the inputs of
+    the graph applications, whose structure uniform positions do not have)
+    from a few seeded roots, at most max_levels per root spread over the
+    search."""
     import gen
     out = []
     for rho, k in densities(n):
         out.append((rho, gen.sample_positions(n, k, seed=zlib.crc32(f"{name}/{k}".encode()), stream=1)))
+    if name in ZIPF:
+        out.extend(feature_rows(name))
     if m == n and n > 1:
         deg = np.diff(rp)
         cand = np.flatnonzero(deg > 0)
