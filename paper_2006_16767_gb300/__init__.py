@@ -492,3 +492,29 @@ class SpMSpVFunction(torch.autograd.Function):
         need_dv, need_dx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         dX, dA = ctx.A.backward(X, dY.contiguous(), need_dx=need_dx, need_da=need_dv)
         return dA, dX, None
+
+
+# ---------------------------------------------------------------- module-level forms
+def spmv(A: Matrix, x, y=None, kernel="auto", stream=None):
+    """y = A x for a dense x (selector-driven unless `kernel` forces a candidate)."""
+    return A.spmv(x, y, kernel=kernel, stream=stream)
+
+
+def spmspv(A: Matrix, **kw):
+    """y = A x for a listed (xidx, xval[, nnz_x]) or dense (x_dense) x; see Matrix.spmspv."""
+    return A.spmspv(**kw)
+
+
+def select(A: Matrix, **kw):
+    """(kernel id, vector features) the selector picks for this x; synchronises."""
+    return A.select(**kw)
+
+
+def spmspv_batched(A: Matrix, **kw):
+    """Y[b] = A x_b for a batch of sparse (xptr, xidx, xval) or dense (X_dense) vectors."""
+    return A.spmspv_batched(**kw)
+
+
+def transpose_view(A: Matrix, stream=None) -> Matrix:
+    """A^T over A's arrays (nothing copied); see Matrix.transpose_view."""
+    return A.transpose_view(stream=stream)

@@ -73,6 +73,14 @@ def test_argument_errors_are_caught_on_the_host(libpath):
     assert L.asv_matrix_transpose_view(None, None, None) == asv.ASV_ERR_ARG
 
 
+def test_python_names_of_the_boundary():
+    import paper_2006_16767_gb300 as asv
+    for name in ("Matrix", "SpMSpVFunction", "spmv", "spmspv", "select", "spmspv_batched", "transpose_view"):
+        assert callable(getattr(asv, name)), name
+    for name in ("spmv", "spmspv", "select", "spmspv_batched", "transpose_view", "bfs", "pagerank", "backward"):
+        assert callable(getattr(asv.Matrix, name)), name
+
+
 def test_no_cpu_fallback_without_the_library(tmp_path, monkeypatch):
     import importlib
 
