@@ -1,4 +1,4 @@
-"""The 1-D row partition and the sparse-x all-gather on 2 gloo ranks (CPU).
+"""The 1-D row partition and the sparse-x all-gather on 2 and 3 gloo ranks (CPU).
 
 Each rank owns a row block with about half the nonzeros and the matching part
 of x; after the all-gather every rank computes its block of y (here with the
@@ -26,6 +26,16 @@ def free_port():
     return p
 
 
+def sparse_input(n, bounds, world):
+    """300 listed nonzeros; with three ranks all of them fall in rank 0's
+    rows, so the other ranks contribute empty lists to the all-gather."""
+    idx, val = gen.sparse_x(n, 300, seed=23)
+    if world == 3:
+        keep = idx < bounds[1]
+        idx, val = idx[keep], val[keep]
+    return idx, val
+
+
 def worker(rank, world, port, q):
     try:
         os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -38,7 +48,7 @@ def worker(rank, world, port, q):
         r0, r1 = bounds[rank], bounds[rank + 1]
         lrp, lc, lv = pdist.local_rows(rp, c, v, r0, r1)
         # x: listed nonzeros, each rank holds the ones in its own row range
-        idx, val = gen.sparse_x(n, 300, seed=23)
+        idx, val = sparse_input(n, bounds, world)
         mine = (idx >= r0) & (idx < r1)
 
         def local_product(gi, gv):
@@ -79,8 +89,8 @@ def test_row_partition_balances_nonzeros():
     assert pdist.owner_of([0, 5, 9], np.array([0, 4, 5, 8])).tolist() == [0, 0, 1, 1]
 
 
-def test_two_gloo_ranks_reassemble_the_product():
-    world = 2
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_reassemble_the_product(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = free_port()
@@ -95,7 +105,9 @@ def test_two_gloo_ranks_reassemble_the_product():
     rp, c = gen.rmat(12, 8, seed=21)
     n = 1 << 12
     v = gen.uniform(len(c), -1, 1, seed=22)
-    idx, val = gen.sparse_x(n, 300, seed=23)
+    idx, val = sparse_input(n, bounds, world)
+    if world == 3:
+        assert 0 < len(idx) < 300
     y_ref, s, _ = oracle.spmspv_rowmajor(n, rp, c, v, idx, val)
     y = np.zeros(n)
     for (r0, r1, yl) in parts:
