@@ -8,7 +8,9 @@ library is missing, importing the binding's functions raises.
 
 The functions keep the C names (``asv_spmv``, ``asv_spmspv``, ...); ``Matrix``
 is a small owner object that keeps the CSR tensors alive for a borrowed
-handle and destroys the handle when collected.
+handle and destroys the handle when collected (a transposed view keeps its
+parent alive). ``spmv``, ``spmspv``, ``select``, ``spmspv_batched`` and
+``transpose_view`` are the same calls in module form.
 """
 from __future__ import annotations
 
