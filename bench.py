@@ -1,23 +1,31 @@
 """Benchmark of the adaptive SpMV/SpMSpV hot path on GB300.
 
-Default workload (one "step"): the R-MAT scale-22 graph (edge factor 16,
-a,b,c = .57,.19,.19; symmetrised, deduplicated), every BFS frontier of 8
-seeded roots multiplied through the Boolean (OR, AND) semiring with
-selector-driven kernel choice and a sparse (list) output, plus one FP32
-PageRank step y = A x with a dense x. Metric: GB/s of useful bytes (the
-byte model of the selected candidate: touched pointers, indices, values,
-gathered x and written y) and its fraction of the measured HBM roofline.
+Default workload (one "step"): the x-density sweep on the FP32 27-point
+stencil, 256^3 grid (16.8M rows, 449M entries, CSR and CSC resident): for
+each density rho in {1e-5, 1e-4, 1e-3, 1e-2, 1e-1, 1}, one selector-driven
+SpMSpV with x given as a list and the output as the structural list, and one
+with x dense and y dense -- twelve products, each choosing its kernel on the
+device. Metric: GB/s of work bytes (for every product, the fewest bytes any
+correct candidate must touch: pointers, indices, values, gathered x and
+written y) and its fraction of the measured HBM roofline.
+
+Sections of the same line: the per-density table of the selected kernel
+against every forced candidate (regret), the R-MAT scale-22 BFS + PageRank
+step, whole BFS searches, incremental PageRank, handle creation, the batched
+form (4096 Zipf-row vectors) and the backward form (16384^2 layer).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload rmat22|stencil256] [--sweep]
+                    [--workload stencil256|rmat22] [--sweep stencil256|rmat22]
 
 --impl reference times the CPU oracle (the only other implementation of the
-method) on a bounded sample of the same workload. --sweep prints the
-per-kernel x-density table (stderr) instead of the JSON line.
+method; its multi-threaded form on every host core) on the same workload,
+metric and unit. --sweep prints the per-kernel x-density table instead of the
+JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -33,6 +41,9 @@ import numpy as np  # noqa: E402
 
 METRIC = "SpMV/SpMSpV GB/s and % HBM peak vs x density; batched & backward vs plain"
 L2_FLUSH_BYTES = 512 << 20
+KNAMES = ("pull_thread", "pull_warp", "pull_bal", "mpull_thread", "mpull_warp", "mpull_bal",
+          "push_thread_atom", "push_warp_atom", "push_bal_atom", "push_thread_sort", "push_warp_sort",
+          "push_bal_sort", "push_thread_priv", "push_warp_priv", "push_bal_priv")
 
 
 def peaks():
@@ -41,6 +52,13 @@ def peaks():
         d = json.load(open(p))
         return float(d.get("hbm_gbs", 6800.0)), "measured"
     return 6800.0, "fallback"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 # ------------------------------------------------------------------ byte model
@@ -64,18 +82,6 @@ def work_bytes(m, n, nnz, nnz_x, nnz_s, nnz_y, s_v, s_x, s_y, x_sparse, sparse_o
 
 
 LONG_ROW, LONG_SEG = 256, 4096  # the library's long-row split (rows > 256 entries, segments of 4096)
-
-# DRAM bytes (read + write) per call of a call class, from the profiler's
-# launch list of one step of this workload (cold caches, per-call ranges):
-# profiles/rmat22_bfs8_pagerank_step_launches.md. Valid for the kernels that
-# list was taken with; a class it does not cover reports null.
-NCU_DRAM_BYTES_PER_CALL = {
-    "bfs:pull_thread": 289735562,
-    "bfs:push_bal_atom": 79029009,
-    "bfs:push_thread_atom": 11932183,
-    "bfs:push_warp_atom": 10722432,
-    "pagerank:pull_warp": 1159183616,
-}
 
 
 def long_row_launches(rowptr):
@@ -114,6 +120,38 @@ def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0):
         c += 1 + 1 + scan + 1 + 1 + 1  # memset, count, scan, copy, scatter, accumulate
     c += 1 if not sparse_out else compaction
     return c
+
+
+# ------------------------------------------------------------------ measured DRAM traffic
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+
+
+def sources_digest(files):
+    """Digest of the library sources a traffic figure was taken with."""
+    h = hashlib.sha256()
+    for f in sorted(files):
+        with open(os.path.join(ROOT, "paper_2006_16767_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(cls, model_bytes):
+    """DRAM bytes per call of a call class, from one-kernel profiler captures
+    of a smaller case of the same call, scaled by the byte model (the
+    captures' traffic follows the model bytes); None when no capture covers
+    the class or its kernels' sources changed since it was taken."""
+    try:
+        tab = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None, None
+    e = tab.get("entries", {}).get(cls)
+    if not e or sources_digest(e["sources"]) != e["sources_digest"]:
+        return None, None
+    scale = model_bytes / e["model_bytes_small"]
+    return int(round(e["dram_bytes_small"] * scale)), {
+        "captured_on": e["small_case"], "dram_bytes_small": e["dram_bytes_small"],
+        "model_bytes_small": e["model_bytes_small"], "scale": round(scale, 4),
+        "summary": e.get("summary")}
 
 
 # ------------------------------------------------------------------ clocks
@@ -159,7 +197,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-# ------------------------------------------------------------------ workload
+# ------------------------------------------------------------------ workloads
 def bfs_frontiers(rowptr, col, roots):
     """Successive BFS frontiers {v : level(v) = l} of each root, ascending.
     Levels come from scipy's BFS predecessor tree by pointer jumping."""
@@ -185,9 +223,209 @@ def bfs_frontiers(rowptr, col, roots):
     return out
 
 
+class Stencil256:
+    """FP32 27-point stencil on a side^3 grid; one product per (density, x
+    format): x as a list with the structural output list, and x dense with a
+    dense y."""
+    name = "stencil256_density_sweep"
+    RHOS = (1e-5, 1e-4, 1e-3, 1e-2, 1e-1, 1.0)
+    dtype = "f32"
+
+    def __init__(self, side=256):
+        import gen
+        self.side = side
+        t = time.time()
+        self.rowptr, self.col, self.val, self.rowsum = gen.stencil27(side, gen.config_seed(5))
+        self.gen_s = time.time() - t
+        self.m = self.n = side ** 3
+        self.nnz = len(self.col)
+        self.colcount = np.bincount(self.col, minlength=self.n)
+        self.xs = []
+        for rho in self.RHOS:
+            k = max(1, int(round(rho * self.n)))
+            idx, val = gen.sparse_x(self.n, k, gen.config_seed(5), 11, np.float32)
+            self.xs.append((rho, idx, val, int(self.colcount[idx].sum())))
+        # call order of a step: ascending density, the list form then the dense form
+        self.plan = [(i, fmt) for i in range(len(self.RHOS)) for fmt in ("list", "dense")]
+
+    @staticmethod
+    def label(rho, fmt):
+        return f"{fmt}:{rho:g}"
+
+    def setup_gpu(self, asv, torch, dev):
+        self.asv, self.torch = asv, torch
+        m, n = self.m, self.n
+        self.rp_d = torch.from_numpy(self.rowptr).to(dev)
+        self.col_d = torch.from_numpy(self.col).to(dev)
+        self.val_d = torch.from_numpy(self.val).to(dev)
+        self.A = asv.Matrix(m, n, self.rp_d, self.col_d, self.val_d)
+        self.idx_d, self.xval_d, self.xd_d = [], [], []
+        for rho, idx, val, _ in self.xs:
+            it = torch.from_numpy(idx).to(dev)
+            vt = torch.from_numpy(val).to(dev)
+            xd = torch.zeros(n, dtype=torch.float32, device=dev)
+            xd[it.long()] = vt
+            self.idx_d.append(it)
+            self.xval_d.append(vt)
+            self.xd_d.append(xd)
+        nr = len(self.RHOS)
+        self.cnt_d = torch.tensor([[len(x[1])] for x in self.xs], dtype=torch.int64, device=dev)
+        self.nnz_y = torch.zeros(nr, dtype=torch.int64, device=dev)
+        self.yidx = [torch.empty(m, dtype=torch.int32, device=dev) for _ in range(nr)]
+        self.yval = [torch.empty(m, dtype=torch.float32, device=dev) for _ in range(nr)]
+        self.yd = [torch.empty(m, dtype=torch.float32, device=dev) for _ in range(nr)]
+        self.calls = []
+        for i, fmt in self.plan:
+            rho = self.RHOS[i]
+            if fmt == "list":
+                kid, vf = asv.asv_select(self.A.handle, self.cnt_d[i], self.idx_d[i], self.xval_d[i],
+                                         out_mode=asv.ASV_OUT_SPARSE)
+            else:
+                kid, vf = asv.asv_select(self.A.handle, x_dense=self.xd_d[i])
+            self.calls.append(dict(kind=self.label(rho, fmt), kid=kid, nnz_x=vf["nnz_x"], nnz_s=vf["nnz_s"],
+                                   fmt=fmt, i=i))
+        self.run_step()
+        torch.cuda.synchronize()
+        ny = self.nnz_y.cpu().numpy()
+        for c in self.calls:
+            sparse = c["fmt"] == "list"
+            c["nnz_y"] = int(ny[c["i"]]) if sparse else m
+            args_ = (m, n, self.nnz, c["nnz_x"], c["nnz_s"], c["nnz_y"], 4, 4, 4, sparse, sparse)
+            c["bytes"] = work_bytes(*args_)
+            c["kbytes"] = useful_bytes(c["kid"], *args_)
+            c["launches"] = launches(c["kid"], sparse, sparse)
+
+    def call(self, c, kernel="auto", xidx=None, xval=None, xd=None, cnt=None):
+        asv, i = self.asv, c["i"]
+        xidx = self.idx_d[i] if xidx is None else xidx
+        xval = self.xval_d[i] if xval is None else xval
+        cnt = self.cnt_d[i] if cnt is None else cnt
+        if c["fmt"] == "list":
+            asv.asv_spmspv(self.A.handle, cnt, xidx, xval, None, asv.ASV_OUT_SPARSE, None, self.yidx[i],
+                           self.yval[i], self.nnz_y[i:i + 1], self.m, kernel)
+        else:
+            asv.asv_spmspv(self.A.handle, None, None, None, self.xd_d[i] if xd is None else xd,
+                           asv.ASV_OUT_DENSE, self.yd[i], kernel=kernel)
+
+    def run_step(self, events=None, direct=False):
+        """One step; direct=True replays the selector's recorded choices as
+        direct launches (for the profiler, which does not see kernels inside
+        conditional graph nodes); the timed steps always run the selector."""
+        nvtx = self.torch.cuda.nvtx if direct else None
+        for j, c in enumerate(self.calls):
+            if events is not None:
+                events[j][0].record()
+            if nvtx:
+                nvtx.range_push(f"{c['kind']}:{KNAMES[c['kid']]}")
+            self.call(c, c["kid"] if direct else "auto")
+            if nvtx:
+                nvtx.range_pop()
+            if events is not None:
+                events[j][1].record()
+
+    # end to end through the public API: inputs from pinned host memory, the
+    # step's results (lists of the exact size the device reports, dense y) back
+    def e2e_setup(self, torch):
+        self.h_idx = [torch.from_numpy(x[1]).pin_memory() for x in self.xs]
+        self.h_val = [torch.from_numpy(x[2]).pin_memory() for x in self.xs]
+        self.h_cnt = self.cnt_d.cpu().pin_memory()
+        self.h_xd = [x.cpu().pin_memory() for x in self.xd_d]
+        self.d_idx = [torch.empty_like(t) for t in self.idx_d]
+        self.d_val = [torch.empty_like(t) for t in self.xval_d]
+        self.d_cnt = torch.empty_like(self.cnt_d)
+        self.d_xd = [torch.empty_like(t) for t in self.xd_d]
+        self.h_nnzy = torch.empty(len(self.RHOS), dtype=torch.int64).pin_memory()
+        self.h_yidx = [torch.empty(self.m, dtype=torch.int32).pin_memory() for _ in self.RHOS]
+        self.h_yval = [torch.empty(self.m, dtype=torch.float32).pin_memory() for _ in self.RHOS]
+        self.h_yd = [torch.empty(self.m, dtype=torch.float32).pin_memory() for _ in self.RHOS]
+        h2d = sum(t.numel() * 4 for t in self.h_idx + self.h_val + self.h_xd) + self.h_cnt.numel() * 8
+        d2h = self.h_nnzy.numel() * 8 + sum(c["nnz_y"] * 8 for c in self.calls if c["fmt"] == "list") + \
+            sum(self.m * 4 for c in self.calls if c["fmt"] == "dense")
+        return h2d, d2h
+
+    def e2e_step(self):
+        torch = self.torch
+        for h, d in zip(self.h_idx + self.h_val + self.h_xd, self.d_idx + self.d_val + self.d_xd):
+            d.copy_(h, non_blocking=True)
+        self.d_cnt.copy_(self.h_cnt, non_blocking=True)
+        for c in self.calls:
+            i = c["i"]
+            self.call(c, "auto", self.d_idx[i], self.d_val[i], self.d_xd[i], self.d_cnt[i])
+        for c in self.calls:
+            if c["fmt"] == "dense":
+                self.h_yd[c["i"]].copy_(self.yd[c["i"]], non_blocking=True)
+        self.h_nnzy.copy_(self.nnz_y, non_blocking=True)
+        torch.cuda.current_stream().synchronize()  # the list sizes decide the copies
+        for c in self.calls:
+            if c["fmt"] == "list":
+                i, k = c["i"], int(self.h_nnzy[c["i"]])
+                self.h_yidx[i][:k].copy_(self.yidx[i][:k], non_blocking=True)
+                self.h_yval[i][:k].copy_(self.yval[i][:k], non_blocking=True)
+
+    def config(self):
+        return {"workload": self.name, "matrix": f"27-point stencil {self.side}^3, FP32, CSR + CSC resident",
+                "m": self.m, "nnz": self.nnz, "x_densities": list(self.RHOS),
+                "calls_per_step": len(self.calls),
+                "formats": "per density: x list -> y list (SpMSpV), x dense -> y dense",
+                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "seed": 20061681}
+
+    # the oracle on the same products (CPU baseline): the row-major product
+    # for a dense x, and for a list the oracle routine whose pattern touches
+    # fewer bytes (column-major push when the listed columns are short)
+    def oracle_prepare(self):
+        import oracle
+        if getattr(self, "_oracle_ready", False):
+            return
+        self.val64 = self.val.astype(np.float64)
+        self.colptr, self.rowidx, perm = oracle.csr_to_csc(self.m, self.n, self.rowptr, self.col)
+        self.val64_csc = self.val64[perm]
+        self.x64 = [(x[1], x[2].astype(np.float64)) for x in self.xs]
+        self.xd64 = [gen_dense(self.n, x[1], x[2]) for x in self.xs]
+        self._oracle_ready = True
+
+    def oracle_step(self, par):
+        import oracle
+        self.oracle_prepare()
+        t = time.perf_counter()
+        for c in self.calls:
+            i = c["i"]
+            if c["fmt"] == "dense":
+                (oracle.csr_pull_par if par else oracle.csr_pull)(self.rowptr, self.col, self.val64, self.xd64[i])
+            elif c["nnz_s"] * 8 < self.nnz * 4:
+                (oracle.csc_push_par if par else oracle.csc_push)(self.m, self.colptr, self.rowidx, self.val64_csc,
+                                                                   *self.x64[i])
+            else:
+                (oracle.spmspv_rowmajor_par if par else oracle.spmspv_rowmajor)(self.n, self.rowptr, self.col,
+                                                                                 self.val64, *self.x64[i])
+        return sum(c["bytes"] for c in self.calls), time.perf_counter() - t
+
+    def plan_calls_host(self):
+        """The step's calls with their byte model from the oracle alone (no
+        GPU), for the reference arm: the selected kernel does not enter the
+        work bytes."""
+        import oracle
+        self.oracle_prepare()
+        self.calls = []
+        for i, fmt in self.plan:
+            rho, idx, val, nnz_s = self.xs[i]
+            sparse = fmt == "list"
+            nnz_y = self.m
+            if sparse:  # the structural output set: rows with an entry in a listed column
+                nnz_y = int(oracle.csc_push(self.m, self.colptr, self.rowidx, None, idx, None)[1].sum())
+            b = work_bytes(self.m, self.n, self.nnz, len(idx), nnz_s, nnz_y, 4, 4, 4, sparse, sparse)
+            self.calls.append(dict(kind=self.label(rho, fmt), fmt=fmt, i=i, nnz_x=len(idx), nnz_s=nnz_s,
+                                   nnz_y=nnz_y, bytes=b))
+
+
+def gen_dense(n, idx, val):
+    import gen
+    return gen.densify(n, idx, np.asarray(val, np.float64))
+
+
 class Rmat22:
     """R-MAT scale 22 BFS frontiers (Boolean) + one FP32 PageRank step."""
     name = "rmat22_bfs8_pagerank"
+    dtype = "u8 (OR,AND) + f32"
 
     def __init__(self, scale=22, edge_factor=16, roots=8):
         import gen
@@ -216,16 +454,17 @@ class Rmat22:
         self.Af = asv.Matrix(self.m, self.n, self.rp_d, self.col_d, self.ones_d)
         self.x_pr = torch.from_numpy(self.pr_x).to(dev)
         self.y_pr = torch.empty(self.m, dtype=torch.float32, device=dev)
-        self.yidx = torch.empty(self.m, dtype=torch.int32, device=dev)
-        self.yval = torch.empty(self.m, dtype=torch.uint8, device=dev)
         # BFS frontiers (inputs, prepared on the host with scipy's BFS)
-        self.frontiers = [torch.from_numpy(f).to(dev) for f in bfs_frontiers(self.rowptr, self.col, self.roots)]
+        self.frontiers_host = bfs_frontiers(self.rowptr, self.col, self.roots)
+        self.frontiers = [torch.from_numpy(f).to(dev) for f in self.frontiers_host]
+        nf = len(self.frontiers)
         self.counts = torch.tensor([[f.numel()] for f in self.frontiers], dtype=torch.int64, device=dev)
-        self.nnz_y = torch.zeros(len(self.frontiers) + 1, dtype=torch.int64, device=dev)
-        # the selector's choice and the byte model of every call
+        self.nnz_y = torch.zeros(nf + 1, dtype=torch.int64, device=dev)
+        # every level product keeps its own output list (the e2e leg reads them all back)
+        self.yidx = [torch.empty(self.m, dtype=torch.int32, device=dev) for _ in range(nf)]
         self.calls = []
         for i, f in enumerate(self.frontiers):
-            kid, vf = asv.asv_select(self.Ab.handle, self.counts[i], f)
+            kid, vf = asv.asv_select(self.Ab.handle, self.counts[i], f, out_mode=asv.ASV_OUT_SPARSE)
             self.calls.append(dict(kind="bfs", kid=kid, nnz_x=vf["nnz_x"], nnz_s=vf["nnz_s"]))
         kid, vf = asv.asv_select(self.Af.handle, x_dense=self.x_pr)
         self.calls.append(dict(kind="pagerank", kid=kid, nnz_x=vf["nnz_x"], nnz_s=vf["nnz_s"]))
@@ -247,31 +486,34 @@ class Rmat22:
                 c["kbytes"] = useful_bytes(c["kid"], *args_)
                 c["launches"] = launches(c["kid"], False, False, long_extra=self.long_extra)
 
-    def run_step(self, events=None, direct=False):
+    def run_step(self, events=None, direct=False, fronts=None, counts=None, x_pr=None):
         """One step. direct=True replays the selector's recorded choices as
         direct launches (the profiler cannot see kernels inside graphs with
         conditional nodes); the timed steps always run the selector."""
         asv = self.asv
         h = self.Ab.handle
+        fronts = self.frontiers if fronts is None else fronts
+        counts = self.counts if counts is None else counts
         nvtx = self.torch.cuda.nvtx if direct else None  # per-call ranges for the profiler's launch list
-        for i, f in enumerate(self.frontiers):
+        for i, f in enumerate(fronts):
             if events is not None:
                 events[i][0].record()
             k = self.calls[i]["kid"] if direct else "auto"
             if nvtx:
-                nvtx.range_push(f"bfs:{asv.KERNELS[k]}")
-            asv.asv_spmspv(h, self.counts[i], f, None, None, asv.ASV_OUT_SPARSE, None, self.yidx, self.yval,
+                nvtx.range_push(f"bfs:{KNAMES[k]}")
+            asv.asv_spmspv(h, counts[i], f, None, None, asv.ASV_OUT_SPARSE, None, self.yidx[i], None,
                            self.nnz_y[i:i + 1], self.m, k)
             if nvtx:
                 nvtx.range_pop()
             if events is not None:
                 events[i][1].record()
-        j = len(self.frontiers)
+        j = len(fronts)
         if events is not None:
             events[j][0].record()
         if nvtx:
-            nvtx.range_push(f"pagerank:{asv.KERNELS[self.calls[j]['kid']]}")
-        asv.asv_spmv(self.Af.handle, self.x_pr, self.y_pr, self.calls[j]["kid"] if direct else "auto")
+            nvtx.range_push(f"pagerank:{KNAMES[self.calls[j]['kid']]}")
+        asv.asv_spmv(self.Af.handle, self.x_pr if x_pr is None else x_pr, self.y_pr,
+                     self.calls[j]["kid"] if direct else "auto")
         if nvtx:
             nvtx.range_pop()
         if events is not None:
@@ -283,31 +525,51 @@ class Rmat22:
         self.h_prx = torch.from_numpy(self.pr_x).pin_memory()
         self.h_ypr = torch.empty(self.m, dtype=torch.float32).pin_memory()
         self.h_nnzy = torch.empty(len(self.frontiers) + 1, dtype=torch.int64).pin_memory()
+        self.h_yidx = [torch.empty(self.m, dtype=torch.int32).pin_memory() for _ in self.frontiers]
         self.d_front = [torch.empty_like(f) for f in self.frontiers]
         self.d_counts = torch.empty_like(self.counts)
         self.d_prx = torch.empty_like(self.x_pr)
         h2d = sum(f.numel() * 4 for f in self.h_front) + self.h_counts.numel() * 8 + self.h_prx.numel() * 4
-        d2h = self.h_ypr.numel() * 4 + self.h_nnzy.numel() * 8
+        d2h = self.h_ypr.numel() * 4 + self.h_nnzy.numel() * 8 + \
+            sum(c["nnz_y"] * 4 for c in self.calls if c["kind"] == "bfs")
         return h2d, d2h
 
     def e2e_step(self):
-        asv = self.asv
         for hf, df in zip(self.h_front, self.d_front):
             df.copy_(hf, non_blocking=True)
         self.d_counts.copy_(self.h_counts, non_blocking=True)
         self.d_prx.copy_(self.h_prx, non_blocking=True)
-        for i, f in enumerate(self.d_front):
-            asv.asv_spmspv(self.Ab.handle, self.d_counts[i], f, None, None, asv.ASV_OUT_SPARSE, None, self.yidx,
-                           self.yval, self.nnz_y[i:i + 1], self.m, "auto")
-        asv.asv_spmv(self.Af.handle, self.d_prx, self.y_pr, "auto")
+        self.run_step(fronts=self.d_front, counts=self.d_counts, x_pr=self.d_prx)
         self.h_ypr.copy_(self.y_pr, non_blocking=True)
         self.h_nnzy.copy_(self.nnz_y, non_blocking=True)
+        self.torch.cuda.current_stream().synchronize()  # the list sizes decide the copies
+        for i in range(len(self.frontiers)):
+            k = int(self.h_nnzy[i])
+            self.h_yidx[i][:k].copy_(self.yidx[i][:k], non_blocking=True)
 
     def config(self):
         return {"workload": self.name, "graph": f"rmat scale {self.scale} edge factor {self.edge_factor}",
-                "n": self.n, "nnz": self.nnz, "roots": self.nroots, "bfs_levels": len(self.frontiers),
+                "n": self.n, "nnz": self.nnz, "roots": self.nroots, "bfs_levels": len(self.frontiers_host),
                 "calls_per_step": len(self.calls), "bfs_output": "sparse list", "pagerank": "fp32 dense x",
                 "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "seed": 20061678}
+
+    def oracle_step(self, par, max_bfs_calls=None):
+        import oracle
+        xs = self.pr_x.astype(np.float64)
+        nb = len(self.calls) - 1 if max_bfs_calls is None else min(max_bfs_calls, len(self.calls) - 1)
+        t_tot, b_tot = 0.0, 0.0
+        t = time.perf_counter()
+        (oracle.csr_pull_par if par else oracle.csr_pull)(self.rowptr, self.col, None, xs)
+        t_tot += time.perf_counter() - t
+        b_tot += self.calls[-1]["bytes"]
+        for i in range(nb):
+            xb = np.zeros(self.n, np.uint8)
+            xb[self.frontiers_host[i]] = 1
+            t = time.perf_counter()
+            oracle.bool_pull(self.rowptr, self.col, xb)
+            t_tot += time.perf_counter() - t
+            b_tot += self.calls[i]["bytes"]
+        return b_tot, t_tot
 
 
 def _time(torch, fn, reps):
@@ -319,6 +581,140 @@ def _time(torch, fn, reps):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def measure(W, torch, dev, steps, warmup, direct=False, world=1, dist=None, clocks_index=None):
+    """Times `steps` steps of workload W (CUDA events on the launching stream,
+    L2 flushed before each step) and the same step end to end through the
+    public API; returns the figures of the JSON line."""
+    asv = W.asv
+    hbm, peak_kind = peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ncalls = len(W.calls)
+    for _ in range(max(3, warmup)):
+        flush.zero_()
+        W.run_step(direct=direct)
+    torch.cuda.synchronize()
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    call_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ncalls)]
+               for _ in range(steps)]
+    clocks = ClockSampler(clocks_index) if clocks_index is not None else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    t_wall = time.perf_counter()
+    for s in range(steps):
+        flush.zero_()
+        torch.cuda.nvtx.range_push("timed_step")
+        step_ev[s][0].record()
+        W.run_step(call_ev[s], direct=direct)
+        step_ev[s][1].record()
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clk = None
+    if clocks:
+        time.sleep(0.2)
+        clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in step_ev) / steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_bytes = sum(c["bytes"] for c in W.calls)
+    value = step_bytes * world / (ms * 1e-3) / 1e9
+
+    # per call class (kind, selected kernel): durations from the per-call
+    # events, recorded on the stream the calls are launched on
+    per_k = {}
+    for s in range(steps):
+        for i, c in enumerate(W.calls):
+            d = call_ev[s][i][0].elapsed_time(call_ev[s][i][1])
+            e = per_k.setdefault((c["kind"], c["kid"]), {"ms": 0.0, "bytes": 0.0, "n": 0})
+            e["ms"] += d
+            e["bytes"] += c["kbytes"]
+            e["n"] += 1
+    dom_key = max(per_k, key=lambda k: per_k[k]["ms"])
+    dom = per_k[dom_key]
+    model = dom["bytes"] / dom["n"]
+    achieved = model / ((dom["ms"] / dom["n"]) * 1e-3) / 1e9
+    cls = f"{dom_key[0]}|{KNAMES[dom_key[1]]}"
+    traffic, prov = traffic_for(cls, model)
+    roof = {"bound": "hbm", "kernel": cls, "achieved": round(achieved, 1), "peak": hbm,
+            "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": traffic,
+            "traffic_unit": "DRAM bytes per call (dram__bytes_read.sum + dram__bytes_write.sum)",
+            "traffic_source": prov,
+            "algorithmic_bytes_per_call": int(model),
+            "share_of_step": round(dom["ms"] / sum(v["ms"] for v in per_k.values()), 3),
+            "note": "a call = feature pass + selector + the chosen kernel and its conversions, "
+                    "one CUDA graph launch; CUDA events on the launch stream"}
+    classes = {}
+    for k, v in sorted(per_k.items(), key=lambda kv: -kv[1]["ms"]):
+        t_call = v["ms"] / v["n"]
+        classes[f"{k[0]}|{KNAMES[k[1]]}"] = {
+            "calls": v["n"] // steps, "ms_per_step": round(v["ms"] / steps, 4), "us_per_call": round(t_call * 1e3, 1),
+            "GBs": round(v["bytes"] / v["n"] / (t_call * 1e-3) / 1e9, 1),
+            "frac": round(v["bytes"] / v["n"] / (t_call * 1e-3) / 1e9 / hbm, 4)}
+
+    # end to end through the public API with pinned host buffers
+    h2d, d2h = W.e2e_setup(torch)
+    for _ in range(2):
+        W.e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, steps // 2)
+    e0.record()
+    for _ in range(e2e_steps):
+        W.e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_val = step_bytes * world / (e2e_ms * 1e-3) / 1e9
+    return {"value": round(value, 2), "ms_per_step": round(ms, 4), "step_work_bytes": int(step_bytes),
+            "frac_of_hbm_roofline": round(value / world / hbm, 4), "roofline": roof,
+            "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "ms_per_step": round(e2e_ms, 4),
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(steps * sum(c["launches"] for c in W.calls)),
+            "clocks": clk, "wall_s_timed": round(wall, 3), "classes": classes}
+
+
+def density_regret(W, torch, dev, reps=3):
+    """Every forced candidate against the selector on each product of the
+    stencil step (L2 flushed before every timing): the selected kernel, the
+    fastest candidate, and regret = selector-driven time / fastest time."""
+    hbm, _ = peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for c in W.calls:
+        times = {}
+        for kk in ["auto"] + list(KNAMES):
+            W.call(c, kk)
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                W.call(c, kk)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                if kk != "auto" and ts[-1] > 20 * times.get("auto", 1e9):
+                    break  # far off the pace: one timing is enough
+            times[kk] = float(np.median(ts))
+        best = min(KNAMES, key=lambda q: times[q])
+        rows.append({"call": c["kind"], "nnz_x": c["nnz_x"], "nnz_s": c["nnz_s"], "selected": KNAMES[c["kid"]],
+                     "auto_us": round(times["auto"] * 1e3, 1), "best": best,
+                     "best_us": round(times[best] * 1e3, 1), "regret": round(times["auto"] / times[best], 3),
+                     "auto_GBs": round(c["bytes"] / (times["auto"] * 1e-3) / 1e9, 1),
+                     "auto_frac": round(c["bytes"] / (times["auto"] * 1e-3) / 1e9 / hbm, 4),
+                     "forced_us": {q: round(times[q] * 1e3, 1) for q in KNAMES}})
+    return rows
 
 
 def bench_batched(asv, torch, dev, reps=3):
@@ -366,6 +762,7 @@ def bench_batched(asv, torch, dev, reps=3):
            "entries": int(xptr[-1]), "multiply_adds": nnz_s, "tune": list(tune),
            "batched_ms": round(t_b, 3), "looped_ms": round(t_l, 3), "speedup_vs_looped": round(t_l / t_b, 2),
            "looped_fixed_ms": fixed, "speedup_vs_best_fixed_looped": round(min(fixed.values()) / t_b, 2),
+           "looped_selector_regret": round(t_l / min(fixed.values()), 3),
            "batched_GBs": round((abytes + ybytes + xptr[-1] * 8) / (t_b * 1e-3) / 1e9, 1),
            "batched_Gmadds": round(nnz_s / (t_b * 1e-3) / 1e9, 1),
            "max_rel_diff_vs_looped": diff}
@@ -504,7 +901,7 @@ def bench_backward(asv, torch, dev, reps=5):
     return out
 
 
-def ncu_case(case, kernel):
+def ncu_case(case, kernel, fmt="dense"):
     """Small inputs (larger than L2, a few GB at most) for one-kernel profiles."""
     import torch
 
@@ -522,10 +919,20 @@ def ncu_case(case, kernel):
             m = n = 1 << 20
             v = np.ones(len(c), np.float32)
         A = asv.Matrix(m, n, *[torch.from_numpy(a).to(dev) for a in (rp, c, v)])
-        x = torch.from_numpy(gen.uniform(n, -1, 1, 1, 0, np.float32)).to(dev)
+        # --fmt dense: x dense, y dense; --fmt list: x as a list of every
+        # column, y as the structural list (the two forms of the stencil step)
+        idx = np.arange(n, dtype=np.int32)
+        x = gen.uniform(n, -1, 1, 1, 0, np.float32)
+        xd = torch.from_numpy(x).to(dev)
+        it, cnt = torch.from_numpy(idx).to(dev), torch.tensor([n], dtype=torch.int64, device=dev)
         y = torch.empty(m, dtype=torch.float32, device=dev)
+        yidx = torch.empty(m, dtype=torch.int32, device=dev)
+        nnz_y = torch.zeros(1, dtype=torch.int64, device=dev)
         for _ in range(3):
-            A.spmv(x, y, kernel=kernel)
+            if fmt == "list":
+                asv.asv_spmspv(A.handle, cnt, it, xd, None, asv.ASV_OUT_SPARSE, None, yidx, y, nnz_y, m, kernel)
+            else:
+                asv.asv_spmspv(A.handle, None, None, None, xd, asv.ASV_OUT_DENSE, y, kernel=kernel)
     elif case == "rmat20_bfs":
         # the densest BFS frontier of one root, Boolean, list in and list out (a BFS level product)
         rp, c = gen.rmat(20, 16, gen.config_seed(2))
@@ -563,7 +970,7 @@ def ncu_case(case, kernel):
         for _ in range(3):
             A.backward(X, dY)
     torch.cuda.synchronize()
-    print("ok", case, kernel)
+    print("ok", case, kernel, fmt)
 
 
 def density_sweep(which, out_path, reps=5):
@@ -636,51 +1043,60 @@ def density_sweep(which, out_path, reps=5):
     out.close()
 
 
-def run_cpu_oracle(W, max_bfs_calls, reps=1):
-    """Times the oracle on a bounded sample; returns (bytes, seconds, sample text)."""
+def cpu_baseline(W):
+    """The oracle on the host cores: its multi-threaded form on every core
+    (the line's figure) and its serial form on one."""
     import oracle
-    n = W.n
-    fr_host = W.frontiers_host if hasattr(W, "frontiers_host") else None
-    xs = W.pr_x.astype(np.float64)
-    t_tot, b_tot = 0.0, 0.0
-    for _ in range(reps):
-        t = time.perf_counter()
-        oracle.csr_pull(W.rowptr, W.col, None, xs)
-        t_tot += time.perf_counter() - t
-        b_tot += W.calls[-1]["bytes"]
-        for i in range(min(max_bfs_calls, len(W.calls) - 1)):
-            xb = np.zeros(n, np.uint8)
-            xb[fr_host[i]] = 1
-            t = time.perf_counter()
-            oracle.bool_pull(W.rowptr, W.col, xb)
-            t_tot += time.perf_counter() - t
-            b_tot += W.calls[i]["bytes"]
-    sample = f"1 PageRank step + first {min(max_bfs_calls, len(W.calls) - 1)} BFS level products, serial FP64 C oracle"
-    return b_tot, t_tot, sample
+    out = {"kind": "oracle", "unit": "GB/s"}
+    try:
+        threads = oracle.par_threads()
+        W.oracle_step(par=True)  # warm (page-in, thread pool)
+        b, t = W.oracle_step(par=True)
+        out.update({"value": round(b / t / 1e9, 4), "cores": threads, "seconds": round(t, 3),
+                    "sample": f"one whole step of {W.name} ({len(W.calls)} products), multi-threaded FP64 C oracle "
+                              f"(row-parallel pull, column-parallel push) on {threads} threads"})
+    except (OSError, subprocess.CalledProcessError) as e:
+        out["parallel_unavailable"] = str(e)[:200]
+    b, t = W.oracle_step(par=False)
+    serial = {"value": round(b / t / 1e9, 4), "cores": 1, "seconds": round(t, 3),
+              "sample": f"one whole step of {W.name}, serial FP64 C oracle"}
+    if "value" not in out:
+        out.update(serial)
+    else:
+        out["serial"] = serial
+    return out
 
 
 # ------------------------------------------------------------------ main
+def make_workload(name):
+    if name in ("stencil256", Stencil256.name):
+        return Stencil256()
+    if name in ("rmat22", Rmat22.name):
+        return Rmat22()
+    raise SystemExit(f"unknown workload {name}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22")
+    ap.add_argument("--workload", default="stencil256", help="stencil256 (default) or rmat22")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched and backward sections")
+    ap.add_argument("--no-extra", action="store_true", help="skip every section but the headline step")
     ap.add_argument("--ncu-case", default=None,
                     help="profiling aid: run one small case (stencil128, rmat20, rmat20_bfs, zipf_batched, "
-                         "bernoulli_backward) "
-                         "with --kernel three times and exit")
+                         "bernoulli_backward) with --kernel (and --fmt) three times and exit")
     ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--fmt", default="dense", choices=["dense", "list"])
     ap.add_argument("--sweep", default=None,
                     help="x-density sweep of every candidate and the selector on stencil256 or rmat22; "
                          "writes JSON lines to --sweep-out")
     ap.add_argument("--sweep-out", default="sweep.jsonl")
     ap.add_argument("--direct", action="store_true",
                     help="profiling aid: run the recorded kernel choices as direct launches instead of the "
-                         "selector graph (ncu cannot profile kernels inside conditional graphs)")
+                         "selector graph (the profiler cannot see kernels inside conditional graph nodes)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -690,7 +1106,7 @@ def main():
     if args.impl == "reference":
         return main_reference(args, rank, world)
     if args.ncu_case:
-        return ncu_case(args.ncu_case, args.kernel)
+        return ncu_case(args.ncu_case, args.kernel, args.fmt)
     if args.sweep:
         return density_sweep(args.sweep, args.sweep_out)
 
@@ -706,110 +1122,37 @@ def main():
     ge.build()
     import paper_2006_16767_gb300 as asv
 
-    W = Rmat22()
+    W = make_workload(args.workload)
     W.setup_gpu(asv, torch, dev)
-    W.frontiers_host = [f.cpu().numpy() for f in W.frontiers]
-    hbm, peak_kind = peaks()
-
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    ncalls = len(W.calls)
-    for _ in range(max(3, args.warmup)):
-        flush.zero_()
-        W.run_step(direct=args.direct)
-    torch.cuda.synchronize()
-
-    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    call_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ncalls)]
-               for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    t_wall = time.perf_counter()
-    for s in range(args.steps):
-        flush.zero_()
-        torch.cuda.nvtx.range_push("timed_step")
-        step_ev[s][0].record()
-        W.run_step(call_ev[s], direct=args.direct)
-        step_ev[s][1].record()
-        torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall
-    if dist:
-        dist.barrier()
-    time.sleep(0.2)
-    clk = clocks.stop()
-
-    step_ms = [a.elapsed_time(b) for a, b in step_ev]
-    ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    step_bytes = sum(c["bytes"] for c in W.calls)
-    value = step_bytes * world / (ms * 1e-3) / 1e9
-
-    # per-kernel durations from the per-call events (same stream as the launches)
-    per_k = {}
-    for s in range(args.steps):
-        for i, c in enumerate(W.calls):
-            d = call_ev[s][i][0].elapsed_time(call_ev[s][i][1])
-            e = per_k.setdefault((c["kind"], c["kid"]), {"ms": 0.0, "bytes": 0.0, "n": 0})
-            e["ms"] += d
-            e["bytes"] += c["kbytes"]
-            e["n"] += 1
-    dom_key = max(per_k, key=lambda k: per_k[k]["ms"])
-    dom = per_k[dom_key]
-    achieved = (dom["bytes"] / dom["n"]) / ((dom["ms"] / dom["n"]) * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": f"{dom_key[0]}:{asv.KERNELS[dom_key[1]]}", "achieved": round(achieved, 1),
-            "peak": hbm, "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
-            "frac": round(achieved / hbm, 4),
-            "traffic": NCU_DRAM_BYTES_PER_CALL.get(f"{dom_key[0]}:{asv.KERNELS[dom_key[1]]}"),
-            "traffic_unit": "bytes per call (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "algorithmic_bytes_per_call": int(dom["bytes"] / dom["n"]),
-            "share_of_step": round(dom["ms"] / sum(v["ms"] for v in per_k.values()), 3),
-            "note": "duration = auto call (feature pass + selector + kernel), CUDA events on the launch stream"}
-    class_ms = {f"{k[0]}:{asv.KERNELS[k[1]]}": round(v["ms"] / args.steps, 4)
-                for k, v in sorted(per_k.items(), key=lambda kv: -kv[1]["ms"])}
-
-    # end to end through the public API with pinned host buffers
-    h2d, d2h = W.e2e_setup(torch)
-    for _ in range(2):
-        W.e2e_step()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(3, args.steps // 2)
-    e0.record()
-    for _ in range(e2e_steps):
-        W.e2e_step()
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    e2e_val = step_bytes * world / (e2e_ms * 1e-3) / 1e9
-
-    out = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-           "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "u8 (OR,AND) + f32", "data": "synthetic", "config": W.config(),
-           "frac_of_hbm_roofline": round(value / world / hbm, 4),
-           "roofline": roof,
-           "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "ms_per_step": round(e2e_ms, 4),
-                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-           "gpu_launches": int(args.steps * sum(c["launches"] for c in W.calls)),
-           "clocks": clk, "wall_s_timed": round(wall, 3),
-           "selected": {asv.KERNELS[k[1]] + ":" + k[0]: v["n"] // args.steps for k, v in per_k.items()},
-           "class_ms_per_step": class_ms}
+    res = measure(W, torch, dev, args.steps, args.warmup, direct=args.direct, world=world, dist=dist,
+                  clocks_index=local)
+    out = {"metric": METRIC, "value": res["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": W.dtype, "data": "synthetic", "config": W.config(),
+           "frac_of_hbm_roofline": res["frac_of_hbm_roofline"], "roofline": res["roofline"], "e2e": res["e2e"],
+           "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "wall_s_timed": res["wall_s_timed"],
+           "step_work_bytes": res["step_work_bytes"], "classes": res["classes"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(W)
     if not args.no_extra:
-        out["bfs"] = bench_bfs(asv, torch, dev, W)
-        out["create"] = bench_create(asv, torch, dev, W)
-        out["pagerank_incremental"] = bench_pagerank(asv, torch, dev, W)
+        if isinstance(W, Stencil256):
+            out["density_regret"] = density_regret(W, torch, dev)
+            del W
+            torch.cuda.empty_cache()
+            R = Rmat22()
+            R.setup_gpu(asv, torch, dev)
+            r = measure(R, torch, dev, max(3, args.steps // 2), args.warmup)
+            r.pop("clocks", None)
+            out["rmat22"] = dict(config=R.config(), **r)
+        else:
+            R = W
+        out["bfs"] = bench_bfs(asv, torch, dev, R)
+        out["create"] = bench_create(asv, torch, dev, R)
+        out["pagerank_incremental"] = bench_pagerank(asv, torch, dev, R)
+        del R
+        torch.cuda.empty_cache()
         out["batched"] = bench_batched(asv, torch, dev)
         out["backward"] = bench_backward(asv, torch, dev)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        b, t, sample = run_cpu_oracle(W, max_bfs_calls=24)
-        out["cpu_baseline"] = {"value": round(b / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                               "sample": sample, "seconds": round(t, 2)}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -817,44 +1160,50 @@ def main():
 
 
 def main_reference(args, rank, world):
-    """The oracle (CPU, serial) on the same workload, metric and unit."""
+    """The oracle (CPU; its multi-threaded form on every host core) on the
+    same workload, metric and unit; rank 0 only."""
     if rank != 0:
         return
     import oracle
-    import gen
-    W = Rmat22()
-    # frontiers from the oracle's own queue BFS, the same roots
-    fronts = []
-    for r in W.roots:
-        fronts += oracle.frontiers(W.n, W.rowptr, W.col, r)
-    W.frontiers_host = fronts
-    colptr, _, _ = oracle.csr_to_csc(W.m, W.n, W.rowptr, W.col)
-    W.calls = []
-    for f in fronts:
-        vf = oracle.vector_features(W.n, W.nnz, colptr, f)
-        xb = np.zeros(W.n, np.uint8)
-        xb[f] = 1
-        nnz_y = int(oracle.bool_pull(W.rowptr, W.col, xb).sum())
-        W.calls.append(dict(kind="bfs", kid=0, nnz_x=len(f), nnz_s=vf["nnz_s"],
-                            bytes=work_bytes(W.m, W.n, W.nnz, len(f), vf["nnz_s"], nnz_y, 0, 0, 0, True, True)))
-    W.calls.append(dict(kind="pagerank", kid=0, nnz_x=W.n, nnz_s=W.nnz,
-                        bytes=work_bytes(W.m, W.n, W.nnz, W.n, W.nnz, W.m, 4, 4, 4, False, False)))
-    per_step_calls = 8
+    W = make_workload(args.workload)
+    if isinstance(W, Stencil256):
+        W.plan_calls_host()
+    else:
+        fronts = []
+        for r in W.roots:
+            fronts += oracle.frontiers(W.n, W.rowptr, W.col, r)
+        W.frontiers_host = fronts
+        colptr, _, _ = oracle.csr_to_csc(W.m, W.n, W.rowptr, W.col)
+        W.calls = []
+        for f in fronts:
+            vf = oracle.vector_features(W.n, W.nnz, colptr, f)
+            xb = np.zeros(W.n, np.uint8)
+            xb[f] = 1
+            nnz_y = int(oracle.bool_pull(W.rowptr, W.col, xb).sum())
+            W.calls.append(dict(kind="bfs", nnz_x=len(f), nnz_s=vf["nnz_s"],
+                                bytes=work_bytes(W.m, W.n, W.nnz, len(f), vf["nnz_s"], nnz_y, 0, 0, 0, True, True)))
+        W.calls.append(dict(kind="pagerank", nnz_x=W.n, nnz_s=W.nnz,
+                            bytes=work_bytes(W.m, W.n, W.nnz, W.n, W.nnz, W.m, 4, 4, 4, False, False)))
+    try:
+        par, threads = True, oracle.par_threads()
+    except (OSError, subprocess.CalledProcessError):
+        par, threads = False, 1
     for _ in range(args.warmup):
-        run_cpu_oracle(W, max_bfs_calls=2)
+        W.oracle_step(par=par)
     tot_b, tot_t = 0.0, 0.0
     for _ in range(args.steps):
-        b, t, sample = run_cpu_oracle(W, max_bfs_calls=per_step_calls)
+        b, t = W.oracle_step(par=par)
         tot_b += b
         tot_t += t
     ms = tot_t / args.steps * 1e3
     val = tot_b / tot_t / 1e9
+    form = f"multi-threaded FP64 C oracle on {threads} threads" if par else "serial FP64 C oracle"
     out = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GB/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle)", "data": "synthetic",
-           "config": {"workload": W.name, "n": W.n, "nnz": W.nnz, "roots": W.nroots},
-           "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(val, 4), "unit": "GB/s",
-                            "sample": f"per step: {sample}"},
+           "config": W.config(),
+           "cpu_baseline": {"kind": "oracle", "cores": threads, "value": round(val, 4), "unit": "GB/s",
+                            "sample": f"per step: one whole step of {W.name} ({len(W.calls)} products), {form}"},
            "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -22,7 +22,7 @@
  *  - Every function returns an asv_status; nothing throws across the ABI.
  *    Argument errors are detected on the host before anything is enqueued.
  *    Errors that only the device can see (capacity overflow, bounded-wait
- *    timeouts, checked-mode bounds) are latched in a per-handle device status
+ *    timeouts, an over-long input list) are latched in a per-handle device status
  *    word and returned by the next call that synchronises (asv_get_status,
  *    asv_select, asv_matrix_features).
  *  - Value dtype is fixed per matrix handle; x and y use the same dtype:
@@ -51,7 +51,7 @@ enum {
     ASV_ERR_CAPACITY = 4,      /* sparse output larger than y_cap (the count is still written) */
     ASV_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                          */
     ASV_ERR_CUDA = 6,          /* a CUDA runtime call failed (see asv_last_cuda_error)        */
-    ASV_ERR_CHECKED = 7,       /* checked mode: a device bounds check failed                  */
+                               /* 7 is reserved (no checked build exists)                    */
     ASV_ERR_NOMEM = 8,         /* device allocation failed                                    */
     ASV_ERR_UNSUPPORTED = 9    /* kernel/dtype/output combination not available               */
 };
@@ -255,11 +255,14 @@ asv_status asv_bfs(asv_matrix A, int32_t source, int32_t* d_level, int32_t kerne
                    void* stream);
 
 /* Run the feature pass and the selector for this x (same x arguments as
- * asv_spmspv) and return the chosen kernel id and the vector features
- * (Sec. V-A Table 1, Sec. VI-B cascaded trees). Synchronises `stream`. */
+ * asv_spmspv) and an output in `out_mode` (the trees are per call format:
+ * x dense or a list, y dense or the structural list), and return the kernel
+ * an ASV_K_AUTO call with these arguments would run and the vector features
+ * (Sec. V-A Table 1, Sec. VI-B cascaded trees). Nothing is written to any
+ * output. Synchronises `stream`. */
 asv_status asv_select(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx,
-                      const void* d_xval, const void* d_x_dense, int32_t* h_kernel,
-                      asv_vfeat* h_feat, void* stream);
+                      const void* d_xval, const void* d_x_dense, int32_t out_mode,
+                      int32_t* h_kernel, asv_vfeat* h_feat, void* stream);
 
 /* The kernel id chosen by the most recent ASV_K_AUTO call on this handle
  * (synchronises `stream`). */
@@ -358,8 +361,14 @@ asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t n_nodes,
  * fixed 4 MB device array inside the library, held by every GPU that loads
  * the library until the process exits. Limit: m + nnz <= 2^29 (2^18 tiles of
  * 2048 items); larger sizes return ASV_ERR_CAPACITY before anything runs.
- * The first call on a device looks up the array's device address (once per
- * device), so make that first call before any stream capture. All calls
+ * The arrays must be a valid CSR -- rowptr[0] = 0, rowptr non-decreasing,
+ * rowptr[m] = nnz, 0 <= colidx[k] < n -- and are NOT checked (no handle, no
+ * validation pass): the kernel only keeps every memory access inside the
+ * stated array sizes, so malformed arrays give an unspecified y, never an
+ * access outside them. The first call on a device looks up the array's device
+ * address (once per device; the address is kept, so do not use this entry
+ * point on a device after cudaDeviceReset), so make that first call before
+ * any stream capture. All calls
  * share the array: calls whose work overlaps on the GPU (different streams,
  * or different host threads, without ordering) race on it. Each call
  * rewrites every scratch entry it reads, so nothing needs clearing between
@@ -367,6 +376,29 @@ asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t n_nodes,
 asv_status asv_spmv_noalloc_f32(int64_t m, int64_t n, int64_t nnz, const int32_t* d_rowptr,
                                 const int32_t* d_colidx, const float* d_val, const float* d_x,
                                 float* d_y, void* stream);
+
+/* ---------------------------------------------------------------- testing hooks */
+
+/* Default number of polls of a bounded device-side wait. */
+#define ASV_WAIT_LIMIT_DEFAULT (1u << 24)
+
+/* Failure injection for tests, on the host side of the device's bounded
+ * waits (no GPU fault, trap or hang is ever provoked). Sets how many times
+ * the first bounded wait of the handle's TMA-staged kernels (the one-row-per-
+ * thread pull waiting for its bulk copies of a warp's span) polls its
+ * mbarrier before it gives up and latches ASV_ERR_TIMEOUT; the warp then
+ * waits for its copies again under the default bound, so none is left in
+ * flight, and leaves its rows unwritten. polls = 0 makes every such wait
+ * give up at once; ASV_WAIT_LIMIT_DEFAULT restores the default. The status
+ * is read (and cleared) by asv_get_status. */
+asv_status asv_debug_set_wait_limit(asv_matrix A, uint32_t polls);
+
+/* Failure injection for tests: with countdown k > 0, the k-th device
+ * allocation of a handle's arrays and workspaces (asv_matrix_create_csr,
+ * asv_matrix_transpose_view) from now on fails as if the device were out of
+ * memory; the creating call then releases whatever it had allocated and
+ * returns ASV_ERR_NOMEM. 0 disarms it. Process-wide. */
+void asv_debug_fail_alloc(int32_t countdown);
 
 /* ---------------------------------------------------------------- status */
 

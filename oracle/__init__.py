@@ -21,6 +21,9 @@ Function -> passage:
   i32_pull           integer (+, x) semiring, 32-bit wrap-around
   pagerank_step      PageRank application, Sec. VII (formula is a reading)
   grad_values        dA on A's pattern, dA_k = dy_row(k) * x_col(k)
+  csr_pull_par, spmspv_rowmajor_par, csc_push_par
+                     the same three products with their outer loop on all
+                     host cores (oracle_omp.c), for the CPU baseline only
 
 The kernel selector has no oracle (parity unpinned): the paper prints no
 decision rules or thresholds (Sec. V-B, VI-B).
@@ -97,6 +100,44 @@ def _get():
     return _lib
 
 
+_SRC_PAR = os.path.join(_HERE, "oracle_omp.c")
+_SO_PAR = os.path.join(_HERE, "liboracle_omp.so")
+_lib_par = None
+
+
+def build_par(force: bool = False) -> str:
+    """Compile oracle_omp.c (the multi-threaded CPU-baseline forms) into
+    liboracle_omp.so with OpenMP."""
+    if not force and _elf_matches_host(_SO_PAR) and os.path.getmtime(_SO_PAR) >= os.path.getmtime(_SRC_PAR):
+        return _SO_PAR
+    tmp = _SO_PAR + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
+                    "-shared", "-fPIC", _SRC_PAR, "-o", tmp, "-lm"], check=True, capture_output=True)
+    os.replace(tmp, _SO_PAR)
+    return _SO_PAR
+
+
+def _get_par():
+    global _lib_par
+    with _lock:
+        if _lib_par is None:
+            build_par()
+            lib = ctypes.CDLL(_SO_PAR)
+            vp, i64 = ctypes.c_void_p, ctypes.c_int64
+            lib.oracle_par_threads.argtypes = []
+            lib.oracle_par_threads.restype = ctypes.c_int
+            lib.oracle_csr_pull_par.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+            lib.oracle_spmspv_rowmajor_par.argtypes = [i64, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp]
+            lib.oracle_csc_push_par.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp, vp]
+            _lib_par = lib
+    return _lib_par
+
+
+def par_threads() -> int:
+    """Threads the multi-threaded forms use (OMP_NUM_THREADS or all cores)."""
+    return int(_get_par().oracle_par_threads())
+
+
 def _p(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
@@ -129,6 +170,39 @@ def spmspv_rowmajor(n, rowptr, col, val, xidx, xval):
     _get().oracle_spmspv_rowmajor(m, n, _p(rowptr), _p(col), _p(val), len(xidx), _p(xidx),
                                   _p(xval), _p(y), _p(s), _p(hit))
     return y, s, hit
+
+
+def csr_pull_par(rowptr, col, val, x):
+    """csr_pull on all host cores (rows divided among threads; identical result)."""
+    rowptr, col, val, x = _i32(rowptr), _i32(col), _f64(val), _f64(x)
+    m = len(rowptr) - 1
+    y = np.empty(m, np.float64)
+    s = np.empty(m, np.float64)
+    _get_par().oracle_csr_pull_par(m, _p(rowptr), _p(col), _p(val), _p(x), _p(y), _p(s))
+    return y, s
+
+
+def spmspv_rowmajor_par(n, rowptr, col, val, xidx, xval):
+    """spmspv_rowmajor on all host cores (rows divided among threads)."""
+    rowptr, col, val, xidx, xval = _i32(rowptr), _i32(col), _f64(val), _i32(xidx), _f64(xval)
+    m = len(rowptr) - 1
+    y = np.empty(m, np.float64)
+    s = np.empty(m, np.float64)
+    hit = np.empty(m, np.uint8)
+    _get_par().oracle_spmspv_rowmajor_par(m, n, _p(rowptr), _p(col), _p(val), len(xidx), _p(xidx),
+                                          _p(xval), _p(y), _p(s), _p(hit))
+    return y, s, hit
+
+
+def csc_push_par(m, colptr, rowidx, val, xidx, xval):
+    """csc_push on all host cores (listed columns divided among threads,
+    atomic additions into y)."""
+    colptr, rowidx, val, xidx, xval = _i32(colptr), _i32(rowidx), _f64(val), _i32(xidx), _f64(xval)
+    y = np.empty(m, np.float64)
+    touched = np.empty(m, np.uint8)
+    _get_par().oracle_csc_push_par(m, _p(colptr), _p(rowidx), _p(val), len(xidx), _p(xidx), _p(xval),
+                                   _p(y), _p(touched))
+    return y, touched
 
 
 def csc_push(m, colptr, rowidx, val, xidx, xval):

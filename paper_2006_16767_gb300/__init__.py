@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libasv.so")
 
 # status codes and enums (mirrors include/asv.h)
 ASV_OK, ASV_ERR_ARG, ASV_ERR_NONCANONICAL, ASV_ERR_OVERFLOW, ASV_ERR_CAPACITY = 0, 1, 2, 3, 4
-ASV_ERR_TIMEOUT, ASV_ERR_CUDA, ASV_ERR_CHECKED, ASV_ERR_NOMEM, ASV_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
+ASV_ERR_TIMEOUT, ASV_ERR_CUDA, ASV_ERR_NOMEM, ASV_ERR_UNSUPPORTED = 5, 6, 8, 9  # 7 is reserved
 ASV_F32, ASV_F64, ASV_BOOL, ASV_I32 = 0, 1, 2, 3
 ASV_OUT_DENSE, ASV_OUT_SPARSE = 0, 1
 ASV_BORROW, ASV_COPY, ASV_VALIDATE = 0, 1, 2
@@ -98,7 +98,7 @@ def lib():
             L.asv_spmspv_masked.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, i32, vp]
             L.asv_bfs.argtypes = [vp, i32, vp, i32, P(i32), vp]
             L.asv_pagerank.argtypes = [vp, ctypes.c_double, ctypes.c_double, i32, vp, i32, P(i32), vp]
-            L.asv_select.argtypes = [vp, vp, vp, vp, vp, P(i32), P(_VFeat), vp]
+            L.asv_select.argtypes = [vp, vp, vp, vp, vp, i32, P(i32), P(_VFeat), vp]
             L.asv_last_kernel.argtypes = [vp, P(i32), vp]
             L.asv_compact.argtypes = [vp, vp, vp, vp, vp, vp]
             L.asv_set_trees.argtypes = [vp, vp, i32, vp, vp]
@@ -107,6 +107,10 @@ def lib():
             L.asv_status_string.argtypes = [i32]
             L.asv_status_string.restype = ctypes.c_char_p
             L.asv_version.argtypes = []
+            L.asv_debug_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
+            L.asv_debug_set_wait_limit.restype = i32
+            L.asv_debug_fail_alloc.argtypes = [i32]
+            L.asv_debug_fail_alloc.restype = None
             for name in ("asv_matrix_create_csr", "asv_matrix_destroy", "asv_matrix_features",
                          "asv_matrix_arrays", "asv_matrix_copy_csc", "asv_spmv", "asv_spmspv", "asv_select", "asv_last_kernel",
                          "asv_compact", "asv_set_trees", "asv_get_status", "asv_last_cuda_error",
@@ -272,10 +276,10 @@ def asv_pagerank(h, damping, eps, max_iter, rank, kernel="auto", stream=None, wa
     return iters.value if wait else None
 
 
-def asv_select(h, nnz_x=None, xidx=None, xval=None, x_dense=None, stream=None):
+def asv_select(h, nnz_x=None, xidx=None, xval=None, x_dense=None, out_mode=ASV_OUT_DENSE, stream=None):
     k = ctypes.c_int32()
     f = _VFeat()
-    _check(lib().asv_select(h, _ptr(nnz_x), _ptr(xidx), _ptr(xval), _ptr(x_dense), ctypes.byref(k),
+    _check(lib().asv_select(h, _ptr(nnz_x), _ptr(xidx), _ptr(xval), _ptr(x_dense), int(out_mode), ctypes.byref(k),
                             ctypes.byref(f), _stream(stream)), "asv_select")
     return k.value, {"nnz_x": f.nnz_x, "nnz_s": f.nnz_s, "x_sparsity": f.x_sparsity,
                      "m_sparsity": f.m_sparsity}
@@ -307,6 +311,21 @@ def asv_set_trees(h, nodes, roots, stream=None):
 
 def asv_get_status(h, stream=None) -> int:
     return int(lib().asv_get_status(h, _stream(stream)))
+
+
+ASV_WAIT_LIMIT_DEFAULT = 1 << 24
+
+
+def asv_debug_set_wait_limit(h, polls):
+    """Testing hook: polls of the first bounded TMA wait of the handle's
+    staged kernels (0 makes it give up at once and latch ASV_ERR_TIMEOUT)."""
+    _check(lib().asv_debug_set_wait_limit(h, int(polls)), "asv_debug_set_wait_limit")
+
+
+def asv_debug_fail_alloc(countdown):
+    """Testing hook: the countdown-th handle allocation from now on fails
+    with ASV_ERR_NOMEM (0 disarms)."""
+    lib().asv_debug_fail_alloc(int(countdown))
 
 
 def asv_version() -> int:
@@ -420,11 +439,12 @@ class Matrix:
         depth = asv_bfs(self.handle, source, level, kernel, stream, wait)
         return level, depth
 
-    def select(self, xidx=None, xval=None, nnz_x=None, x_dense=None, stream=None):
+    def select(self, xidx=None, xval=None, nnz_x=None, x_dense=None, sparse_out=False, stream=None):
         dev = (x_dense if x_dense is not None else xidx).device
         if x_dense is None and nnz_x is None:
             nnz_x = torch.tensor([xidx.numel()], dtype=torch.int64, device=dev)
-        return asv_select(self.handle, nnz_x, xidx, xval, x_dense, stream)
+        return asv_select(self.handle, nnz_x, xidx, xval, x_dense, ASV_OUT_SPARSE if sparse_out else ASV_OUT_DENSE,
+                          stream)
 
     def update_values(self, val=None, stream=None):
         asv_matrix_update_values(self.handle, val, stream)

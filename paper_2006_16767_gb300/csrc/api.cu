@@ -4,6 +4,7 @@
 // -> SWITCH conditional node of a CUDA graph whose branches are the
 // candidates (with their own format conversion), so the chosen kernel runs
 // with no host round-trip.
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
@@ -38,8 +39,16 @@ const char* kernel_name(int k) {
 }
 }  // namespace asv
 
+// Testing hook (asv_debug_fail_alloc): when positive, the allocation that
+// brings the countdown to zero fails as if the device were out of memory.
+static std::atomic<int32_t> g_fail_alloc{0};
+
 static asv_status dalloc(asv_matrix_s* H, void** p, size_t bytes, bool zero) {
     if (bytes < 16) bytes = 16;
+    if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+        *p = nullptr;
+        return ASV_ERR_NOMEM;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         g_last_cuda = (int32_t)e;
@@ -358,17 +367,19 @@ extern "C" asv_status asv_matrix_update_values(asv_matrix A, const void* d_val, 
 
 // ---------------------------------------------------------------- dispatch
 // One candidate, including the vector-format conversion it needs: pull
-// kernels on a sparse x first scatter it into the zero-invariant dense and
-// bitmap workspaces (and clear them afterwards); push kernels on a dense x
-// first compact its bitmap into an ascending list.
+// kernels on a sparse x first scatter it into the zero-invariant dense (and,
+// when the kernel reads it, bitmap) workspaces and clear them afterwards;
+// push kernels on a dense x first compact its bitmap into an ascending list.
 static void enqueue_candidate(asv_matrix_s* H, int k, int x_sparse, int om, cudaStream_t s) {
     if (k < ASV_K_PUSH_THREAD_ATOM) {
         const bool masked = k >= ASV_K_MPULL_THREAD;
         const int dist = k % 3;
-        if (x_sparse) launch_x_scatter(H, true, s);
+        // the bitmap serves validation, output flags and Boolean terms
+        const bool bits = masked || om == ASV_OUT_SPARSE || H->dtype == ASV_BOOL;
+        if (x_sparse) launch_x_scatter(H, true, bits, s);
         launch_pull(H, dist, masked, om == ASV_OUT_SPARSE, nullptr, s);
         if (om == ASV_OUT_SPARSE) launch_finalize(H, false, om, s);
-        if (x_sparse) launch_x_scatter(H, false, s);
+        if (x_sparse) launch_x_scatter(H, false, bits, s);
     } else {
         const int q = k - ASV_K_PUSH_THREAD_ATOM;
         const int dist = q % 3, wb = q / 3;
@@ -731,12 +742,15 @@ extern "C" asv_status asv_spmv(asv_matrix A, const void* d_x, void* d_y, int32_t
 }
 
 extern "C" asv_status asv_select(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx, const void* d_xval,
-                                 const void* d_x_dense, int32_t* h_kernel, asv_vfeat* h_feat, void* stream) {
+                                 const void* d_x_dense, int32_t out_mode, int32_t* h_kernel, asv_vfeat* h_feat,
+                                 void* stream) {
     if (!A) return ASV_ERR_ARG;
+    if (out_mode != ASV_OUT_DENSE && out_mode != ASV_OUT_SPARSE) return ASV_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     DescInit di;
-    asv_status st = prepare_call(A, d_nnz_x, d_xidx, d_xval, d_x_dense, ASV_OUT_DENSE, A->ws.ywork, nullptr,
-                                 nullptr, nullptr, 0, di);
+    // no candidate runs: the output pointers only have to be valid, never written
+    asv_status st = prepare_call(A, d_nnz_x, d_xidx, d_xval, d_x_dense, out_mode, A->ws.ywork, A->ws.xlist_idx,
+                                 A->ws.ywork, (int64_t*)A->ws.hist, 0, di);
     if (st != ASV_OK) return st;
     launch_features(A, di, select_arg(A, 0ull), s);
     CallDesc hd;
@@ -941,6 +955,14 @@ extern "C" asv_status asv_get_status(asv_matrix A, void* stream) {
 
 extern "C" int32_t asv_last_cuda_error(void) { return g_last_cuda; }
 
+extern "C" asv_status asv_debug_set_wait_limit(asv_matrix A, uint32_t polls) {
+    if (!A) return ASV_ERR_ARG;
+    A->wait_limit = polls;
+    return ASV_OK;
+}
+
+extern "C" void asv_debug_fail_alloc(int32_t countdown) { g_fail_alloc.store(countdown > 0 ? countdown : 0); }
+
 extern "C" const char* asv_status_string(asv_status s) {
     switch (s) {
         case ASV_OK: return "ok";
@@ -950,7 +972,6 @@ extern "C" const char* asv_status_string(asv_status s) {
         case ASV_ERR_CAPACITY: return "sparse output exceeds y_cap";
         case ASV_ERR_TIMEOUT: return "bounded device wait timed out";
         case ASV_ERR_CUDA: return "CUDA runtime error";
-        case ASV_ERR_CHECKED: return "device bounds check failed";
         case ASV_ERR_NOMEM: return "out of device memory";
         case ASV_ERR_UNSUPPORTED: return "unsupported combination";
     }

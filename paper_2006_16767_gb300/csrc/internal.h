@@ -111,6 +111,8 @@ struct asv_matrix_s {
     int pull_lanes = 8;   // lanes per row of the (sub-)warp pull kernels
     int pull_unroll = 4;  // rows per lane group loaded together (2: more resident warps)
     bool pull_tma = true; // one-row-per-thread pull stages its spans with TMA bulk copies
+    // polls of the first bounded wait on a TMA copy (asv_debug_set_wait_limit)
+    uint32_t wait_limit = 1u << 24;
     // selector tables
     asv::TreeNode* d_trees = nullptr;
     int32_t* d_roots = nullptr;
@@ -217,7 +219,7 @@ struct FeatLaunch {
 };
 void feature_launch(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, FeatLaunch& fl);
 void launch_features(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, cudaStream_t s);
-void launch_x_scatter(asv_matrix_s* H, bool set, cudaStream_t s);
+void launch_x_scatter(asv_matrix_s* H, bool set, bool bits, cudaStream_t s);
 void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s);
 void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s);
 void launch_compact_public(asv_matrix_s* H, const void* x, int32_t* idx, void* val, int64_t* count,
@@ -233,9 +235,9 @@ struct PullIO {
 void launch_pull(asv_matrix_s* H, int dist, bool masked, bool sparse_out, const PullIO* direct,
                  cudaStream_t s);
 
-void launch_pull_bal_f32_raw(int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col, const float* val,
-                             const float* x, float* y, const int32_t* tile_row, int32_t* carry_row, double* carry_val,
-                             int64_t ntiles, cudaStream_t s);
+void launch_pull_bal_f32_raw(int64_t m, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                             const float* val, const float* x, float* y, const int32_t* tile_row, int32_t* carry_row,
+                             double* carry_val, int64_t ntiles, cudaStream_t s);
 void launch_partition_raw(const int32_t* rowptr, int64_t m, int64_t nnz, int64_t ntiles, int32_t* tile_row,
                           cudaStream_t s);
 

@@ -28,7 +28,9 @@ std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {nullptr};
 
 // Device address of the array on the current device (host code only sees a
-// stand-in symbol), looked up once per device.
+// stand-in symbol), looked up once per device and kept for the life of the
+// process: a cudaDeviceReset reloads the module and may move the array, so
+// this entry point must not be used on a device after it has been reset.
 cudaError_t scratch_address(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -67,7 +69,10 @@ extern "C" asv_status asv_spmv_noalloc_f32(int64_t m, int64_t n, int64_t nnz, co
     // every tile entry and carry used below is rewritten by this call, so
     // nothing left from an earlier call needs clearing
     asv::launch_partition_raw(d_rowptr, m, nnz, ntiles, tile_row, s);
-    asv::launch_pull_bal_f32_raw(m, nnz, d_rowptr, d_colidx, d_val, d_x, d_y, tile_row, carry_row, carry_val, ntiles, s);
+    // the arrays are not validated; the kernel's bounds checks keep every
+    // access inside them even when they are not a valid CSR
+    asv::launch_pull_bal_f32_raw(m, n, nnz, d_rowptr, d_colidx, d_val, d_x, d_y, tile_row, carry_row, carry_val, ntiles,
+                                 s);
     e = cudaGetLastError();
     return e == cudaSuccess ? ASV_OK : ASV_ERR_CUDA;
 }

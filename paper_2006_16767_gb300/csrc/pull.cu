@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
                                                                   const int32_t* __restrict__ rowptr,
                                                                   const int32_t* __restrict__ col,
                                                                   const T* __restrict__ val, PullArg a, void* ywork,
-                                                                  uint8_t* yflag, int32_t* status) {
+                                                                  uint8_t* yflag, int32_t* status,
+                                                                  uint32_t wait_limit) {
     using S = Sr<T>;
     constexpr bool kStageVals = !S::kPattern && !MASK;
     __shared__ __align__(16) int32_t s_col[kStageWarps][kStageCap];
@@ -137,9 +138,10 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
                     if (val != nullptr) sv[k - a0] = __ldg(val + k);
                 }
             }
-            if (nbulk > 0 && !mbar_wait(&s_bar[w], 0)) {
-                // the copy did not land within the limit: report, wait once
-                // more (bounded) so no copy is left in flight, and give up
+            if (nbulk > 0 && !mbar_wait(&s_bar[w], 0, wait_limit)) {
+                // the copy did not land within the limit: report, wait again
+                // under the default bound so no copy is left in flight when
+                // the warp leaves, and give up
                 latch_status(status, ASV_ERR_TIMEOUT);
                 mbar_wait(&s_bar[w], 0);
                 return;
@@ -282,11 +284,13 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
 // Stages a tile's products into shared memory. Column ids (and values) are
 // read with 128-bit loads over the 16-byte-aligned span covering [k0, k1);
 // every load of the thread's groups is issued before any of them is used.
-template <class T, bool MASK, bool SOUT, bool VEC>
+// With CHK (unvalidated caller arrays) a column id outside [0, ncols)
+// contributes nothing instead of gathering outside x.
+template <class T, bool MASK, bool SOUT, bool VEC, bool CHK = false>
 __device__ __forceinline__ void stage_products(const int32_t* __restrict__ col, const T* __restrict__ val,
                                                const T* __restrict__ x, const uint32_t* __restrict__ xbits,
                                                int64_t k0, int64_t k1, int64_t nnz, typename Sr<T>::Part* s_prod,
-                                               uint32_t* s_eff) {
+                                               uint32_t* s_eff, int64_t ncols = 0) {
     using S = Sr<T>;
     using P = typename S::Part;
     constexpr int MAXG = (kBalD / 4 + 1 + kBalB - 1) / kBalB;
@@ -335,7 +339,8 @@ __device__ __forceinline__ void stage_products(const int32_t* __restrict__ col, 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t k = base + q;
-            const bool in = gi < ngroups && k >= k0 && k < k1;
+            const bool in = gi < ngroups && k >= k0 && k < k1 &&
+                            (!CHK || (uint64_t)(uint32_t)c[j][q] < (uint64_t)ncols);
             if constexpr (S::kPattern) {
                 bitv[j][q] = in && bool_gather(x, xbits, c[j][q]);  // the term itself
                 eff[j][q] = bitv[j][q];
@@ -374,12 +379,17 @@ __device__ __forceinline__ void stage_products(const int32_t* __restrict__ col, 
     }
 }
 
-template <class T, bool MASK, bool SOUT, bool VEC>
+// CHK: the CSR arrays come from a caller who did not build a handle and were
+// never validated, so a tile whose bounds a malformed row-pointer array makes
+// inconsistent is skipped (it writes nothing), the merge never walks past
+// the tile's entries, and column ids outside [0, ncols) are dropped: every
+// access stays inside the arrays whatever their contents.
+template <class T, bool MASK, bool SOUT, bool VEC, bool CHK = false>
 __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, const int32_t* __restrict__ rowptr,
                                                     const int32_t* __restrict__ col, const T* __restrict__ val,
                                                     const int32_t* __restrict__ tile_row, PullArg a, void* ywork,
                                                     uint8_t* yflag, int32_t* carry_row,
-                                                    typename Sr<T>::Atom* carry_val) {
+                                                    typename Sr<T>::Atom* carry_val, int64_t ncols = 0) {
     using S = Sr<T>;
     using P = typename S::Part;
     constexpr int B = kBalB, IPT = kBalIPT, D = kBalD, NW = B / 32;
@@ -401,12 +411,19 @@ __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, cons
     const int32_t r0 = tile_row[t], r1 = tile_row[t + 1];
     const int64_t k0 = d0 - r0, k1 = d1 - r1;
     const int nrows = r1 - r0, nk = (int)(k1 - k0);
+    if (CHK && (nrows < 0 || nk < 0 || k0 < 0 || k1 > nnz)) {  // the same verdict in every thread
+        if (threadIdx.x == 0) {
+            carry_row[t] = -1;
+            carry_val[t] = S::to_atom(T(0));
+        }
+        return;
+    }
 
     for (int i = threadIdx.x; i < nrows; i += B) s_end[i] = __ldg(rowptr + r0 + 1 + i);
     if (SOUT)
         for (int i = threadIdx.x; i < D / 32; i += B) s_eff[i] = 0u;
     if (SOUT) __syncthreads();
-    stage_products<T, MASK, SOUT, VEC>(col, val, x, p.xbits, k0, k1, nnz, s_prod, s_eff);
+    stage_products<T, MASK, SOUT, VEC, CHK>(col, val, x, p.xbits, k0, k1, nnz, s_prod, s_eff, ncols);
     __syncthreads();
 
     // this thread's share of the tile's merge path
@@ -424,13 +441,14 @@ __global__ void __launch_bounds__(kBalB) k_pull_bal(int64_t m, int64_t nnz, cons
     S::acc_zero(acc);
     bool hit = false;
     for (int step = dt; step < dte; ++step) {
-        if (ri < nrows && (int64_t)s_end[ri] <= k0 + ki) {
+        if (ri < nrows && ((int64_t)s_end[ri] <= k0 + ki || (CHK && ki >= nk))) {
             s_row[ri] = S::acc_part(acc);
             S::acc_zero(acc);
             if (SOUT && hit && !row_masked(p.ymask, (int64_t)r0 + ri)) yflag[(int64_t)r0 + ri] = 1;
             hit = false;
             ++ri;
         } else {
+            if (CHK && ki >= nk) break;
             S::acc_add(acc, s_prod[ki]);
             if (SOUT) hit |= (s_eff[ki >> 5] >> (ki & 31)) & 1u;
             ++ki;
@@ -525,16 +543,17 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     if (dist == 0) {
         const unsigned g = (unsigned)((m + 32 * kStageWarps - 1) / (32 * kStageWarps));
         int32_t* st = H->ws.status;
+        const uint32_t wl = H->wait_limit;
         if (m > 0) {
             if (vec && H->pull_tma)
                 k_pull_thread<T, MASK, SOUT, true, true><<<g, 32 * kStageWarps, 0, s>>>(m, H->nnz, H->rowptr, H->col,
-                                                                                      val, a, ywork, yt, st);
+                                                                                      val, a, ywork, yt, st, wl);
             else if (vec)
                 k_pull_thread<T, MASK, SOUT, true, false><<<g, 32 * kStageWarps, 0, s>>>(m, H->nnz, H->rowptr, H->col,
-                                                                                       val, a, ywork, yt, st);
+                                                                                       val, a, ywork, yt, st, wl);
             else
                 k_pull_thread<T, MASK, SOUT, false, false><<<g, 32 * kStageWarps, 0, s>>>(m, H->nnz, H->rowptr, H->col,
-                                                                                        val, a, ywork, yt, st);
+                                                                                        val, a, ywork, yt, st, wl);
         }
     } else if (dist == 1) {
         launch_pull_warp_dtype<T, MASK, SOUT>(H, a, vec, s);
@@ -555,22 +574,23 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     if (fork) cudaStreamWaitEvent(s, H->ev_join, 0);
 }
 
-// The FP32 balanced pull on caller-owned arrays and caller-provided scratch
-// (tile table, carries); used by the allocation-free entry point.
-void launch_pull_bal_f32_raw(int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col, const float* val,
-                             const float* x, float* y, const int32_t* tile_row, int32_t* carry_row, double* carry_val,
-                             int64_t ntiles, cudaStream_t s) {
+// The FP32 balanced pull on caller-owned, unvalidated arrays and
+// caller-provided scratch (tile table, carries), with the bounds checks of
+// the CHK form; used by the allocation-free entry point.
+void launch_pull_bal_f32_raw(int64_t m, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                             const float* val, const float* x, float* y, const int32_t* tile_row, int32_t* carry_row,
+                             double* carry_val, int64_t ntiles, cudaStream_t s) {
     if (ntiles == 0) return;
     PullArg a;
     a.desc = nullptr;
     a.io = PullIO{x, nullptr, y};
     const bool vec = ((uintptr_t)col % 16 == 0) && ((uintptr_t)val % 16 == 0);
     if (vec)
-        k_pull_bal<float, false, false, true><<<(int)ntiles, kBalB, 0, s>>>(m, nnz, rowptr, col, val, tile_row, a,
-                                                                            nullptr, nullptr, carry_row, carry_val);
+        k_pull_bal<float, false, false, true, true><<<(int)ntiles, kBalB, 0, s>>>(
+            m, nnz, rowptr, col, val, tile_row, a, nullptr, nullptr, carry_row, carry_val, n);
     else
-        k_pull_bal<float, false, false, false><<<(int)ntiles, kBalB, 0, s>>>(m, nnz, rowptr, col, val, tile_row, a,
-                                                                             nullptr, nullptr, carry_row, carry_val);
+        k_pull_bal<float, false, false, false, true><<<(int)ntiles, kBalB, 0, s>>>(
+            m, nnz, rowptr, col, val, tile_row, a, nullptr, nullptr, carry_row, carry_val, n);
     k_pull_bal_fixup<float><<<(int)((ntiles + 255) / 256), 256, 0, s>>>(ntiles, carry_row, carry_val, nullptr, y,
                                                                         nullptr, 0);
 }

@@ -180,6 +180,9 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
                 emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xx), p0 + k);
         }
     }
+    // any lane may have queued a hub of this warp; lane 0 reads the queue
+    // entries, so order those lanes' stores before its reads
+    __syncwarp();
     help_long<T, WB, true>(colptr, rowidx, valc, desc, ws, ym, lane);
 }
 

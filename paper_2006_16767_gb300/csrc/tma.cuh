@@ -44,9 +44,10 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
-// Bounded wait for phase `phase` of `bar`; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-    for (uint32_t it = 0; it < kMbarSpinLimit; ++it)
+// Bounded wait for phase `phase` of `bar`: at most `limit` polls; false
+// when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t limit = kMbarSpinLimit) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_test(bar, phase)) return true;
     return false;
 }

@@ -282,7 +282,25 @@ void launch_features(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, c
 }
 
 // ---------------------------------------------------------------- sparse x -> dense x + bitmap
-template <class T>
+// Sets (or clears) x's bit in the scatter bitmap. Lanes of a warp whose
+// entries fall into the same 32-bit word (a sorted list puts up to 32 of
+// them there) combine their bits first, so each word takes one atomic per
+// warp instead of one per entry.
+__device__ __forceinline__ void scatter_bit(uint32_t* xbits, int32_t j, bool set) {
+    const uint32_t w = (uint32_t)j >> 5;
+    if (!set) {
+        xbits[w] = 0u;
+        return;
+    }
+    const unsigned peers = __match_any_sync(__activemask(), w);
+    const uint32_t word = __reduce_or_sync(peers, 1u << (j & 31));
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(&xbits[w], word);
+}
+
+// Scatters a listed x into the zero-invariant dense workspace (set) or
+// restores it to zero (clear). BITS: also the scatter bitmap, which only the
+// kernels that validate entries, flag output rows or read Boolean terms use.
+template <class T, bool BITS>
 __global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32_t* xbits, int set) {
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
@@ -302,31 +320,29 @@ __global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             xdense[j[q]] = v[q];
-            if (set)
-                atomicOr(&xbits[j[q] >> 5], 1u << (j[q] & 31));
-            else
-                xbits[j[q] >> 5] = 0u;
+            if (BITS) scatter_bit(xbits, j[q], set);
         }
     }
     for (; t < nx; t += stride) {
         const int32_t j = xidx[t];
-        if (set) {
-            xdense[j] = vals ? xval[t] : Sr<T>::one();
-            atomicOr(&xbits[j >> 5], 1u << (j & 31));
-        } else {
-            xdense[j] = T(0);
-            xbits[j >> 5] = 0u;
-        }
+        xdense[j] = set ? (vals ? xval[t] : Sr<T>::one()) : T(0);
+        if (BITS) scatter_bit(xbits, j, set);
     }
 }
 
-void launch_x_scatter(asv_matrix_s* H, bool set, cudaStream_t s) {
+template <class T>
+static void x_scatter_dtype(asv_matrix_s* H, bool set, bool bits, int g, cudaStream_t s) {
+    if (bits) k_x_scatter<T, true><<<g, 256, 0, s>>>(H->d_desc, (T*)H->ws.xdense, H->ws.xbits_scat, set);
+    else k_x_scatter<T, false><<<g, 256, 0, s>>>(H->d_desc, (T*)H->ws.xdense, H->ws.xbits_scat, set);
+}
+
+void launch_x_scatter(asv_matrix_s* H, bool set, bool bits, cudaStream_t s) {
     const int g = feat_grid(H, H->n);
     switch (H->dtype) {
-        case ASV_F32: k_x_scatter<float><<<g, 256, 0, s>>>(H->d_desc, (float*)H->ws.xdense, H->ws.xbits_scat, set); break;
-        case ASV_F64: k_x_scatter<double><<<g, 256, 0, s>>>(H->d_desc, (double*)H->ws.xdense, H->ws.xbits_scat, set); break;
-        case ASV_I32: k_x_scatter<int32_t><<<g, 256, 0, s>>>(H->d_desc, (int32_t*)H->ws.xdense, H->ws.xbits_scat, set); break;
-        case ASV_BOOL: k_x_scatter<bool8><<<g, 256, 0, s>>>(H->d_desc, (bool8*)H->ws.xdense, H->ws.xbits_scat, set); break;
+        case ASV_F32: x_scatter_dtype<float>(H, set, bits, g, s); break;
+        case ASV_F64: x_scatter_dtype<double>(H, set, bits, g, s); break;
+        case ASV_I32: x_scatter_dtype<int32_t>(H, set, bits, g, s); break;
+        case ASV_BOOL: x_scatter_dtype<bool8>(H, set, true, g, s); break;
     }
 }
 
@@ -424,25 +440,46 @@ __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwor
             }
         }
         __syncthreads();
-        for (int32_t k = threadIdx.x; k < tot; k += B) pol.emit(base + k, stage[k]);
+        // four items per thread in flight: every source value of a group is
+        // loaded before any of the group's outputs is stored (a store can
+        // alias the next source load, so the compiler would not reorder them)
+        for (int32_t k0 = threadIdx.x; k0 < tot; k0 += 4 * B) {
+            int32_t j[4];
+            typename Policy::V v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t k = k0 + u * B;
+                j[u] = k < tot ? stage[k] : 0;
+                if (k < tot) v[u] = pol.load(j[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t k = k0 + u * B;
+                if (k < tot) pol.store(base + k, j[u], v[u]);
+            }
+        }
         __syncthreads();
         base += tot;
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) pol.count(base);
 }
 
+// An output policy of the compaction: load(j) reads item j's value, store()
+// writes item j at output position pos.
 // dense x -> ascending list (values gathered from x)
 template <class T>
 struct XListPolicy {
+    using V = T;
     const CallDesc* desc;
     int32_t* idx;
     T* val;
     const T* x;
     __device__ void begin() { x = (const T*)desc->x_dense; }
     __device__ void clear_word(uint32_t*, int64_t) {}
-    __device__ void emit(int32_t pos, int64_t j) {
-        idx[pos] = (int32_t)j;
-        if (!Sr<T>::kPattern) val[pos] = x[j];
+    __device__ T load(int32_t j) const { return Sr<T>::kPattern ? Sr<T>::one() : x[j]; }
+    __device__ void store(int32_t pos, int32_t j, T v) const {
+        idx[pos] = j;
+        if (!Sr<T>::kPattern) val[pos] = v;
     }
     __device__ void count(int32_t) {}
 };
@@ -450,15 +487,17 @@ struct XListPolicy {
 // public dense -> sparse conversion
 template <class T>
 struct PublicCompactPolicy {
+    using V = T;
     const T* x;
     int32_t* idx;
     T* val;
     int64_t* count_out;
     __device__ void begin() {}
     __device__ void clear_word(uint32_t*, int64_t) {}
-    __device__ void emit(int32_t pos, int64_t j) {
-        idx[pos] = (int32_t)j;
-        if (val) val[pos] = x[j];
+    __device__ T load(int32_t j) const { return val ? x[j] : T(0); }
+    __device__ void store(int32_t pos, int32_t j, T v) const {
+        idx[pos] = j;
+        if (val) val[pos] = v;
     }
     __device__ void count(int32_t c) { *count_out = c; }
 };
@@ -467,6 +506,7 @@ struct PublicCompactPolicy {
 // accumulators (re-zeroed as they are read) or the pull kernels' dense y.
 template <class T, bool FROM_ACC>
 struct OutSparsePolicy {
+    using V = T;
     const CallDesc* desc;
     typename Sr<T>::Atom* acc;
     const T* ywork;
@@ -480,18 +520,15 @@ struct OutSparsePolicy {
         cap = desc->y_cap;
     }
     __device__ void clear_word(uint32_t* bits, int64_t w) { bits[w] = 0u; }
-    __device__ void emit(int32_t pos, int64_t i) {
-        T v;
-        if (Sr<T>::kPattern) {
-            v = Sr<T>::one();
-        } else if (FROM_ACC) {
-            v = Sr<T>::from_atom(acc[i]);
-            acc[i] = typename Sr<T>::Atom(0);
-        } else {
-            v = ywork[i];
-        }
+    __device__ T load(int32_t i) const {
+        if (Sr<T>::kPattern) return Sr<T>::one();
+        if (FROM_ACC) return Sr<T>::from_atom(acc[i]);
+        return ywork[i];
+    }
+    __device__ void store(int32_t pos, int32_t i, T v) const {
+        if (FROM_ACC && !Sr<T>::kPattern) acc[i] = typename Sr<T>::Atom(0);
         if (pos < cap) {
-            yidx[pos] = (int32_t)i;
+            yidx[pos] = i;
             if (yval) yval[pos] = v;
         }
     }
@@ -525,31 +562,65 @@ void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- dense write-out of the push accumulators
+// Sixteen rows per thread: one 16-byte load of their flags (the flag array is
+// padded to a multiple of 16 bytes, so the load never leaves it), then y_i =
+// the accumulator of a flagged row (re-zeroed) or 0, written with 16-byte
+// stores when y is 16-byte aligned. Most groups of a sparse product have no
+// flag set and only write zeros.
+constexpr int kFinRows = 16;
 template <class T>
 __global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, typename Sr<T>::Atom* acc, uint8_t* yflag,
                                                         const CallDesc* __restrict__ desc) {
+    using S = Sr<T>;
     T* __restrict__ y = (T*)desc->y;
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i >= m) return;
-    const bool f = yflag[i] != 0;
-    if (Sr<T>::kPattern) {
-        y[i] = f ? Sr<T>::one() : T(0);
-    } else if (f) {
-        y[i] = Sr<T>::from_atom(acc[i]);
-        acc[i] = typename Sr<T>::Atom(0);
-    } else {
-        y[i] = T(0);
+    const bool vec = ((uintptr_t)y & 15) == 0;
+    const int64_t ngroups = (m + kFinRows - 1) / kFinRows;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = g * kFinRows;
+        const uint4 fw = *reinterpret_cast<const uint4*>(yflag + i0);
+        const bool any = (fw.x | fw.y | fw.z | fw.w) != 0u;
+        T v[kFinRows];
+        const uint8_t* fb = reinterpret_cast<const uint8_t*>(&fw);
+#pragma unroll
+        for (int u = 0; u < kFinRows; ++u) {
+            if (S::kPattern) v[u] = fb[u] ? S::one() : T(0);
+            else v[u] = T(0);
+        }
+        if (any) {
+            if constexpr (!S::kPattern) {
+#pragma unroll
+                for (int u = 0; u < kFinRows; ++u)
+                    if (fb[u]) v[u] = S::from_atom(acc[i0 + u]);
+#pragma unroll
+                for (int u = 0; u < kFinRows; ++u)
+                    if (fb[u]) acc[i0 + u] = typename S::Atom(0);
+            }
+            *reinterpret_cast<uint4*>(yflag + i0) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (vec && i0 + kFinRows <= m) {
+            constexpr int kPer = 16 / sizeof(T);
+#pragma unroll
+            for (int u = 0; u < kFinRows; u += kPer) {
+                uint4 w;
+                memcpy(&w, &v[u], 16);
+                *reinterpret_cast<uint4*>(y + i0 + u) = w;
+            }
+        } else {
+            for (int u = 0; u < kFinRows && i0 + u < m; ++u) y[i0 + u] = v[u];
+        }
     }
-    if (f) yflag[i] = 0;
 }
 
 template <class T>
 static void finalize_dtype(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s) {
     using Atom = typename Sr<T>::Atom;
     if (out_mode == ASV_OUT_DENSE) {
-        if (H->m > 0)
-            k_finalize_dense<T><<<(unsigned)((H->m + 255) / 256), 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag,
-                                                                            H->d_desc);
+        if (H->m > 0) {
+            const int64_t ngroups = (H->m + kFinRows - 1) / kFinRows;
+            const int64_t g = std::min<int64_t>((ngroups + 255) / 256, (int64_t)H->num_sms * 8);
+            k_finalize_dense<T><<<(unsigned)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag, H->d_desc);
+        }
     } else if (from_acc) {
         OutSparsePolicy<T, true> pol{H->d_desc, (Atom*)H->ws.acc, nullptr, H->ws.status, nullptr, nullptr, 0};
         compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s);

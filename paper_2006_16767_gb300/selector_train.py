@@ -199,10 +199,11 @@ def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
                     xd[it.long()] = 1
                 cnt = torch.tensor([len(idx)], dtype=torch.int64, device=dev)
                 for xs in (0, 1):
-                    kid, vf = asv.asv_select(A.handle, cnt, it, xv, None if xs else xd)
+                    _, vf = asv.asv_select(A.handle, cnt, it, xv, None if xs else xd)
                     feats = [float(A.features()[f]) for f in FEATURES[:9]] + [
                         float(vf["nnz_x"]), float(vf["x_sparsity"]), float(vf["nnz_s"]), float(vf["m_sparsity"])]
                     for om in (0, 1):
+                        kid, _ = asv.asv_select(A.handle, cnt, it, xv, None if xs else xd, out_mode=om)
                         times = [None] * NK
                         best = float("inf")
                         for kk in range(NK):

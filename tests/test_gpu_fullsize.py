@@ -49,6 +49,46 @@ def test_stencil256_dense_and_listed_x():
         assert_rows_close(yd[rows], ref, s, "f32", f"stencil256 listed x rho={rho}")
 
 
+def test_stencil256_benchmark_step_calls():
+    # the twelve selector-driven products of the benchmark step, in its launch
+    # configuration: per density, x listed -> the structural output list (the
+    # whole index set bit for bit, values on sampled rows), and x dense -> y
+    # dense (sampled rows)
+    g = 256
+    rp, c, v, _ = gen.stencil27(g, gen.config_seed(5))
+    m = n = g ** 3
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), to_dev(v))
+    colptr, rowidx, _ = oracle.csr_to_csc(m, n, rp, c)
+    rows = np.sort(gen.randint(4096, m, 54)).astype(np.int64)
+    rp_s, c_s, v_s = sub_csr(rp, c, v, rows)
+    v_s = v_s.astype(np.float64)
+    yidx = torch.empty(m, dtype=torch.int32, device=DEV)
+    yval = torch.empty(m, dtype=torch.float32, device=DEV)
+    nnz_y = torch.zeros(1, dtype=torch.int64, device=DEV)
+    yd = torch.empty(m, dtype=torch.float32, device=DEV)
+    for rho in (1e-5, 1e-4, 1e-3, 1e-2, 1e-1, 1.0):
+        k = max(1, int(round(rho * n)))
+        idx, val = gen.sparse_x(n, k, gen.config_seed(5), 11, np.float32)
+        it, vt = to_dev(idx), to_dev(val)
+        cnt = torch.tensor([k], dtype=torch.int64, device=DEV)
+        asv.asv_spmspv(A.handle, cnt, it, vt, None, asv.ASV_OUT_SPARSE, None, yidx, yval, nnz_y, m, "auto")
+        xd = torch.zeros(n, dtype=torch.float32, device=DEV)
+        xd[it.long()] = vt
+        asv.asv_spmspv(A.handle, None, None, None, xd, asv.ASV_OUT_DENSE, yd, kernel="auto")
+        assert A.status() == asv.ASV_OK
+        touched = np.flatnonzero(oracle.csc_push(m, colptr, rowidx, None, idx, None)[1])
+        ny = int(nnz_y.item())
+        got_idx = yidx[:ny].cpu().numpy()
+        assert np.array_equal(got_idx, touched), f"rho={rho}: output index set"
+        ref, s, hit = oracle.spmspv_rowmajor(n, rp_s, c_s, v_s, idx, val.astype(np.float64))
+        pos = np.searchsorted(got_idx, rows)
+        inset = hit.astype(bool)
+        assert np.array_equal(inset, (pos < ny) & (got_idx[np.minimum(pos, ny - 1)] == rows))
+        gv = yval[:ny].cpu().numpy()[pos[inset]]
+        assert_rows_close(gv, ref[inset], s[inset], "f32", f"stencil256 list->list rho={rho}")
+        assert_rows_close(yd.cpu().numpy()[rows], ref, s, "f32", f"stencil256 dense->dense rho={rho}")
+
+
 def test_rmat22_bfs_levels_products_and_pagerank():
     rp, c = gen.rmat(22, 16, gen.config_seed(2))
     n = 1 << 22

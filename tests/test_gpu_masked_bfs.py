@@ -234,17 +234,36 @@ def test_incremental_pagerank_fp64_matches_oracle(k):
         assert np.max(np.abs(got - want) / want) <= 1e-11, f"pagerank k={k} eps={eps}"
 
 
-def test_incremental_pagerank_fp32_and_arguments():
+@pytest.mark.parametrize("k", ["auto", "pull_warp", "push_bal_atom"])
+def test_incremental_pagerank_fp32_matches_oracle(k):
+    # Every value of the iteration is nonnegative (A's entries, the deltas,
+    # the column scaling), so sum |a x| of a product row equals the row's
+    # value and the FP32 product bound 2e-6 * sum |a x| is a relative bound.
+    # A delta after k products then carries a relative error of at most
+    # k (2e-6 + 3u) (the product, the division by the column count, the
+    # scaling by the damping; u = 2^-24), and so does each vertex's rank,
+    # which adds them up in FP32 (one more u per product). The threshold is
+    # one where every keep/drop decision of the oracle's run lies at least
+    # 1.9e-3 (relative) away from eps -- far beyond that error -- so both
+    # runs keep the same entries and run the same number of products.
+    rp, c = gen.rmat(10, 8, seed=42)
+    n = 1 << 10
+    eps = 1.8112434987143081e-06
+    A = asv.Matrix(n, n, to_dev(rp), to_dev(c), to_dev(np.ones(len(c), np.float32)))
+    want, it, margin = oracle.pagerank_delta(n, rp, c, None, 0.85, eps, 100)
+    tol = it * (2e-6 + 4 * 2.0 ** -24)
+    assert it < 100 and margin > 10 * tol
+    rank, iters = A.pagerank(0.85, eps, 100, kernel=k)
+    got = rank.cpu().numpy().astype(np.float64)
+    assert iters == it, f"pagerank k={k}: {iters} products vs {it}"
+    rel = np.abs(got - want) / want
+    assert np.all(rel <= tol), f"pagerank k={k}: max relative error {rel.max():.3g} > {tol:.3g}"
+
+
+def test_incremental_pagerank_fp32_arguments():
     rp, c = gen.rmat(12, 8, seed=42)
     n = 1 << 12
     A = asv.Matrix(n, n, to_dev(rp), to_dev(c), to_dev(np.ones(len(c), np.float32)))
-    want, it, _ = oracle.pagerank_delta(n, rp, c, None, 0.85, 1e-8, 40)
-    rank, iters = A.pagerank(0.85, 1e-8, 40)
-    got = rank.cpu().numpy().astype(np.float64)
-    # FP32 products and FP32 deltas: a few keep/drop decisions may differ
-    # near the threshold, each moving a rank by about eps
-    assert np.max(np.abs(got - want)) <= 1e-4 * want.max() + 40 * 1e-8
-    assert abs(iters - it) <= 2
     r0, i0 = A.pagerank(0.85, 1e-8, 0)
     assert i0 == 0 and np.allclose(r0.cpu().numpy(), 0.15 / n)
     for bad in (dict(damping=1.0), dict(damping=-0.1), dict(eps=-1.0), dict(max_iter=-1)):

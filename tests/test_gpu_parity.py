@@ -260,9 +260,14 @@ def test_vector_features_and_selection():
         nzi = idx[val != 0]
         want2 = oracle.vector_features(n, len(c), colptr, nzi)
         assert f2["nnz_x"] == want2["nnz_x"] and f2["nnz_s"] == want2["nnz_s"]
-        # the auto call runs the kernel the selector names
+        # the auto call runs the kernel the selector names for its call
+        # format (the trees differ between a dense and a list output)
         A.spmspv(xidx=to_dev(idx), xval=to_dev(val))
         assert A.last_kernel() == kid
+        kid3, f3 = A.select(xidx=to_dev(idx), xval=to_dev(val), sparse_out=True)
+        assert f3 == f
+        A.spmspv(xidx=to_dev(idx), xval=to_dev(val), sparse_out=True)
+        assert A.last_kernel() == kid3
 
 
 def test_compaction_ieee_bit_exact():
