@@ -328,11 +328,54 @@ asv_status asv_autotune_batched(asv_matrix A, int32_t B, int64_t max_entries, co
 asv_status asv_spmspv_backward(asv_matrix A, int32_t B, const void* d_X, const void* d_dY, void* d_dX,
                                void* d_dA, void* stream);
 
+/* ---------------------------------------------------------------- single-call tuning */
+
+/* Launch shape of the pull candidates; it changes their speed, never their
+ * result. lanes: lanes per row of the sub-warp pull (2, 4, 8, 16 or 32);
+ * unroll: rows per lane group loaded together (2 or 4); tma: 1 = the
+ * one-row-per-thread pull stages each warp's span with TMA bulk copies. */
+typedef struct {
+    int32_t lanes;
+    int32_t unroll;
+    int32_t tma;
+} asv_pull_tune;
+
+/* Per-matrix tuner of the single-call kernels (the counterpart of
+ * asv_autotune_batched for the plain product): times the pull candidates'
+ * launch shapes on a dense x of ones -- lanes x unroll of the sub-warp pull,
+ * starting from the creation-time choice and moving outwards, then TMA
+ * staging on or off for the one-row-per-thread pull -- until budget_ms of
+ * wall time has passed, and keeps the fastest in the handle (later calls,
+ * forced or selector-driven, use it). With cache_path, a line
+ * "<gpu>|m=..|n=..|nnz=..|max_row=..|dtype=..|pull\tlanes\tunroll\ttma" is
+ * read if present (no timing) or appended. *h_out (may be NULL) receives the
+ * settings kept. Allocates and frees a scratch x and y; synchronises `stream`.
+ * The handle's other calls must not run concurrently. */
+asv_status asv_autotune(asv_matrix A, const char* cache_path, uint32_t budget_ms, asv_pull_tune* h_out,
+                        void* stream);
+
+/* The handle's current pull launch shape (creation-time choice or the
+ * tuner's). */
+asv_status asv_pull_tuning(asv_matrix A, asv_pull_tune* h_out);
+
+/* Backward pass of the same product with the batch listed instead of dense:
+ * X as a CSR of vectors -- d_xptr[B+1] device int64 offsets (relative to
+ * d_xptr[0]), d_xidx column ids in [0, n), distinct within a vector, d_xval
+ * values (NULL = ones) -- as asv_spmspv_batched takes it. Writes d_dX[B][n]
+ * = dY A and d_dA[nnz] (CSR order), dA_k = sum_b dy_b[row(k)] * x_b[col(k)]
+ * (only the listed entries of x contribute). The list is converted on the
+ * device into the vector-minor dense layout the dA kernel reads; a column id
+ * outside [0, n) is skipped and latches ASV_ERR_ARG. FP32 handles,
+ * 1 <= B <= 128; either output may be NULL (d_xptr is needed for dA). */
+asv_status asv_spmspv_backward_list(asv_matrix A, int32_t B, const int64_t* d_xptr,
+                                    const int32_t* d_xidx, const void* d_xval, const void* d_dY,
+                                    void* d_dX, void* d_dA, void* stream);
+
 /* ---------------------------------------------------------------- selector */
 
 /* Replace the handle's decision trees (cascaded CART trees: computing
  * pattern, then workload distribution given the pattern, then write-back for
- * the push pattern; Sec. V-B / VI-B). `nodes` holds n_nodes (<= 1024) records
+ * the push pattern; Sec. V-B / VI-B). `nodes` holds n_nodes (<= 2048) records
  * of 5 doubles {feature, threshold, left, right, leaf_class}; feature < 0
  * marks a leaf. h_roots[20] holds five roots for each of the four call
  * formats (x dense, y dense), (x dense, y list), (x list, y dense),

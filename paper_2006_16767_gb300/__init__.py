@@ -56,6 +56,10 @@ class AsvTune(ctypes.Structure):
                 ("hot_columns", ctypes.c_int32)]
 
 
+class AsvPullTune(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("unroll", ctypes.c_int32), ("tma", ctypes.c_int32)]
+
+
 class _MFeat(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("max_row", ctypes.c_int64), ("min_row", ctypes.c_int64),
@@ -107,6 +111,12 @@ def lib():
             L.asv_status_string.argtypes = [i32]
             L.asv_status_string.restype = ctypes.c_char_p
             L.asv_version.argtypes = []
+            L.asv_spmspv_backward_list.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+            L.asv_spmspv_backward_list.restype = i32
+            L.asv_autotune.argtypes = [vp, ctypes.c_char_p, ctypes.c_uint32, P(AsvPullTune), vp]
+            L.asv_autotune.restype = i32
+            L.asv_pull_tuning.argtypes = [vp, P(AsvPullTune)]
+            L.asv_pull_tuning.restype = i32
             L.asv_debug_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
             L.asv_debug_set_wait_limit.restype = i32
             L.asv_debug_fail_alloc.argtypes = [i32]
@@ -232,6 +242,25 @@ def asv_autotune_batched(h, B, max_entries=0, xptr=None, xidx=None, xval=None, X
 def asv_spmspv_backward(h, B, X, dY, dX=None, dA=None, stream=None):
     _check(lib().asv_spmspv_backward(h, int(B), _ptr(X), _ptr(dY), _ptr(dX), _ptr(dA), _stream(stream)),
            "asv_spmspv_backward")
+
+
+def asv_spmspv_backward_list(h, B, xptr, xidx, xval, dY, dX=None, dA=None, stream=None):
+    _check(lib().asv_spmspv_backward_list(h, int(B), _ptr(xptr), _ptr(xidx), _ptr(xval), _ptr(dY), _ptr(dX),
+                                          _ptr(dA), _stream(stream)), "asv_spmspv_backward_list")
+
+
+def asv_autotune(h, cache_path=None, budget_ms=2000, stream=None):
+    """Tunes the handle's pull launch shape; returns (lanes, unroll, tma)."""
+    t = AsvPullTune()
+    cp = None if cache_path is None else str(cache_path).encode()
+    _check(lib().asv_autotune(h, cp, int(budget_ms), ctypes.byref(t), _stream(stream)), "asv_autotune")
+    return t.lanes, t.unroll, t.tma
+
+
+def asv_pull_tuning(h):
+    t = AsvPullTune()
+    _check(lib().asv_pull_tuning(h, ctypes.byref(t)), "asv_pull_tuning")
+    return t.lanes, t.unroll, t.tma
 
 
 def asv_spmv_noalloc_f32(m, n, rowptr, col, val, x, y, stream=None):
@@ -477,6 +506,21 @@ class Matrix:
         dA = torch.empty(self.nnz, dtype=torch.float32, device=dY.device) if need_da else None
         asv_spmspv_backward(self.handle, B, X, dY, dX, dA, stream)
         return dX, dA
+
+    def backward_list(self, xptr, xidx, xval, dY, need_dx=True, need_da=True, stream=None):
+        """backward() with the batch listed (xptr int64[B+1], xidx, xval or None)."""
+        B = dY.shape[0]
+        dX = torch.empty((B, self.n), dtype=torch.float32, device=dY.device) if need_dx else None
+        dA = torch.empty(self.nnz, dtype=torch.float32, device=dY.device) if need_da else None
+        asv_spmspv_backward_list(self.handle, B, xptr, xidx, xval, dY, dX, dA, stream)
+        return dX, dA
+
+    def autotune(self, cache_path=None, budget_ms=2000, stream=None):
+        """Tune the pull kernels' launch shape for this matrix; (lanes, unroll, tma)."""
+        return asv_autotune(self.handle, cache_path, budget_ms, stream)
+
+    def pull_tuning(self):
+        return asv_pull_tuning(self.handle)
 
     def last_kernel(self, stream=None) -> int:
         return asv_last_kernel(self.handle, stream)

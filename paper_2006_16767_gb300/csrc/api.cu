@@ -5,6 +5,7 @@
 // candidates (with their own format conversion), so the chosen kernel runs
 // with no host round-trip.
 #include <atomic>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
@@ -262,6 +263,7 @@ static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s
         std::vector<TreeNode> nodes;
         int32_t roots[kRootsLen];
         default_trees(dtype, nodes, roots);
+        update_lazy(H, nodes, roots);
         CKH(cudaMemcpyAsync(H->d_trees, nodes.data(), sizeof(TreeNode) * nodes.size(), cudaMemcpyHostToDevice, s));
         CKH(cudaMemcpyAsync(H->d_roots, roots, sizeof(roots), cudaMemcpyHostToDevice, s));
     }
@@ -401,7 +403,7 @@ static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om, const DescIn
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, g, ASV_K_PULL_BAL, cudaGraphCondAssignDefault));
     CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    launch_features(H, di, select_arg(H, (unsigned long long)h), cs);
+    launch_features(H, di, select_arg(H, (unsigned long long)h, 2 * xs + om), cs);
     cudaGraph_t g2;
     CK(cudaStreamEndCapture(cs, &g2));
     cudaGraphNode_t feat;
@@ -440,7 +442,7 @@ static asv_status launch_auto(asv_matrix_s* H, const DescInit& di, int om, cudaS
     // the feature node's arguments change only when the call's pointers do
     if (memcmp(&H->last_di[xs][om], &di, sizeof(di)) != 0) {
         FeatLaunch fl;
-        feature_launch(H, di, select_arg(H, H->cond[xs][om]), fl);
+        feature_launch(H, di, select_arg(H, H->cond[xs][om], 2 * xs + om), fl);
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof(kp));
         kp.func = fl.func;
@@ -574,7 +576,7 @@ static asv_status build_loop_graph(asv_matrix_s* H, const DescInit& di, int32_t 
             cudaGraphConditionalHandle hs;
             CKL(cudaGraphConditionalHandleCreate(&hs, body, ASV_K_PULL_BAL, cudaGraphCondAssignDefault));
             CKL(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-            launch_features(H, di, select_arg(H, (unsigned long long)hs), cs);
+            launch_features(H, di, select_arg(H, (unsigned long long)hs, 2 + ASV_OUT_SPARSE), cs);
             cudaGraph_t cap;
             CKL(cudaStreamEndCapture(cs, &cap));
             cudaGraphNode_t feat;
@@ -808,6 +810,9 @@ extern "C" asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t
     CK(cudaMemcpyAsync(A->d_trees, nodes.data(), sizeof(TreeNode) * n_nodes, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(A->d_roots, r, sizeof(r), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+    update_lazy(A, nodes, r);
+    // the selector graphs' feature nodes take the new lazy hint at their next call
+    memset(A->last_di, 0xff, sizeof(A->last_di));
     return ASV_OK;
 }
 
@@ -932,6 +937,171 @@ extern "C" asv_status asv_autotune_batched(asv_matrix A, int32_t B, int64_t max_
     return ASV_OK;
 }
 
+// ---------------------------------------------------------------- single-call tuner
+// The pull kernels' launch shape -- lanes per row and rows per lane group of
+// the sub-warp pull, TMA staging of the one-row-per-thread pull -- changes
+// their speed, never their result. The tuner times the candidates on a dense
+// x of ones through the direct (descriptor-free) launch path, within the time
+// budget, and keeps the fastest of each in the handle.
+static std::string pull_tune_key(asv_matrix A) {
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, A->dev);
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s|m=%lld|n=%lld|nnz=%lld|max_row=%lld|dtype=%d|pull", p.name, (long long)A->m,
+             (long long)A->n, (long long)A->nnz, (long long)A->h_mfeat.max_row, (int)A->dtype);
+    return buf;
+}
+
+static bool pull_tune_ok(const asv_pull_tune& t) {
+    const int l = t.lanes;
+    return (l == 2 || l == 4 || l == 8 || l == 16 || l == 32) && (t.unroll == 2 || t.unroll == 4) &&
+           (t.tma == 0 || t.tma == 1);
+}
+
+extern "C" asv_status asv_autotune(asv_matrix A, const char* cache_path, uint32_t budget_ms, asv_pull_tune* h_out,
+                                   void* stream) {
+    if (!A) return ASV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto current = [&]() { return asv_pull_tune{A->pull_lanes, A->pull_unroll, A->pull_tma ? 1 : 0}; };
+    const std::string key = pull_tune_key(A);
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[1024];
+            while (fgets(line, sizeof(line), f)) {
+                asv_pull_tune t{0, 0, 0};
+                char k[600];
+                if (sscanf(line, "%599[^\t]\t%d\t%d\t%d", k, &t.lanes, &t.unroll, &t.tma) == 4 && key == k &&
+                    pull_tune_ok(t)) {
+                    fclose(f);
+                    A->pull_lanes = t.lanes;
+                    A->pull_unroll = t.unroll;
+                    A->pull_tma = t.tma != 0;
+                    if (h_out) *h_out = t;
+                    return ASV_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    if (A->m == 0 || A->nnz == 0) {
+        if (h_out) *h_out = current();
+        return ASV_OK;
+    }
+    // a dense x of ones and a y, owned by the tuner for its duration
+    const size_t vs = vsize(A->dtype);
+    void *x = nullptr, *y = nullptr;
+    CK(cudaMalloc(&x, vs * std::max<int64_t>(A->n, 1)));
+    {
+        cudaError_t e = cudaMalloc(&y, vs * A->m);
+        if (e != cudaSuccess) {
+            cudaFree(x);
+            g_last_cuda = (int32_t)e;
+            return e == cudaErrorMemoryAllocation ? ASV_ERR_NOMEM : ASV_ERR_CUDA;
+        }
+    }
+    {
+        std::vector<unsigned char> ones(vs * std::max<int64_t>(A->n, 1));
+        for (int64_t j = 0; j < std::max<int64_t>(A->n, 1); ++j) {
+            unsigned char* q = ones.data() + vs * j;
+            switch (A->dtype) {
+                case ASV_F32: { const float o = 1.f; memcpy(q, &o, 4); break; }
+                case ASV_F64: { const double o = 1.0; memcpy(q, &o, 8); break; }
+                case ASV_I32: { const int32_t o = 1; memcpy(q, &o, 4); break; }
+                default: q[0] = 1; break;
+            }
+        }
+        cudaError_t e = cudaMemcpyAsync(x, ones.data(), ones.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(x);
+            cudaFree(y);
+            g_last_cuda = (int32_t)e;
+            return ASV_ERR_CUDA;
+        }
+    }
+    const PullIO io{x, nullptr, y};
+    const auto t_start = std::chrono::steady_clock::now();
+    auto elapsed_ms = [&]() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // one warm-up and three timed launches of `dist` with the handle's
+    // current settings; the median of the three
+    auto time_pull = [&](int dist) -> float {
+        launch_pull(A, dist, false, false, &io, s);
+        float t[3];
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(e0, s);
+            launch_pull(A, dist, false, false, &io, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t[r], e0, e1);
+        }
+        std::sort(t, t + 3);
+        return t[1];
+    };
+    const asv_pull_tune start = current();
+    asv_pull_tune best = start;
+    // the sub-warp pull: lanes per row x rows per lane group, starting from
+    // the creation-time choice, then its neighbours outwards
+    float bw = time_pull(1);
+    const int lanes[] = {2, 4, 8, 16, 32};
+    std::vector<asv_pull_tune> cands;
+    for (int l : lanes)
+        for (int u : {2, 4})
+            if (l != start.lanes || u != start.unroll) cands.push_back({l, u, start.tma});
+    std::stable_sort(cands.begin(), cands.end(), [&](const asv_pull_tune& p, const asv_pull_tune& q) {
+        auto d = [&](const asv_pull_tune& t) { return std::abs(__builtin_ctz(t.lanes) - __builtin_ctz(start.lanes)); };
+        return d(p) < d(q);
+    });
+    for (const asv_pull_tune& c : cands) {
+        if (elapsed_ms() > budget_ms) break;
+        A->pull_lanes = c.lanes;
+        A->pull_unroll = c.unroll;
+        const float t = time_pull(1);
+        if (t < bw) {
+            bw = t;
+            best.lanes = c.lanes;
+            best.unroll = c.unroll;
+        }
+    }
+    A->pull_lanes = best.lanes;
+    A->pull_unroll = best.unroll;
+    // TMA staging of the one-row-per-thread pull (arithmetic types only)
+    if (A->dtype != ASV_BOOL && elapsed_ms() <= budget_ms) {
+        const float t_cur = time_pull(0);
+        A->pull_tma = !A->pull_tma;
+        const float t_alt = time_pull(0);
+        if (t_alt < t_cur) best.tma = A->pull_tma ? 1 : 0;
+        A->pull_tma = best.tma != 0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t e = cudaGetLastError();
+    cudaFree(x);
+    cudaFree(y);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int32_t)e;
+        return ASV_ERR_CUDA;
+    }
+    if (h_out) *h_out = best;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s\t%d\t%d\t%d\n", key.c_str(), best.lanes, best.unroll, best.tma);
+            fclose(f);
+        }
+    }
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_pull_tuning(asv_matrix A, asv_pull_tune* h_out) {
+    if (!A || !h_out) return ASV_ERR_ARG;
+    *h_out = asv_pull_tune{A->pull_lanes, A->pull_unroll, A->pull_tma ? 1 : 0};
+    return ASV_OK;
+}
+
 extern "C" asv_status asv_spmspv_backward(asv_matrix A, int32_t B, const void* d_X, const void* d_dY, void* d_dX,
                                           void* d_dA, void* stream) {
     if (!A || B < 0 || !d_dY || (d_dA && !d_X)) return ASV_ERR_ARG;
@@ -940,6 +1110,18 @@ extern "C" asv_status asv_spmspv_backward(asv_matrix A, int32_t B, const void* d
     if (B == 0) return ASV_OK;
     CK(batched_backward(A, B, (const float*)d_X, (const float*)d_dY, (float*)d_dX, (float*)d_dA,
                         (cudaStream_t)stream));
+    return ASV_OK;
+}
+
+extern "C" asv_status asv_spmspv_backward_list(asv_matrix A, int32_t B, const int64_t* d_xptr, const int32_t* d_xidx,
+                                               const void* d_xval, const void* d_dY, void* d_dX, void* d_dA,
+                                               void* stream) {
+    if (!A || B < 0 || !d_dY || (d_dA && !d_xptr)) return ASV_ERR_ARG;
+    if (A->dtype != ASV_F32) return ASV_ERR_UNSUPPORTED;
+    if (B > 128) return ASV_ERR_UNSUPPORTED;
+    if (B == 0) return ASV_OK;
+    CK(batched_backward(A, B, nullptr, (const float*)d_dY, (float*)d_dX, (float*)d_dA, (cudaStream_t)stream,
+                        d_dA ? d_xptr : nullptr, d_xidx, (const float*)d_xval));
     return ASV_OK;
 }
 

@@ -742,8 +742,26 @@ static void transpose(const float* in, float* out, int64_t rows, int64_t cols, c
     k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
 }
 
+// A listed batch (CSR of vectors) into the vector-minor dense layout Xt[n][B]
+// that the dA kernel reads (zeroed before): block b writes vector b's
+// entries; a column id outside [0, n) is skipped and reported.
+__global__ void k_list_to_xt(const int64_t* __restrict__ xptr, const int32_t* __restrict__ xidx,
+                             const float* __restrict__ xval, int64_t n, int32_t B, float* Xt, int32_t* status) {
+    const int32_t b = blockIdx.x;
+    const int64_t base = xptr[0];
+    const int64_t lo = xptr[b] - base, hi = xptr[b + 1] - base;
+    for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+        const int32_t j = xidx[t];
+        if ((uint64_t)(uint32_t)j >= (uint64_t)n) {
+            latch_status(status, ASV_ERR_ARG);
+            continue;
+        }
+        Xt[(int64_t)j * B + b] = xval ? xval[t] : 1.0f;
+    }
+}
+
 cudaError_t batched_backward(asv_matrix_s* H, int32_t B, const float* X, const float* dY, float* dX, float* dA,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int64_t* xptr, const int32_t* xidx, const float* xval) {
     cudaError_t e = bwd_workspace(H, B);
     if (e != cudaSuccess) return e;
     BatchWs& bw = H->bws;
@@ -764,7 +782,12 @@ cudaError_t batched_backward(asv_matrix_s* H, int32_t B, const float* X, const f
         transpose(dXt, dX, H->n, B, s);
     }
     if (dA && H->m > 0 && H->nnz > 0) {
-        transpose(X, Xt, B, H->n, s);
+        if (xptr) {  // listed x: conversion to the layout the kernel reads (Sec. VI-A online conversion)
+            cudaMemsetAsync(Xt, 0, 4 * (size_t)B * H->n, s);
+            k_list_to_xt<<<B, 256, 0, s>>>(xptr, xidx, xval, H->n, B, Xt, H->ws.status);
+        } else {
+            transpose(X, Xt, B, H->n, s);
+        }
         const unsigned g = (unsigned)((H->m + 7) / 8);
         switch (vpl) {
             case 1: k_bwd_da<1><<<g, 256, 0, s>>>(H->m, B, H->rowptr, H->col, dYt, Xt, dA); break;

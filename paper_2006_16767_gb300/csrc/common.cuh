@@ -206,7 +206,8 @@ struct TreeNode {
     int32_t left, right, leaf;
     double thr;
 };
-constexpr int kMaxTreeNodes = 1024;
+constexpr int kMaxTreeNodes = 2048;  // node table of a handle (all formats' trees)
+constexpr int kTreeWindow = 1024;    // nodes of one call format staged in shared memory
 
 // Rows longer than kLongRow entries are taken out of the one-row-per-thread
 // and sub-warp pull kernels and summed by a warp per segment of at most

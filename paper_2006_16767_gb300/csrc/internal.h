@@ -108,6 +108,10 @@ struct asv_matrix_s {
     int32_t* multi_row = nullptr;
     int32_t* multi_base = nullptr;
     int64_t nseg = 0, nmulti = 0;
+    // Boolean handles: pieces of long-row segments handed to the second pass
+    // of a list-output product, and their count (reset by the feature pass)
+    int4* long_rest = nullptr;
+    unsigned int* long_rest_n = nullptr;
     int pull_lanes = 8;   // lanes per row of the (sub-)warp pull kernels
     int pull_unroll = 4;  // rows per lane group loaded together (2: more resident warps)
     bool pull_tma = true; // one-row-per-thread pull stages its spans with TMA bulk copies
@@ -116,6 +120,9 @@ struct asv_matrix_s {
     // selector tables
     asv::TreeNode* d_trees = nullptr;
     int32_t* d_roots = nullptr;
+    // per call format: its pattern tree starts with a feature that a listed
+    // x gives for free (the lazy evaluation of the list feature pass)
+    int32_t lazy_ok[4] = {0, 0, 0, 0};
     // per-call state
     asv::CallDesc* d_desc = nullptr;
     asv::Ws ws{};
@@ -248,12 +255,18 @@ void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s
 cudaError_t batched_forward(asv_matrix_s* H, int32_t B, int64_t max_entries, const int64_t* xptr, const int32_t* xidx,
                             const float* xval, const float* Xdense, float* Y, int R, int GB, int hot,
                             cudaStream_t s);
+// X dense [B][n], or (xptr != NULL) listed as a CSR of vectors
 cudaError_t batched_backward(asv_matrix_s* H, int32_t B, const float* X, const float* dY, float* dX, float* dA,
-                             cudaStream_t s);
+                             cudaStream_t s, const int64_t* xptr = nullptr, const int32_t* xidx = nullptr,
+                             const float* xval = nullptr);
 void batch_release(asv_matrix_s* H);
 
 // select.cu
-SelectArg select_arg(asv_matrix_s* H, unsigned long long cond);
+// fmt: the call format 2 * (x listed) + (sparse output) the feature node
+// serves (-1 = none: no lazy evaluation)
+SelectArg select_arg(asv_matrix_s* H, unsigned long long cond, int fmt = -1);
+// recomputes lazy_ok from a node table and its roots
+void update_lazy(asv_matrix_s* H, const std::vector<TreeNode>& nodes, const int32_t* roots);
 void default_trees(int32_t dtype, std::vector<TreeNode>& nodes, int32_t roots[kRootsLen]);
 
 }  // namespace asv

@@ -326,6 +326,12 @@ cudaError_t build_long_rows(asv_matrix_s* H, cudaStream_t s) {
     if ((e = grab((void**)&H->long_hit, ns)) != cudaSuccess) return e;
     if ((e = grab((void**)&H->multi_row, 4 * nm)) != cudaSuccess) return e;
     if ((e = grab((void**)&H->multi_base, 4 * nm)) != cudaSuccess) return e;
+    if (H->dtype == ASV_BOOL) {
+        // at most (kLongSeg - 256) / 512 + 1 = 8 pieces per segment go to the second pass
+        if ((e = grab((void**)&H->long_rest, 16 * 8 * ns)) != cudaSuccess) return e;
+        if ((e = grab((void**)&H->long_rest_n, 16)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(H->long_rest_n, 0, 16, s)) != cudaSuccess) return e;
+    }
     k_long_fill<<<grid, 256, 0, s>>>(H->rowptr, H->m, H->seg, H->multi_row, H->multi_base, d_cnt);
     if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(h), s)) != cudaSuccess) return e;
     H->nseg = (int64_t)ns;

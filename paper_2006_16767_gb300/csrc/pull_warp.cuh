@@ -201,11 +201,20 @@ __device__ __forceinline__ typename Sr<T>::Atom atom_combine(typename Sr<T>::Ato
     else return a + b;
 }
 
+// Boolean products with a list output (BFS levels) hand the rest of a
+// segment without a true term in its first kLongFirst chunks to a second
+// pass: most segments stop within their first chunk, and the launch used to
+// wait on the few that walked 32 chunks one load latency after another. The
+// rest goes out as pieces of kLongPiece entries ({row, begin, end, 0}) that
+// any warp of k_pull_long_rest takes.
+constexpr int kLongFirst = 2;
+constexpr int kLongPiece = 512;
+
 template <class T, bool MASK, bool SOUT, bool VEC>
 __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, const int4* __restrict__ seg,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
                                                    PullArg a, void* ywork, uint8_t* yflag, uint64_t* part,
-                                                   uint8_t* part_hit) {
+                                                   uint8_t* part_hit, int4* rest, unsigned int* rest_n) {
     using S = Sr<T>;
     using P = typename S::Part;
     const PullIO p = resolve(a, ywork, SOUT);
@@ -219,12 +228,16 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     const int32_t e = row_masked(p.ymask, row) ? b : d.z;  // a masked row sums nothing (y = 0)
     const int32_t a0 = b & ~3;
     const int nsteps = (e - a0 + 127) >> 7;
+    int lim = nsteps;
+    if constexpr (S::kPattern && SOUT) {
+        if (rest != nullptr) lim = min(nsteps, kLongFirst);
+    }
     bool hit = false;
     typename S::Acc acc;
     S::acc_zero(acc);
     Chunk<T, MASK, VEC> cur;
     chunk_load(cur, col, val, nnz, a0 + 4 * lane, b, e);
-    for (int t = 0; t < nsteps; ++t) {
+    for (int t = 0; t < lim; ++t) {
         const int32_t base = a0 + 128 * t + 4 * lane;
         Chunk<T, MASK, VEC> nxt;
         chunk_load(nxt, col, val, nnz, base + 128, b, e);
@@ -242,19 +255,67 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = S::part_add(v, shfl_xor(v, o));
     const bool h = SOUT && __any_sync(0xffffffffu, hit);
-    if (lane != 0) return;
     if constexpr (S::kPattern && SOUT) {
         // a Boolean sparse output is its flags: any segment with a true term
         // settles its row, so no partials and no fix-up
-        if (h) yflag[row] = 1;
+        if (h) {
+            if (lane == 0) yflag[row] = 1;
+        } else if (lim < nsteps) {
+            const int32_t r0 = a0 + 128 * lim;
+            const int32_t np = (e - r0 + kLongPiece - 1) / kLongPiece;
+            unsigned int q0 = 0;
+            if (lane == 0) q0 = atomicAdd(rest_n, (unsigned int)np);
+            q0 = __shfl_sync(0xffffffffu, q0, 0);
+            for (int32_t k = lane; k < np; k += 32)
+                rest[q0 + k] = make_int4(row, r0 + k * kLongPiece, min(e, r0 + (k + 1) * kLongPiece), 0);
+        }
         return;
     }
+    if (lane != 0) return;
     if (d.w) {
         y[row] = S::part_T(v);
         if (SOUT && h) yflag[row] = 1;
     } else {
         part[sg] = atom_bits(S::to_atom(v));
         if (SOUT) part_hit[sg] = h ? 1 : 0;
+    }
+}
+
+// The second pass of the Boolean list-output products: a warp per piece,
+// skipped when the row is already settled, stopping at the first true term.
+template <class T, bool MASK, bool VEC>
+__global__ void __launch_bounds__(256) k_pull_long_rest(const int4* __restrict__ rest,
+                                                        const unsigned int* __restrict__ rest_n, int64_t nnz,
+                                                        const int32_t* __restrict__ col, PullArg a, void* ywork,
+                                                        uint8_t* yflag) {
+    using S = Sr<T>;
+    const PullIO p = resolve(a, ywork, true);
+    const T* __restrict__ x = (const T*)p.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = *rest_n;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
+        const int4 d = rest[w];
+        int done = 0;
+        if (lane == 0) done = *(volatile const uint8_t*)(yflag + d.x);
+        if (__shfl_sync(0xffffffffu, done, 0)) continue;  // settled by another piece or the first chunks
+        const int32_t b = d.y, e = d.z;
+        const int nsteps = (e - b + 127) >> 7;
+        bool hit = false;
+        Chunk<T, MASK, VEC> cur;
+        chunk_load(cur, col, (const T*)nullptr, nnz, b + 4 * lane, b, e);
+        for (int t = 0; t < nsteps; ++t) {
+            const int32_t base = b + 128 * t + 4 * lane;
+            Chunk<T, MASK, VEC> nxt;
+            chunk_load(nxt, col, (const T*)nullptr, nnz, base + 128, b, e);
+            const typename S::Acc acc = chunk_sum<T, MASK, true, VEC>(cur, (const T*)nullptr, x, p.xbits, base, hit);
+            if (__any_sync(0xffffffffu, acc != 0u)) {
+                hit = true;
+                break;
+            }
+            cur = nxt;
+        }
+        if (lane == 0 && hit) yflag[d.x] = 1;
     }
 }
 
@@ -286,12 +347,27 @@ void launch_pull_long_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStr
     if (H->nseg == 0) return;
     const T* val = (const T*)H->val;
     const unsigned g = (unsigned)((H->nseg + 7) / 8);
+    // the second pass of Boolean list-output products (see k_pull_long)
+    const bool two = Sr<T>::kPattern && SOUT && H->long_rest != nullptr;
+    int4* rest = two ? H->long_rest : nullptr;
+    unsigned int* rest_n = two ? H->long_rest_n : nullptr;
     if (vec)
         k_pull_long<T, MASK, SOUT, true><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->seg, H->col, val, a, H->ws.ywork,
-                                                           H->ws.yflag, H->long_part, H->long_hit);
+                                                           H->ws.yflag, H->long_part, H->long_hit, rest, rest_n);
     else
         k_pull_long<T, MASK, SOUT, false><<<g, 256, 0, s>>>(H->nseg, H->nnz, H->seg, H->col, val, a, H->ws.ywork,
-                                                            H->ws.yflag, H->long_part, H->long_hit);
+                                                            H->ws.yflag, H->long_part, H->long_hit, rest, rest_n);
+    if constexpr (Sr<T>::kPattern && SOUT) {
+        if (two) {
+            const unsigned gr = (unsigned)H->num_sms * 4;
+            if (vec)
+                k_pull_long_rest<T, MASK, true><<<gr, 256, 0, s>>>(rest, rest_n, H->nnz, H->col, a, H->ws.ywork,
+                                                                   H->ws.yflag);
+            else
+                k_pull_long_rest<T, MASK, false><<<gr, 256, 0, s>>>(rest, rest_n, H->nnz, H->col, a, H->ws.ywork,
+                                                                    H->ws.yflag);
+        }
+    }
     if (H->nmulti > 0 && !(Sr<T>::kPattern && SOUT)) {
         const unsigned gf = (unsigned)std::min<int64_t>((H->nmulti + 255) / 256, (int64_t)H->num_sms * 4);
         k_pull_long_fixup<T><<<gf, 256, 0, s>>>(H->nmulti, H->multi_row, H->multi_base, H->rowptr, H->long_part,

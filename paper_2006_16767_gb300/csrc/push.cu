@@ -48,6 +48,26 @@ __device__ __forceinline__ void emit(const Ws& ws, const uint32_t* ymask, int32_
     }
 }
 
+// N write-backs of one thread (rows r[u] < 0 are skipped; item u's
+// effective index is pos0 + u * pstride). For a Boolean atomic write-back
+// all the flag reads are issued before any store.
+template <class T, int WB, int N>
+__device__ __forceinline__ void emit_batch(const Ws& ws, const uint32_t* ymask, const int32_t (&r)[N],
+                                           const typename Sr<T>::Part (&p)[N], int64_t pos0, int64_t pstride) {
+    if constexpr (WB == WB_ATOM && Sr<T>::kPattern) {
+        uint8_t f[N];
+#pragma unroll
+        for (int u = 0; u < N; ++u) f[u] = r[u] >= 0 ? ws.yflag[r[u]] : (uint8_t)1;
+#pragma unroll
+        for (int u = 0; u < N; ++u)
+            if (!f[u] && !row_masked(ymask, r[u])) ws.yflag[r[u]] = 1;
+    } else {
+#pragma unroll
+        for (int u = 0; u < N; ++u)
+            if (r[u] >= 0) emit<T, WB>(ws, ymask, r[u], p[u], pos0 + u * pstride);
+    }
+}
+
 template <class T>
 __device__ __forceinline__ T list_val(const CallDesc* d, int64_t t) {
     if (Sr<T>::kPattern || d->xval == nullptr) return Sr<T>::one();
@@ -166,8 +186,19 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
             pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
         }
         const bool lng = e - b > kLongCol;
-        if (!lng)
-            for (int32_t k = b; k < e; ++k) emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
+        if (!lng) {
+            // eight entries of the column loaded before their write-backs
+            for (int32_t k0 = b; k0 < e; k0 += 8) {
+                int32_t rr[8];
+                typename S::Part pp[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    rr[u] = k0 + u < e ? __ldg(rowidx + k0 + u) : -1;
+                    pp[u] = k0 + u < e ? S::mul(load_val(valc, k0 + u), xj) : typename S::Part(0);
+                }
+                emit_batch<T, WB, 8>(ws, ym, rr, pp, pos0 + k0, 1);
+            }
+        }
         // hubs go to the shared queue; the rest of the long columns to the warp
         const bool queued = lng && e - b > kLongSeg && queue_long(ws, t);
         for (unsigned pend = __ballot_sync(0xffffffffu, lng && !queued); pend; pend &= pend - 1) {
@@ -205,7 +236,17 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
             if (__shfl_sync(0xffffffffu, queued, 0)) continue;
         }
         const int64_t pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
-        for (int32_t k = b + lane; k < e; k += 32) emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
+        for (int32_t k0 = b + lane; k0 < e; k0 += 128) {
+            int32_t rr[4];
+            typename S::Part pp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t k = k0 + 32 * u;
+                rr[u] = k < e ? __ldg(rowidx + k) : -1;
+                pp[u] = k < e ? S::mul(load_val(valc, k), xj) : typename S::Part(0);
+            }
+            emit_batch<T, WB, 4>(ws, ym, rr, pp, pos0 + k0, 32);
+        }
     }
     help_long<T, WB, false>(colptr, rowidx, valc, desc, ws, ym, lane);
 }
@@ -274,15 +315,24 @@ __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ co
 #pragma unroll
             for (int u = 0; u < kPushIPT; ++u) s_t[w][lane * kPushIPT + u] = max(v[u], carry);
             __syncwarp();
-#pragma unroll 4
+            // every item's row index and value is loaded before the first
+            // write-back (a flag or accumulator store could alias a later
+            // load, so the compiler would not reorder them itself)
+            int32_t rr[kPushIPT];
+            typename S::Part pp[kPushIPT];
+#pragma unroll
             for (int s2 = 0; s2 < kPushIPT; ++s2) {
                 const int64_t e = e0 + s2 * 32 + lane;
-                if (e > elast) break;
-                const int q = s_t[w][s2 * 32 + lane];
-                const int64_t k = (int64_t)s_base[w][q] + e;
-                const T xq = S::kPattern ? S::one() : s_xv[w][S::kPattern ? 0 : q];
-                emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xq), e);
+                rr[s2] = -1;
+                if (e <= elast) {
+                    const int q = s_t[w][s2 * 32 + lane];
+                    const int64_t k = (int64_t)s_base[w][q] + e;
+                    const T xq = S::kPattern ? S::one() : s_xv[w][S::kPattern ? 0 : q];
+                    rr[s2] = __ldg(rowidx + k);
+                    pp[s2] = S::mul(load_val(valc, k), xq);
+                }
             }
+            emit_batch<T, WB, kPushIPT>(ws, ym, rr, pp, e0 + lane, 32);
             __syncwarp();
         } else {
 #pragma unroll 2

@@ -13,7 +13,15 @@ namespace asv {
 static_assert(kTreeNodesF32 <= kMaxTreeNodes && kTreeNodesBool <= kMaxTreeNodes,
               "compiled-in trees exceed the selector's node table");
 
-SelectArg select_arg(asv_matrix_s* H, unsigned long long cond) {
+void update_lazy(asv_matrix_s* H, const std::vector<TreeNode>& nodes, const int32_t* roots) {
+    for (int f = 0; f < 4; ++f) {
+        const int r = roots[kRootsPerFormat * f];
+        // a leaf, or a split on a matrix feature, nnz_x or x_sparsity (ids 0..10)
+        H->lazy_ok[f] = (f >= 2 && r >= 0 && r < (int)nodes.size() && nodes[r].feature < 11) ? 1 : 0;
+    }
+}
+
+SelectArg select_arg(asv_matrix_s* H, unsigned long long cond, int fmt) {
     SelectArg sa;
     const asv_mfeat& m = H->h_mfeat;
     const double mf[9] = {(double)m.m, (double)m.n, (double)m.nnz, (double)m.max_row, (double)m.min_row,
@@ -24,9 +32,11 @@ SelectArg select_arg(asv_matrix_s* H, unsigned long long cond) {
     sa.last_kid = H->d_last_kid;
     sa.cond = cond;
     sa.enabled = 1;
+    sa.lazy = (fmt >= 2 && fmt < 4) ? H->lazy_ok[fmt] : 0;
     sa.lcol = H->ws.lcol;
     sa.lcol_n = H->ws.lcol_n;
     sa.lcol_cap = H->ws.lcol_cap;
+    sa.long_rest_n = H->long_rest_n;
     return sa;
 }
 

@@ -36,6 +36,20 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
     desc->vfeat[3] = nnz > 0 ? (double)ns / (double)nnz : 0.0;
 }
 
+// Returns the push kernels' hub-column queue and the Boolean pull's
+// long-row piece queue of the previous call to their empty state (one
+// block, all its threads).
+template <int B>
+__device__ __forceinline__ void reset_hub_queue(const SelectArg& sa) {
+    if (threadIdx.x == 0 && sa.long_rest_n) *sa.long_rest_n = 0u;
+    if (!sa.lcol_n) return;
+    __shared__ int32_t s_nq;
+    if (threadIdx.x == 0) s_nq = min((int32_t)*(volatile unsigned int*)sa.lcol_n, sa.lcol_cap);
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < s_nq; i += B) sa.lcol[i] = make_int2(-1, 0);
+    if (threadIdx.x == 0) *sa.lcol_n = 0u;
+}
+
 // `blocks` is the number of blocks that take part (all of them call this);
 // the one that draws the last ticket publishes. ch counts the listed columns
 // longer than kLongSeg.
@@ -43,10 +57,9 @@ template <int B>
 __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long ch,
                                               unsigned long long* counters, unsigned int* ticket, CallDesc* desc,
                                               const DescInit& di, int64_t n, int64_t nnz, int32_t* status,
-                                              const SelectArg& sa, unsigned blocks) {
+                                              const SelectArg& sa, unsigned blocks, TreeNode* sn) {
     __shared__ unsigned long long sm[B / 32 + 1];
     __shared__ bool last;
-    __shared__ TreeNode sn[kMaxTreeNodes];
     cx = block_reduce_sum<B>(cx, sm);
     cs = block_reduce_sum<B>(cs, sm);
     ch = block_reduce_sum<B>(ch, sm);
@@ -76,13 +89,7 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
     }
     // the last block returns the push kernels' hub-column queue of the
     // previous call to its empty state
-    if (last && sa.lcol_n) {
-        __shared__ int32_t s_nq;
-        if (threadIdx.x == 0) s_nq = min((int32_t)*(volatile unsigned int*)sa.lcol_n, sa.lcol_cap);
-        __syncthreads();
-        for (int32_t i = threadIdx.x; i < s_nq; i += B) sa.lcol[i] = make_int2(-1, 0);
-        if (threadIdx.x == 0) *sa.lcol_n = 0u;
-    }
+    if (last) reset_hub_queue<B>(sa);
     // the last block also walks the selector's trees (Sec. VI-B), so the
     // choice is ready when the feature pass ends
     if (last && sa.enabled) {
@@ -119,6 +126,7 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
                                                   uint32_t* xbits, unsigned long long* counters, unsigned int* ticket,
                                                   CallDesc* desc, DescInit di, int64_t nnz, int32_t* status,
                                                   SelectArg sa) {
+    __shared__ TreeNode sn[kTreeWindow];
     const bool VEC = ((uintptr_t)x & 15) == 0;
     const int lane = threadIdx.x & 31;
     const int64_t nwords = (n + 31) >> 5;
@@ -182,7 +190,7 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
             }
         }
     }
-    finish_counts<B>(cx, cs, ch, counters, ticket, desc, di, n, nnz, status, sa, gridDim.x);
+    finish_counts<B>(cx, cs, ch, counters, ticket, desc, di, n, nnz, status, sa, gridDim.x, sn);
 }
 
 // Sparse x: nnz_s = sum of the listed columns' lengths.
@@ -191,12 +199,52 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
                                                    const int32_t* __restrict__ colptr, unsigned long long* counters,
                                                    unsigned int* ticket, CallDesc* desc, DescInit di, int64_t n,
                                                    int64_t nnz, int32_t* status, SelectArg sa) {
+    __shared__ TreeNode sn[kTreeWindow];
     int64_t nx = *nnz_x_dev;
     if (nx < 0) nx = 0;
     if (nx > n) nx = n + 1;  // reported and clamped when the totals are published
     // only the blocks the list reaches take part (a short list costs one block)
     const unsigned blocks = (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (min(nx, n) + B - 1) / B));
     if (blockIdx.x >= blocks) return;
+    // Lazy, cost-ordered evaluation (Sec. VI-C: cheap features first): a list
+    // gives nnz_x and x_sparsity for free, while nnz_s and m_sparsity cost a
+    // pass of gathers over its columns' pointers. When the call format's trees
+    // start with a free feature, every taking part block walks them with the
+    // free features alone; if the path needs no other feature and the chosen
+    // kernel reads neither nnz_s nor the hub count (the pull kernels and the
+    // warp push with atomics), block 0 publishes the call without them and
+    // the pass ends there.
+    if (sa.enabled && sa.lazy && nx <= n) {
+        __shared__ int s_kid;
+        int lo, hi;
+        const int* r = stage_trees(sa, 2 + di.out_mode, sn, lo, hi);
+        if (threadIdx.x == 0) {
+            double f[13];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) f[q] = sa.mf[q];
+            f[9] = (double)nx;
+            f[10] = n > 0 ? (double)nx / (double)n : 0.0;
+            f[11] = f[12] = 0.0;
+            int kid = pick_kernel(sn, lo, hi, sa.trees, r, f, 11);
+            if (!(kid >= ASV_K_PULL_THREAD && kid <= ASV_K_MPULL_BAL) && kid != ASV_K_PUSH_WARP_ATOM) kid = -1;
+            s_kid = kid;
+        }
+        __syncthreads();
+        const int kid = s_kid;
+        if (kid >= 0) {
+            if (blockIdx.x == 0) {
+                if (threadIdx.x == 0) {
+                    publish_desc(desc, di, (unsigned long long)nx, 0ull, 0ull, n, nnz);
+                    desc->nnz_s = -1;  // not computed
+                    desc->vfeat[2] = desc->vfeat[3] = -1.0;
+                    commit_kernel(sa, desc, kid);
+                }
+                reset_hub_queue<B>(sa);
+            }
+            return;
+        }
+        __syncthreads();  // sn is reused by the selector of the full pass
+    }
     // four list entries per thread in flight: their column lengths are
     // independent gathers
     const int64_t nl = min(nx, n);
@@ -221,7 +269,7 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
         ch += d > kLongSeg;
     }
     finish_counts<B>(blockIdx.x == 0 && threadIdx.x == 0 ? (unsigned long long)nx : 0ull, cs, ch, counters, ticket,
-                     desc, di, n, nnz, status, sa, blocks);
+                     desc, di, n, nnz, status, sa, blocks, sn);
 }
 
 // Few blocks per SM: every block of the feature pass ends with atomics on
@@ -301,13 +349,24 @@ __device__ __forceinline__ void scatter_bit(uint32_t* xbits, int32_t j, bool set
 // restores it to zero (clear). BITS: also the scatter bitmap, which only the
 // kernels that validate entries, flag output rows or read Boolean terms use.
 template <class T, bool BITS>
-__global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32_t* xbits, int set) {
+__global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32_t* xbits, int set, int64_t n) {
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
     const T* __restrict__ xval = (const T*)desc->xval;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const bool vals = xval && !Sr<T>::kPattern;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // a list covering more than a quarter of the columns is cleared by
+    // writing the whole workspace (16-byte stores) rather than by reading the
+    // list again and scattering zeros
+    if (!set && 4 * nx > n) {
+        const int64_t nv = (int64_t)((n * sizeof(T)) / 16);
+        for (int64_t i = t; i < nv; i += stride) reinterpret_cast<uint4*>(xdense)[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int64_t j = nv * (16 / (int64_t)sizeof(T)) + t; j < n; j += stride) xdense[j] = T(0);
+        if (BITS)
+            for (int64_t w = t; w < (n + 31) / 32; w += stride) xbits[w] = 0u;
+        return;
+    }
     // four entries per thread in flight (independent index and value loads)
     for (; t + 3 * stride < nx; t += 4 * stride) {
         int32_t j[4];
@@ -332,8 +391,8 @@ __global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32
 
 template <class T>
 static void x_scatter_dtype(asv_matrix_s* H, bool set, bool bits, int g, cudaStream_t s) {
-    if (bits) k_x_scatter<T, true><<<g, 256, 0, s>>>(H->d_desc, (T*)H->ws.xdense, H->ws.xbits_scat, set);
-    else k_x_scatter<T, false><<<g, 256, 0, s>>>(H->d_desc, (T*)H->ws.xdense, H->ws.xbits_scat, set);
+    if (bits) k_x_scatter<T, true><<<g, 256, 0, s>>>(H->d_desc, (T*)H->ws.xdense, H->ws.xbits_scat, set, H->n);
+    else k_x_scatter<T, false><<<g, 256, 0, s>>>(H->d_desc, (T*)H->ws.xdense, H->ws.xbits_scat, set, H->n);
 }
 
 void launch_x_scatter(asv_matrix_s* H, bool set, bool bits, cudaStream_t s) {
@@ -408,7 +467,10 @@ __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwor
     constexpr int RUN = BYTES ? kRun : 1;  // words per thread and round
     constexpr int CAP = B * 32;            // items per round at most
     __shared__ int32_t sm[B / 32 + 1];
-    __shared__ int32_t stage[CAP];
+    // slot k lives at k + k / 32: a thread writes its items to consecutive
+    // slots, so with every thread holding 32 items (a dense set) the lanes
+    // of a warp would otherwise all hit one bank at each step
+    __shared__ int32_t stage[CAP + CAP / 32];
     int64_t lo, hi;
     block_range(nwords, lo, hi);
     const bool vec = ((uintptr_t)words & 15) == 0;
@@ -436,7 +498,8 @@ __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwor
             while (mask) {
                 const int b = __ffs(mask) - 1;
                 mask &= mask - 1;
-                stage[p++] = (int32_t)(BYTES ? w * 4 + (b >> 3) : w * 32 + b);
+                stage[p + (p >> 5)] = (int32_t)(BYTES ? w * 4 + (b >> 3) : w * 32 + b);
+                ++p;
             }
         }
         __syncthreads();
@@ -449,7 +512,7 @@ __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwor
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int32_t k = k0 + u * B;
-                j[u] = k < tot ? stage[k] : 0;
+                j[u] = k < tot ? stage[k + (k >> 5)] : 0;
                 if (k < tot) v[u] = pol.load(j[u]);
             }
 #pragma unroll
@@ -562,52 +625,39 @@ void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- dense write-out of the push accumulators
-// Sixteen rows per thread: one 16-byte load of their flags (the flag array is
-// padded to a multiple of 16 bytes, so the load never leaves it), then y_i =
-// the accumulator of a flagged row (re-zeroed) or 0, written with 16-byte
-// stores when y is 16-byte aligned. Most groups of a sparse product have no
-// flag set and only write zeros.
-constexpr int kFinRows = 16;
+// y_i = the accumulator of a flagged row (re-zeroed, its flag cleared) or 0.
+// Grid-stride over rows with consecutive threads on consecutive rows (every
+// warp access is one run of 32 rows), four rows per thread in flight: all
+// their flag and accumulator loads are issued before the stores.
 template <class T>
 __global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, typename Sr<T>::Atom* acc, uint8_t* yflag,
                                                         const CallDesc* __restrict__ desc) {
     using S = Sr<T>;
     T* __restrict__ y = (T*)desc->y;
-    const bool vec = ((uintptr_t)y & 15) == 0;
-    const int64_t ngroups = (m + kFinRows - 1) / kFinRows;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i0 = g * kFinRows;
-        const uint4 fw = *reinterpret_cast<const uint4*>(yflag + i0);
-        const bool any = (fw.x | fw.y | fw.z | fw.w) != 0u;
-        T v[kFinRows];
-        const uint8_t* fb = reinterpret_cast<const uint8_t*>(&fw);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += 4 * stride) {
+        bool f[4];
+        T v[4];
 #pragma unroll
-        for (int u = 0; u < kFinRows; ++u) {
-            if (S::kPattern) v[u] = fb[u] ? S::one() : T(0);
-            else v[u] = T(0);
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * stride;
+            f[u] = i < m && yflag[i] != 0;
         }
-        if (any) {
-            if constexpr (!S::kPattern) {
 #pragma unroll
-                for (int u = 0; u < kFinRows; ++u)
-                    if (fb[u]) v[u] = S::from_atom(acc[i0 + u]);
-#pragma unroll
-                for (int u = 0; u < kFinRows; ++u)
-                    if (fb[u]) acc[i0 + u] = typename S::Atom(0);
-            }
-            *reinterpret_cast<uint4*>(yflag + i0) = make_uint4(0u, 0u, 0u, 0u);
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (S::kPattern) v[u] = f[u] ? S::one() : T(0);
+            else v[u] = f[u] ? S::from_atom(acc[i]) : T(0);
         }
-        if (vec && i0 + kFinRows <= m) {
-            constexpr int kPer = 16 / sizeof(T);
 #pragma unroll
-            for (int u = 0; u < kFinRows; u += kPer) {
-                uint4 w;
-                memcpy(&w, &v[u], 16);
-                *reinterpret_cast<uint4*>(y + i0 + u) = w;
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= m) break;
+            y[i] = v[u];
+            if (f[u]) {
+                if (!S::kPattern) acc[i] = typename S::Atom(0);
+                yflag[i] = 0;
             }
-        } else {
-            for (int u = 0; u < kFinRows && i0 + u < m; ++u) y[i0 + u] = v[u];
         }
     }
 }
@@ -617,8 +667,7 @@ static void finalize_dtype(asv_matrix_s* H, bool from_acc, int out_mode, cudaStr
     using Atom = typename Sr<T>::Atom;
     if (out_mode == ASV_OUT_DENSE) {
         if (H->m > 0) {
-            const int64_t ngroups = (H->m + kFinRows - 1) / kFinRows;
-            const int64_t g = std::min<int64_t>((ngroups + 255) / 256, (int64_t)H->num_sms * 8);
+            const int64_t g = std::min<int64_t>((H->m + 1023) / 1024, (int64_t)H->num_sms * 8);
             k_finalize_dense<T><<<(unsigned)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag, H->d_desc);
         }
     } else if (from_acc) {

@@ -11,7 +11,10 @@ frontier of a BFS is the union of the ranks' parts.
 
 The exchange runs through torch.distributed (NCCL between GPUs, gloo on CPU
 ranks in tests). The local product is a callable, so the same driver serves
-the library's device kernels and host-side checks.
+the library's device kernels and host-side checks. allgather_list reads the
+list lengths on the host; allgather_list_device keeps them on the device
+(padded exchange, packing by a scatter), so a device-side loop of products
+is not stalled by the exchange.
 """
 from __future__ import annotations
 
@@ -70,6 +73,49 @@ def allgather_list(idx: torch.Tensor, val: torch.Tensor | None, group=None):
     gv = [torch.empty_like(pad_v) for _ in range(world)]
     dist.all_gather(gv, pad_v, group=group)
     return out_i, torch.cat([g[:s] for g, s in zip(gv, sizes)])
+
+
+def list_capacity(bounds):
+    """Entries a rank's part of x can hold at most: its row-block length
+    (x shares the row partition, and listed ids are distinct)."""
+    return max(1, max(bounds[r + 1] - bounds[r] for r in range(len(bounds) - 1)))
+
+
+def allgather_list_device(idx: torch.Tensor, val: torch.Tensor | None, count: torch.Tensor, cap: int,
+                          group=None):
+    """All-gather of variable-length lists without a host synchronisation:
+    every rank sends its list padded to `cap` entries and its length as a
+    one-element int64 tensor `count` (on the lists' device); the gathered
+    segments are packed in rank order by a scatter whose target positions
+    come from the counts' prefix sums, all on the device. Returns
+    (idx_buffer, val_buffer or None, total) where the first `total` entries
+    (a one-element device tensor, the form the library's list count takes)
+    hold the concatenation. No operation reads a count on the host, so the
+    exchange can sit between device-side products without stalling them."""
+    world = dist.get_world_size(group)
+    dev = idx.device
+    counts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(counts, count.reshape(1).to(torch.int64), group=group)
+    counts = torch.cat(counts)
+    offs = torch.cumsum(counts, 0) - counts
+    pos = torch.arange(cap, dtype=torch.int64, device=dev)
+    # target of entry i of rank r: offs[r] + i when i < counts[r], else the
+    # dump slot world * cap (one past the packed region's largest extent)
+    tgt = torch.where(pos[None, :] < counts[:, None], offs[:, None] + pos[None, :],
+                      torch.full((1, 1), world * cap, dtype=torch.int64, device=dev)).reshape(-1)
+
+    def gather_pack(t):
+        pad = torch.zeros(cap, dtype=t.dtype, device=dev)
+        pad[: t.numel()] = t
+        parts = [torch.empty_like(pad) for _ in range(world)]
+        dist.all_gather(parts, pad, group=group)
+        out = torch.zeros(world * cap + 1, dtype=t.dtype, device=dev)
+        out.scatter_(0, tgt, torch.cat(parts))
+        return out
+
+    out_i = gather_pack(idx)
+    out_v = None if val is None else gather_pack(val)
+    return out_i, out_v, counts.sum().reshape(1)
 
 
 def partitioned_spmspv(local_product, x_idx_local, x_val_local, group=None):

@@ -268,7 +268,7 @@ def load(path):
 TREE_FEATURES = (MODEL_FEATURES[0], tuple(range(13)), tuple(range(13)), tuple(range(13)), MODEL_FEATURES[2])
 
 
-def _fit_one(X, y, seed):
+def _fit_one(X, y, seed, leaf_nodes=(8, 16, 24)):
     from sklearn.model_selection import GridSearchCV, train_test_split
     from sklearn.tree import DecisionTreeClassifier
     if len(set(y.tolist())) < 2 or len(y) < 10:
@@ -277,17 +277,57 @@ def _fit_one(X, y, seed):
     Xtr, Xte, ytr, yte = train_test_split(X, y, test_size=0.3, random_state=seed)
     folds = max(2, min(5, int(np.bincount(ytr).min()) if len(set(ytr.tolist())) > 1 else 2))
     # max_leaf_nodes keeps the 20 trees of a value type within the selector's
-    # 1024-node table (at most 47 nodes each)
+    # 2048-node table (at most 47 nodes each, 135 for a cost-ordered one)
     gs = GridSearchCV(DecisionTreeClassifier(random_state=seed),
                       {"max_depth": list(range(1, 11)), "class_weight": [None, "balanced"],
-                       "max_leaf_nodes": [8, 16, 24]}, cv=folds)
+                       "max_leaf_nodes": list(leaf_nodes)}, cv=folds)
     gs.fit(Xtr, ytr)
     acc = float(gs.score(Xte, yte))
     clf = DecisionTreeClassifier(random_state=seed, **gs.best_params_).fit(X, y)
     return clf, None, acc
 
 
-def fit(path, seed=0, rows=None):
+# Features a listed x gives without a pass over it: the matrix features,
+# nnz_x and x_sparsity (nnz_s and m_sparsity need the list's column pointers).
+CHEAP = tuple(range(11))
+# the trees a lazy decision walks: pattern, then the masked-pull or pull
+# distribution (the push kernels the lazy path may run need no other tree)
+LAZY_TREES = (0, 2, 3)
+
+
+def _fit_cost_ordered(X, y, cols, seed, impure=0.05, min_leaf=20):
+    """A tree whose upper levels test only the cheap features (Sec. VI-C:
+    rules on cheap features first): a CART tree fitted on the cheap columns,
+    whose leaves that still mix labels (more than `impure` of their samples
+    off the majority) are replaced by a small tree fitted on every column of
+    the tree's samples there. Returns (nodes, accuracy of stage one)."""
+    from sklearn.tree import DecisionTreeClassifier
+    c1 = [c for c in cols if c in CHEAP]
+    clf1, leaf1, acc1 = _fit_one(X[:, c1], y, seed, leaf_nodes=(4, 8))
+    if clf1 is None:
+        return [(-1, 0.0, 0, 0, leaf1)], acc1
+    out = export_tree(clf1, c1)
+    leaves = clf1.apply(X[:, c1])
+    for li in sorted(set(leaves.tolist())):
+        sel = leaves == li
+        ys = y[sel]
+        if len(ys) < min_leaf or len(set(ys.tolist())) < 2:
+            continue
+        if float(np.mean(ys != np.bincount(ys).argmax())) <= impure:
+            continue
+        clf2 = DecisionTreeClassifier(random_state=seed, max_leaf_nodes=8, min_samples_leaf=3).fit(X[sel][:, cols], ys)
+        sub = export_tree(clf2, cols)
+        base = len(out)
+        # sub's root takes the leaf's place; its other nodes are appended
+        remap = lambda c: base + c - 1  # noqa: E731
+        f, thr, l, r, lf = sub[0]
+        out[li] = (f, thr, remap(l), remap(r), lf) if f >= 0 else sub[0]
+        for (f, thr, l, r, lf) in sub[1:]:
+            out.append((f, thr, remap(l), remap(r), lf) if f >= 0 else (f, thr, 0, 0, lf))
+    return out, acc1
+
+
+def fit(path, seed=0, rows=None, cost_ordered=False):
     import warnings
     warnings.filterwarnings("ignore")
     rows = rows if rows is not None else load(path)
@@ -300,8 +340,11 @@ def fit(path, seed=0, rows=None):
             Y = np.asarray([labels(r["t"]) for r in sub], np.int64).reshape(-1, 5)
             for tree in range(5):
                 cols = TREE_FEATURES[tree]
-                clf, leaf, acc = _fit_one(X[:, cols] if len(sub) else X, Y[:, tree], seed)
-                nodes_m = export_tree(clf, cols) if clf is not None else [(-1, 0.0, 0, 0, leaf)]
+                if cost_ordered and fmt >= 2 and tree in LAZY_TREES and len(sub):
+                    nodes_m, acc = _fit_cost_ordered(X, Y[:, tree], cols, seed)
+                else:
+                    clf, leaf, acc = _fit_one(X[:, cols] if len(sub) else X, Y[:, tree], seed)
+                    nodes_m = export_tree(clf, cols) if clf is not None else [(-1, 0.0, 0, 0, leaf)]
                 base = len(nodes)
                 for (f, thr, l, r, lf) in nodes_m:
                     nodes.append((f, thr, l + base if f >= 0 else 0, r + base if f >= 0 else 0, lf))
@@ -351,6 +394,47 @@ def regret(path, trees, rows=None):
     return {f"{dt}/fmt{f}": {"mean": round(float(np.mean(v)), 4), "p90": round(float(np.percentile(v, 90)), 4),
                              "max": round(float(np.max(v)), 4), "samples": len(v)}
             for (dt, f), v in sorted(out.items())}
+
+
+def lazy_walk(trees, dt, fmt, feat):
+    """The device's lazy decision for a listed x (Sec. VI-C): the kernel the
+    trees pick from the cheap features alone, or None when the path needs
+    nnz_s / m_sparsity or the kernel reads them (every push kernel but the
+    warp push with atomics)."""
+    if fmt < 2:
+        return None
+    T = trees[dt if dt in trees else "f32"]
+    nodes, roots = T["nodes"], T["roots"]
+
+    def walk(root):
+        i = root
+        while nodes[i][0] >= 0:
+            f, thr, l, r, _ = nodes[i]
+            if f not in CHEAP:
+                return None
+            i = l if feat[f] <= thr else r
+        return nodes[i][4]
+    r = roots[5 * fmt: 5 * fmt + 5]
+    pat = walk(r[0])
+    if pat is None:
+        return None
+    pat = min(max(pat, 0), 2)
+    dist = walk(r[1 + pat])
+    wb = walk(r[4]) if pat == 0 else 0
+    if dist is None or wb is None:
+        return None
+    k = kernel_id(pat, dist, wb)
+    return k if k <= 5 or k == 7 else None
+
+
+def lazy_fraction(trees, rows):
+    """Share of the listed-x samples the lazy walk decides, per value type."""
+    out = {}
+    for dt in sorted({r["dtype"] for r in rows}):
+        sub = [r for r in rows if r["dtype"] == dt and r["fmt"] >= 2]
+        got = [lazy_walk(trees, dt, r["fmt"], r["feat"]) is not None for r in sub]
+        out[dt] = round(float(np.mean(got)), 4) if got else 0.0
+    return out
 
 
 def held_out(path, seed=0):
@@ -470,9 +554,10 @@ if __name__ == "__main__":
     if cmd == "collect":
         collect(sys.argv[2], budget_s=float(sys.argv[3]) if len(sys.argv) > 3 else 900.0)
     elif cmd == "fit":
-        trees, rep = fit(sys.argv[2])
+        trees, rep = fit(sys.argv[2], cost_ordered="--cost-ordered" in sys.argv)
         print(json.dumps(rep, indent=1))
         print(json.dumps(regret(sys.argv[2], trees), indent=1))
+        print(json.dumps({"lazy_fraction": lazy_fraction(trees, load(sys.argv[2]))}))
         if "--held-out" in sys.argv:
             print(json.dumps(held_out(sys.argv[2]), indent=1))
         if "--emit" in sys.argv:

@@ -70,8 +70,18 @@ def worker(rank, world, port, q):
         nxt_local = (np.flatnonzero(yb) + r0).astype(np.int32)
         fr = [None] * world
         dist.all_gather_object(fr, nxt_local)
+        # the same exchange with the lengths kept in device tensors: the packed
+        # buffer's first `total` entries equal the host-side concatenation
+        cap = pdist.list_capacity(bounds)
+        xi, xv = torch.from_numpy(idx[mine]), torch.from_numpy(val[mine])
+        bi, bv, tot = pdist.allgather_list_device(xi, xv, torch.tensor([xi.numel()], dtype=torch.int64), cap)
+        hi, hv = pdist.allgather_list(xi, xv)
+        k = int(tot.item())
+        same = k == hi.numel() and torch.equal(bi[:k], hi) and torch.equal(bv[:k], hv)
+        ei, ev, etot = pdist.allgather_list_device(xi[:0], None, torch.zeros(1, dtype=torch.int64), cap)
+        same = same and int(etot.item()) == 0 and ev is None
         if rank == 0:
-            q.put(("ok", bounds, parts, fr, len(c)))
+            q.put(("ok", bounds, parts, fr, len(c), same))
         dist.barrier()
         dist.destroy_process_group()
     except Exception as e:  # report to the parent instead of hanging it
@@ -101,7 +111,8 @@ def test_gloo_ranks_reassemble_the_product(world):
     for p in procs:
         p.join(timeout=60)
     assert res[0] == "ok", res
-    _, bounds, parts, fr, nnz = res
+    _, bounds, parts, fr, nnz, same = res
+    assert same, "device-count exchange differs from the host-count one"
     rp, c = gen.rmat(12, 8, seed=21)
     n = 1 << 12
     v = gen.uniform(len(c), -1, 1, seed=22)

@@ -131,6 +131,43 @@ def test_backward_matches_oracle():
     assert_rows_close(dA, ref, scale, "f32", "dA")
 
 
+def test_backward_with_a_listed_batch_matches_oracle():
+    # the same gradients with X given as a CSR of vectors: offsets that do
+    # not start at 0 (they are relative to xptr[0], as for a slice of a
+    # larger batch), listed explicit zeros (they contribute nothing), and a
+    # batch without values (all ones)
+    m, n, B = 700, 500, 40
+    rp, c, v = gen.bernoulli(m, n, 0.05, 0.02, 15)
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), to_dev(v))
+    colptr, rowidx, perm = oracle.csr_to_csc(m, n, rp, c)
+    vv = v.astype(np.float64)
+    lists = [gen.sample_positions(n, int(k), seed=16 + b, stream=1) for b, k in
+             enumerate(np.linspace(1, n // 2, B).astype(int))]
+    xptr = np.concatenate([[7], 7 + np.cumsum([len(q) for q in lists])]).astype(np.int64)
+    xidx = np.concatenate(lists).astype(np.int32)
+    dY = gen.uniform(B * m, -1, 1, 17, 0, np.float32).reshape(B, m)
+    for with_vals in (True, False):
+        xval = gen.uniform(len(xidx), -1, 1, 18, 0, np.float32)
+        xval[::5] = 0.0
+        Xd = np.zeros((B, n))
+        for b in range(B):
+            lo, hi = xptr[b] - xptr[0], xptr[b + 1] - xptr[0]
+            Xd[b, xidx[lo:hi]] = xval[lo:hi] if with_vals else 1.0
+        dX, dA = A.backward_list(to_dev(xptr), to_dev(xidx), to_dev(xval) if with_vals else None, to_dev(dY))
+        dX, dA = dX.cpu().numpy(), dA.cpu().numpy()
+        assert A.status() == asv.ASV_OK
+        for b in range(B):
+            ref, s = oracle.csc_pull(colptr, rowidx, vv[perm], dY[b].astype(np.float64))
+            assert_rows_close(dX[b], ref, s, "f32", f"dx vector {b}")
+        ref = np.zeros(len(c))
+        scale = np.zeros(len(c))
+        for b in range(B):
+            g = oracle.grad_values(rp, c, dY[b].astype(np.float64), Xd[b])
+            ref += g
+            scale += np.abs(g)
+        assert_rows_close(dA, ref, scale, "f32", f"dA (values={with_vals})")
+
+
 def test_autograd_layer_against_fp64_finite_differences():
     # the leading 256 x 256 block of the differentiable-layer workload's own
     # matrix (16384^2, 5%-dense Bernoulli pattern, N(0, 0.02) values), with

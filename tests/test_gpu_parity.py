@@ -10,7 +10,7 @@ import torch
 
 import gen
 import oracle
-from tests._util import TOL, assert_rows_close
+from tests._util import TOL, assert_rows_close, sparse_result
 
 pytestmark = pytest.mark.gpu
 
@@ -376,3 +376,58 @@ def test_set_trees_drives_the_switch_branch():
         assert kid == want
     with pytest.raises(asv.AsvError):
         A.set_trees([(0, 1.0, 5, 6, 0)], [0] * 20)  # child index out of range
+
+
+def test_lazy_feature_evaluation_for_listed_x():
+    # trees whose list-format pattern root splits on x_sparsity (a free
+    # feature of a listed x): below the threshold the decision needs
+    # m_sparsity (full feature pass), above it the pull / masked pull / warp
+    # push named by the leaves is decided without the pass. Every call must
+    # give the oracle's result and run the kernel the full walk (asv_select)
+    # names; the structural output set must match too.
+    name, m, n, rp, c, v = mat_skewed(np.float32)
+    A = make(m, n, rp, c, v)
+    for hi_pat, hi_dist, lo_pat in [(2, 1, 0), (1, 0, 2), (0, 1, 1), (0, 2, 2)]:
+        # 0: x_sparsity <= 0.05 ? node 1 : leaf hi_pat; 1: m_sparsity <= 0.5 ? leaf lo_pat : leaf 0
+        nodes = [(10, 0.05, 1, 2, 0), (12, 0.5, 3, 4, 0), (-1, 0, 0, 0, hi_pat), (-1, 0, 0, 0, lo_pat),
+                 (-1, 0, 0, 0, 0), (-1, 0, 0, 0, hi_dist), (-1, 0, 0, 0, 0)]
+        A.set_trees(nodes, [0, 5, 5, 5, 6] * 4)
+        for rho in (0.01, 0.2):
+            k = int(rho * n)
+            idx, val = gen.sparse_x(n, k, 33, 11, np.float32)
+            y_ref, s, hit = oracle.spmspv_rowmajor(n, rp, c, v.astype(np.float64), idx, val.astype(np.float64))
+            kid_d, _ = A.select(xidx=to_dev(idx), xval=to_dev(val))
+            y = A.spmspv(xidx=to_dev(idx), xval=to_dev(val))
+            assert A.last_kernel() == kid_d
+            assert_rows_close(y.cpu().numpy(), y_ref, s, "f32", f"lazy {asv.KERNELS[kid_d]} rho={rho}")
+            kid_s, _ = A.select(xidx=to_dev(idx), xval=to_dev(val), sparse_out=True)
+            yi, yv, ny = A.spmspv(xidx=to_dev(idx), xval=to_dev(val), sparse_out=True)
+            assert A.last_kernel() == kid_s
+            got_idx, got_val = sparse_result(yi, yv, ny)
+            assert np.array_equal(got_idx, np.flatnonzero(hit))
+            assert_rows_close(got_val, y_ref[got_idx], s[got_idx], "f32", f"lazy list out rho={rho}")
+            assert A.status() == asv.ASV_OK
+
+
+def test_single_call_autotuner_keeps_results_and_caches(tmp_path):
+    # the tuner changes only the pull kernels' launch shape: every setting it
+    # keeps must give the oracle's result, and a cached setting is reused
+    for dt in (np.float32, np.float64):
+        name, m, n, rp, c, v = mat_skewed(dt)
+        A = make(m, n, rp, c, v)
+        cache = tmp_path / "pull.tsv"
+        t1 = A.autotune(cache_path=cache, budget_ms=3000)
+        assert t1[0] in (2, 4, 8, 16, 32) and t1[1] in (2, 4) and t1[2] in (0, 1)
+        assert A.pull_tuning() == t1
+        lines = cache.read_text().strip().splitlines()
+        assert len(lines) >= 1 and lines[-1].endswith("\t".join(str(q) for q in t1))
+        B = make(m, n, rp, c, v)
+        assert B.autotune(cache_path=cache, budget_ms=0) == t1 and B.pull_tuning() == t1
+        assert len(cache.read_text().strip().splitlines()) == len(lines)  # read, not appended
+        x = gen.uniform(n, -1, 1, 91).astype(dt)
+        y_ref, s = oracle.csr_pull(rp, c, v.astype(np.float64), x.astype(np.float64))
+        for k in ("pull_thread", "pull_warp", "auto"):
+            y = A.spmv(to_dev(x), kernel=k).cpu().numpy()
+            assert_rows_close(y, y_ref, s, "f32" if dt == np.float32 else "f64", f"tuned {k}")
+        # a zero budget still returns a valid setting (the creation-time one)
+        assert make(m, n, rp, c, v).autotune(budget_ms=0)[0] in (2, 4, 8, 16, 32)

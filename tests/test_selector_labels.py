@@ -86,3 +86,54 @@ def test_host_tree_walk_follows_thresholds():
     assert st.predict(trees, "f32", 2, f) == st.kernel_id(PUSH, 2, 0)
     f[12] = 0.5
     assert st.predict(trees, "f32", 3, f) == st.kernel_id(PULL, 1, 0)
+
+
+def _walk(nodes, root, feat):
+    i = root
+    path = []
+    while nodes[i][0] >= 0:
+        f, thr, l, r, _ = nodes[i]
+        path.append(f)
+        i = l if feat[f] <= thr else r
+    return nodes[i][4], path
+
+
+def test_cost_ordered_tree_tests_cheap_features_first():
+    import pytest
+    pytest.importorskip("sklearn")
+    # labels: x_sparsity (feature 10, cheap) splits pull from the rest; among
+    # the sparse samples, m_sparsity (feature 12, a pass over the list)
+    # separates push from masked pull
+    rng = np.random.default_rng(3)
+    X = np.zeros((600, 13))
+    X[:, 10] = rng.uniform(0, 1, 600)
+    X[:, 12] = rng.uniform(0, 1, 600)
+    X[:, 2] = 1e6
+    y = np.where(X[:, 10] > 0.5, PULL, np.where(X[:, 12] > 0.3, MPULL, PUSH)).astype(np.int64)
+    nodes, _ = st._fit_cost_ordered(X, y, tuple(range(13)), seed=0)
+    n = len(nodes)
+    for (f, thr, l, r, lf) in nodes:  # a valid table: children inside it
+        assert f < 0 or (0 <= l < n and 0 <= r < n)
+    assert nodes[0][0] in st.CHEAP  # the root splits on a cheap feature
+    agree = 0
+    for x, lab in zip(X, y):
+        got, path = _walk(nodes, 0, x)
+        agree += got == lab
+        if lab == PULL:  # the dense side is decided from cheap features alone
+            assert all(f in st.CHEAP for f in path)
+    assert agree / len(y) > 0.97
+
+
+def test_lazy_walk_decides_only_on_cheap_paths():
+    # pattern tree: x_sparsity <= 0.5 -> test m_sparsity, else pull; pull and
+    # masked-pull distribution trees: thread; push trees: warp, atomic
+    nodes = [(10, 0.5, 1, 2, 0), (12, 0.1, 3, 4, 0), (-1, 0.0, 0, 0, PULL), (-1, 0.0, 0, 0, PUSH),
+             (-1, 0.0, 0, 0, MPULL), (-1, 0.0, 0, 0, 0), (-1, 0.0, 0, 0, 1), (-1, 0.0, 0, 0, 0)]
+    roots = [0, 6, 5, 5, 7] * 4
+    trees = {"f32": {"nodes": nodes, "roots": roots}}
+    feat = [0.0] * 13
+    feat[10] = 0.9
+    assert st.lazy_walk(trees, "f32", 3, feat) == st.kernel_id(PULL, 0, 0)
+    assert st.lazy_walk(trees, "f32", 0, feat) is None  # dense x: no lazy path
+    feat[10] = 0.1
+    assert st.lazy_walk(trees, "f32", 2, feat) is None  # needs m_sparsity
