@@ -344,23 +344,47 @@ class Stencil256:
         return h2d, d2h
 
     def e2e_step(self):
+        """One step through the public API with its copies: every call's input
+        goes host -> device on a copy stream and the call waits only for its
+        own input, so later inputs cross the link while earlier products run;
+        every dense output goes back on a second copy stream as soon as its
+        product is done; the list outputs, whose sizes only the device knows,
+        go back after one read of their counts at the end."""
         torch = self.torch
-        for h, d in zip(self.h_idx + self.h_val + self.h_xd, self.d_idx + self.d_val + self.d_xd):
-            d.copy_(h, non_blocking=True)
-        self.d_cnt.copy_(self.h_cnt, non_blocking=True)
-        for c in self.calls:
+        cur = torch.cuda.current_stream()
+        if not hasattr(self, "s_in"):
+            self.s_in, self.s_out = torch.cuda.Stream(), torch.cuda.Stream()
+            self.ev_in = [torch.cuda.Event() for _ in self.calls]
+            self.ev_done = [torch.cuda.Event() for _ in self.calls]
+        self.s_in.wait_stream(cur)
+        self.s_out.wait_stream(cur)
+        with torch.cuda.stream(self.s_in):
+            self.d_cnt.copy_(self.h_cnt, non_blocking=True)
+            for j, c in enumerate(self.calls):
+                i = c["i"]
+                if c["fmt"] == "list":
+                    self.d_idx[i].copy_(self.h_idx[i], non_blocking=True)
+                    self.d_val[i].copy_(self.h_val[i], non_blocking=True)
+                else:
+                    self.d_xd[i].copy_(self.h_xd[i], non_blocking=True)
+                self.ev_in[j].record(self.s_in)
+        for j, c in enumerate(self.calls):
             i = c["i"]
+            cur.wait_event(self.ev_in[j])
             self.call(c, "auto", self.d_idx[i], self.d_val[i], self.d_xd[i], self.d_cnt[i])
-        for c in self.calls:
+            self.ev_done[j].record(cur)
             if c["fmt"] == "dense":
-                self.h_yd[c["i"]].copy_(self.yd[c["i"]], non_blocking=True)
+                self.s_out.wait_event(self.ev_done[j])
+                with torch.cuda.stream(self.s_out):
+                    self.h_yd[i].copy_(self.yd[i], non_blocking=True)
         self.h_nnzy.copy_(self.nnz_y, non_blocking=True)
-        torch.cuda.current_stream().synchronize()  # the list sizes decide the copies
+        cur.synchronize()  # the list sizes decide the copies
         for c in self.calls:
             if c["fmt"] == "list":
                 i, k = c["i"], int(self.h_nnzy[c["i"]])
                 self.h_yidx[i][:k].copy_(self.yidx[i][:k], non_blocking=True)
                 self.h_yval[i][:k].copy_(self.yval[i][:k], non_blocking=True)
+        cur.wait_stream(self.s_out)
 
     def config(self):
         return {"workload": self.name, "matrix": f"27-point stencil {self.side}^3, FP32, CSR + CSC resident",
@@ -436,7 +460,8 @@ class Rmat22:
         self.n = self.m = 1 << scale
         self.nnz = len(self.col)
         self.long_extra = long_row_launches(self.rowptr)
-        self.long_extra_flags = min(self.long_extra, 1)  # a Boolean sparse output needs no fix-up
+        # a Boolean list output: the long-row pass and its second pass, no fix-up
+        self.long_extra_flags = 2 if self.long_extra else 0
         deg = np.diff(self.rowptr)
         cand = np.flatnonzero(deg > 0)
         pick = gen.randint(roots, len(cand), gen.config_seed(2), stream=7)

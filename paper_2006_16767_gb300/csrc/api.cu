@@ -229,7 +229,9 @@ static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s
     AL(w.xlist_val, vs * n, false);
     AL(w.xscan, 4 * (n + 1), false);
     AL(w.acc, 8 * m, true);
-    AL(w.yflag, (m + 16) & ~(int64_t)15, true);
+    // padded to whole 512-row groups: the dense write-out loads the flags of
+    // a group with 16-byte loads whatever m is
+    AL(w.yflag, ((m + 511) & ~(int64_t)511) + 16, true);
     AL(w.ywork, vs * m, false);
     const size_t pv = vs == 8 ? 8 : 4;
     AL(w.pkeys[0], 4 * nnz, false);

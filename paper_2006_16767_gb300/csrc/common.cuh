@@ -225,7 +225,8 @@ struct Ws {
     void* xlist_val;         // n values
     int32_t* xscan;          // n+1 exclusive scan of listed column lengths
     void* acc;               // m 8-byte accumulators, zero-invariant
-    uint8_t* yflag;          // m bytes (padded), zero-invariant: rows in the structural output set
+    uint8_t* yflag;          // m bytes (padded to whole 512-byte groups), zero-invariant: rows in the
+                             // structural output set
     void* ywork;             // m values (pull kernels' dense y in sparse-output mode)
     uint32_t* pkeys[2];      // pair buffers for sort / privatised write-back
     void* pvals[2];

@@ -206,23 +206,37 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
         S::acc_zero(acc);
         if (mine && !off) {
             int32_t k = rb;
-            if constexpr (!MASK && !SOUT && kStageVals) {
+            if constexpr (!MASK && kStageVals) {
                 // eight gathers in flight per lane before their products are
-                // added (the gathers, not HBM, bound a lane's walk of its row)
+                // added (the gathers, not HBM, bound a lane's walk of its row);
+                // with a list output the same columns' bits say whether the
+                // row is in the structural output set
                 constexpr int GD = 8;
                 for (; k + GD <= re; k += GD) {
                     T xg[GD];
+                    uint32_t hb = 0u;
 #pragma unroll
-                    for (int u = 0; u < GD; ++u) xg[u] = __ldg(x + sc[k + u - a0]);
+                    for (int u = 0; u < GD; ++u) {
+                        const int32_t c = sc[k + u - a0];
+                        xg[u] = __ldg(x + c);
+                        if (SOUT) hb |= (uint32_t)test_bit(p.xbits, c);
+                    }
 #pragma unroll
                     for (int u = 0; u < GD; ++u) S::acc_add(acc, S::mul(val ? sv[k + u - a0] : S::one(), xg[u]));
+                    if (SOUT) hit |= hb != 0u;
                 }
                 if (k + 4 <= re) {
                     T xg[4];
+                    uint32_t hb = 0u;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) xg[u] = __ldg(x + sc[k + u - a0]);
+                    for (int u = 0; u < 4; ++u) {
+                        const int32_t c = sc[k + u - a0];
+                        xg[u] = __ldg(x + c);
+                        if (SOUT) hb |= (uint32_t)test_bit(p.xbits, c);
+                    }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) S::acc_add(acc, S::mul(val ? sv[k + u - a0] : S::one(), xg[u]));
+                    if (SOUT) hit |= hb != 0u;
                     k += 4;
                 }
             }

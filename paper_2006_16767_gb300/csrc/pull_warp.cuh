@@ -207,7 +207,7 @@ __device__ __forceinline__ typename Sr<T>::Atom atom_combine(typename Sr<T>::Ato
 // wait on the few that walked 32 chunks one load latency after another. The
 // rest goes out as pieces of kLongPiece entries ({row, begin, end, 0}) that
 // any warp of k_pull_long_rest takes.
-constexpr int kLongFirst = 2;
+constexpr int kLongFirst = 1;
 constexpr int kLongPiece = 512;
 
 template <class T, bool MASK, bool SOUT, bool VEC>
@@ -240,7 +240,9 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     for (int t = 0; t < lim; ++t) {
         const int32_t base = a0 + 128 * t + 4 * lane;
         Chunk<T, MASK, VEC> nxt;
-        chunk_load(nxt, col, val, nnz, base + 128, b, e);
+        // the next chunk is loaded before this one's gathers -- unless this
+        // is the last chunk this warp walks (the rest goes to the second pass)
+        if (t + 1 < lim || lim == nsteps) chunk_load(nxt, col, val, nnz, base + 128, b, e);
         S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(cur, val, x, p.xbits, base, hit));
         if constexpr (S::kPattern) {
             // OR is settled by the first hit (a deeper prefetch, and warps

@@ -402,12 +402,23 @@ __global__ void __launch_bounds__(B) k_list_scan(int32_t* xscan, const CallDesc*
         int32_t e = base + block_excl_scan<B>(c, sm, &tot);
 #pragma unroll
         for (int q = 0; q < kRun; ++q) {
-            if (t0 + q >= hi) break;
-            xscan[t0 + q] = e;
-            if (OWNERS)
-                for (int64_t ch = ((int64_t)e + CH - 1) / CH; ch * CH < (int64_t)e + v[q]; ++ch)
-                    chunk_t0[ch] = (int32_t)(t0 + q);
-            e += v[q];
+            const bool valid = t0 + q < hi;
+            if (valid) xscan[t0 + q] = e;
+            if (OWNERS) {
+                // chunks [c0, c1) start inside this entry's items; a hub
+                // column's run of chunks is written by the whole warp
+                const int64_t c0 = ((int64_t)e + CH - 1) / CH, c1 = ((int64_t)e + v[q] + CH - 1) / CH;
+                const int64_t cnt = valid ? c1 - c0 : 0;
+                if (cnt <= 8)
+                    for (int64_t ch = c0; ch < c0 + cnt; ++ch) chunk_t0[ch] = (int32_t)(t0 + q);
+                for (unsigned pend = __ballot_sync(0xffffffffu, cnt > 8); pend; pend &= pend - 1) {
+                    const int src = __ffs(pend) - 1;
+                    const int64_t lo = __shfl_sync(0xffffffffu, c0, src), n1 = __shfl_sync(0xffffffffu, c1, src);
+                    const int32_t owner = (int32_t)__shfl_sync(0xffffffffu, t0 + q, src);
+                    for (int64_t ch = lo + (threadIdx.x & 31); ch < n1; ch += 32) chunk_t0[ch] = owner;
+                }
+            }
+            e += valid ? v[q] : 0;
         }
         base += tot;
     }

@@ -306,7 +306,10 @@ void feature_launch(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, Fe
             default: fl.func = feat_dense_func<bool8>(); break;
         }
         const int64_t nsuper = (H->n + 127) / 128;
-        fl.grid = dim3((unsigned)max((int64_t)1, min((nsuper + 7) / 8, (int64_t)H->num_sms * 4)));
+        // six blocks per SM (the kernel's registers leave room for six): the
+        // pass streams x with one 16-byte load per lane and step, so the
+        // number of warps in flight sets its bandwidth
+        fl.grid = dim3((unsigned)max((int64_t)1, min((nsuper + 7) / 8, (int64_t)H->num_sms * 6)));
         fl.xptr = di.user_x_dense;
         fl.xbits = H->ws.xbits_dense;
         void* a[11] = {&fl.xptr, &fl.n, &fl.colptr, &fl.xbits, &fl.counters, &fl.ticket, &fl.desc, &fl.di,
@@ -626,39 +629,48 @@ void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
 
 // ---------------------------------------------------------------- dense write-out of the push accumulators
 // y_i = the accumulator of a flagged row (re-zeroed, its flag cleared) or 0.
-// Grid-stride over rows with consecutive threads on consecutive rows (every
-// warp access is one run of 32 rows), four rows per thread in flight: all
-// their flag and accumulator loads are issued before the stores.
+// A warp takes 512 rows per step: its lanes load the rows' flags with one
+// 16-byte load each (the flag array is padded to a multiple of 16 bytes),
+// stage them in shared memory, and then handle the rows 32 at a time with
+// consecutive lanes on consecutive rows, so every accumulator load and
+// every y store of a warp is one contiguous run. A group of 512 rows without
+// a flag (most of them for a sparse product) only writes zeros.
+constexpr int kFinRows = 512;
 template <class T>
 __global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, typename Sr<T>::Atom* acc, uint8_t* yflag,
                                                         const CallDesc* __restrict__ desc) {
     using S = Sr<T>;
+    __shared__ __align__(16) uint8_t s_f[8][kFinRows];
     T* __restrict__ y = (T*)desc->y;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += 4 * stride) {
-        bool f[4];
-        T v[4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t ngroups = (m + kFinRows - 1) / kFinRows;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t g = (int64_t)blockIdx.x * 8 + w; g < ngroups; g += nw) {
+        const int64_t i0 = g * kFinRows;
+        const uint4 fw = *reinterpret_cast<const uint4*>(yflag + i0 + 16 * lane);
+        *reinterpret_cast<uint4*>(&s_f[w][16 * lane]) = fw;
+        const bool any = __any_sync(0xffffffffu, (fw.x | fw.y | fw.z | fw.w) != 0u);
+        __syncwarp();
+        if (any) *reinterpret_cast<uint4*>(yflag + i0 + 16 * lane) = make_uint4(0u, 0u, 0u, 0u);
+        // sixteen rows per lane in flight: loads first, then the stores
+        T v[16];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t i = i0 + u * stride;
-            f[u] = i < m && yflag[i] != 0;
+        for (int u = 0; u < 16; ++u) {
+            const int64_t i = i0 + 32 * u + lane;
+            const bool f = any && s_f[w][32 * u + lane] != 0;
+            if (S::kPattern) v[u] = f ? S::one() : T(0);
+            else v[u] = f ? S::from_atom(acc[i]) : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t i = i0 + u * stride;
-            if (S::kPattern) v[u] = f[u] ? S::one() : T(0);
-            else v[u] = f[u] ? S::from_atom(acc[i]) : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t i = i0 + u * stride;
+        for (int u = 0; u < 16; ++u) {
+            const int64_t i = i0 + 32 * u + lane;
             if (i >= m) break;
             y[i] = v[u];
-            if (f[u]) {
-                if (!S::kPattern) acc[i] = typename S::Atom(0);
-                yflag[i] = 0;
+            if constexpr (!S::kPattern) {
+                if (any && s_f[w][32 * u + lane]) acc[i] = typename S::Atom(0);
             }
         }
+        __syncwarp();
     }
 }
 
@@ -667,7 +679,8 @@ static void finalize_dtype(asv_matrix_s* H, bool from_acc, int out_mode, cudaStr
     using Atom = typename Sr<T>::Atom;
     if (out_mode == ASV_OUT_DENSE) {
         if (H->m > 0) {
-            const int64_t g = std::min<int64_t>((H->m + 1023) / 1024, (int64_t)H->num_sms * 8);
+            const int64_t groups = (H->m + kFinRows - 1) / kFinRows;
+            const int64_t g = std::min<int64_t>((groups + 7) / 8, (int64_t)H->num_sms * 8);
             k_finalize_dense<T><<<(unsigned)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag, H->d_desc);
         }
     } else if (from_acc) {

@@ -65,7 +65,10 @@ CORPUS_SEED = 7919
 ZIPF = {"zipf_200k": (200_000, 131_072, np.log(40), 1.0, 1.2, 1),
         "zipf_1m_64k": (1_000_000, 65_536, np.log(20), 1.0, 1.1, 2),
         "zipf_500k_256k": (500_000, 262_144, np.log(30), 0.8, 1.3, 7),
-        "zipf_100k_32k": (100_000, 32_768, np.log(80), 1.2, 1.0, 8)}
+        "zipf_100k_32k": (100_000, 32_768, np.log(80), 1.2, 1.0, 8),
+        # a million rows over 131,072 columns: the row count at which a hub-heavy
+        # list's push (atomics on rows every hub reaches) loses to the pull
+        "zipf_1m_131k": (1_000_000, 131_072, np.log(40), 1.0, 1.2, 11)}
 
 
 def corpus():
@@ -162,7 +165,7 @@ def vectors(name, rp, c, n, m, roots=2, max_levels=8):
 
 
 # ------------------------------------------------------------------ collection (GPU)
-def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
+def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool"), graphs=True, only=None):
     import torch
 
     import gen
@@ -174,6 +177,8 @@ def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
     for name, make in corpus():
         if time.time() - t_start > budget_s:
             break
+        if only and name not in only:
+            continue
         rp, c, v, n = make()
         m = len(rp) - 1
         rpt, ct = torch.from_numpy(rp).to(dev), torch.from_numpy(c).to(dev)
@@ -214,12 +219,26 @@ def collect(path, budget_s=900.0, reps=3, dtypes=("f32", "bool")):
                                     asv.asv_spmspv(A.handle, cnt, it, xv, None if xs else xd, 1, None, yidx,
                                                    yval, nnz_y, m, kernel=kk)
                             call()
+                            # the candidate as one CUDA graph launch, as the
+                            # selector-driven call runs it (a forced call from
+                            # the host adds a host launch per kernel)
+                            run = call
+                            if graphs:
+                                try:
+                                    torch.cuda.synchronize()
+                                    g = torch.cuda.CUDAGraph()
+                                    with torch.cuda.graph(g):
+                                        call()
+                                    run = g.replay
+                                except RuntimeError:
+                                    torch.cuda.synchronize()
+                                    run = call
                             ts = []
                             for r in range(reps):
                                 flush.zero_()
                                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                                 e0.record()
-                                call()
+                                run()
                                 e1.record()
                                 torch.cuda.synchronize()
                                 ts.append(e0.elapsed_time(e1))
@@ -552,7 +571,8 @@ if __name__ == "__main__":
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     cmd = sys.argv[1]
     if cmd == "collect":
-        collect(sys.argv[2], budget_s=float(sys.argv[3]) if len(sys.argv) > 3 else 900.0)
+        collect(sys.argv[2], budget_s=float(sys.argv[3]) if len(sys.argv) > 3 else 900.0,
+                only=sys.argv[4].split(",") if len(sys.argv) > 4 else None)
     elif cmd == "fit":
         trees, rep = fit(sys.argv[2], cost_ordered="--cost-ordered" in sys.argv)
         print(json.dumps(rep, indent=1))

@@ -40,10 +40,20 @@ def test_launch_mirror_matches_the_profiled_step():
     # step (Boolean list in / list out; PageRank dense, forced in the replay)
     K = {name: i for i, name in enumerate(("pull_thread", "pull_warp", "pull_bal", "mpull_thread", "mpull_warp",
                                           "mpull_bal", "push_thread_atom", "push_warp_atom", "push_bal_atom"))}
-    long_flags = 1  # long-row pass, no fix-up for a Boolean list output
-    assert bench.launches(K["pull_thread"], True, True, long_extra=long_flags) == 91 // 13
+    long_flags = 2  # long-row pass and its second pass, no fix-up for a Boolean list output
+    assert bench.launches(K["pull_thread"], True, True, long_extra=long_flags) == 104 // 13
     assert bench.launches(K["push_bal_atom"], True, True) == 90 // 15
     assert bench.launches(K["push_thread_atom"], True, True) == 88 // 22
     assert bench.launches(K["push_warp_atom"], True, True) == 24 // 6
     # the selector-driven PageRank call runs the feature pass the forced replay skips
     assert bench.launches(K["pull_warp"], False, False, long_extra=2) == 3 + 1
+
+
+def test_launch_mirror_matches_the_profiled_stencil_step():
+    # launches per call in the committed launch list of the stencil step
+    # (per density: x listed -> y listed, x dense -> y dense)
+    K = {"pull_thread": 0, "push_warp_atom": 7}
+    assert bench.launches(K["push_warp_atom"], True, True) == 4  # features, push, compaction (2)
+    assert bench.launches(K["push_warp_atom"], False, False) == 5  # features, x compaction (2), push, write-out
+    assert bench.launches(K["pull_thread"], True, True) == 6  # features, scatter, pull, compaction (2), clear
+    assert bench.launches(K["pull_thread"], False, False) == 2  # features, pull
