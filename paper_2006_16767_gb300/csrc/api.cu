@@ -217,7 +217,6 @@ static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s
     AL(H->carry_row, 4 * (H->ntiles + 1), false);
     AL(H->carry_val, 8 * (H->ntiles + 1), false);
     AL(H->d_trees, sizeof(TreeNode) * kMaxTreeNodes, false);
-    AL(H->d_roots, 4 * kRootsLen, false);
     AL(H->d_desc, sizeof(CallDesc), true);
     AL(H->d_last_kid, 4, true);
     // workspaces
@@ -267,7 +266,6 @@ static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s
         default_trees(dtype, nodes, roots);
         update_lazy(H, nodes, roots);
         CKH(cudaMemcpyAsync(H->d_trees, nodes.data(), sizeof(TreeNode) * nodes.size(), cudaMemcpyHostToDevice, s));
-        CKH(cudaMemcpyAsync(H->d_roots, roots, sizeof(roots), cudaMemcpyHostToDevice, s));
     }
     // lanes per row for the sub-warp pull: about six entries per lane; fewer
     // lanes also want two rows per group rather than four (measured on GB300)
@@ -392,10 +390,58 @@ static void enqueue_candidate(asv_matrix_s* H, int k, int x_sparse, int om, cuda
     }
 }
 
+// The candidate whose chain runs beside the SWITCH node of a selector graph
+// rather than as one of its branches: the warp push with atomic write-back,
+// which the trees pick at the sparse end of the density range on matrices
+// without hub columns, where a whole call takes a few tens of microseconds
+// and the conditional node's own dispatch (about 10 us on GB300, measured
+// with an empty branch) would add a fifth to a third to it. The chain
+// depends on the feature node only, its kernels return at once unless the
+// pass chose its candidate (Gate), and that candidate's SWITCH branch is
+// empty; when it is chosen, the SWITCH node's dispatch overlaps the chain
+// instead of preceding it. (With the three atomic pushes as direct chains,
+// four branches beside each other, the R-MAT pull calls ran at half speed;
+// with one or two chains they did not. The cause was not found, so one
+// chain is kept.)
+static constexpr int kDirect[1] = {ASV_K_PUSH_WARP_ATOM};
+
+static bool is_direct(int k) {
+    for (int d : kDirect)
+        if (d == k) return true;
+    return false;
+}
+
+// Captures the direct chains into graph g, each after node `after`; the
+// nodes that end them are appended to *tails when it is given.
+static cudaError_t capture_direct_chains(asv_matrix_s* H, cudaGraph_t g, cudaGraphNode_t after, int xs, int om,
+                                         std::vector<cudaGraphNode_t>* tails) {
+    cudaStream_t cs = H->cap_stream;
+    for (int k : kDirect) {
+        cudaError_t r = cudaStreamBeginCaptureToGraph(cs, g, &after, nullptr, 1, cudaStreamCaptureModeRelaxed);
+        if (r != cudaSuccess) return r;
+        H->gate_kid = k;
+        enqueue_candidate(H, k, xs, om, cs);
+        H->gate_kid = -1;
+        if (tails) {
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            r = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+            if (r == cudaSuccess) tails->insert(tails->end(), deps, deps + nd);
+        }
+        cudaGraph_t cap;
+        const cudaError_t e = cudaStreamEndCapture(cs, &cap);
+        if (r != cudaSuccess) return r;
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // The selector-driven graph of one (x format, output mode): a feature-pass
 // node whose last block also walks the trees and sets the SWITCH value, then
-// the SWITCH node with one branch per candidate. The feature node's
-// arguments are replaced before every launch, so one graph serves all calls.
+// the SWITCH node with one branch per candidate, and beside it the direct
+// chains of the atomic pushes. The feature node's arguments are replaced
+// before every launch, so one graph serves all calls.
 static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om, const DescInit& di) {
     if (H->gexec[xs][om]) return ASV_OK;
     if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
@@ -422,12 +468,14 @@ static asv_status build_auto_graph(asv_matrix_s* H, int xs, int om, const DescIn
     cudaGraphNode_t cn;
     CK(cudaGraphAddNode(&cn, g, &feat, nullptr, 1, &cp));
     for (int k = 0; k < ASV_K_COUNT; ++k) {
+        if (is_direct(k)) continue;  // an empty branch
         CK(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[k], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeRelaxed));
         enqueue_candidate(H, k, xs, om, cs);
         cudaGraph_t bk;
         CK(cudaStreamEndCapture(cs, &bk));
     }
+    CK(capture_direct_chains(H, g, feat, xs, om, nullptr));
     cudaGraphExec_t ex;
     CK(cudaGraphInstantiate(&ex, g, 0));
     H->graph[xs][om] = g;
@@ -508,7 +556,7 @@ static asv_status spmspv_impl(asv_matrix A, const uint32_t* d_ymask, const int64
         st = launch_auto(A, di, out_mode, s);
         if (st != ASV_OK) return st;
     } else {
-        SelectArg none = select_arg(A, 0ull);
+        SelectArg none = select_arg(A, 0ull, 2 * di.x_sparse + out_mode);
         none.enabled = 0;
         launch_features(A, di, none, s);
         enqueue_candidate(A, kernel, di.x_sparse, out_mode, s);
@@ -566,7 +614,7 @@ static asv_status build_loop_graph(asv_matrix_s* H, const DescInit& di, int32_t 
         CKL(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp));
         cudaGraph_t body = wp.conditional.phGraph_out[0];
         if (kernel != ASV_K_AUTO) {
-            SelectArg none = select_arg(H, 0ull);
+            SelectArg none = select_arg(H, 0ull, 2 + ASV_OUT_SPARSE);
             none.enabled = 0;
             CKL(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
             launch_features(H, di, none, cs);
@@ -595,12 +643,17 @@ static asv_status build_loop_graph(asv_matrix_s* H, const DescInit& di, int32_t 
             cudaGraphNode_t sn;
             CKL(cudaGraphAddNode(&sn, body, &feat, nullptr, 1, &sp));
             for (int k = 0; k < ASV_K_COUNT; ++k) {
+                if (is_direct(k)) continue;  // an empty branch
                 CKL(cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed));
                 enqueue_candidate(H, k, 1, ASV_OUT_SPARSE, cs);
                 CKL(cudaStreamEndCapture(cs, &cap));
             }
-            CKL(cudaStreamBeginCaptureToGraph(cs, body, &sn, nullptr, 1, cudaStreamCaptureModeRelaxed));
+            // the step waits for the SWITCH node and every direct chain
+            std::vector<cudaGraphNode_t> join{sn};
+            CKL(capture_direct_chains(H, body, feat, 1, ASV_OUT_SPARSE, &join));
+            CKL(cudaStreamBeginCaptureToGraph(cs, body, join.data(), nullptr, join.size(),
+                                              cudaStreamCaptureModeRelaxed));
             step(cs, (unsigned long long)hw);
             CKL(cudaStreamEndCapture(cs, &cap));
         }
@@ -756,7 +809,10 @@ extern "C" asv_status asv_select(asv_matrix A, const int64_t* d_nnz_x, const int
     asv_status st = prepare_call(A, d_nnz_x, d_xidx, d_xval, d_x_dense, out_mode, A->ws.ywork, A->ws.xlist_idx,
                                  A->ws.ywork, (int64_t*)A->ws.hist, 0, di);
     if (st != ASV_OK) return st;
-    launch_features(A, di, select_arg(A, 0ull), s);
+    // the full pass: every feature is reported, so no lazy evaluation
+    SelectArg sa = select_arg(A, 0ull, 2 * di.x_sparse + out_mode);
+    sa.lazy = 0;
+    launch_features(A, di, sa, s);
     CallDesc hd;
     CK(cudaMemcpyAsync(&hd, A->d_desc, sizeof(hd), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -810,11 +866,21 @@ extern "C" asv_status asv_set_trees(asv_matrix A, const double* h_nodes, int32_t
     r[kRootsLen - 1] = n_nodes;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(A->d_trees, nodes.data(), sizeof(TreeNode) * n_nodes, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(A->d_roots, r, sizeof(r), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     update_lazy(A, nodes, r);
-    // the selector graphs' feature nodes take the new lazy hint at their next call
+    // the selector graphs' feature nodes take the new roots, windows and lazy
+    // hints at their next call; the BFS and PageRank graphs hold them in
+    // their captured feature nodes, so they are rebuilt at their next call
+    // (a graph still executing is freed when it completes)
     memset(A->last_di, 0xff, sizeof(A->last_di));
+    for (int k = 0; k <= ASV_K_COUNT; ++k) {
+        if (A->bfs_exec[k]) cudaGraphExecDestroy(A->bfs_exec[k]);
+        if (A->bfs_graph[k]) cudaGraphDestroy(A->bfs_graph[k]);
+        if (A->pr_exec[k]) cudaGraphExecDestroy(A->pr_exec[k]);
+        if (A->pr_graph[k]) cudaGraphDestroy(A->pr_graph[k]);
+        A->bfs_exec[k] = A->pr_exec[k] = nullptr;
+        A->bfs_graph[k] = A->pr_graph[k] = nullptr;
+    }
     return ASV_OK;
 }
 

@@ -189,6 +189,18 @@ struct CallDesc {
     int64_t nhub;            // listed columns longer than kLongSeg (hubs of the thread/warp push)
 };
 
+// Predicate of a kernel in one of the selector graph's direct candidate
+// chains, which run beside the SWITCH node rather than inside it: such a
+// kernel does its work only if the feature pass chose `kid` for the call,
+// and otherwise returns at once. kid < 0 (every other launch): always runs.
+struct Gate {
+    const CallDesc* desc;
+    int32_t kid;
+    __device__ __forceinline__ bool off() const {
+        return kid >= 0 && *(volatile const int32_t*)&desc->kid != kid;
+    }
+};
+
 // Row i is excluded by the output mask.
 __device__ __forceinline__ bool row_masked(const uint32_t* __restrict__ ymask, int64_t i) {
     return ymask != nullptr && ((__ldg(ymask + (i >> 5)) >> (i & 31)) & 1u);

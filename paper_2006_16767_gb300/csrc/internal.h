@@ -119,7 +119,10 @@ struct asv_matrix_s {
     uint32_t wait_limit = 1u << 24;
     // selector tables
     asv::TreeNode* d_trees = nullptr;
-    int32_t* d_roots = nullptr;
+    // the table's roots and, per call format, the window of nodes a feature
+    // pass stages (kernel arguments of every selector-enabled pass)
+    int32_t h_roots[asv::kRootsLen] = {};
+    int32_t win_lo[4] = {0, 0, 0, 0}, win_hi[4] = {0, 0, 0, 0};
     // per call format: its pattern tree starts with a feature that a listed
     // x gives for free (the lazy evaluation of the list feature pass)
     int32_t lazy_ok[4] = {0, 0, 0, 0};
@@ -134,6 +137,9 @@ struct asv_matrix_s {
     unsigned long long cond[2][2] = {{0, 0}, {0, 0}};
     asv::DescInit last_di[2][2];  // arguments the feature node of each graph was last given
     cudaStream_t cap_stream = nullptr;
+    // while a direct candidate chain of a selector graph is captured: the
+    // candidate whose chain it is (the Gate of its kernels), else -1
+    int32_t gate_kid = -1;
     // the long-row pass of the thread and sub-warp pulls runs beside the
     // short-row kernel: a side stream joined by two events (in a graph
     // capture they become a fork and a join of the captured graph)
@@ -227,6 +233,8 @@ struct FeatLaunch {
 void feature_launch(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, FeatLaunch& fl);
 void launch_features(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, cudaStream_t s);
 void launch_x_scatter(asv_matrix_s* H, bool set, bool bits, cudaStream_t s);
+// the Gate of the kernels launched now (see gate_kid)
+inline Gate gate_of(const asv_matrix_s* H) { return Gate{H->d_desc, H->gate_kid}; }
 void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s);
 void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s);
 void launch_compact_public(asv_matrix_s* H, const void* x, int32_t* idx, void* val, int64_t* count,
@@ -263,9 +271,10 @@ void batch_release(asv_matrix_s* H);
 
 // select.cu
 // fmt: the call format 2 * (x listed) + (sparse output) the feature node
-// serves (-1 = none: no lazy evaluation)
-SelectArg select_arg(asv_matrix_s* H, unsigned long long cond, int fmt = -1);
-// recomputes lazy_ok from a node table and its roots
+// serves; its trees, roots and lazy hint go into the arguments
+SelectArg select_arg(asv_matrix_s* H, unsigned long long cond, int fmt);
+// records a node table's roots and recomputes the per-format windows and
+// lazy hints from it
 void update_lazy(asv_matrix_s* H, const std::vector<TreeNode>& nodes, const int32_t* roots);
 void default_trees(int32_t dtype, std::vector<TreeNode>& nodes, int32_t roots[kRootsLen]);
 

@@ -165,7 +165,8 @@ __device__ __forceinline__ void help_long(const int32_t* __restrict__ colptr, co
 
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
-                                                     const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
+                                                     const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws, Gate gate) {
+    if (gate.off()) return;
     using S = Sr<T>;
     const uint32_t* __restrict__ ym = desc->ymask;
     const int lane = threadIdx.x & 31;
@@ -219,7 +220,8 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
 
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
-                                                   const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
+                                                   const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws, Gate gate) {
+    if (gate.off()) return;
     using S = Sr<T>;
     const uint32_t* __restrict__ ym = desc->ymask;
     const int lane = threadIdx.x & 31;
@@ -263,7 +265,8 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
 // columns) fall back to one binary search per item.
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
-                                                  const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws) {
+                                                  const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws, Gate gate) {
+    if (gate.off()) return;
     using S = Sr<T>;
     constexpr int CH = 32 * kPushIPT;
     __shared__ int32_t s_t[8][CH];          // item -> list index of its column
@@ -357,7 +360,8 @@ __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ co
 // launches. Pass 1: each block writes its entries' lengths and their sum.
 template <int B>
 __global__ void __launch_bounds__(B) k_list_deg(const int32_t* __restrict__ colptr, const CallDesc* __restrict__ desc,
-                                                int32_t* deg, int32_t* blk) {
+                                                int32_t* deg, int32_t* blk, Gate gate) {
+    if (gate.off()) return;
     __shared__ int32_t sm[B / 32 + 1];
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
@@ -383,7 +387,8 @@ __global__ void __launch_bounds__(B) k_list_deg(const int32_t* __restrict__ colp
 // entry, so no search and no atomics.
 template <int B, bool OWNERS>
 __global__ void __launch_bounds__(B) k_list_scan(int32_t* xscan, const CallDesc* __restrict__ desc,
-                                                 const int32_t* __restrict__ blk, int32_t* chunk_t0) {
+                                                 const int32_t* __restrict__ blk, int32_t* chunk_t0, Gate gate) {
+    if (gate.off()) return;
     constexpr int CH = 32 * kPushIPT;
     __shared__ int32_t sm[B / 32 + 1];
     const int64_t nx = desc->nnz_x;
@@ -577,18 +582,19 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
     const int grid = H->num_sms * 8;
     const CallDesc* d = H->d_desc;
     Ws ws = H->ws;
+    const Gate gate = gate_of(H);
     if (dist == 2 || wb != WB_ATOM) {
-        k_list_deg<256><<<H->G, 256, 0, s>>>(H->colptr, d, ws.xscan, ws.blk);
+        k_list_deg<256><<<H->G, 256, 0, s>>>(H->colptr, d, ws.xscan, ws.blk, gate);
         if (dist == 2)
-            k_list_scan<256, true><<<H->G, 256, 0, s>>>(ws.xscan, d, ws.blk, ws.chunk_t0);
+            k_list_scan<256, true><<<H->G, 256, 0, s>>>(ws.xscan, d, ws.blk, ws.chunk_t0, gate);
         else
-            k_list_scan<256, false><<<H->G, 256, 0, s>>>(ws.xscan, d, ws.blk, ws.chunk_t0);
+            k_list_scan<256, false><<<H->G, 256, 0, s>>>(ws.xscan, d, ws.blk, ws.chunk_t0, gate);
     }
 #define TRAV(WBV)                                                                                   \
     do {                                                                                            \
-        if (dist == 0) k_push_thread<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws); \
-        else if (dist == 1) k_push_warp<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws); \
-        else k_push_bal<T, WBV><<<grid * 4, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws);      \
+        if (dist == 0) k_push_thread<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
+        else if (dist == 1) k_push_warp<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
+        else k_push_bal<T, WBV><<<grid * 4, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
     } while (0)
     if (wb == WB_ATOM) TRAV(WB_ATOM);
     else TRAV(WB_SORT);

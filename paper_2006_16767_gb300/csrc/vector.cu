@@ -36,15 +36,23 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
     desc->vfeat[3] = nnz > 0 ? (double)ns / (double)nnz : 0.0;
 }
 
+// The hub-column queue's length as the previous call left it, read by
+// thread 0 of every block at the start of the feature pass (only the push
+// kernels, which run after the pass, change it), so the block that resets
+// the queue does not wait for the read.
+__device__ __forceinline__ unsigned hub_queue_len(const SelectArg& sa) {
+    return (threadIdx.x == 0 && sa.lcol_n) ? *(volatile unsigned int*)sa.lcol_n : 0u;
+}
+
 // Returns the push kernels' hub-column queue and the Boolean pull's
 // long-row piece queue of the previous call to their empty state (one
-// block, all its threads).
+// block, all its threads; nq from hub_queue_len, valid in thread 0).
 template <int B>
-__device__ __forceinline__ void reset_hub_queue(const SelectArg& sa) {
+__device__ __forceinline__ void reset_hub_queue(const SelectArg& sa, unsigned nq) {
     if (threadIdx.x == 0 && sa.long_rest_n) *sa.long_rest_n = 0u;
     if (!sa.lcol_n) return;
     __shared__ int32_t s_nq;
-    if (threadIdx.x == 0) s_nq = min((int32_t)*(volatile unsigned int*)sa.lcol_n, sa.lcol_cap);
+    if (threadIdx.x == 0) s_nq = min((int32_t)nq, sa.lcol_cap);
     __syncthreads();
     for (int32_t i = threadIdx.x; i < s_nq; i += B) sa.lcol[i] = make_int2(-1, 0);
     if (threadIdx.x == 0) *sa.lcol_n = 0u;
@@ -57,7 +65,7 @@ template <int B>
 __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long ch,
                                               unsigned long long* counters, unsigned int* ticket, CallDesc* desc,
                                               const DescInit& di, int64_t n, int64_t nnz, int32_t* status,
-                                              const SelectArg& sa, unsigned blocks, TreeNode* sn) {
+                                              const SelectArg& sa, unsigned blocks, TreeNode* sn, unsigned nq) {
     __shared__ unsigned long long sm[B / 32 + 1];
     __shared__ bool last;
     cx = block_reduce_sum<B>(cx, sm);
@@ -89,9 +97,9 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
     }
     // the last block returns the push kernels' hub-column queue of the
     // previous call to its empty state
-    if (last) reset_hub_queue<B>(sa);
-    // the last block also walks the selector's trees (Sec. VI-B), so the
-    // choice is ready when the feature pass ends
+    if (last) reset_hub_queue<B>(sa, nq);
+    // the last block also walks the selector's trees (Sec. VI-B), staged at
+    // the start of the pass, so the choice is ready when the feature pass ends
     if (last && sa.enabled) {
         __syncthreads();
         run_selector(sa, desc, sn);
@@ -127,6 +135,10 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
                                                   CallDesc* desc, DescInit di, int64_t nnz, int32_t* status,
                                                   SelectArg sa) {
     __shared__ TreeNode sn[kTreeWindow];
+    // the selector's trees are staged while the pass runs (the last block
+    // walks them)
+    if (sa.enabled) stage_window<B>(sa, sn);
+    const unsigned nq = hub_queue_len(sa);
     const bool VEC = ((uintptr_t)x & 15) == 0;
     const int lane = threadIdx.x & 31;
     const int64_t nwords = (n + 31) >> 5;
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
             }
         }
     }
-    finish_counts<B>(cx, cs, ch, counters, ticket, desc, di, n, nnz, status, sa, gridDim.x, sn);
+    finish_counts<B>(cx, cs, ch, counters, ticket, desc, di, n, nnz, status, sa, gridDim.x, sn, nq);
 }
 
 // Sparse x: nnz_s = sum of the listed columns' lengths.
@@ -201,11 +213,16 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
                                                    int64_t nnz, int32_t* status, SelectArg sa) {
     __shared__ TreeNode sn[kTreeWindow];
     int64_t nx = *nnz_x_dev;
+    const unsigned nq = hub_queue_len(sa);
     if (nx < 0) nx = 0;
     if (nx > n) nx = n + 1;  // reported and clamped when the totals are published
     // only the blocks the list reaches take part (a short list costs one block)
     const unsigned blocks = (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (min(nx, n) + B - 1) / B));
+    // block 0 always takes part: its copy of the selector's trees is issued
+    // together with the load of nnz_x
+    if (sa.enabled && blockIdx.x == 0) stage_window<B>(sa, sn);
     if (blockIdx.x >= blocks) return;
+    if (sa.enabled && blockIdx.x != 0) stage_window<B>(sa, sn);
     // Lazy, cost-ordered evaluation (Sec. VI-C: cheap features first): a list
     // gives nnz_x and x_sparsity for free, while nnz_s and m_sparsity cost a
     // pass of gathers over its columns' pointers. When the call format's trees
@@ -215,19 +232,20 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
     // warp push with atomics), block 0 publishes the call without them and
     // the pass ends there.
     if (sa.enabled && sa.lazy && nx <= n) {
+        __shared__ double s_f[13];
         __shared__ int s_kid;
-        int lo, hi;
-        const int* r = stage_trees(sa, 2 + di.out_mode, sn, lo, hi);
         if (threadIdx.x == 0) {
-            double f[13];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) f[q] = sa.mf[q];
-            f[9] = (double)nx;
-            f[10] = n > 0 ? (double)nx / (double)n : 0.0;
-            f[11] = f[12] = 0.0;
-            int kid = pick_kernel(sn, lo, hi, sa.trees, r, f, 11);
+            for (int q = 0; q < 9; ++q) s_f[q] = sa.mf[q];
+            s_f[9] = (double)nx;
+            s_f[10] = n > 0 ? (double)nx / (double)n : 0.0;
+            s_f[11] = s_f[12] = 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int kid = pick_kernel(sa, sn, s_f, 11);
             if (!(kid >= ASV_K_PULL_THREAD && kid <= ASV_K_MPULL_BAL) && kid != ASV_K_PUSH_WARP_ATOM) kid = -1;
-            s_kid = kid;
+            if (threadIdx.x == 0) s_kid = kid;
         }
         __syncthreads();
         const int kid = s_kid;
@@ -239,11 +257,10 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
                     desc->vfeat[2] = desc->vfeat[3] = -1.0;
                     commit_kernel(sa, desc, kid);
                 }
-                reset_hub_queue<B>(sa);
+                reset_hub_queue<B>(sa, nq);
             }
             return;
         }
-        __syncthreads();  // sn is reused by the selector of the full pass
     }
     // four list entries per thread in flight: their column lengths are
     // independent gathers
@@ -269,7 +286,7 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
         ch += d > kLongSeg;
     }
     finish_counts<B>(blockIdx.x == 0 && threadIdx.x == 0 ? (unsigned long long)nx : 0ull, cs, ch, counters, ticket,
-                     desc, di, n, nnz, status, sa, blocks, sn);
+                     desc, di, n, nnz, status, sa, blocks, sn, nq);
 }
 
 // Few blocks per SM: every block of the feature pass ends with atomics on
@@ -442,7 +459,9 @@ __device__ __forceinline__ void load_run(const uint32_t* __restrict__ words, int
 // Items of each block's range, one run of kRun words (two 16-byte loads) per
 // thread and round.
 template <int B, bool BYTES>
-__global__ void __launch_bounds__(B) k_items_count(const uint32_t* __restrict__ words, int64_t nwords, int32_t* blk) {
+__global__ void __launch_bounds__(B) k_items_count(const uint32_t* __restrict__ words, int64_t nwords, int32_t* blk,
+                                                   Gate gate) {
+    if (gate.off()) return;
     __shared__ int32_t sm[B / 32 + 1];
     int64_t lo, hi;
     block_range(nwords, lo, hi);
@@ -466,7 +485,8 @@ __global__ void __launch_bounds__(B) k_items_count(const uint32_t* __restrict__ 
 // contiguous rather than one scattered word per thread.
 template <int B, bool BYTES, class Policy>
 __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwords, const int32_t* __restrict__ blk,
-                                                   Policy pol) {
+                                                   Policy pol, Gate gate) {
+    if (gate.off()) return;
     constexpr int RUN = BYTES ? kRun : 1;  // words per thread and round
     constexpr int CAP = B * 32;            // items per round at most
     __shared__ int32_t sm[B / 32 + 1];
@@ -608,8 +628,9 @@ template <bool BYTES, class Policy>
 static void compact_items(asv_matrix_s* H, uint32_t* words, int64_t nitems, const Policy& pol, cudaStream_t s) {
     const int64_t nwords = BYTES ? (nitems + 3) / 4 : (nitems + 31) / 32;
     const int G = H->G;
-    k_items_count<256, BYTES><<<G, 256, 0, s>>>(words, nwords, H->ws.blk);
-    k_items_write<256, BYTES, Policy><<<G, 256, 0, s>>>(words, nwords, H->ws.blk, pol);
+    const Gate gate = gate_of(H);
+    k_items_count<256, BYTES><<<G, 256, 0, s>>>(words, nwords, H->ws.blk, gate);
+    k_items_write<256, BYTES, Policy><<<G, 256, 0, s>>>(words, nwords, H->ws.blk, pol, gate);
 }
 
 template <class T>
@@ -638,7 +659,8 @@ void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
 constexpr int kFinRows = 512;
 template <class T>
 __global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, typename Sr<T>::Atom* acc, uint8_t* yflag,
-                                                        const CallDesc* __restrict__ desc) {
+                                                        const CallDesc* __restrict__ desc, Gate gate) {
+    if (gate.off()) return;
     using S = Sr<T>;
     __shared__ __align__(16) uint8_t s_f[8][kFinRows];
     T* __restrict__ y = (T*)desc->y;
@@ -681,7 +703,7 @@ static void finalize_dtype(asv_matrix_s* H, bool from_acc, int out_mode, cudaStr
         if (H->m > 0) {
             const int64_t groups = (H->m + kFinRows - 1) / kFinRows;
             const int64_t g = std::min<int64_t>((groups + 7) / 8, (int64_t)H->num_sms * 8);
-            k_finalize_dense<T><<<(unsigned)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag, H->d_desc);
+            k_finalize_dense<T><<<(unsigned)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag, H->d_desc, gate_of(H));
         }
     } else if (from_acc) {
         OutSparsePolicy<T, true> pol{H->d_desc, (Atom*)H->ws.acc, nullptr, H->ws.status, nullptr, nullptr, 0};
