@@ -92,16 +92,32 @@ def long_row_launches(rowptr):
     return int((deg > LONG_ROW).any()) + int((deg > LONG_SEG).any())
 
 
-def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0):
+def direct_chain_launches(x_sparse, sparse_out):
+    """Kernels of the warp push's direct chain (it runs beside the SWITCH node
+    of every selector-driven call and returns at once unless chosen): x
+    compaction for a dense x, the push, the write-out."""
+    return (0 if x_sparse else 2) + 1 + (2 if sparse_out else 1)
+
+
+def launches(kid, x_sparse, sparse_out, auto=True, long_extra=0, bool_fused=False):
     """Kernel launches of one call (mirrors the library's dispatch). The
     selector runs inside the feature pass and the SWITCH node launches no
-    kernel of its own, so auto and forced calls launch the same kernels."""
+    kernel of its own; a selector-driven call whose choice is not the warp
+    push with atomics also launches that candidate's direct chain, whose
+    kernels return at once. bool_fused: a Boolean list-output product on a
+    matrix with long rows, whose thread pull runs the long rows' first chunks
+    in its own launch (one extra launch: the second pass)."""
     c = 1  # feature pass
     compaction = 2  # block counts, write (each block sums the counts before it)
     scan = 2
+    if auto and kid != 7:
+        c += direct_chain_launches(x_sparse, sparse_out)
     if kid <= 5:
         dist = kid % 3
-        c += (2 if dist == 2 else 1 + long_extra)
+        if dist == 0 and bool_fused:
+            c += 2
+        else:
+            c += (2 if dist == 2 else 1 + long_extra)
         if x_sparse:
             c += 2
         if sparse_out:
@@ -339,7 +355,7 @@ class Stencil256:
         self.h_yval = [torch.empty(self.m, dtype=torch.float32).pin_memory() for _ in self.RHOS]
         self.h_yd = [torch.empty(self.m, dtype=torch.float32).pin_memory() for _ in self.RHOS]
         h2d = sum(t.numel() * 4 for t in self.h_idx + self.h_val + self.h_xd) + self.h_cnt.numel() * 8
-        d2h = self.h_nnzy.numel() * 8 + sum(c["nnz_y"] * 8 for c in self.calls if c["fmt"] == "list") + \
+        d2h = sum(8 + c["nnz_y"] * 8 for c in self.calls if c["fmt"] == "list") + \
             sum(self.m * 4 for c in self.calls if c["fmt"] == "dense")
         return h2d, d2h
 
@@ -348,16 +364,18 @@ class Stencil256:
         goes host -> device on a copy stream and the call waits only for its
         own input, so later inputs cross the link while earlier products run;
         every dense output goes back on a second copy stream as soon as its
-        product is done; the list outputs, whose sizes only the device knows,
-        go back after one read of their counts at the end."""
+        product is done; a list output, whose size only the device knows, goes
+        back on a third as soon as its count (read on a fourth) reaches the
+        host, while the later products run."""
         torch = self.torch
         cur = torch.cuda.current_stream()
         if not hasattr(self, "s_in"):
-            self.s_in, self.s_out = torch.cuda.Stream(), torch.cuda.Stream()
+            self.s_in, self.s_out, self.s_cnt, self.s_list = (torch.cuda.Stream() for _ in range(4))
             self.ev_in = [torch.cuda.Event() for _ in self.calls]
             self.ev_done = [torch.cuda.Event() for _ in self.calls]
-        self.s_in.wait_stream(cur)
-        self.s_out.wait_stream(cur)
+            self.ev_cnt = [torch.cuda.Event() for _ in self.calls]
+        for st in (self.s_in, self.s_out, self.s_cnt, self.s_list):
+            st.wait_stream(cur)
         with torch.cuda.stream(self.s_in):
             self.d_cnt.copy_(self.h_cnt, non_blocking=True)
             for j, c in enumerate(self.calls):
@@ -377,14 +395,21 @@ class Stencil256:
                 self.s_out.wait_event(self.ev_done[j])
                 with torch.cuda.stream(self.s_out):
                     self.h_yd[i].copy_(self.yd[i], non_blocking=True)
-        self.h_nnzy.copy_(self.nnz_y, non_blocking=True)
-        cur.synchronize()  # the list sizes decide the copies
-        for c in self.calls:
+            else:
+                self.s_cnt.wait_event(self.ev_done[j])
+                with torch.cuda.stream(self.s_cnt):
+                    self.h_nnzy[i:i + 1].copy_(self.nnz_y[i:i + 1], non_blocking=True)
+                    self.ev_cnt[j].record(self.s_cnt)
+        for j, c in enumerate(self.calls):
             if c["fmt"] == "list":
-                i, k = c["i"], int(self.h_nnzy[c["i"]])
-                self.h_yidx[i][:k].copy_(self.yidx[i][:k], non_blocking=True)
-                self.h_yval[i][:k].copy_(self.yval[i][:k], non_blocking=True)
+                self.ev_cnt[j].synchronize()  # this list's size decides its copy
+                i = c["i"]
+                k = int(self.h_nnzy[i])
+                with torch.cuda.stream(self.s_list):
+                    self.h_yidx[i][:k].copy_(self.yidx[i][:k], non_blocking=True)
+                    self.h_yval[i][:k].copy_(self.yval[i][:k], non_blocking=True)
         cur.wait_stream(self.s_out)
+        cur.wait_stream(self.s_list)
 
     def config(self):
         return {"workload": self.name, "matrix": f"27-point stencil {self.side}^3, FP32, CSR + CSC resident",
@@ -503,7 +528,8 @@ class Rmat22:
                 args_ = (self.m, self.n, self.nnz, c["nnz_x"], c["nnz_s"], c["nnz_y"], 0, 0, 0, True, True)
                 c["bytes"] = work_bytes(*args_)
                 c["kbytes"] = useful_bytes(c["kid"], *args_)
-                c["launches"] = launches(c["kid"], True, True, long_extra=self.long_extra_flags)
+                c["launches"] = launches(c["kid"], True, True, long_extra=self.long_extra_flags,
+                                         bool_fused=bool(self.long_extra))
             else:
                 c["nnz_y"] = self.m
                 args_ = (self.m, self.n, self.nnz, c["nnz_x"], c["nnz_s"], self.m, 4, 4, 4, False, False)
@@ -555,22 +581,56 @@ class Rmat22:
         self.d_counts = torch.empty_like(self.counts)
         self.d_prx = torch.empty_like(self.x_pr)
         h2d = sum(f.numel() * 4 for f in self.h_front) + self.h_counts.numel() * 8 + self.h_prx.numel() * 4
-        d2h = self.h_ypr.numel() * 4 + self.h_nnzy.numel() * 8 + \
-            sum(c["nnz_y"] * 4 for c in self.calls if c["kind"] == "bfs")
+        d2h = self.h_ypr.numel() * 4 + sum(8 + c["nnz_y"] * 4 for c in self.calls if c["kind"] == "bfs")
         return h2d, d2h
 
     def e2e_step(self):
-        for hf, df in zip(self.h_front, self.d_front):
-            df.copy_(hf, non_blocking=True)
-        self.d_counts.copy_(self.h_counts, non_blocking=True)
-        self.d_prx.copy_(self.h_prx, non_blocking=True)
-        self.run_step(fronts=self.d_front, counts=self.d_counts, x_pr=self.d_prx)
-        self.h_ypr.copy_(self.y_pr, non_blocking=True)
-        self.h_nnzy.copy_(self.nnz_y, non_blocking=True)
-        self.torch.cuda.current_stream().synchronize()  # the list sizes decide the copies
-        for i in range(len(self.frontiers)):
+        """One step through the public API with its copies: the counts and then
+        every frontier go host -> device on a copy stream, each product waiting
+        only for its own input; each new frontier goes back on another copy
+        stream as soon as its size (read on a third) reaches the host, and the
+        PageRank y on a fourth, while the later products run."""
+        torch = self.torch
+        asv = self.asv
+        cur = torch.cuda.current_stream()
+        nf = len(self.frontiers)
+        if not hasattr(self, "s_in"):
+            self.s_in, self.s_out, self.s_cnt, self.s_list = (torch.cuda.Stream() for _ in range(4))
+            self.ev_in = [torch.cuda.Event() for _ in range(nf + 1)]
+            self.ev_done = [torch.cuda.Event() for _ in range(nf + 1)]
+            self.ev_cnt = [torch.cuda.Event() for _ in range(nf)]
+        for st in (self.s_in, self.s_out, self.s_cnt, self.s_list):
+            st.wait_stream(cur)
+        with torch.cuda.stream(self.s_in):
+            self.d_counts.copy_(self.h_counts, non_blocking=True)
+            for i, (hf, df) in enumerate(zip(self.h_front, self.d_front)):
+                df.copy_(hf, non_blocking=True)
+                self.ev_in[i].record(self.s_in)
+            self.d_prx.copy_(self.h_prx, non_blocking=True)
+            self.ev_in[nf].record(self.s_in)
+        h = self.Ab.handle
+        for i in range(nf):
+            cur.wait_event(self.ev_in[i])
+            asv.asv_spmspv(h, self.d_counts[i], self.d_front[i], None, None, asv.ASV_OUT_SPARSE, None, self.yidx[i],
+                           None, self.nnz_y[i:i + 1], self.m, "auto")
+            self.ev_done[i].record(cur)
+            self.s_cnt.wait_event(self.ev_done[i])
+            with torch.cuda.stream(self.s_cnt):
+                self.h_nnzy[i:i + 1].copy_(self.nnz_y[i:i + 1], non_blocking=True)
+                self.ev_cnt[i].record(self.s_cnt)
+        cur.wait_event(self.ev_in[nf])
+        asv.asv_spmv(self.Af.handle, self.d_prx, self.y_pr, "auto")
+        self.ev_done[nf].record(cur)
+        self.s_out.wait_event(self.ev_done[nf])
+        with torch.cuda.stream(self.s_out):
+            self.h_ypr.copy_(self.y_pr, non_blocking=True)
+        for i in range(nf):
+            self.ev_cnt[i].synchronize()  # this frontier's size decides its copy
             k = int(self.h_nnzy[i])
-            self.h_yidx[i][:k].copy_(self.yidx[i][:k], non_blocking=True)
+            with torch.cuda.stream(self.s_list):
+                self.h_yidx[i][:k].copy_(self.yidx[i][:k], non_blocking=True)
+        cur.wait_stream(self.s_out)
+        cur.wait_stream(self.s_list)
 
     def config(self):
         return {"workload": self.name, "graph": f"rmat scale {self.scale} edge factor {self.edge_factor}",

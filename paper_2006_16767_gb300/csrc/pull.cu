@@ -18,6 +18,7 @@ template <class T, bool MASK, bool SOUT>
 void launch_pull_warp_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStream_t s);
 template <class T, bool MASK, bool SOUT>
 void launch_pull_long_dtype(asv_matrix_s* H, const PullArg& a, bool vec, cudaStream_t s);
+void launch_pull_bool_fused(asv_matrix_s* H, const PullArg& a, bool masked, bool vec, cudaStream_t s);
 
 constexpr int kBalB = 256;   // threads per balanced tile
 constexpr int kBalIPT = 8;   // merge items per thread
@@ -27,7 +28,8 @@ int64_t pull_tile_items(int32_t) { return kBalD; }
 
 // ---------------------------------------------------------------- one row per thread
 // Rows too long to stage (or a warp whose 32 rows do not fit the stage) are
-// summed straight from global memory, one row per thread.
+// summed straight from global memory, one row per thread (arithmetic
+// semirings; Boolean rows take pull_rows_bool).
 template <class T, bool MASK, bool SOUT>
 __device__ __forceinline__ typename Sr<T>::Acc row_direct(const int32_t* __restrict__ col, const T* __restrict__ val,
                                                           const T* __restrict__ x, const uint32_t* __restrict__ xbits,
@@ -35,29 +37,6 @@ __device__ __forceinline__ typename Sr<T>::Acc row_direct(const int32_t* __restr
     using S = Sr<T>;
     typename S::Acc acc;
     S::acc_zero(acc);
-    if constexpr (S::kPattern) {
-        // the first term alone (with a dense frontier most rows stop there),
-        // then four terms per step with their index loads and bit gathers in
-        // flight together; OR is settled by the first true term
-        if (b < e && bool_gather(x, xbits, __ldg(col + b))) {
-            hit = true;
-            return 1u;
-        }
-        for (int32_t k = b + 1; k < e; k += 4) {
-            int32_t c[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) c[u] = k + u < e ? __ldg(col + k + u) : -1;
-            uint32_t t = 0u;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) t |= c[u] >= 0 ? bool_gather(x, xbits, c[u]) : 0u;
-            if (t) {
-                acc = 1u;
-                hit = true;
-                break;
-            }
-        }
-        return acc;
-    }
     for (int32_t k = b; k < e; ++k) {
         const int32_t c = __ldg(col + k);
         if (MASK || SOUT) {
@@ -99,6 +78,12 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t r0 = ((int64_t)blockIdx.x * kStageWarps + w) * 32;
     if (r0 >= m) return;
+    if constexpr (S::kPattern) {
+        // Boolean rows stop at their first hit, so copying whole spans would
+        // read indices the walk never touches: they take the direct walk
+        pull_rows_bool<SOUT>(m, rowptr, col, p, (bool8*)y, yflag, r0, lane);
+        return;
+    }
     const int64_t i = r0 + lane;
     const int32_t rb = __ldg(rowptr + min(i, m));
     const int32_t span_end = __ldg(rowptr + min(r0 + 32, m));
@@ -110,9 +95,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
     const bool off = mine && row_masked(p.ymask, i);  // excluded by the output mask: y_i = 0
     bool hit = false;
     typename S::Acc acc;
-    // Boolean rows stop at their first hit, so copying whole spans would read
-    // indices the direct walk never touches: they take the direct path
-    if (!S::kPattern && span_end - a0 <= kStageCap) {
+    if (span_end - a0 <= kStageCap) {
         const int nchunks = (span_end - a0 + 3) >> 2;
         int32_t* sc = s_col[w];
         T* sv = kStageVals ? s_val[w] : nullptr;
@@ -256,40 +239,12 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
                 }
             }
         }
-    } else if constexpr (S::kPattern) {
-        // each lane walks the first 32 entries of its row alone (most rows
-        // stop early); a row still undecided after them would hold the whole
-        // warp for a serial chain of loads, so the warp finishes those rows
-        // together, 64 terms (two coalesced index loads and their bit
-        // gathers) per step
-        constexpr unsigned FULL = 0xffffffffu;
-        constexpr int32_t kAlone = 32;
-        S::acc_zero(acc);
-        if (mine && !off) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, min(re, rb + kAlone), hit);
-        const bool coop = mine && !off && !acc && re - rb > kAlone;
-        for (unsigned pend = __ballot_sync(FULL, coop); pend; pend &= pend - 1) {
-            const int src = __ffs(pend) - 1;
-            const int32_t b = __shfl_sync(FULL, rb, src) + kAlone, e = __shfl_sync(FULL, re, src);
-            bool found = false;
-            for (int32_t k0 = b; k0 < e && !found; k0 += 64) {
-                const int32_t k1 = k0 + lane, k2 = k0 + 32 + lane;
-                const int32_t c1 = k1 < e ? __ldg(col + k1) : -1, c2 = k2 < e ? __ldg(col + k2) : -1;
-                const uint32_t t = (c1 >= 0 ? bool_gather(x, p.xbits, c1) : 0u) |
-                                   (c2 >= 0 ? bool_gather(x, p.xbits, c2) : 0u);
-                found = __any_sync(FULL, t != 0u);
-            }
-            if (lane == src && found) {
-                acc = 1u;
-                hit = true;
-            }
-        }
     } else {
         if (mine && !off) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, re, hit);
         else S::acc_zero(acc);
     }
     if (mine) {
-        // a Boolean sparse output is its flags (the emitted values are one)
-        if (!(S::kPattern && SOUT)) y[i] = S::part_T(S::acc_part(acc));
+        y[i] = S::part_T(S::acc_part(acc));
         if (SOUT && hit) yflag[i] = 1;
     }
 }
@@ -546,15 +501,19 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     // rows over kLongRow entries: their warp-per-segment pass (and fix-up)
     // goes first, on the side stream; the short-row kernel then fills the SMs
     // that the pass's tail -- segments walked to their end -- leaves idle.
-    // The two write disjoint rows.
-    const bool fork = dist != 2 && H->nseg > 0;
+    // The two write disjoint rows. A Boolean list-output thread pull runs
+    // both in one launch instead (k_pull_bool_fused).
+    const bool fused = Sr<T>::kPattern && SOUT && dist == 0 && H->nseg > 0 && H->long_rest != nullptr;
+    const bool fork = dist != 2 && H->nseg > 0 && !fused;
     if (fork) {
         cudaEventRecord(H->ev_fork, s);
         cudaStreamWaitEvent(H->side_stream, H->ev_fork, 0);
         launch_pull_long_dtype<T, MASK, SOUT>(H, a, vec, H->side_stream);
         cudaEventRecord(H->ev_join, H->side_stream);
     }
-    if (dist == 0) {
+    if (fused) {
+        if constexpr (Sr<T>::kPattern && SOUT) launch_pull_bool_fused(H, a, MASK, vec, s);
+    } else if (dist == 0) {
         const unsigned g = (unsigned)((m + 32 * kStageWarps - 1) / (32 * kStageWarps));
         int32_t* st = H->ws.status;
         const uint32_t wl = H->wait_limit;

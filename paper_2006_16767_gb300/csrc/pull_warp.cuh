@@ -210,6 +210,48 @@ __device__ __forceinline__ typename Sr<T>::Atom atom_combine(typename Sr<T>::Ato
 constexpr int kLongFirst = 1;
 constexpr int kLongPiece = 512;
 
+// One warp's segment sg of a Boolean list-output product: its first
+// kLongFirst chunks; a true term sets the row's flag, otherwise the rest of
+// the segment is queued for k_pull_long_rest as pieces of kLongPiece entries.
+template <bool MASK, bool VEC>
+__device__ __forceinline__ void long_seg_bool_first(int64_t sg, int64_t nnz, const int4* __restrict__ seg,
+                                                    const int32_t* __restrict__ col, const PullIO& p, uint8_t* yflag,
+                                                    int4* rest, unsigned int* rest_n, int lane) {
+    using T = bool8;
+    const bool8* __restrict__ x = (const bool8*)p.x;
+    const int4 d = __ldg(seg + sg);  // {row, begin, end, whole row}
+    const int32_t row = d.x, b = d.y;
+    const int32_t e = row_masked(p.ymask, row) ? b : d.z;  // a masked row has no term
+    const int32_t a0 = b & ~3;
+    const int nsteps = (e - a0 + 127) >> 7;
+    const int lim = min(nsteps, kLongFirst);
+    bool hit = false;
+    uint32_t acc = 0u;
+    Chunk<T, MASK, VEC> cur;
+    chunk_load(cur, col, (const T*)nullptr, nnz, a0 + 4 * lane, b, e);
+    for (int t = 0; t < lim; ++t) {
+        const int32_t base = a0 + 128 * t + 4 * lane;
+        Chunk<T, MASK, VEC> nxt;
+        // the next chunk is loaded before this one's gathers -- unless this
+        // is the last chunk this warp walks (the rest goes to the second pass)
+        if (t + 1 < lim || lim == nsteps) chunk_load(nxt, col, (const T*)nullptr, nnz, base + 128, b, e);
+        acc |= chunk_sum<T, MASK, true, VEC>(cur, (const T*)nullptr, x, p.xbits, base, hit);
+        if (__any_sync(0xffffffffu, acc != 0u)) break;
+        cur = nxt;
+    }
+    if (__any_sync(0xffffffffu, hit)) {
+        if (lane == 0) yflag[row] = 1;
+    } else if (lim < nsteps) {
+        const int32_t r0 = a0 + 128 * lim;
+        const int32_t np = (e - r0 + kLongPiece - 1) / kLongPiece;
+        unsigned int q0 = 0;
+        if (lane == 0) q0 = atomicAdd(rest_n, (unsigned int)np);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        for (int32_t k = lane; k < np; k += 32)
+            rest[q0 + k] = make_int4(row, r0 + k * kLongPiece, min(e, r0 + (k + 1) * kLongPiece), 0);
+    }
+}
+
 template <class T, bool MASK, bool SOUT, bool VEC>
 __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, const int4* __restrict__ seg,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
@@ -223,26 +265,26 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     const int lane = threadIdx.x & 31;
     const int64_t sg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (sg >= nseg) return;
+    if constexpr (S::kPattern && SOUT) {
+        if (rest != nullptr) {
+            long_seg_bool_first<MASK, VEC>(sg, nnz, seg, col, p, yflag, rest, rest_n, lane);
+            return;
+        }
+    }
     const int4 d = __ldg(seg + sg);  // {row, begin, end, whole row}
     const int32_t row = d.x, b = d.y;
     const int32_t e = row_masked(p.ymask, row) ? b : d.z;  // a masked row sums nothing (y = 0)
     const int32_t a0 = b & ~3;
     const int nsteps = (e - a0 + 127) >> 7;
-    int lim = nsteps;
-    if constexpr (S::kPattern && SOUT) {
-        if (rest != nullptr) lim = min(nsteps, kLongFirst);
-    }
     bool hit = false;
     typename S::Acc acc;
     S::acc_zero(acc);
     Chunk<T, MASK, VEC> cur;
     chunk_load(cur, col, val, nnz, a0 + 4 * lane, b, e);
-    for (int t = 0; t < lim; ++t) {
+    for (int t = 0; t < nsteps; ++t) {
         const int32_t base = a0 + 128 * t + 4 * lane;
         Chunk<T, MASK, VEC> nxt;
-        // the next chunk is loaded before this one's gathers -- unless this
-        // is the last chunk this warp walks (the rest goes to the second pass)
-        if (t + 1 < lim || lim == nsteps) chunk_load(nxt, col, val, nnz, base + 128, b, e);
+        chunk_load(nxt, col, val, nnz, base + 128, b, e);  // the next chunk before this one's gathers
         S::acc_add(acc, chunk_sum<T, MASK, SOUT, VEC>(cur, val, x, p.xbits, base, hit));
         if constexpr (S::kPattern) {
             // OR is settled by the first hit (a deeper prefetch, and warps
@@ -260,17 +302,7 @@ __global__ void __launch_bounds__(256) k_pull_long(int64_t nseg, int64_t nnz, co
     if constexpr (S::kPattern && SOUT) {
         // a Boolean sparse output is its flags: any segment with a true term
         // settles its row, so no partials and no fix-up
-        if (h) {
-            if (lane == 0) yflag[row] = 1;
-        } else if (lim < nsteps) {
-            const int32_t r0 = a0 + 128 * lim;
-            const int32_t np = (e - r0 + kLongPiece - 1) / kLongPiece;
-            unsigned int q0 = 0;
-            if (lane == 0) q0 = atomicAdd(rest_n, (unsigned int)np);
-            q0 = __shfl_sync(0xffffffffu, q0, 0);
-            for (int32_t k = lane; k < np; k += 32)
-                rest[q0 + k] = make_int4(row, r0 + k * kLongPiece, min(e, r0 + (k + 1) * kLongPiece), 0);
-        }
+        if (h && lane == 0) yflag[row] = 1;
         return;
     }
     if (lane != 0) return;
@@ -320,6 +352,36 @@ __global__ void __launch_bounds__(256) k_pull_long_rest(const int4* __restrict__
         if (lane == 0 && hit) yflag[d.x] = 1;
     }
 }
+
+// Boolean products with a list output on a matrix with long rows (the BFS
+// levels of a power-law graph): the long-row segments' first chunks and the
+// one-row-per-thread walk of the other rows in one launch of 128-thread
+// blocks. Blocks [0, lblocks) take four segments each (a warp per segment),
+// the others 128 rows each (32 per warp). Blocks are dispatched in about
+// index order, so the segments -- whose first chunks and queued rests are
+// the long pole -- start first and the row blocks fill the SMs as segment
+// blocks finish, with no gap between two launches and no second stream.
+template <bool MASK, bool VEC>
+__global__ void __launch_bounds__(128) k_pull_bool_fused(int64_t m, int64_t nseg, int64_t nnz, unsigned lblocks,
+                                                         const int32_t* __restrict__ rowptr,
+                                                         const int4* __restrict__ seg, const int32_t* __restrict__ col,
+                                                         PullArg a, void* ywork, uint8_t* yflag, int4* rest,
+                                                         unsigned int* rest_n) {
+    const PullIO p = resolve(a, ywork, true);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (blockIdx.x < lblocks) {
+        const int64_t sg = (int64_t)blockIdx.x * 4 + w;
+        if (sg < nseg) long_seg_bool_first<MASK, VEC>(sg, nnz, seg, col, p, yflag, rest, rest_n, lane);
+        return;
+    }
+    const int64_t r0 = ((int64_t)(blockIdx.x - lblocks) * 4 + w) * 32;
+    if (r0 >= m) return;
+    pull_rows_bool<true>(m, rowptr, col, p, nullptr, yflag, r0, lane);
+}
+
+// The fused launch above, then the second pass over the queued rests (the
+// Boolean list-output thread pull on a matrix with long rows).
+void launch_pull_bool_fused(asv_matrix_s* H, const PullArg& a, bool masked, bool vec, cudaStream_t s);
 
 template <class T>
 __global__ void k_pull_long_fixup(int64_t nmulti, const int32_t* __restrict__ multi_row,

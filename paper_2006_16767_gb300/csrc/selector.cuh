@@ -109,16 +109,18 @@ __device__ __forceinline__ void commit_kernel(const SelectArg& sa, CallDesc* des
 }
 
 // Called by every thread of the block that published the descriptor, once
-// it holds all the features; the call format's window was staged at the
-// start of the pass. Warp 0 walks the trees and lane 0 commits the choice.
-__device__ __forceinline__ void run_selector(const SelectArg& sa, CallDesc* desc, const TreeNode* sn) {
+// it holds all the features (vf: the four vector features as published, in
+// shared memory); the call format's window was staged at the start of the
+// pass. Warp 0 walks the trees and lane 0 commits the choice.
+__device__ __forceinline__ void run_selector(const SelectArg& sa, CallDesc* desc, const TreeNode* sn,
+                                             const double* vf) {
     __shared__ double s_f[13];
     if (threadIdx.x < 32) {
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int q = 0; q < 9; ++q) s_f[q] = sa.mf[q];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) s_f[9 + q] = desc->vfeat[q];
+            for (int q = 0; q < 4; ++q) s_f[9 + q] = vf[q];
         }
         __syncwarp();
         const int kid = pick_kernel(sa, sn, s_f, 13);

@@ -59,8 +59,9 @@ __device__ __forceinline__ void reset_hub_queue(const SelectArg& sa, unsigned nq
 }
 
 // `blocks` is the number of blocks that take part (all of them call this);
-// the one that draws the last ticket publishes. ch counts the listed columns
-// longer than kLongSeg.
+// the one that draws the last ticket publishes (a pass of one block, a short
+// list, publishes its own totals and leaves the counters and the ticket
+// alone). ch counts the listed columns longer than kLongSeg.
 template <int B>
 __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long ch,
                                               unsigned long long* counters, unsigned int* ticket, CallDesc* desc,
@@ -68,22 +69,31 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
                                               const SelectArg& sa, unsigned blocks, TreeNode* sn, unsigned nq) {
     __shared__ unsigned long long sm[B / 32 + 1];
     __shared__ bool last;
+    __shared__ double s_vf[4];  // the published vector features, for the selector
     cx = block_reduce_sum<B>(cx, sm);
     cs = block_reduce_sum<B>(cs, sm);
     ch = block_reduce_sum<B>(ch, sm);
+    const bool alone = blocks == 1;
     if (threadIdx.x == 0) {
-        if (cx) atomicAdd(&counters[0], cx);
-        if (cs) atomicAdd(&counters[1], cs);
-        if (ch) atomicAdd(&counters[2], ch);
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == blocks - 1;
+        if (alone) {
+            last = true;
+        } else {
+            if (cx) atomicAdd(&counters[0], cx);
+            if (cs) atomicAdd(&counters[1], cs);
+            if (ch) atomicAdd(&counters[2], ch);
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == blocks - 1;
+        }
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
-        __threadfence();
-        unsigned long long nx = atomicExch(&counters[0], 0ull);
-        unsigned long long ns = atomicExch(&counters[1], 0ull);
-        unsigned long long nh = atomicExch(&counters[2], 0ull);
+        unsigned long long nx = cx, ns = cs, nh = ch;
+        if (!alone) {
+            __threadfence();
+            nx = atomicExch(&counters[0], 0ull);
+            ns = atomicExch(&counters[1], 0ull);
+            nh = atomicExch(&counters[2], 0ull);
+        }
         // a list with repeated or out-of-range entries could exceed the
         // workspaces sized for nnz_x <= n and nnz_s <= nnz: clamp and report
         if (nx > (unsigned long long)n || ns > (unsigned long long)nnz) {
@@ -92,8 +102,14 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
             ns = ns > (unsigned long long)nnz ? (unsigned long long)nnz : ns;
         }
         publish_desc(desc, di, nx, ns, nh < nx ? nh : nx, n, nnz);
-        __threadfence();
-        atomicExch(ticket, 0u);
+        s_vf[0] = (double)nx;
+        s_vf[1] = n > 0 ? (double)nx / (double)n : 0.0;
+        s_vf[2] = (double)ns;
+        s_vf[3] = nnz > 0 ? (double)ns / (double)nnz : 0.0;
+        if (!alone) {
+            __threadfence();
+            atomicExch(ticket, 0u);
+        }
     }
     // the last block returns the push kernels' hub-column queue of the
     // previous call to its empty state
@@ -102,7 +118,7 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
     // the start of the pass, so the choice is ready when the feature pass ends
     if (last && sa.enabled) {
         __syncthreads();
-        run_selector(sa, desc, sn);
+        run_selector(sa, desc, sn, s_vf);
     }
 }
 

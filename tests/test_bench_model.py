@@ -37,23 +37,34 @@ def test_push_and_validated_pull_bytes():
 
 def test_launch_mirror_matches_the_profiled_step():
     # launches per call of each class in the committed launch list of one
-    # step (Boolean list in / list out; PageRank dense, forced in the replay)
+    # step (Boolean list in / list out; PageRank dense, forced in the replay);
+    # the replay launches the recorded choice directly, so no direct chain
     K = {name: i for i, name in enumerate(("pull_thread", "pull_warp", "pull_bal", "mpull_thread", "mpull_warp",
                                           "mpull_bal", "push_thread_atom", "push_warp_atom", "push_bal_atom"))}
     long_flags = 2  # long-row pass and its second pass, no fix-up for a Boolean list output
-    assert bench.launches(K["pull_thread"], True, True, long_extra=long_flags) == 104 // 13
-    assert bench.launches(K["push_bal_atom"], True, True) == 90 // 15
-    assert bench.launches(K["push_thread_atom"], True, True) == 88 // 22
-    assert bench.launches(K["push_warp_atom"], True, True) == 24 // 6
-    # the selector-driven PageRank call runs the feature pass the forced replay skips
-    assert bench.launches(K["pull_warp"], False, False, long_extra=2) == 3 + 1
+    # features, scatter, the fused long-row + thread pass, the second pass, compaction (2), clear
+    assert bench.launches(K["pull_thread"], True, True, auto=False, long_extra=long_flags, bool_fused=True) == 105 // 15
+    assert bench.launches(K["push_bal_atom"], True, True, auto=False) == 96 // 16
+    assert bench.launches(K["push_thread_atom"], True, True, auto=False) == 48 // 12
+    assert bench.launches(K["push_warp_atom"], True, True, auto=False) == 52 // 13
+    # the replay of the PageRank call skips the feature pass (3 launches): the
+    # selector-driven call adds it and the warp push's direct chain (4)
+    assert bench.launches(K["pull_warp"], False, False, auto=False, long_extra=2) == 3 + 1
+    assert bench.launches(K["pull_warp"], False, False, long_extra=2) == 3 + 1 + 4
+    # a selector-driven call that picks the warp push launches its chain only
+    assert bench.launches(K["push_warp_atom"], True, True) == bench.launches(K["push_warp_atom"], True, True, auto=False)
 
 
 def test_launch_mirror_matches_the_profiled_stencil_step():
     # launches per call in the committed launch list of the stencil step
     # (per density: x listed -> y listed, x dense -> y dense)
     K = {"pull_thread": 0, "push_warp_atom": 7}
-    assert bench.launches(K["push_warp_atom"], True, True) == 4  # features, push, compaction (2)
-    assert bench.launches(K["push_warp_atom"], False, False) == 5  # features, x compaction (2), push, write-out
-    assert bench.launches(K["pull_thread"], True, True) == 6  # features, scatter, pull, compaction (2), clear
-    assert bench.launches(K["pull_thread"], False, False) == 2  # features, pull
+    assert bench.launches(K["push_warp_atom"], True, True, auto=False) == 4  # features, push, compaction (2)
+    # features, x compaction (2), push, write-out
+    assert bench.launches(K["push_warp_atom"], False, False, auto=False) == 5
+    # features, scatter, pull, compaction (2), clear
+    assert bench.launches(K["pull_thread"], True, True, auto=False) == 6
+    assert bench.launches(K["pull_thread"], False, False, auto=False) == 2  # features, pull
+    # selector-driven: the pulls also launch the warp push's chain (3 and 4 kernels)
+    assert bench.launches(K["pull_thread"], True, True) == 6 + 3
+    assert bench.launches(K["pull_thread"], False, False) == 2 + 4
