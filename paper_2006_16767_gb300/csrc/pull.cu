@@ -57,7 +57,11 @@ __device__ __forceinline__ typename Sr<T>::Acc row_direct(const int32_t* __restr
 // With lanes on consecutive rows, the x gathers of one step land on
 // neighbouring columns for banded and mesh-like matrices, so a warp's gather
 // touches one or two cache lines instead of one per lane.
-constexpr int kStageCap = 1024;  // entries staged per warp
+// entries staged per warp: a 32-row span of the 27-point stencil (at most
+// 868 entries from its 16-byte-aligned start) fits, and four warps' stages
+// (28.7 KB) leave room for seven blocks per SM where 1,024 entries left six
+// (the stencil's dense-x product 718 -> 687 us on GB300)
+constexpr int kStageCap = 896;
 constexpr int kStageWarps = 4;
 
 template <class T, bool MASK, bool SOUT, bool VEC, bool TMA>
@@ -76,14 +80,16 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
     const T* __restrict__ x = (const T*)p.x;
     T* __restrict__ y = (T*)p.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t r0 = ((int64_t)blockIdx.x * kStageWarps + w) * 32;
-    if (r0 >= m) return;
     if constexpr (S::kPattern) {
         // Boolean rows stop at their first hit, so copying whole spans would
-        // read indices the walk never touches: they take the direct walk
-        pull_rows_bool<SOUT>(m, rowptr, col, p, (bool8*)y, yflag, r0, lane);
+        // read indices the walk never touches: they take the direct walk,
+        // kBoolRows groups of 32 rows per warp
+        const int64_t rw = ((int64_t)blockIdx.x * kStageWarps + w) * 32 * kBoolRows;
+        if (rw < m) pull_rows_bool<SOUT>(m, rowptr, col, p, (bool8*)y, yflag, rw, lane);
         return;
     }
+    const int64_t r0 = ((int64_t)blockIdx.x * kStageWarps + w) * 32;
+    if (r0 >= m) return;
     const int64_t i = r0 + lane;
     const int32_t rb = __ldg(rowptr + min(i, m));
     const int32_t span_end = __ldg(rowptr + min(r0 + 32, m));
@@ -514,7 +520,8 @@ static void pull_dispatch(asv_matrix_s* H, int dist, const PullIO* direct, cudaS
     if (fused) {
         if constexpr (Sr<T>::kPattern && SOUT) launch_pull_bool_fused(H, a, MASK, vec, s);
     } else if (dist == 0) {
-        const unsigned g = (unsigned)((m + 32 * kStageWarps - 1) / (32 * kStageWarps));
+        const int64_t rows_per_block = 32 * kStageWarps * (Sr<T>::kPattern ? kBoolRows : 1);
+        const unsigned g = (unsigned)((m + rows_per_block - 1) / rows_per_block);
         int32_t* st = H->ws.status;
         const uint32_t wl = H->wait_limit;
         if (m > 0) {

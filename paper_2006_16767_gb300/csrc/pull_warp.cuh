@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) k_pull_long_rest(const int4* __restrict__
 // levels of a power-law graph): the long-row segments' first chunks and the
 // one-row-per-thread walk of the other rows in one launch of 128-thread
 // blocks. Blocks [0, lblocks) take four segments each (a warp per segment),
-// the others 128 rows each (32 per warp). Blocks are dispatched in about
+// the others 128 * kBoolRows rows each. Blocks are dispatched in about
 // index order, so the segments -- whose first chunks and queued rests are
 // the long pole -- start first and the row blocks fill the SMs as segment
 // blocks finish, with no gap between two launches and no second stream.
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(128) k_pull_bool_fused(int64_t m, int64_t nseg
         if (sg < nseg) long_seg_bool_first<MASK, VEC>(sg, nnz, seg, col, p, yflag, rest, rest_n, lane);
         return;
     }
-    const int64_t r0 = ((int64_t)(blockIdx.x - lblocks) * 4 + w) * 32;
+    const int64_t r0 = ((int64_t)(blockIdx.x - lblocks) * 4 + w) * 32 * kBoolRows;
     if (r0 >= m) return;
     pull_rows_bool<true>(m, rowptr, col, p, nullptr, yflag, r0, lane);
 }

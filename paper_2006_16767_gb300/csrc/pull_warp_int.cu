@@ -7,7 +7,7 @@ ASV_INSTANTIATE_PULL_WARP(bool8)
 
 void launch_pull_bool_fused(asv_matrix_s* H, const PullArg& a, bool masked, bool vec, cudaStream_t s) {
     const unsigned lblocks = (unsigned)((H->nseg + 3) / 4);
-    const unsigned g = lblocks + (unsigned)((H->m + 127) / 128);
+    const unsigned g = lblocks + (unsigned)((H->m + 128 * kBoolRows - 1) / (128 * kBoolRows));
 #define FUSED(MK, V)                                                                                          \
     k_pull_bool_fused<MK, V><<<g, 128, 0, s>>>(H->m, H->nseg, H->nnz, lblocks, H->rowptr, H->seg, H->col, a,  \
                                                 H->ws.ywork, H->ws.yflag, H->long_rest, H->long_rest_n)

@@ -384,8 +384,11 @@ __device__ __forceinline__ void scatter_bit(uint32_t* xbits, int32_t j, bool set
 // Scatters a listed x into the zero-invariant dense workspace (set) or
 // restores it to zero (clear). BITS: also the scatter bitmap, which only the
 // kernels that validate entries, flag output rows or read Boolean terms use.
+// A Boolean x is its bitmap alone: every Boolean kernel reads its terms
+// from the bitmap when there is one, so the byte vector is never written.
 template <class T, bool BITS>
 __global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32_t* xbits, int set, int64_t n) {
+    constexpr bool kDense = !(Sr<T>::kPattern && BITS);
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
     const T* __restrict__ xval = (const T*)desc->xval;
@@ -396,9 +399,11 @@ __global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32
     // writing the whole workspace (16-byte stores) rather than by reading the
     // list again and scattering zeros
     if (!set && 4 * nx > n) {
-        const int64_t nv = (int64_t)((n * sizeof(T)) / 16);
-        for (int64_t i = t; i < nv; i += stride) reinterpret_cast<uint4*>(xdense)[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (int64_t j = nv * (16 / (int64_t)sizeof(T)) + t; j < n; j += stride) xdense[j] = T(0);
+        if (kDense) {
+            const int64_t nv = (int64_t)((n * sizeof(T)) / 16);
+            for (int64_t i = t; i < nv; i += stride) reinterpret_cast<uint4*>(xdense)[i] = make_uint4(0u, 0u, 0u, 0u);
+            for (int64_t j = nv * (16 / (int64_t)sizeof(T)) + t; j < n; j += stride) xdense[j] = T(0);
+        }
         if (BITS)
             for (int64_t w = t; w < (n + 31) / 32; w += stride) xbits[w] = 0u;
         return;
@@ -414,13 +419,13 @@ __global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            xdense[j[q]] = v[q];
+            if (kDense) xdense[j[q]] = v[q];
             if (BITS) scatter_bit(xbits, j[q], set);
         }
     }
     for (; t < nx; t += stride) {
         const int32_t j = xidx[t];
-        xdense[j] = set ? (vals ? xval[t] : Sr<T>::one()) : T(0);
+        if (kDense) xdense[j] = set ? (vals ? xval[t] : Sr<T>::one()) : T(0);
         if (BITS) scatter_bit(xbits, j, set);
     }
 }
