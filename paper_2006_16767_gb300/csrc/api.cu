@@ -258,6 +258,7 @@ static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s
 
     CKH(P ? invert_perm(P->perm, nnz, H->perm, s) : build_csc(H, s));
     CKH(build_features(H, s));  // synchronises
+    H->narrow_acc = dtype == ASV_F32 && H->h_mfeat.max_row <= kNarrowRow;
     CKH(build_partition(H, s));
     CKH(build_long_rows(H, s));  // synchronises
     {
@@ -399,10 +400,10 @@ static void enqueue_candidate(asv_matrix_s* H, int k, int x_sparse, int om, cuda
 // depends on the feature node only, its kernels return at once unless the
 // pass chose its candidate (Gate), and that candidate's SWITCH branch is
 // empty; when it is chosen, the SWITCH node's dispatch overlaps the chain
-// instead of preceding it. (With the three atomic pushes as direct chains,
-// four branches beside each other, the R-MAT pull calls ran at half speed;
-// with one or two chains they did not. The cause was not found, so one
-// chain is kept.)
+// instead of preceding it. (More chains measured worse, for a cause not
+// found: with the three atomic pushes as direct chains the R-MAT pull calls
+// ran at half speed, and with the warp and balanced pushes the R-MAT BFS
+// step took 6.3 ms instead of 4.9 ms, so one chain is kept.)
 static constexpr int kDirect[1] = {ASV_K_PUSH_WARP_ATOM};
 
 static bool is_direct(int k) {

@@ -1,5 +1,6 @@
 // Shared device-side definitions of the adaptive SpMV/SpMSpV library (sm_103a).
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -226,6 +227,9 @@ constexpr int kTreeWindow = 1024;    // nodes of one call format staged in share
 // kLongSeg entries (a list built once per matrix): a thread walking a
 // power-law hub row of 10^5 entries alone would serialise the whole call.
 constexpr int kLongRow = 256;
+// Rows of at most kNarrowRow entries let an FP32 push accumulate in FP32:
+// kNarrowRow * 2^-24 < 2e-6 (the FP32 tolerance relative to sum |a_ij x_j|).
+constexpr int kNarrowRow = 32;
 constexpr int kLongSeg = 4096;
 
 // Handle workspaces, passed by value to the kernels that use them.

@@ -140,6 +140,10 @@ struct asv_matrix_s {
     // while a direct candidate chain of a selector graph is captured: the
     // candidate whose chain it is (the Gate of its kernels), else -1
     int32_t gate_kid = -1;
+    // an FP32 matrix whose rows have at most kNarrowRow entries: the push with
+    // atomic write-back and a dense output adds in FP32 (its error bound stays
+    // within the FP32 tolerance, see push.cu)
+    bool narrow_acc = false;
     // the long-row pass of the thread and sub-warp pulls runs beside the
     // short-row kernel: a side stream joined by two events (in a graph
     // capture they become a fork and a join of the captured graph)
@@ -236,7 +240,8 @@ void launch_x_scatter(asv_matrix_s* H, bool set, bool bits, cudaStream_t s);
 // the Gate of the kernels launched now (see gate_kid)
 inline Gate gate_of(const asv_matrix_s* H) { return Gate{H->d_desc, H->gate_kid}; }
 void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s);
-void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s);
+// narrow: the push accumulated into FP32 accumulators (narrow_acc)
+void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s, bool narrow = false);
 void launch_compact_public(asv_matrix_s* H, const void* x, int32_t* idx, void* val, int64_t* count,
                            cudaStream_t s);
 

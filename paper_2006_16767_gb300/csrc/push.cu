@@ -9,14 +9,21 @@
 //
 // Accumulation of the floating-point types is in FP64 (products are formed in
 // the value type), so the order in which atomics land does not move an FP32
-// result by more than one rounding.
+// result by more than one rounding -- except on FP32 matrices whose rows all
+// have at most kNarrowRow entries, whose atomics for a dense output add in
+// FP32 (WB_ATOM_N):
+// y_i then sums at most k <= 32 products, and k FP32 products added in any
+// order stay within k * 2^-24 * sum |a_ij x_j| <= 1.91e-6 * sum |a_ij x_j| of
+// the exact sum (the FP32 tolerance is 2e-6 of it), with half the
+// accumulator bytes and FP32 atomics.
 #include "internal.h"
 #include "prims.cuh"
 #include "sort.cuh"
 
 namespace asv {
 
-enum { WB_ATOM = 0, WB_SORT = 1, WB_PRIV = 2 };
+enum { WB_ATOM = 0, WB_SORT = 1, WB_PRIV = 2, WB_ATOM_N = 3 };
+__host__ __device__ constexpr bool wb_atomic(int wb) { return wb == WB_ATOM || wb == WB_ATOM_N; }
 constexpr int kPrivBits = 12;  // rows per privatised tile = 4096
 constexpr int kPushIPT = 8;    // effective nonzeros per lane per balanced chunk
 
@@ -28,10 +35,11 @@ template <class T, int WB>
 __device__ __forceinline__ void emit(const Ws& ws, const uint32_t* ymask, int32_t r, typename Sr<T>::Part p,
                                      int64_t pos) {
     using S = Sr<T>;
-    if (WB == WB_ATOM) {
+    if (wb_atomic(WB)) {
         if (row_masked(ymask, r)) return;  // excluded by the output mask (pairs are masked when reduced)
         if constexpr (!S::kPattern) {
-            atomicAdd((typename S::Atom*)ws.acc + r, S::to_atom(S::part_T(p)));
+            if constexpr (WB == WB_ATOM_N) atomicAdd((T*)ws.acc + r, S::part_T(p));
+            else atomicAdd((typename S::Atom*)ws.acc + r, S::to_atom(S::part_T(p)));
             ws.yflag[r] = 1;
         } else {
             // a Boolean search reaches most rows many times: a (possibly
@@ -54,7 +62,7 @@ __device__ __forceinline__ void emit(const Ws& ws, const uint32_t* ymask, int32_
 template <class T, int WB, int N>
 __device__ __forceinline__ void emit_batch(const Ws& ws, const uint32_t* ymask, const int32_t (&r)[N],
                                            const typename Sr<T>::Part (&p)[N], int64_t pos0, int64_t pstride) {
-    if constexpr (WB == WB_ATOM && Sr<T>::kPattern) {
+    if constexpr (wb_atomic(WB) && Sr<T>::kPattern) {
         uint8_t f[N];
 #pragma unroll
         for (int u = 0; u < N; ++u) f[u] = r[u] >= 0 ? ws.yflag[r[u]] : (uint8_t)1;
@@ -106,7 +114,7 @@ __device__ __forceinline__ void push_segment(const int32_t* __restrict__ colptr,
     const int32_t j = desc->xidx[t];
     const T xj = list_val<T>(desc, t);
     const int32_t b = __ldg(colptr + j), e = __ldg(colptr + j + 1);
-    const int64_t pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
+    const int64_t pos0 = !wb_atomic(WB) ? (int64_t)ws.xscan[t] - b : 0;
     const int32_t sb = b + s * kLongSeg, se = min(sb + kLongSeg, e);
     for (int32_t k = sb + lane; k < se; k += 32)
         emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xj), pos0 + k);
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
             xj = list_val<T>(desc, t);
             b = __ldg(colptr + j);
             e = __ldg(colptr + j + 1);
-            pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
+            pos0 = !wb_atomic(WB) ? (int64_t)ws.xscan[t] - b : 0;
         }
         const bool lng = e - b > kLongCol;
         if (!lng) {
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
             if (lane == 0) queued = queue_long(ws, t);
             if (__shfl_sync(0xffffffffu, queued, 0)) continue;
         }
-        const int64_t pos0 = (WB != WB_ATOM) ? (int64_t)ws.xscan[t] - b : 0;
+        const int64_t pos0 = !wb_atomic(WB) ? (int64_t)ws.xscan[t] - b : 0;
         for (int32_t k0 = b + lane; k0 < e; k0 += 128) {
             int32_t rr[4];
             typename S::Part pp[4];
@@ -318,24 +326,19 @@ __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ co
 #pragma unroll
             for (int u = 0; u < kPushIPT; ++u) s_t[w][lane * kPushIPT + u] = max(v[u], carry);
             __syncwarp();
-            // every item's row index and value is loaded before the first
-            // write-back (a flag or accumulator store could alias a later
-            // load, so the compiler would not reorder them itself)
-            int32_t rr[kPushIPT];
-            typename S::Part pp[kPushIPT];
-#pragma unroll
+            // one write-back per item, four items per step: loading all eight
+            // of a lane's items before the first write-back measured slower
+            // (36 instead of 32 registers, six blocks per SM instead of eight:
+            // 622 vs 588 us summed over one root's BFS levels of R-MAT scale 20)
+#pragma unroll 4
             for (int s2 = 0; s2 < kPushIPT; ++s2) {
                 const int64_t e = e0 + s2 * 32 + lane;
-                rr[s2] = -1;
-                if (e <= elast) {
-                    const int q = s_t[w][s2 * 32 + lane];
-                    const int64_t k = (int64_t)s_base[w][q] + e;
-                    const T xq = S::kPattern ? S::one() : s_xv[w][S::kPattern ? 0 : q];
-                    rr[s2] = __ldg(rowidx + k);
-                    pp[s2] = S::mul(load_val(valc, k), xq);
-                }
+                if (e > elast) break;
+                const int q = s_t[w][s2 * 32 + lane];
+                const int64_t k = (int64_t)s_base[w][q] + e;
+                const T xq = S::kPattern ? S::one() : s_xv[w][S::kPattern ? 0 : q];
+                emit<T, WB>(ws, ym, __ldg(rowidx + k), S::mul(load_val(valc, k), xq), e);
             }
-            emit_batch<T, WB, kPushIPT>(ws, ym, rr, pp, e0 + lane, 32);
             __syncwarp();
         } else {
 #pragma unroll 2
@@ -583,7 +586,13 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
     const CallDesc* d = H->d_desc;
     Ws ws = H->ws;
     const Gate gate = gate_of(H);
-    if (dist == 2 || wb != WB_ATOM) {
+    // atomics into FP32 accumulators where every row is short enough (see
+    // above) and the output is dense: the dense write-out then reads half the
+    // bytes (the stencil's products at x densities 0.1 and 0.01: 490 -> 434 and
+    // 182 -> 135 us), while the list output's compaction measured slower on
+    // FP32 accumulators (94.9 -> 202.7 us for a 15.8M-row list) and keeps FP64
+    if (std::is_same<T, float>::value && wb == WB_ATOM && H->narrow_acc && out_mode == ASV_OUT_DENSE) wb = WB_ATOM_N;
+    if (dist == 2 || !wb_atomic(wb)) {
         k_list_deg<256><<<H->G, 256, 0, s>>>(H->colptr, d, ws.xscan, ws.blk, gate);
         if (dist == 2)
             k_list_scan<256, true><<<H->G, 256, 0, s>>>(ws.xscan, d, ws.blk, ws.chunk_t0, gate);
@@ -596,8 +605,13 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
         else if (dist == 1) k_push_warp<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
         else k_push_bal<T, WBV><<<grid * 4, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
     } while (0)
-    if (wb == WB_ATOM) TRAV(WB_ATOM);
-    else TRAV(WB_SORT);
+    if (wb == WB_ATOM_N) {
+        if constexpr (std::is_same<T, float>::value) TRAV(WB_ATOM_N);
+    } else if (wb == WB_ATOM) {
+        TRAV(WB_ATOM);
+    } else {
+        TRAV(WB_SORT);
+    }
 #undef TRAV
     using V = PV<T>;
     if (wb == WB_SORT) {
@@ -621,7 +635,7 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
         k_bin_scatter<T><<<grid, 256, 0, s>>>(ws.pkeys[0], (const T*)ws.pvals[0], ws.pkeys[1], (T*)ws.pvals[1], d, cursor);
         if (nbins > 0) k_priv_accumulate<T><<<nbins, 256, 0, s>>>(ws.pkeys[1], (const T*)ws.pvals[1], bins, H->m, ws, d);
     }
-    launch_finalize(H, true, out_mode, s);
+    launch_finalize(H, true, out_mode, s, wb == WB_ATOM_N);
 }
 
 void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s) {

@@ -609,13 +609,22 @@ struct PublicCompactPolicy {
     __device__ void count(int32_t c) { *count_out = c; }
 };
 
+// The push accumulator of a row as a value: an A (the value type's Atom, or
+// the value type itself for the FP32 accumulators of short-row matrices).
+template <class T, class A>
+__device__ __forceinline__ T acc_value(A a) {
+    if constexpr (std::is_same<A, T>::value) return a;
+    else return Sr<T>::from_atom(a);
+}
+
 // structural output set -> (yidx, yval, nnz_y); the source is the push
-// accumulators (re-zeroed as they are read) or the pull kernels' dense y.
-template <class T, bool FROM_ACC>
+// accumulators of type A (re-zeroed as they are read) or the pull kernels'
+// dense y.
+template <class T, bool FROM_ACC, class A = typename Sr<T>::Atom>
 struct OutSparsePolicy {
     using V = T;
     const CallDesc* desc;
-    typename Sr<T>::Atom* acc;
+    A* acc;
     const T* ywork;
     int32_t* status;
     int32_t* yidx;
@@ -629,11 +638,11 @@ struct OutSparsePolicy {
     __device__ void clear_word(uint32_t* bits, int64_t w) { bits[w] = 0u; }
     __device__ T load(int32_t i) const {
         if (Sr<T>::kPattern) return Sr<T>::one();
-        if (FROM_ACC) return Sr<T>::from_atom(acc[i]);
+        if (FROM_ACC) return acc_value<T, A>(acc[i]);
         return ywork[i];
     }
     __device__ void store(int32_t pos, int32_t i, T v) const {
-        if (FROM_ACC && !Sr<T>::kPattern) acc[i] = typename Sr<T>::Atom(0);
+        if (FROM_ACC && !Sr<T>::kPattern) acc[i] = A(0);
         if (pos < cap) {
             yidx[pos] = i;
             if (yval) yval[pos] = v;
@@ -678,8 +687,8 @@ void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
 // every y store of a warp is one contiguous run. A group of 512 rows without
 // a flag (most of them for a sparse product) only writes zeros.
 constexpr int kFinRows = 512;
-template <class T>
-__global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, typename Sr<T>::Atom* acc, uint8_t* yflag,
+template <class T, class A = typename Sr<T>::Atom>
+__global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, A* acc, uint8_t* yflag,
                                                         const CallDesc* __restrict__ desc, Gate gate) {
     if (gate.off()) return;
     using S = Sr<T>;
@@ -702,7 +711,7 @@ __global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, typename Sr<T
             const int64_t i = i0 + 32 * u + lane;
             const bool f = any && s_f[w][32 * u + lane] != 0;
             if (S::kPattern) v[u] = f ? S::one() : T(0);
-            else v[u] = f ? S::from_atom(acc[i]) : T(0);
+            else v[u] = f ? acc_value<T, A>(acc[i]) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
@@ -710,24 +719,24 @@ __global__ void __launch_bounds__(256) k_finalize_dense(int64_t m, typename Sr<T
             if (i >= m) break;
             y[i] = v[u];
             if constexpr (!S::kPattern) {
-                if (any && s_f[w][32 * u + lane]) acc[i] = typename S::Atom(0);
+                if (any && s_f[w][32 * u + lane]) acc[i] = A(0);
             }
         }
         __syncwarp();
     }
 }
 
-template <class T>
-static void finalize_dtype(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s) {
-    using Atom = typename Sr<T>::Atom;
+template <class T, class Atom>
+static void finalize_acc(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s) {
     if (out_mode == ASV_OUT_DENSE) {
         if (H->m > 0) {
             const int64_t groups = (H->m + kFinRows - 1) / kFinRows;
             const int64_t g = std::min<int64_t>((groups + 7) / 8, (int64_t)H->num_sms * 8);
-            k_finalize_dense<T><<<(unsigned)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag, H->d_desc, gate_of(H));
+            k_finalize_dense<T, Atom><<<(unsigned)g, 256, 0, s>>>(H->m, (Atom*)H->ws.acc, H->ws.yflag, H->d_desc,
+                                                                 gate_of(H));
         }
     } else if (from_acc) {
-        OutSparsePolicy<T, true> pol{H->d_desc, (Atom*)H->ws.acc, nullptr, H->ws.status, nullptr, nullptr, 0};
+        OutSparsePolicy<T, true, Atom> pol{H->d_desc, (Atom*)H->ws.acc, nullptr, H->ws.status, nullptr, nullptr, 0};
         compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s);
     } else {
         OutSparsePolicy<T, false> pol{H->d_desc, nullptr, (const T*)H->ws.ywork, H->ws.status, nullptr, nullptr, 0};
@@ -735,12 +744,16 @@ static void finalize_dtype(asv_matrix_s* H, bool from_acc, int out_mode, cudaStr
     }
 }
 
-void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s) {
+// narrow: the push accumulated in FP32 (FP32 matrices with short rows only)
+void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s, bool narrow) {
     switch (H->dtype) {
-        case ASV_F32: finalize_dtype<float>(H, from_acc, out_mode, s); break;
-        case ASV_F64: finalize_dtype<double>(H, from_acc, out_mode, s); break;
-        case ASV_I32: finalize_dtype<int32_t>(H, from_acc, out_mode, s); break;
-        case ASV_BOOL: finalize_dtype<bool8>(H, from_acc, out_mode, s); break;
+        case ASV_F32:
+            if (narrow) finalize_acc<float, float>(H, from_acc, out_mode, s);
+            else finalize_acc<float, typename Sr<float>::Atom>(H, from_acc, out_mode, s);
+            break;
+        case ASV_F64: finalize_acc<double, typename Sr<double>::Atom>(H, from_acc, out_mode, s); break;
+        case ASV_I32: finalize_acc<int32_t, typename Sr<int32_t>::Atom>(H, from_acc, out_mode, s); break;
+        case ASV_BOOL: finalize_acc<bool8, typename Sr<bool8>::Atom>(H, from_acc, out_mode, s); break;
     }
 }
 

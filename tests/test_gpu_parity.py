@@ -431,3 +431,29 @@ def test_single_call_autotuner_keeps_results_and_caches(tmp_path):
             assert_rows_close(y, y_ref, s, "f32" if dt == np.float32 else "f64", f"tuned {k}")
         # a zero budget still returns a valid setting (the creation-time one)
         assert make(m, n, rp, c, v).autotune(budget_ms=0)[0] in (2, 4, 8, 16, 32)
+
+
+def short_rows_pattern(m, n, row_len, seed):
+    """Every row holds exactly row_len entries at random columns."""
+    rows = [gen.sample_positions(n, row_len, seed=seed, stream=i) for i in range(m)]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    return rp, np.concatenate(rows).astype(np.int32)
+
+
+@pytest.mark.parametrize("row_len", [32, 33])
+@pytest.mark.parametrize("k", ["push_thread_atom", "push_warp_atom", "push_bal_atom", "auto"])
+def test_fp32_push_accumulation_stays_in_tolerance(row_len, k):
+    # rows of 32 entries: the FP32 atomic push adds in FP32 (32 products in
+    # any order stay within 32 * 2^-24 < 2e-6 of sum |a x|); 33 entries keep
+    # FP64 accumulators. Values spread over six decades with both signs, so
+    # the sums cancel and rounding is at its worst relative to the scale.
+    m, n = 3000, 2048
+    rp, c = short_rows_pattern(m, n, row_len, seed=41)
+    mag = 10.0 ** gen.uniform(len(c), -3, 3, seed=42, dtype=np.float64)
+    sign = np.where(gen.uniform(len(c), 0, 1, seed=43, dtype=np.float64) < 0.5, -1.0, 1.0)
+    v = (mag * sign).astype(np.float32)
+    A = make(m, n, rp, c, v)
+    for rho, idx, val in x_cases(n, seed=44, dtype=np.float32):
+        for dense_in in (False, True):
+            for sparse_out in (False, True):
+                check(A, k, f"rows{row_len}", n, rp, c, v, idx, val, np.float32, "f32", dense_in, sparse_out)
