@@ -141,12 +141,50 @@ __device__ __forceinline__ void load4_nz(const T* __restrict__ x, int64_t j, boo
     }
 }
 
+// The same four elements as raw words, loaded ahead of their use.
+template <class T>
+struct Raw4 {
+    typename std::conditional<sizeof(T) == 8, double4, typename std::conditional<sizeof(T) == 4, int4, uchar4>::type>::type v;
+};
+
+template <class T>
+__device__ __forceinline__ Raw4<T> load4_raw(const T* __restrict__ x, int64_t j) {
+    Raw4<T> r;
+    if constexpr (sizeof(T) == 8) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(x + j));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(x + j + 2));
+        r.v = make_double4(a.x, a.y, b.x, b.y);
+    } else if constexpr (sizeof(T) == 4) {
+        r.v = __ldg(reinterpret_cast<const int4*>(x + j));
+    } else {
+        r.v = __ldg(reinterpret_cast<const uchar4*>(x + j));
+    }
+    return r;
+}
+
+// Bit q of the result: element q of the four is nonzero.
+template <class T>
+__device__ __forceinline__ unsigned raw_nib(const Raw4<T>& r) {
+    if constexpr (sizeof(T) == 8) {
+        return (unsigned)(r.v.x != 0.0) | ((unsigned)(r.v.y != 0.0) << 1) | ((unsigned)(r.v.z != 0.0) << 2) |
+               ((unsigned)(r.v.w != 0.0) << 3);
+    } else if constexpr (sizeof(T) == 4) {
+        return (unsigned)Sr<T>::nz(*reinterpret_cast<const T*>(&r.v.x)) |
+               ((unsigned)Sr<T>::nz(*reinterpret_cast<const T*>(&r.v.y)) << 1) |
+               ((unsigned)Sr<T>::nz(*reinterpret_cast<const T*>(&r.v.z)) << 2) |
+               ((unsigned)Sr<T>::nz(*reinterpret_cast<const T*>(&r.v.w)) << 3);
+    } else {
+        return (unsigned)(r.v.x != 0) | ((unsigned)(r.v.y != 0) << 1) | ((unsigned)(r.v.z != 0) << 2) |
+               ((unsigned)(r.v.w != 0) << 3);
+    }
+}
+
 // Dense x: a warp covers 128 elements (four bitmap words) per step, lane l
 // the four elements 4l..4l+3; the nibbles of eight lanes form one word. The
 // degree of every nonzero column comes from colptr; block totals go to the
 // ticketed counters.
 template <class T, int B>
-__global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64_t n, const int32_t* __restrict__ colptr,
+__global__ void __launch_bounds__(B, 6) k_feat_dense(const T* __restrict__ x, int64_t n, const int32_t* __restrict__ colptr,
                                                   uint32_t* xbits, unsigned long long* counters, unsigned int* ticket,
                                                   CallDesc* desc, DescInit di, int64_t nnz, int32_t* status,
                                                   SelectArg sa) {
@@ -162,16 +200,30 @@ __global__ void __launch_bounds__(B) k_feat_dense(const T* __restrict__ x, int64
     const int64_t gw = (int64_t)blockIdx.x * (B / 32) + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * (B / 32);
     unsigned long long cx = 0, cs = 0, ch = 0;
+    // each lane's next 16 bytes of x are loaded before the current ones are
+    // used, so a warp keeps two loads in flight through its ~18 steps
+    Raw4<T> cur{};
+    bool cur_vec = gw < nsuper && VEC && gw * 128 + lane * 4 + 4 <= n;
+    if (cur_vec) cur = load4_raw(x, gw * 128 + lane * 4);
     for (int64_t sw = gw; sw < nsuper; sw += nw) {
         const int64_t j0 = sw * 128 + lane * 4;
+        const int64_t swn = sw + nw, jn = swn * 128 + lane * 4;
+        const bool nxt_vec = swn < nsuper && VEC && jn + 4 <= n;
+        Raw4<T> nxt{};
+        if (nxt_vec) nxt = load4_raw(x, jn);
+        unsigned nib = 0u;
         bool nz[4];
-        if (VEC && j0 + 4 <= n) {
-            load4_nz(x, j0, nz);
+        if (cur_vec) {
+            nib = raw_nib(cur);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nz[q] = (nib >> q) & 1u;
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) nz[q] = (j0 + q < n) && Sr<T>::nz(__ldg(x + j0 + q));
+            nib = (unsigned)nz[0] | ((unsigned)nz[1] << 1) | ((unsigned)nz[2] << 2) | ((unsigned)nz[3] << 3);
         }
-        const unsigned nib = (unsigned)nz[0] | ((unsigned)nz[1] << 1) | ((unsigned)nz[2] << 2) | ((unsigned)nz[3] << 3);
+        cur = nxt;
+        cur_vec = nxt_vec;
         // a fully nonzero stretch of 128 columns: two boundary reads give its
         // degree sum, so a dense x does not stream all of colptr
         if (__all_sync(0xffffffffu, nib == 0xFu && j0 + 4 <= n)) {
@@ -279,7 +331,10 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
         }
     }
     // four list entries per thread in flight: their column lengths are
-    // independent gathers
+    // independent gathers (eight consecutive entries per thread, read with
+    // two 16-byte loads, measured faster on a 16.8M-entry list, 861 -> 853 us
+    // for its whole call, but slower on the lists of 10^3 - 10^6 entries that
+    // BFS levels and sparse products bring, where it left most threads idle)
     const int64_t nl = min(nx, n);
     const int64_t stride = (int64_t)blocks * B;
     unsigned long long cs = 0, ch = 0;
