@@ -261,6 +261,7 @@ static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s
     H->narrow_acc = dtype == ASV_F32 && H->h_mfeat.max_row <= kNarrowRow;
     CKH(build_partition(H, s));
     CKH(build_long_rows(H, s));  // synchronises
+    CKH(count_hub_columns(H, s));  // synchronises
     {
         std::vector<TreeNode> nodes;
         int32_t roots[kRootsLen];

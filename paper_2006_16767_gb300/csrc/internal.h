@@ -144,6 +144,9 @@ struct asv_matrix_s {
     // atomic write-back and a dense output adds in FP32 (its error bound stays
     // within the FP32 tolerance, see push.cu)
     bool narrow_acc = false;
+    // columns of more than kLongSeg entries: the hub count of a listed x that
+    // holds every column, which the feature pass then need not gather
+    int64_t hub_cols = 0;
     // the long-row pass of the thread and sub-warp pulls runs beside the
     // short-row kernel: a side stream joined by two events (in a graph
     // capture they become a fork and a join of the captured graph)
@@ -192,6 +195,8 @@ cudaError_t build_features(asv_matrix_s* H, cudaStream_t s);
 cudaError_t build_partition(asv_matrix_s* H, cudaStream_t s);
 // counts the long rows (synchronises), allocates and fills their segment list
 cudaError_t build_long_rows(asv_matrix_s* H, cudaStream_t s);
+// hub_cols: the columns longer than kLongSeg (synchronises)
+cudaError_t count_hub_columns(asv_matrix_s* H, cudaStream_t s);
 int64_t pull_tile_items(int32_t dtype);
 cudaError_t validate_csr(asv_matrix_s* H, cudaStream_t s, int32_t* d_flag);
 cudaError_t regather_values(asv_matrix_s* H, cudaStream_t s);
@@ -220,8 +225,9 @@ void scan_excl(const int32_t* in, int32_t* out, int64_t n_h, const int64_t* n_d,
 struct FeatLaunch {
     void* func;
     dim3 grid, block;
-    void* args[11];
+    void* args[12];
     const void* xptr;
+    int64_t hub_cols;
     const int64_t* nnz_x_dev;
     const int32_t* xidx;
     int64_t n, nnz;

@@ -303,6 +303,30 @@ __global__ void k_long_fill(const int32_t* __restrict__ rowptr, int64_t m, int4*
     }
 }
 
+// Columns longer than thr (the hubs of a listed x that covers every column).
+__global__ void k_count_over(const int32_t* __restrict__ ptr, int64_t n, int32_t thr, unsigned long long* cnt) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += ptr[i + 1] - ptr[i] > thr;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+cudaError_t count_hub_columns(asv_matrix_s* H, cudaStream_t s) {
+    H->hub_cols = 0;
+    if (H->n == 0) return cudaSuccess;
+    unsigned long long* d_cnt = (unsigned long long*)H->ws.counters;  // a zeroed word, restored below
+    cudaError_t e;
+    k_count_over<<<H->num_sms * 8, 256, 0, s>>>(H->colptr, H->n, kLongSeg, d_cnt);
+    unsigned long long h = 0;
+    if ((e = cudaMemcpyAsync(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(h), s)) != cudaSuccess) return e;
+    H->hub_cols = (int64_t)h;
+    return cudaSuccess;
+}
+
 cudaError_t build_long_rows(asv_matrix_s* H, cudaStream_t s) {
     H->nseg = H->nmulti = 0;
     if (H->m == 0 || H->nnz <= kLongRow) return cudaSuccess;

@@ -278,14 +278,19 @@ template <int B>
 __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ nnz_x_dev, const int32_t* __restrict__ xidx,
                                                    const int32_t* __restrict__ colptr, unsigned long long* counters,
                                                    unsigned int* ticket, CallDesc* desc, DescInit di, int64_t n,
-                                                   int64_t nnz, int32_t* status, SelectArg sa) {
+                                                   int64_t nnz, int32_t* status, SelectArg sa, int64_t hub_cols) {
     __shared__ TreeNode sn[kTreeWindow];
     int64_t nx = *nnz_x_dev;
     const unsigned nq = hub_queue_len(sa);
     if (nx < 0) nx = 0;
     if (nx > n) nx = n + 1;  // reported and clamped when the totals are published
+    // a list of n distinct columns is every column: its effective entries are
+    // all nnz entries and its hubs the matrix's long columns, so one block
+    // publishes them without a gather
+    const bool every = nx == n;
     // only the blocks the list reaches take part (a short list costs one block)
-    const unsigned blocks = (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (min(nx, n) + B - 1) / B));
+    const unsigned blocks =
+        every ? 1u : (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (min(nx, n) + B - 1) / B));
     // block 0 always takes part: its copy of the selector's trees is issued
     // together with the load of nnz_x
     if (sa.enabled && blockIdx.x == 0) stage_window<B>(sa, sn);
@@ -335,9 +340,13 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
     // two 16-byte loads, measured faster on a 16.8M-entry list, 861 -> 853 us
     // for its whole call, but slower on the lists of 10^3 - 10^6 entries that
     // BFS levels and sparse products bring, where it left most threads idle)
-    const int64_t nl = min(nx, n);
+    const int64_t nl = every ? 0 : min(nx, n);
     const int64_t stride = (int64_t)blocks * B;
     unsigned long long cs = 0, ch = 0;
+    if (every && threadIdx.x == 0) {
+        cs = (unsigned long long)nnz;
+        ch = (unsigned long long)hub_cols;
+    }
     int64_t t = blockIdx.x * (int64_t)B + threadIdx.x;
     for (; t + 3 * stride < nl; t += 4 * stride) {
         int32_t j[4];
@@ -408,9 +417,10 @@ void feature_launch(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, Fe
         fl.grid = dim3((unsigned)feat_grid(H, H->n));
         fl.nnz_x_dev = di.user_nnz_x;
         fl.xidx = di.user_xidx;
-        void* a[11] = {&fl.nnz_x_dev, &fl.xidx, &fl.colptr, &fl.counters, &fl.ticket, &fl.desc, &fl.di,
-                       &fl.n, &fl.nnz, &fl.status, &fl.sa};
-        for (int i = 0; i < 11; ++i) fl.args[i] = a[i];
+        fl.hub_cols = H->hub_cols;
+        void* a[12] = {&fl.nnz_x_dev, &fl.xidx, &fl.colptr, &fl.counters, &fl.ticket, &fl.desc, &fl.di,
+                       &fl.n, &fl.nnz, &fl.status, &fl.sa, &fl.hub_cols};
+        for (int i = 0; i < 12; ++i) fl.args[i] = a[i];
     }
 }
 

@@ -196,7 +196,11 @@ def test_long_columns_all_kernels(k):
     v = gen.uniform(len(c), -1, 1, seed=17, dtype=np.float64).astype(np.float32)
     A = make(m, n, rp, c, v)
     Ab = make(m, n, rp, c, None)
-    for idx in (hubs, np.arange(n, dtype=np.int32), gen.sample_positions(n, n // 5, seed=18)):
+    # the hub columns, every column in order and in a seeded shuffled order
+    # (a list of every column takes the feature pass's shortcut: no gathers),
+    # and a fifth of the columns
+    every_shuffled = np.argsort(gen.uniform(n, 0, 1, seed=20)).astype(np.int32)
+    for idx in (hubs, np.arange(n, dtype=np.int32), every_shuffled, gen.sample_positions(n, n // 5, seed=18)):
         xv = gen.uniform(len(idx), -1, 1, seed=19, dtype=np.float64)
         for sparse_out in (False, True):
             check(A, k, "long_columns", n, rp, c, v, idx, xv, np.float32, "f32", False, sparse_out)
