@@ -122,26 +122,8 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
     }
 }
 
-// Four consecutive elements of x with one 128-bit (or, for bytes, 32-bit) load.
-template <class T>
-__device__ __forceinline__ void load4_nz(const T* __restrict__ x, int64_t j, bool nz[4]) {
-    if constexpr (sizeof(T) == 8) {
-        const double2 a = __ldg(reinterpret_cast<const double2*>(x + j));
-        const double2 b = __ldg(reinterpret_cast<const double2*>(x + j + 2));
-        nz[0] = a.x != 0.0; nz[1] = a.y != 0.0; nz[2] = b.x != 0.0; nz[3] = b.y != 0.0;
-    } else if constexpr (sizeof(T) == 4) {
-        const int4 a = __ldg(reinterpret_cast<const int4*>(x + j));
-        nz[0] = Sr<T>::nz(*reinterpret_cast<const T*>(&a.x));
-        nz[1] = Sr<T>::nz(*reinterpret_cast<const T*>(&a.y));
-        nz[2] = Sr<T>::nz(*reinterpret_cast<const T*>(&a.z));
-        nz[3] = Sr<T>::nz(*reinterpret_cast<const T*>(&a.w));
-    } else {
-        const uchar4 a = __ldg(reinterpret_cast<const uchar4*>(x + j));
-        nz[0] = a.x != 0; nz[1] = a.y != 0; nz[2] = a.z != 0; nz[3] = a.w != 0;
-    }
-}
-
-// The same four elements as raw words, loaded ahead of their use.
+// Four consecutive elements of x as raw words, with one 128-bit (for bytes,
+// 32-bit; for 8-byte values, two 128-bit) load, issued ahead of their use.
 template <class T>
 struct Raw4 {
     typename std::conditional<sizeof(T) == 8, double4, typename std::conditional<sizeof(T) == 4, int4, uchar4>::type>::type v;
