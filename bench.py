@@ -986,7 +986,7 @@ def bench_backward(asv, torch, dev, reps=5):
     return out
 
 
-def ncu_case(case, kernel, fmt="dense"):
+def ncu_case(case, kernel, fmt="dense", density=None):
     """Small inputs (larger than L2, a few GB at most) for one-kernel profiles."""
     import torch
 
@@ -1005,17 +1005,28 @@ def ncu_case(case, kernel, fmt="dense"):
             v = np.ones(len(c), np.float32)
         A = asv.Matrix(m, n, *[torch.from_numpy(a).to(dev) for a in (rp, c, v)])
         # --fmt dense: x dense, y dense; --fmt list: x as a list of every
-        # column, y as the structural list (the two forms of the stencil step)
-        idx = np.arange(n, dtype=np.int32)
-        x = gen.uniform(n, -1, 1, 1, 0, np.float32)
+        # column, y as the structural list (the two forms of the stencil step);
+        # --density rho: x of round(rho n) random entries (list or dense) and,
+        # with a list, a dense y (the stencil step's sparse-x calls)
+        if density is None:
+            idx = np.arange(n, dtype=np.int32)
+            x = gen.uniform(n, -1, 1, 1, 0, np.float32)
+        else:
+            idx, xs = gen.sparse_x(n, max(1, int(round(density * n))), gen.config_seed(5), 11, np.float32)
+            x = gen.densify(n, idx, xs, np.float32)
         xd = torch.from_numpy(x).to(dev)
+        xl = torch.from_numpy(x[idx]).to(dev)
         it, cnt = torch.from_numpy(idx).to(dev), torch.tensor([n], dtype=torch.int64, device=dev)
         y = torch.empty(m, dtype=torch.float32, device=dev)
         yidx = torch.empty(m, dtype=torch.int32, device=dev)
         nnz_y = torch.zeros(1, dtype=torch.int64, device=dev)
+        if density is not None:
+            cnt = torch.tensor([len(idx)], dtype=torch.int64, device=dev)
         for _ in range(3):
-            if fmt == "list":
-                asv.asv_spmspv(A.handle, cnt, it, xd, None, asv.ASV_OUT_SPARSE, None, yidx, y, nnz_y, m, kernel)
+            if fmt == "list" and density is not None:
+                asv.asv_spmspv(A.handle, cnt, it, xl, None, asv.ASV_OUT_DENSE, y, kernel=kernel)
+            elif fmt == "list":
+                asv.asv_spmspv(A.handle, cnt, it, xl, None, asv.ASV_OUT_SPARSE, None, yidx, y, nnz_y, m, kernel)
             else:
                 asv.asv_spmspv(A.handle, None, None, None, xd, asv.ASV_OUT_DENSE, y, kernel=kernel)
     elif case == "rmat20_bfs":
@@ -1175,6 +1186,8 @@ def main():
                          "bernoulli_backward) with --kernel (and --fmt) three times and exit")
     ap.add_argument("--kernel", default="auto")
     ap.add_argument("--fmt", default="dense", choices=["dense", "list"])
+    ap.add_argument("--density", type=float, default=None,
+                    help="with --ncu-case stencil128: x of this density instead of a full one")
     ap.add_argument("--sweep", default=None,
                     help="x-density sweep of every candidate and the selector on stencil256 or rmat22; "
                          "writes JSON lines to --sweep-out")
@@ -1191,7 +1204,7 @@ def main():
     if args.impl == "reference":
         return main_reference(args, rank, world)
     if args.ncu_case:
-        return ncu_case(args.ncu_case, args.kernel, args.fmt)
+        return ncu_case(args.ncu_case, args.kernel, args.fmt, args.density)
     if args.sweep:
         return density_sweep(args.sweep, args.sweep_out)
 

@@ -76,6 +76,21 @@ __device__ __forceinline__ void emit_batch(const Ws& ws, const uint32_t* ymask, 
     }
 }
 
+// N write-backs of one thread at the effective indexes pos[u] (rows r[u] < 0
+// are skipped; effective indexes are those of the 32-bit list scan), the
+// Boolean flag reads again issued before any store.
+template <class T, int WB, int N>
+__device__ __forceinline__ void emit_slots(const Ws& ws, const uint32_t* ymask, const int32_t (&r)[N],
+                                           const typename Sr<T>::Part (&p)[N], const int32_t (&pos)[N]) {
+    if constexpr (wb_atomic(WB) && Sr<T>::kPattern) {
+        emit_batch<T, WB, N>(ws, ymask, r, p, 0, 0);
+    } else {
+#pragma unroll
+        for (int u = 0; u < N; ++u)
+            if (r[u] >= 0) emit<T, WB>(ws, ymask, r[u], p[u], pos[u]);
+    }
+}
+
 template <class T>
 __device__ __forceinline__ T list_val(const CallDesc* d, int64_t t) {
     if (Sr<T>::kPattern || d->xval == nullptr) return Sr<T>::one();
@@ -226,38 +241,86 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
     help_long<T, WB, true>(colptr, rowidx, valc, desc, ws, ym, lane);
 }
 
+// One warp per listed column, G consecutive list entries per warp and round:
+// on a list that gives every warp two groups of 32 or more, G = 32 -- lane l
+// loads the pointers of the group's column l, then the warp walks the
+// group's columns of at most 32 entries four at a time, lane l taking entry
+// l of each, so such a column costs one load latency instead of the chain
+// list entry -> column pointers -> entries (the stencil's products at x
+// density 0.1: 468 -> 407 us listed, 427 -> 356 us dense); groups of 8 on a
+// list ten times shorter measured slower (137 -> 144 us), so shorter lists
+// keep G = 1. Longer columns follow one after another; hubs go to the queue.
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                                    const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws, Gate gate) {
     if (gate.off()) return;
     using S = Sr<T>;
+    using P = typename S::Part;
+    constexpr unsigned FULL = 0xffffffffu;
     const uint32_t* __restrict__ ym = desc->ymask;
     const int lane = threadIdx.x & 31;
     const int64_t nx = desc->nnz_x;
     const int32_t* __restrict__ xidx = desc->xidx;
     const int64_t wpb = blockDim.x / 32;
-    for (int64_t t = blockIdx.x * wpb + (threadIdx.x >> 5); t < nx; t += (int64_t)gridDim.x * wpb) {
-        const int32_t j = xidx[t];
-        const T xj = list_val<T>(desc, t);
-        const int32_t b = __ldg(colptr + j), e = __ldg(colptr + j + 1);
-        if (e - b > kLongSeg) {
-            bool queued = false;
-            if (lane == 0) queued = queue_long(ws, t);
-            if (__shfl_sync(0xffffffffu, queued, 0)) continue;
+    const int64_t nw = (int64_t)gridDim.x * wpb;
+    const int G = nx >= 64 * nw ? 32 : 1;
+    for (int64_t t0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * G; t0 < nx; t0 += nw * G) {
+        const int64_t t = t0 + lane;
+        const bool valid = lane < G && t < nx;
+        int32_t b = 0, len = 0, pos0 = 0;
+        T xj = S::one();
+        if (valid) {
+            const int32_t j = xidx[t];
+            xj = list_val<T>(desc, t);
+            b = __ldg(colptr + j);
+            len = __ldg(colptr + j + 1) - b;
+            if (!wb_atomic(WB)) pos0 = ws.xscan[t] - b;
         }
-        const int64_t pos0 = !wb_atomic(WB) ? (int64_t)ws.xscan[t] - b : 0;
-        for (int32_t k0 = b + lane; k0 < e; k0 += 128) {
+        const bool queued = valid && len > kLongSeg && queue_long(ws, t);
+        for (unsigned pend = __ballot_sync(FULL, valid && len <= 32); pend;) {
             int32_t rr[4];
-            typename S::Part pp[4];
+            P pp[4];
+            int32_t ps[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int32_t k = k0 + 32 * u;
-                rr[u] = k < e ? __ldg(rowidx + k) : -1;
-                pp[u] = k < e ? S::mul(load_val(valc, k), xj) : typename S::Part(0);
+                const bool has = pend != 0u;
+                const int src = has ? __ffs(pend) - 1 : 0;
+                pend &= pend - 1u;
+                const int32_t bb = __shfl_sync(FULL, b, src);
+                const int32_t ll = __shfl_sync(FULL, len, src);
+                T xx = S::one();
+                if constexpr (!S::kPattern) xx = __shfl_sync(FULL, xj, src);
+                const int32_t p0 = !wb_atomic(WB) ? __shfl_sync(FULL, pos0, src) : 0;
+                const int32_t k = bb + lane;
+                const bool on = has && lane < ll;
+                rr[u] = on ? __ldg(rowidx + k) : -1;
+                pp[u] = on ? S::mul(load_val(valc, k), xx) : P(0);
+                ps[u] = p0 + k;
             }
-            emit_batch<T, WB, 4>(ws, ym, rr, pp, pos0 + k0, 32);
+            emit_slots<T, WB, 4>(ws, ym, rr, pp, ps);
+        }
+        for (unsigned pend = __ballot_sync(FULL, valid && len > 32 && !queued); pend; pend &= pend - 1u) {
+            const int src = __ffs(pend) - 1;
+            const int32_t bb = __shfl_sync(FULL, b, src), ee = bb + __shfl_sync(FULL, len, src);
+            T xx = S::one();
+            if constexpr (!S::kPattern) xx = __shfl_sync(FULL, xj, src);
+            const int64_t p0 = !wb_atomic(WB) ? (int64_t)__shfl_sync(FULL, pos0, src) : 0;
+            for (int32_t k0 = bb + lane; k0 < ee; k0 += 128) {
+                int32_t rr[4];
+                P pp[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t k = k0 + 32 * u;
+                    rr[u] = k < ee ? __ldg(rowidx + k) : -1;
+                    pp[u] = k < ee ? S::mul(load_val(valc, k), xx) : P(0);
+                }
+                emit_batch<T, WB, 4>(ws, ym, rr, pp, p0 + k0, 32);
+            }
         }
     }
+    // any lane may have queued a hub of this warp; lane 0 reads the queue
+    // entries, so order those lanes' stores before its reads
+    __syncwarp();
     help_long<T, WB, false>(colptr, rowidx, valc, desc, ws, ym, lane);
 }
 
