@@ -244,7 +244,7 @@ static asv_status finish_handle(asv_matrix* out, asv_matrix_s* H, cudaStream_t s
     AL(w.hist, 4 * hist_n, false);
     AL(w.blk, 4 * (G + 1), false);
     AL(w.status, 4, true);
-    AL(w.counters, 24, true);
+    AL(w.counters, 32, true);
     AL(w.ticket, 4, true);
     w.lcol_cap = (int32_t)std::min<int64_t>(nnz / kLongSeg + 1, (int64_t)1 << 30);
     AL(w.lcol, sizeof(int2) * (size_t)w.lcol_cap, false);

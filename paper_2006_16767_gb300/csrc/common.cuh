@@ -184,7 +184,8 @@ struct CallDesc {
     int32_t out_mode;
     int32_t x_sparse;        // 1 when x arrived as a list
     int32_t kid;             // kernel chosen for this call
-    int32_t pad;
+    int32_t x_ident;         // 1: the list is every column in order (xidx[t] = t), so the
+                             // pull kernels read its values in place (x_dense = xval)
     double vfeat[4];         // nnz_x, x_sparsity, nnz_s, m_sparsity
     const uint32_t* ymask;   // output mask: bit i set = row i excluded from y (NULL = none)
     int64_t nhub;            // listed columns longer than kLongSeg (hubs of the thread/warp push)

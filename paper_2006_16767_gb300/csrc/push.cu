@@ -14,8 +14,8 @@
 // FP32 (WB_ATOM_N):
 // y_i then sums at most k <= 32 products, and k FP32 products added in any
 // order stay within k * 2^-24 * sum |a_ij x_j| <= 1.91e-6 * sum |a_ij x_j| of
-// the exact sum (the FP32 tolerance is 2e-6 of it), with half the
-// accumulator bytes and FP32 atomics.
+// the exact sum (the FP32 tolerance is 2e-6 of it); those atomics add
+// straight into the zeroed output, with no accumulator to write out.
 #include "internal.h"
 #include "prims.cuh"
 #include "sort.cuh"
@@ -38,9 +38,14 @@ __device__ __forceinline__ void emit(const Ws& ws, const uint32_t* ymask, int32_
     if (wb_atomic(WB)) {
         if (row_masked(ymask, r)) return;  // excluded by the output mask (pairs are masked when reduced)
         if constexpr (!S::kPattern) {
-            if constexpr (WB == WB_ATOM_N) atomicAdd((T*)ws.acc + r, S::part_T(p));
-            else atomicAdd((typename S::Atom*)ws.acc + r, S::to_atom(S::part_T(p)));
-            ws.yflag[r] = 1;
+            if constexpr (WB == WB_ATOM_N) {
+                // straight into the dense output, zeroed before the push: no
+                // flag (a dense output needs no structural set)
+                atomicAdd((T*)ws.acc + r, S::part_T(p));
+            } else {
+                atomicAdd((typename S::Atom*)ws.acc + r, S::to_atom(S::part_T(p)));
+                ws.yflag[r] = 1;
+            }
         } else {
             // a Boolean search reaches most rows many times: a (possibly
             // L1-stale) read that already sees the flag saves the store; a
@@ -89,6 +94,30 @@ __device__ __forceinline__ void emit_slots(const Ws& ws, const uint32_t* ymask, 
         for (int u = 0; u < N; ++u)
             if (r[u] >= 0) emit<T, WB>(ws, ymask, r[u], p[u], pos[u]);
     }
+}
+
+// The workspaces a push kernel writes through: with FP32 accumulation for a
+// dense output (WB_ATOM_N) the accumulators are the output itself.
+template <int WB>
+__device__ __forceinline__ Ws push_ws(Ws w, const CallDesc* d) {
+    if constexpr (WB == WB_ATOM_N) w.acc = d->y;
+    return w;
+}
+
+// Zeroes the dense output ahead of a push that accumulates into it (16-byte
+// stores from the first aligned element).
+template <class T>
+__global__ void __launch_bounds__(256) k_zero_out(int64_t m, const CallDesc* __restrict__ desc, Gate gate) {
+    if (gate.off()) return;
+    T* __restrict__ y = (T*)desc->y;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    constexpr int64_t V = 16 / sizeof(T);
+    const int64_t head = min(m, (int64_t)(((16 - ((uintptr_t)y & 15)) & 15) / sizeof(T)));
+    if (tid < head) y[tid] = T(0);
+    const int64_t nv = (m - head) / V;
+    uint4* __restrict__ yv = reinterpret_cast<uint4*>(y + head);
+    for (int64_t i = tid; i < nv; i += nt) yv[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t i = head + nv * V + tid; i < m; i += nt) y[i] = T(0);
 }
 
 template <class T>
@@ -188,8 +217,9 @@ __device__ __forceinline__ void help_long(const int32_t* __restrict__ colptr, co
 
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
-                                                     const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws, Gate gate) {
+                                                     const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws_in, Gate gate) {
     if (gate.off()) return;
+    const Ws ws = push_ws<WB>(ws_in, desc);
     using S = Sr<T>;
     const uint32_t* __restrict__ ym = desc->ymask;
     const int lane = threadIdx.x & 31;
@@ -252,8 +282,9 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
 // keep G = 1. Longer columns follow one after another; hubs go to the queue.
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
-                                                   const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws, Gate gate) {
+                                                   const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws_in, Gate gate) {
     if (gate.off()) return;
+    const Ws ws = push_ws<WB>(ws_in, desc);
     using S = Sr<T>;
     using P = typename S::Part;
     constexpr unsigned FULL = 0xffffffffu;
@@ -264,6 +295,10 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
     const int64_t wpb = blockDim.x / 32;
     const int64_t nw = (int64_t)gridDim.x * wpb;
     const int G = nx >= 64 * nw ? 32 : 1;
+    // columns of a group walked together (their loads in flight at once);
+    // eight measured slower than four (the stencil's listed products at x
+    // densities 0.1 and 0.01: 408 -> 456 and 141 -> 177 us, 32 -> 40 registers)
+    constexpr int GU = 4;
     for (int64_t t0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * G; t0 < nx; t0 += nw * G) {
         const int64_t t = t0 + lane;
         const bool valid = lane < G && t < nx;
@@ -278,11 +313,11 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
         }
         const bool queued = valid && len > kLongSeg && queue_long(ws, t);
         for (unsigned pend = __ballot_sync(FULL, valid && len <= 32); pend;) {
-            int32_t rr[4];
-            P pp[4];
-            int32_t ps[4];
+            int32_t rr[GU];
+            P pp[GU];
+            int32_t ps[GU];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < GU; ++u) {
                 const bool has = pend != 0u;
                 const int src = has ? __ffs(pend) - 1 : 0;
                 pend &= pend - 1u;
@@ -297,7 +332,7 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
                 pp[u] = on ? S::mul(load_val(valc, k), xx) : P(0);
                 ps[u] = p0 + k;
             }
-            emit_slots<T, WB, 4>(ws, ym, rr, pp, ps);
+            emit_slots<T, WB, GU>(ws, ym, rr, pp, ps);
         }
         for (unsigned pend = __ballot_sync(FULL, valid && len > 32 && !queued); pend; pend &= pend - 1u) {
             const int src = __ffs(pend) - 1;
@@ -336,8 +371,9 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
 // columns) fall back to one binary search per item.
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_bal(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
-                                                  const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws, Gate gate) {
+                                                  const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws_in, Gate gate) {
     if (gate.off()) return;
+    const Ws ws = push_ws<WB>(ws_in, desc);
     using S = Sr<T>;
     constexpr int CH = 32 * kPushIPT;
     __shared__ int32_t s_t[8][CH];          // item -> list index of its column
@@ -649,11 +685,13 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
     const CallDesc* d = H->d_desc;
     Ws ws = H->ws;
     const Gate gate = gate_of(H);
-    // atomics into FP32 accumulators where every row is short enough (see
-    // above) and the output is dense: the dense write-out then reads half the
-    // bytes (the stencil's products at x densities 0.1 and 0.01: 490 -> 434 and
-    // 182 -> 135 us), while the list output's compaction measured slower on
-    // FP32 accumulators (94.9 -> 202.7 us for a 15.8M-row list) and keeps FP64
+    // FP32 atomics where every row is short enough (see above) and the output
+    // is dense, added straight into the zeroed output: no flags and no
+    // write-out pass (FP32 accumulators written out by a pass took the
+    // stencil's products at x densities 0.1 and 0.01 from 490 to 434 and from
+    // 182 to 135 us against FP64 ones); the list output's compaction measured
+    // slower on FP32 accumulators (94.9 -> 202.7 us for a 15.8M-row list) and
+    // keeps FP64
     if (std::is_same<T, float>::value && wb == WB_ATOM && H->narrow_acc && out_mode == ASV_OUT_DENSE) wb = WB_ATOM_N;
     if (dist == 2 || !wb_atomic(wb)) {
         k_list_deg<256><<<H->G, 256, 0, s>>>(H->colptr, d, ws.xscan, ws.blk, gate);
@@ -669,7 +707,10 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
         else k_push_bal<T, WBV><<<grid * 4, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
     } while (0)
     if (wb == WB_ATOM_N) {
-        if constexpr (std::is_same<T, float>::value) TRAV(WB_ATOM_N);
+        if constexpr (std::is_same<T, float>::value) {
+            if (H->m > 0) k_zero_out<T><<<H->num_sms * 4, 256, 0, s>>>(H->m, d, gate);
+            TRAV(WB_ATOM_N);
+        }
     } else if (wb == WB_ATOM) {
         TRAV(WB_ATOM);
     } else {
@@ -698,7 +739,7 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
         k_bin_scatter<T><<<grid, 256, 0, s>>>(ws.pkeys[0], (const T*)ws.pvals[0], ws.pkeys[1], (T*)ws.pvals[1], d, cursor);
         if (nbins > 0) k_priv_accumulate<T><<<nbins, 256, 0, s>>>(ws.pkeys[1], (const T*)ws.pvals[1], bins, H->m, ws, d);
     }
-    launch_finalize(H, true, out_mode, s, wb == WB_ATOM_N);
+    if (wb != WB_ATOM_N) launch_finalize(H, true, out_mode, s);
 }
 
 void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s) {

@@ -30,6 +30,7 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
     desc->x_sparse = di.x_sparse;
     desc->ymask = di.ymask;
     desc->nhub = (int64_t)nh;
+    desc->x_ident = 0;
     desc->vfeat[0] = (double)nx;
     desc->vfeat[1] = n > 0 ? (double)nx / (double)n : 0.0;
     desc->vfeat[2] = (double)ns;
@@ -62,17 +63,22 @@ __device__ __forceinline__ void reset_hub_queue(const SelectArg& sa, unsigned nq
 // the one that draws the last ticket publishes (a pass of one block, a short
 // list, publishes its own totals and leaves the counters and the ticket
 // alone). ch counts the listed columns longer than kLongSeg.
+// With ident, cm counts the list entries t whose column is not t: none means
+// the list is every column in order, and the call's pull kernels read its
+// values in place.
 template <int B>
 __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned long long cs, unsigned long long ch,
                                               unsigned long long* counters, unsigned int* ticket, CallDesc* desc,
                                               const DescInit& di, int64_t n, int64_t nnz, int32_t* status,
-                                              const SelectArg& sa, unsigned blocks, TreeNode* sn, unsigned nq) {
+                                              const SelectArg& sa, unsigned blocks, TreeNode* sn, unsigned nq,
+                                              bool ident = false, unsigned long long cm = 0) {
     __shared__ unsigned long long sm[B / 32 + 1];
     __shared__ bool last;
     __shared__ double s_vf[4];  // the published vector features, for the selector
     cx = block_reduce_sum<B>(cx, sm);
     cs = block_reduce_sum<B>(cs, sm);
     ch = block_reduce_sum<B>(ch, sm);
+    if (ident) cm = block_reduce_sum<B>(cm, sm);
     const bool alone = blocks == 1;
     if (threadIdx.x == 0) {
         if (alone) {
@@ -81,18 +87,20 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
             if (cx) atomicAdd(&counters[0], cx);
             if (cs) atomicAdd(&counters[1], cs);
             if (ch) atomicAdd(&counters[2], ch);
+            if (cm) atomicAdd(&counters[3], cm);
             __threadfence();
             last = atomicAdd(ticket, 1u) == blocks - 1;
         }
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
-        unsigned long long nx = cx, ns = cs, nh = ch;
+        unsigned long long nx = cx, ns = cs, nh = ch, nm = cm;
         if (!alone) {
             __threadfence();
             nx = atomicExch(&counters[0], 0ull);
             ns = atomicExch(&counters[1], 0ull);
             nh = atomicExch(&counters[2], 0ull);
+            nm = atomicExch(&counters[3], 0ull);
         }
         // a list with repeated or out-of-range entries could exceed the
         // workspaces sized for nnz_x <= n and nnz_s <= nnz: clamp and report
@@ -102,6 +110,10 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
             ns = ns > (unsigned long long)nnz ? (unsigned long long)nnz : ns;
         }
         publish_desc(desc, di, nx, ns, nh < nx ? nh : nx, n, nnz);
+        if (ident && nm == 0 && nx == (unsigned long long)n) {
+            desc->x_ident = 1;
+            desc->x_dense = di.xval;
+        }
         s_vf[0] = (double)nx;
         s_vf[1] = n > 0 ? (double)nx / (double)n : 0.0;
         s_vf[2] = (double)ns;
@@ -270,9 +282,15 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
     // all nnz entries and its hubs the matrix's long columns, so one block
     // publishes them without a gather
     const bool every = nx == n;
+    // such a list with values is also checked for being every column in
+    // order (xidx[t] = t, which an ascending list of every column is): the
+    // pull kernels then read its values in place, with no scatter into the
+    // dense workspace (a pass over the indices instead of a pass over indices
+    // and values plus a write and a clear of the workspace)
+    const bool ident = every && di.xval != nullptr && n > 0;
     // only the blocks the list reaches take part (a short list costs one block)
     const unsigned blocks =
-        every ? 1u : (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (min(nx, n) + B - 1) / B));
+        every && !ident ? 1u : (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (min(nx, n) + B - 1) / B));
     // block 0 always takes part: its copy of the selector's trees is issued
     // together with the load of nnz_x
     if (sa.enabled && blockIdx.x == 0) stage_window<B>(sa, sn);
@@ -286,7 +304,7 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
     // kernel reads neither nnz_s nor the hub count (the pull kernels and the
     // warp push with atomics), block 0 publishes the call without them and
     // the pass ends there.
-    if (sa.enabled && sa.lazy && nx <= n) {
+    if (sa.enabled && sa.lazy && nx <= n && !ident) {
         __shared__ double s_f[13];
         __shared__ int s_kid;
         if (threadIdx.x == 0) {
@@ -325,7 +343,7 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
     const int64_t nl = every ? 0 : min(nx, n);
     const int64_t stride = (int64_t)blocks * B;
     unsigned long long cs = 0, ch = 0;
-    if (every && threadIdx.x == 0) {
+    if (every && blockIdx.x == 0 && threadIdx.x == 0) {
         cs = (unsigned long long)nnz;
         ch = (unsigned long long)hub_cols;
     }
@@ -347,8 +365,25 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
         cs += (unsigned long long)d;
         ch += d > kLongSeg;
     }
+    // the order check: four indices per thread and step (16-byte loads where
+    // the list is 16-byte aligned), counting entries t whose column is not t
+    unsigned long long cm = 0;
+    if (ident) {
+        const int64_t gt = blockIdx.x * (int64_t)B + threadIdx.x;
+        int64_t q0 = 0;
+        if (((uintptr_t)xidx & 15) == 0) {
+            const int64_t n4 = n / 4;
+            for (int64_t q = gt; q < n4; q += stride) {
+                const int4 v = __ldg(reinterpret_cast<const int4*>(xidx) + q);
+                const int32_t j = (int32_t)(4 * q);
+                cm += (v.x != j) + (v.y != j + 1) + (v.z != j + 2) + (v.w != j + 3);
+            }
+            q0 = 4 * n4;
+        }
+        for (int64_t q = q0 + gt; q < n; q += stride) cm += __ldg(xidx + q) != (int32_t)q;
+    }
     finish_counts<B>(blockIdx.x == 0 && threadIdx.x == 0 ? (unsigned long long)nx : 0ull, cs, ch, counters, ticket,
-                     desc, di, n, nnz, status, sa, blocks, sn, nq);
+                     desc, di, n, nnz, status, sa, blocks, sn, nq, ident, cm);
 }
 
 // Few blocks per SM: every block of the feature pass ends with atomics on
@@ -442,6 +477,16 @@ __global__ void k_x_scatter(const CallDesc* __restrict__ desc, T* xdense, uint32
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const bool vals = xval && !Sr<T>::kPattern;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // a list of every column in order: the pull kernels read its values in
+    // place, so only the bitmap is set (every bit below n) or cleared
+    if (desc->x_ident) {
+        if (BITS) {
+            const int64_t full = n >> 5;
+            for (int64_t w = t; w < (n + 31) / 32; w += stride)
+                xbits[w] = !set ? 0u : (w < full ? 0xffffffffu : ((1u << (n & 31)) - 1u));
+        }
+        return;
+    }
     // a list covering more than a quarter of the columns is cleared by
     // writing the whole workspace (16-byte stores) rather than by reading the
     // list again and scattering zeros
