@@ -527,6 +527,8 @@ static asv_status prepare_call(asv_matrix_s* H, const int64_t* d_nnz_x, const in
     di.y_cap = y_cap;
     di.out_mode = om;
     di.x_sparse = xs ? 1 : 0;
+    di.y_ident_ok = om == ASV_OUT_SPARSE && H->dtype != ASV_BOOL && d_yval != nullptr && H->m > 0 &&
+                    H->h_mfeat.min_row >= 1 && y_cap >= H->m;
     if (xs) {
         di.x_dense = H->ws.xdense;
         di.xbits = H->ws.xbits_scat;

@@ -189,6 +189,10 @@ struct CallDesc {
     double vfeat[4];         // nnz_x, x_sparsity, nnz_s, m_sparsity
     const uint32_t* ymask;   // output mask: bit i set = row i excluded from y (NULL = none)
     int64_t nhub;            // listed columns longer than kLongSeg (hubs of the thread/warp push)
+    int32_t y_ident;         // 1: the list output is every row in order (x reaches every column,
+                             // no row is empty, no mask): the pull kernels write its values in
+                             // place and the compaction only writes the indices
+    int32_t pad;
 };
 
 // Predicate of a kernel in one of the selector graph's direct candidate

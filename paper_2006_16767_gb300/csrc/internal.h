@@ -27,6 +27,10 @@ struct DescInit {
     const uint32_t* ymask;  // output mask (NULL = none)
     int32_t out_mode;
     int32_t x_sparse;
+    // a list output whose set is every row when x reaches every column: the
+    // matrix has no empty row, the output has values and room for m entries
+    // (the output mask, set after this, is checked on the device)
+    int32_t y_ident_ok;
 };
 
 // Device-resident state of a driver loop (BFS, PageRank). The loop graph is

@@ -475,7 +475,7 @@ __global__ void k_pull_bal_fixup(int64_t ntiles, const int32_t* __restrict__ car
                                  const typename Sr<T>::Atom* __restrict__ carry_val, const CallDesc* desc,
                                  void* ydirect, void* ywork, int sparse_out) {
     using S = Sr<T>;
-    T* y = (T*)(desc ? (sparse_out ? ywork : desc->y) : ydirect);
+    T* y = (T*)(desc ? (sparse_out ? (desc->y_ident ? desc->yval : ywork) : desc->y) : ydirect);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = carry_row[t];
         if (r < 0) continue;

@@ -23,7 +23,7 @@ __device__ __forceinline__ PullIO resolve(const PullArg& a, void* ywork, bool sp
         PullIO p;
         p.x = a.desc->x_dense;
         p.xbits = a.desc->xbits;
-        p.y = sparse_out ? ywork : a.desc->y;
+        p.y = sparse_out ? (a.desc->y_ident ? a.desc->yval : ywork) : a.desc->y;
         p.ymask = a.desc->ymask;
         return p;
     }

@@ -31,6 +31,7 @@ __device__ __forceinline__ void publish_desc(CallDesc* desc, const DescInit& di,
     desc->ymask = di.ymask;
     desc->nhub = (int64_t)nh;
     desc->x_ident = 0;
+    desc->y_ident = 0;
     desc->vfeat[0] = (double)nx;
     desc->vfeat[1] = n > 0 ? (double)nx / (double)n : 0.0;
     desc->vfeat[2] = (double)ns;
@@ -114,6 +115,9 @@ __device__ __forceinline__ void finish_counts(unsigned long long cx, unsigned lo
             desc->x_ident = 1;
             desc->x_dense = di.xval;
         }
+        // x reaches every column and no row is empty: every row is in the
+        // structural output set
+        if (di.y_ident_ok && di.ymask == nullptr && nx == (unsigned long long)n) desc->y_ident = 1;
         s_vf[0] = (double)nx;
         s_vf[1] = n > 0 ? (double)nx / (double)n : 0.0;
         s_vf[2] = (double)ns;
@@ -195,7 +199,9 @@ __global__ void __launch_bounds__(B, 6) k_feat_dense(const T* __restrict__ x, in
     const int64_t nw = (int64_t)gridDim.x * (B / 32);
     unsigned long long cx = 0, cs = 0, ch = 0;
     // each lane's next 16 bytes of x are loaded before the current ones are
-    // used, so a warp keeps two loads in flight through its ~18 steps
+    // used, so a warp keeps two loads in flight through its ~18 steps (three,
+    // with five blocks per SM instead of six, measured no faster: the
+    // stencil's dense-x calls 0.3-4 % slower)
     Raw4<T> cur{};
     bool cur_vec = gw < nsuper && VEC && gw * 128 + lane * 4 + 4 <= n;
     if (cur_vec) cur = load4_raw(x, gw * 128 + lane * 4);
@@ -573,8 +579,8 @@ __device__ __forceinline__ void load_run(const uint32_t* __restrict__ words, int
 // thread and round.
 template <int B, bool BYTES>
 __global__ void __launch_bounds__(B) k_items_count(const uint32_t* __restrict__ words, int64_t nwords, int32_t* blk,
-                                                   Gate gate) {
-    if (gate.off()) return;
+                                                   Gate gate, const int32_t* skip) {
+    if (gate.off() || (skip && *skip)) return;
     __shared__ int32_t sm[B / 32 + 1];
     int64_t lo, hi;
     block_range(nwords, lo, hi);
@@ -609,6 +615,10 @@ __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwor
     __shared__ int32_t stage[CAP + CAP / 32];
     int64_t lo, hi;
     block_range(nwords, lo, hi);
+    if (pol.every_item()) {
+        pol.write_every(words, lo, hi);
+        return;
+    }
     const bool vec = ((uintptr_t)words & 15) == 0;
     int32_t base = block_prefix<B>(blk, blockIdx.x, sm);  // blk holds the raw block counts
     pol.begin();
@@ -674,6 +684,8 @@ struct XListPolicy {
     T* val;
     const T* x;
     __device__ void begin() { x = (const T*)desc->x_dense; }
+    __device__ bool every_item() const { return false; }
+    __device__ void write_every(uint32_t*, int64_t, int64_t) {}
     __device__ void clear_word(uint32_t*, int64_t) {}
     __device__ T load(int32_t j) const { return Sr<T>::kPattern ? Sr<T>::one() : x[j]; }
     __device__ void store(int32_t pos, int32_t j, T v) const {
@@ -692,6 +704,8 @@ struct PublicCompactPolicy {
     T* val;
     int64_t* count_out;
     __device__ void begin() {}
+    __device__ bool every_item() const { return false; }
+    __device__ void write_every(uint32_t*, int64_t, int64_t) {}
     __device__ void clear_word(uint32_t*, int64_t) {}
     __device__ T load(int32_t j) const { return val ? x[j] : T(0); }
     __device__ void store(int32_t pos, int32_t j, T v) const {
@@ -722,10 +736,22 @@ struct OutSparsePolicy {
     int32_t* yidx;
     T* yval;
     int64_t cap;
+    int64_t m;  // rows of the output (the flags' items)
     __device__ void begin() {
         yidx = desc->yidx;
         yval = (T*)desc->yval;
         cap = desc->y_cap;
+    }
+    // every row is in the set (y_ident): the pull wrote the values in place,
+    // so this block clears its range of flag words and writes the indices
+    // of its rows; block 0 publishes the count m
+    __device__ bool every_item() const { return !FROM_ACC && desc->y_ident; }
+    __device__ void write_every(uint32_t* words, int64_t lo, int64_t hi) const {
+        int32_t* __restrict__ yi = desc->yidx;
+        for (int64_t w = lo + threadIdx.x; w < hi; w += blockDim.x) words[w] = 0u;
+        const int64_t e = min(4 * hi, m);
+        for (int64_t i = 4 * lo + threadIdx.x; i < e; i += blockDim.x) yi[i] = (int32_t)i;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *desc->nnz_y = m;
     }
     __device__ void clear_word(uint32_t* bits, int64_t w) { bits[w] = 0u; }
     __device__ T load(int32_t i) const {
@@ -747,11 +773,12 @@ struct OutSparsePolicy {
 };
 
 template <bool BYTES, class Policy>
-static void compact_items(asv_matrix_s* H, uint32_t* words, int64_t nitems, const Policy& pol, cudaStream_t s) {
+static void compact_items(asv_matrix_s* H, uint32_t* words, int64_t nitems, const Policy& pol, cudaStream_t s,
+                          const int32_t* skip = nullptr) {
     const int64_t nwords = BYTES ? (nitems + 3) / 4 : (nitems + 31) / 32;
     const int G = H->G;
     const Gate gate = gate_of(H);
-    k_items_count<256, BYTES><<<G, 256, 0, s>>>(words, nwords, H->ws.blk, gate);
+    k_items_count<256, BYTES><<<G, 256, 0, s>>>(words, nwords, H->ws.blk, gate, skip);
     k_items_write<256, BYTES, Policy><<<G, 256, 0, s>>>(words, nwords, H->ws.blk, pol, gate);
 }
 
@@ -831,8 +858,9 @@ static void finalize_acc(asv_matrix_s* H, bool from_acc, int out_mode, cudaStrea
         OutSparsePolicy<T, true, Atom> pol{H->d_desc, (Atom*)H->ws.acc, nullptr, H->ws.status, nullptr, nullptr, 0};
         compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s);
     } else {
-        OutSparsePolicy<T, false> pol{H->d_desc, nullptr, (const T*)H->ws.ywork, H->ws.status, nullptr, nullptr, 0};
-        compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s);
+        OutSparsePolicy<T, false> pol{H->d_desc, nullptr, (const T*)H->ws.ywork, H->ws.status, nullptr, nullptr, 0,
+                                      H->m};
+        compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s, &H->d_desc->y_ident);
     }
 }
 
