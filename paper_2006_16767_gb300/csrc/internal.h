@@ -145,8 +145,9 @@ struct asv_matrix_s {
     // candidate whose chain it is (the Gate of its kernels), else -1
     int32_t gate_kid = -1;
     // an FP32 matrix whose rows have at most kNarrowRow entries: the push with
-    // atomic write-back and a dense output adds in FP32 (its error bound stays
-    // within the FP32 tolerance, see push.cu)
+    // atomic write-back and a dense output adds in FP32, and the one-row-per-
+    // thread pull sums a row with a plain FMA chain (their error bounds stay
+    // within the FP32 tolerance, see push.cu and pull.cu)
     bool narrow_acc = false;
     // columns of more than kLongSeg entries: the hub count of a listed x that
     // holds every column, which the feature pass then need not gather

@@ -8,11 +8,15 @@ afterwards by clearing it. These cases check that path and its neighbours:
 the in-order list with structural zeros among its values, the same columns
 in another order (the ordinary scatter), the in-order list without values
 (all ones), and a partial list right after, which would read whatever the
-in-order call left in the workspaces. Every pull candidate and the
-selector, dense and list output, with and without an output mask; FP32 and
-FP64 within the per-row tolerances, int32 bit for bit. The matrices have
-empty rows, rows long enough for the long-row pass, and a column count that
-leaves the bitmap's last word partly used.
+in-order call left in the workspaces. On a matrix without empty rows, a
+list of every column reaches every row, so an unmasked list output is every
+row in order: the pull kernels then write its values in place and the
+compaction only writes the indices. Every pull candidate and the selector,
+dense and list output, with and without an output mask; FP32 and FP64 within
+the per-row tolerances, int32 bit for bit. The matrices have empty rows (the
+R-MAT graph), no empty row (the rectangular one), rows long enough for the
+long-row pass, and a column count that leaves the bitmap's last word partly
+used.
 """
 import numpy as np
 import pytest

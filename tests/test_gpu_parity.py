@@ -445,12 +445,15 @@ def short_rows_pattern(m, n, row_len, seed):
 
 
 @pytest.mark.parametrize("row_len", [32, 33])
-@pytest.mark.parametrize("k", ["push_thread_atom", "push_warp_atom", "push_bal_atom", "auto"])
+@pytest.mark.parametrize("k", ["push_thread_atom", "push_warp_atom", "push_bal_atom", "pull_thread", "mpull_thread",
+                               "auto"])
 def test_fp32_push_accumulation_stays_in_tolerance(row_len, k):
-    # rows of 32 entries: the FP32 atomic push adds in FP32 (32 products in
-    # any order stay within 32 * 2^-24 < 2e-6 of sum |a x|); 33 entries keep
-    # FP64 accumulators. Values spread over six decades with both signs, so
-    # the sums cancel and rounding is at its worst relative to the scale.
+    # rows of 32 entries: the FP32 atomic push adds in FP32 and the thread
+    # pull sums each row with a plain FMA chain (32 products, each rounded
+    # once, in any order stay within 32 * 2^-24 < 2e-6 of sum |a x|); 33
+    # entries keep FP64 accumulators and the compensated sum. Values spread
+    # over six decades with both signs, so the sums cancel and rounding is at
+    # its worst relative to the scale.
     m, n = 3000, 2048
     rp, c = short_rows_pattern(m, n, row_len, seed=41)
     mag = 10.0 ** gen.uniform(len(c), -3, 3, seed=42, dtype=np.float64)

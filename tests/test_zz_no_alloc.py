@@ -5,7 +5,8 @@ real-time loops where cudaMalloc/cudaFree would synchronise the device,
 runtimes that own all device memory through their own pool -- so it takes
 caller-owned CSR arrays and keeps its scratch in a fixed array inside the
 library. Every call here is checked row by row against the FP64 CPU oracle
-within the FP32 tolerance of the parity tests, in an order that makes a call
+within the FP32 tolerance of the parity tests, and against the handle's
+entry point on the same arrays within the same tolerance, in an order that makes a call
 follow a larger one (the scratch then holds more tiles than the call uses),
 and once with no value array (all ones). The file sorts last so that a run
 stopping at the first failure has run every other test."""
@@ -28,7 +29,10 @@ def to_dev(a):
 
 def check_call(rp, c, v, x, m, n, label):
     """One allocation-free product, compared per row with the oracle:
-    |y - y_ref| <= 2e-6 * sum |a x|, and exactly 0 where that sum is 0."""
+    |y - y_ref| <= 2e-6 * sum |a x|, and exactly 0 where that sum is 0; and
+    with the handle's own entry point (asv_spmv, which allocates its
+    workspaces once at handle creation) on the same arrays, within the same
+    per-row tolerance."""
     y = torch.full((m,), float("nan"), dtype=torch.float32, device=DEV)
     st = asv.asv_spmv_noalloc_f32(m, n, to_dev(rp), to_dev(c), None if v is None else to_dev(v), to_dev(x), y)
     assert st is None or st == asv.ASV_OK
@@ -39,6 +43,11 @@ def check_call(rp, c, v, x, m, n, label):
     err = np.abs(got - y_ref)
     bad = ~(err <= TOL * s)
     assert not bad.any(), f"{label}: {int(bad.sum())} rows outside 2e-6 * sum|a x|"
+    vh = np.ones(len(c), np.float32) if v is None else v
+    A = asv.Matrix(m, n, to_dev(rp), to_dev(c), to_dev(vh))
+    yh = A.spmv(to_dev(x), kernel="pull_bal").cpu().numpy().astype(np.float64)
+    bad = ~(np.abs(got - yh) <= TOL * s)
+    assert not bad.any(), f"{label}: {int(bad.sum())} rows differ from asv_spmv by more than 2e-6 * sum|a x|"
 
 
 def test_no_alloc_matches_the_oracle_on_consecutive_calls():
