@@ -95,6 +95,11 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
     }
     const int64_t r0 = ((int64_t)blockIdx.x * kStageWarps + w) * 32;
     if (r0 >= m) return;
+    // a list output over a list of every column in order: every column's bit
+    // is set, so a row is in the set when it has an entry (no bit tests), and
+    // when every row is in it (y_ident) the flags are not written either
+    const bool allx = SOUT && a.desc && a.desc->x_ident;
+    const bool noflag = SOUT && a.desc && a.desc->y_ident;
     const int64_t i = r0 + lane;
     const int32_t rb = __ldg(rowptr + min(i, m));
     const int32_t span_end = __ldg(rowptr + min(r0 + 32, m));
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
                     for (int u = 0; u < GD; ++u) {
                         const int32_t c = sc[k + u - a0];
                         xg[u] = __ldg(x + c);
-                        if (SOUT) hb |= (uint32_t)test_bit(p.xbits, c);
+                        if (SOUT && !allx) hb |= (uint32_t)test_bit(p.xbits, c);
                     }
                     if constexpr (NARROW) {
 #pragma unroll
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
                     for (int u = 0; u < 4; ++u) {
                         const int32_t c = sc[k + u - a0];
                         xg[u] = __ldg(x + c);
-                        if (SOUT) hb |= (uint32_t)test_bit(p.xbits, c);
+                        if (SOUT && !allx) hb |= (uint32_t)test_bit(p.xbits, c);
                     }
                     if constexpr (NARROW) {
 #pragma unroll
@@ -248,7 +253,7 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
             for (; k < re; ++k) {
                 const int32_t c = sc[k - a0];
                 if (MASK || SOUT) {
-                    const bool bit = test_bit(p.xbits, c);
+                    const bool bit = allx || test_bit(p.xbits, c);
                     hit |= bit;
                     if (MASK && !bit) continue;
                 }
@@ -263,13 +268,14 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
             }
         }
         if constexpr (NARROW) acc.s = ps;  // c stays 0: the value is ps
+        if (allx) hit = mine && !off && re > rb;
     } else {
         if (mine && !off) acc = row_direct<T, MASK, SOUT>(col, val, x, p.xbits, rb, re, hit);
         else S::acc_zero(acc);
     }
     if (mine) {
         y[i] = S::part_T(S::acc_part(acc));
-        if (SOUT && hit) yflag[i] = 1;
+        if (SOUT && hit && !noflag) yflag[i] = 1;
     }
 }
 
