@@ -204,7 +204,12 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
         __syncwarp();
         S::acc_zero(acc);
         float ps = 0.f;  // the NARROW sum
-        if (mine && !off) {
+        // the walk, compiled for each (bit tests, value array) pair so that
+        // neither per-entry condition costs an instruction in the loop
+        auto walk = [&](auto bits_tag, auto vals_tag) {
+            constexpr bool BITS = decltype(bits_tag)::value;
+            constexpr bool VALS = decltype(vals_tag)::value;
+            (void)VALS;
             int32_t k = rb;
             if constexpr (!MASK && kStageVals) {
                 // eight gathers in flight per lane before their products are
@@ -219,14 +224,14 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
                     for (int u = 0; u < GD; ++u) {
                         const int32_t c = sc[k + u - a0];
                         xg[u] = __ldg(x + c);
-                        if (SOUT && !allx) hb |= (uint32_t)test_bit(p.xbits, c);
+                        if (SOUT && BITS) hb |= (uint32_t)test_bit(p.xbits, c);
                     }
                     if constexpr (NARROW) {
 #pragma unroll
-                        for (int u = 0; u < GD; ++u) ps = __fmaf_rn(val ? sv[k + u - a0] : 1.f, xg[u], ps);
+                        for (int u = 0; u < GD; ++u) ps = __fmaf_rn(VALS ? sv[k + u - a0] : 1.f, xg[u], ps);
                     } else {
 #pragma unroll
-                        for (int u = 0; u < GD; ++u) S::acc_add(acc, S::mul(val ? sv[k + u - a0] : S::one(), xg[u]));
+                        for (int u = 0; u < GD; ++u) S::acc_add(acc, S::mul(VALS ? sv[k + u - a0] : S::one(), xg[u]));
                     }
                     if (SOUT) hit |= hb != 0u;
                 }
@@ -237,14 +242,14 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
                     for (int u = 0; u < 4; ++u) {
                         const int32_t c = sc[k + u - a0];
                         xg[u] = __ldg(x + c);
-                        if (SOUT && !allx) hb |= (uint32_t)test_bit(p.xbits, c);
+                        if (SOUT && BITS) hb |= (uint32_t)test_bit(p.xbits, c);
                     }
                     if constexpr (NARROW) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) ps = __fmaf_rn(val ? sv[k + u - a0] : 1.f, xg[u], ps);
+                        for (int u = 0; u < 4; ++u) ps = __fmaf_rn(VALS ? sv[k + u - a0] : 1.f, xg[u], ps);
                     } else {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) S::acc_add(acc, S::mul(val ? sv[k + u - a0] : S::one(), xg[u]));
+                        for (int u = 0; u < 4; ++u) S::acc_add(acc, S::mul(VALS ? sv[k + u - a0] : S::one(), xg[u]));
                     }
                     if (SOUT) hit |= hb != 0u;
                     k += 4;
@@ -253,18 +258,29 @@ __global__ void __launch_bounds__(32 * kStageWarps) k_pull_thread(int64_t m, int
             for (; k < re; ++k) {
                 const int32_t c = sc[k - a0];
                 if (MASK || SOUT) {
-                    const bool bit = allx || test_bit(p.xbits, c);
+                    const bool bit = !BITS || test_bit(p.xbits, c);
                     hit |= bit;
                     if (MASK && !bit) continue;
                 }
                 T v;
-                if constexpr (kStageVals) v = (val != nullptr) ? sv[k - a0] : S::one();
+                if constexpr (kStageVals) v = VALS ? sv[k - a0] : S::one();
                 else v = load_val(val, k);
                 if constexpr (NARROW) ps = __fmaf_rn(v, __ldg(x + c), ps);
                 else S::acc_add(acc, S::mul(v, __ldg(x + c)));
                 if constexpr (S::kPattern) {
                     if (acc) break;
                 }
+            }
+        };
+        if (mine && !off) {
+            using Y = std::true_type;
+            using N = std::false_type;
+            if (allx) {
+                if (val != nullptr) walk(N{}, Y{});
+                else walk(N{}, N{});
+            } else {
+                if (val != nullptr) walk(Y{}, Y{});
+                else walk(Y{}, N{});
             }
         }
         if constexpr (NARROW) acc.s = ps;  // c stays 0: the value is ps
