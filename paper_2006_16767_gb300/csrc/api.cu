@@ -387,8 +387,13 @@ static void enqueue_candidate(asv_matrix_s* H, int k, int x_sparse, int om, cuda
     } else {
         const int q = k - ASV_K_PUSH_THREAD_ATOM;
         const int dist = q % 3, wb = q / 3;
-        if (!x_sparse) launch_x_compact_list(H, s);
-        launch_push(H, dist, wb, om, s);
+        // the warp push with atomics reads a dense x's bitmap directly when x
+        // has fewer nonzeros than its group form takes (two groups of 32 per
+        // warp of its grid: 8 blocks of 8 warps per SM), so that list is
+        // never compacted
+        const int64_t bits_below = (!x_sparse && k == ASV_K_PUSH_WARP_ATOM) ? (int64_t)4096 * H->num_sms : 0;
+        if (!x_sparse) launch_x_compact_list(H, s, bits_below);
+        launch_push(H, dist, wb, om, s, bits_below);
     }
 }
 

@@ -207,6 +207,16 @@ struct Gate {
     }
 };
 
+// When the two launches of an ordered compaction return at once: a flag set
+// (flag != NULL and *flag != 0), or a device count below a bound (count !=
+// NULL and *count < below).
+struct CompactSkip {
+    const int32_t* flag = nullptr;
+    const int64_t* count = nullptr;
+    int64_t below = 0;
+    __device__ __forceinline__ bool on() const { return (flag && *flag) || (count && *count < below); }
+};
+
 // Row i is excluded by the output mask.
 __device__ __forceinline__ bool row_masked(const uint32_t* __restrict__ ymask, int64_t i) {
     return ymask != nullptr && ((__ldg(ymask + (i >> 5)) >> (i & 31)) & 1u);

@@ -250,7 +250,9 @@ void launch_features(asv_matrix_s* H, const DescInit& di, const SelectArg& sa, c
 void launch_x_scatter(asv_matrix_s* H, bool set, bool bits, cudaStream_t s);
 // the Gate of the kernels launched now (see gate_kid)
 inline Gate gate_of(const asv_matrix_s* H) { return Gate{H->d_desc, H->gate_kid}; }
-void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s);
+// bits_below > 0: skipped when x has fewer nonzeros than that (the warp push
+// with atomics then reads the feature pass's bitmap instead of a list)
+void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s, int64_t bits_below = 0);
 // narrow: the push accumulated into FP32 accumulators (narrow_acc)
 void launch_finalize(asv_matrix_s* H, bool from_acc, int out_mode, cudaStream_t s, bool narrow = false);
 void launch_compact_public(asv_matrix_s* H, const void* x, int32_t* idx, void* val, int64_t* count,
@@ -273,7 +275,9 @@ void launch_partition_raw(const int32_t* rowptr, int64_t m, int64_t nnz, int64_t
                           cudaStream_t s);
 
 // push.cu
-void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s);
+// bits_below > 0 (the warp push on a dense x): an x of fewer nonzeros than
+// that is read from the feature pass's bitmap, its list never built
+void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s, int64_t bits_below = 0);
 
 // batched.cu
 cudaError_t batched_forward(asv_matrix_s* H, int32_t B, int64_t max_entries, const int64_t* xptr, const int32_t* xidx,

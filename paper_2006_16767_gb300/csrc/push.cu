@@ -153,10 +153,13 @@ constexpr int kHubWaitIters = 256;  // x ~128 ns of sleep: a few tens of microse
 template <class T, int WB>
 __device__ __forceinline__ void push_segment(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                              const T* __restrict__ valc, const CallDesc* __restrict__ desc,
-                                             const Ws& ws, const uint32_t* ym, int64_t t, int32_t s, int lane) {
+                                             const Ws& ws, const uint32_t* ym, int64_t t, int32_t s, int lane,
+                                             bool bm) {
     using S = Sr<T>;
-    const int32_t j = desc->xidx[t];
-    const T xj = list_val<T>(desc, t);
+    // bm: t is the column itself (a dense x read from its bitmap, no list)
+    const int32_t j = bm ? (int32_t)t : desc->xidx[t];
+    T xj = S::one();
+    if constexpr (!S::kPattern) xj = bm ? ((const T*)desc->x_dense)[j] : list_val<T>(desc, t);
     const int32_t b = __ldg(colptr + j), e = __ldg(colptr + j + 1);
     const int64_t pos0 = !wb_atomic(WB) ? (int64_t)ws.xscan[t] - b : 0;
     const int32_t sb = b + s * kLongSeg, se = min(sb + kLongSeg, e);
@@ -178,7 +181,7 @@ __device__ __forceinline__ bool queue_long(const Ws& ws, int64_t t) {
 template <class T, int WB, bool WAIT>
 __device__ __forceinline__ void help_long(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                           const T* __restrict__ valc, const CallDesc* __restrict__ desc,
-                                          const Ws& ws, const uint32_t* ym, int lane) {
+                                          const Ws& ws, const uint32_t* ym, int lane, bool bm = false) {
     int32_t nq = 0;
     if (lane == 0) {
         const int64_t want = WAIT ? min(desc->nhub, (int64_t)ws.lcol_cap) : 0;
@@ -198,7 +201,7 @@ __device__ __forceinline__ void help_long(const int32_t* __restrict__ colptr, co
                 t = *(volatile int32_t*)&ws.lcol[q].x;
             }
             if (t >= 0) {
-                const int32_t j = desc->xidx[t];
+                const int32_t j = bm ? t : desc->xidx[t];
                 nseg = (__ldg(colptr + j + 1) - __ldg(colptr + j) + kLongSeg - 1) / kLongSeg;
             }
         }
@@ -210,7 +213,7 @@ __device__ __forceinline__ void help_long(const int32_t* __restrict__ colptr, co
             if (lane == 0) s = atomicAdd(&ws.lcol[q].y, 1);
             s = __shfl_sync(0xffffffffu, s, 0);
             if (s >= nseg) break;
-            push_segment<T, WB>(colptr, rowidx, valc, desc, ws, ym, t, s, lane);
+            push_segment<T, WB>(colptr, rowidx, valc, desc, ws, ym, t, s, lane, bm);
         }
     }
 }
@@ -280,9 +283,16 @@ __global__ void __launch_bounds__(256) k_push_thread(const int32_t* __restrict__
 // density 0.1: 468 -> 407 us listed, 427 -> 356 us dense); groups of 8 on a
 // list ten times shorter measured slower (137 -> 144 us), so shorter lists
 // keep G = 1. Longer columns follow one after another; hubs go to the queue.
+// With bits_below > 0 (a dense x, atomic write-back) an x of fewer nonzeros
+// than that -- the lists that would keep G = 1 -- is read from the feature
+// pass's bitmap instead of a compacted list: lane l of a warp takes bitmap
+// word l of the warp's stretch of 32 words and, round by round, the next set
+// bit of it, so a round holds up to 32 columns walked as a group (their x
+// values gathered from the dense x); the list's compaction is skipped.
 template <class T, int WB>
 __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
-                                                   const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws_in, Gate gate) {
+                                                   const T* __restrict__ valc, const CallDesc* __restrict__ desc, Ws ws_in, Gate gate,
+                                                   int64_t ncols, int64_t bits_below) {
     if (gate.off()) return;
     const Ws ws = push_ws<WB>(ws_in, desc);
     using S = Sr<T>;
@@ -299,19 +309,16 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
     // eight measured slower than four (the stencil's listed products at x
     // densities 0.1 and 0.01: 408 -> 456 and 141 -> 177 us, 32 -> 40 registers)
     constexpr int GU = 4;
-    for (int64_t t0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * G; t0 < nx; t0 += nw * G) {
-        const int64_t t = t0 + lane;
-        const bool valid = lane < G && t < nx;
+    const bool bm = wb_atomic(WB) && nx < bits_below;
+    // one round: lane l holds column j (list entry t) when valid
+    auto round = [&](bool valid, int32_t j, int64_t t, T xj) {
         int32_t b = 0, len = 0, pos0 = 0;
-        T xj = S::one();
         if (valid) {
-            const int32_t j = xidx[t];
-            xj = list_val<T>(desc, t);
             b = __ldg(colptr + j);
             len = __ldg(colptr + j + 1) - b;
             if (!wb_atomic(WB)) pos0 = ws.xscan[t] - b;
         }
-        const bool queued = valid && len > kLongSeg && queue_long(ws, t);
+        const bool queued = valid && len > kLongSeg && queue_long(ws, bm ? (int64_t)j : t);
         for (unsigned pend = __ballot_sync(FULL, valid && len <= 32); pend;) {
             int32_t rr[GU];
             P pp[GU];
@@ -352,11 +359,42 @@ __global__ void __launch_bounds__(256) k_push_warp(const int32_t* __restrict__ c
                 emit_batch<T, WB, 4>(ws, ym, rr, pp, p0 + k0, 32);
             }
         }
+    };
+    const int64_t warp = blockIdx.x * wpb + (threadIdx.x >> 5);
+    if (bm) {
+        const uint32_t* __restrict__ xb = desc->xbits;
+        const T* __restrict__ xd = (const T*)desc->x_dense;
+        const int64_t nwords = (ncols + 31) >> 5;
+        for (int64_t w0 = warp * 32; w0 < nwords; w0 += nw * 32) {
+            uint32_t bits = w0 + lane < nwords ? __ldg(xb + w0 + lane) : 0u;
+            while (__any_sync(FULL, bits != 0u)) {
+                const bool valid = bits != 0u;
+                const int32_t j = valid ? (int32_t)((w0 + lane) * 32 + __ffs(bits) - 1) : 0;
+                bits &= bits - 1u;
+                T xj = S::one();
+                if constexpr (!S::kPattern) {
+                    if (valid) xj = xd[j];
+                }
+                round(valid, j, 0, xj);
+            }
+        }
+    } else {
+        for (int64_t t0 = warp * G; t0 < nx; t0 += nw * G) {
+            const int64_t t = t0 + lane;
+            const bool valid = lane < G && t < nx;
+            int32_t j = 0;
+            T xj = S::one();
+            if (valid) {
+                j = xidx[t];
+                xj = list_val<T>(desc, t);
+            }
+            round(valid, j, t, xj);
+        }
     }
     // any lane may have queued a hub of this warp; lane 0 reads the queue
     // entries, so order those lanes' stores before its reads
     __syncwarp();
-    help_long<T, WB, false>(colptr, rowidx, valc, desc, ws, ym, lane);
+    help_long<T, WB, false>(colptr, rowidx, valc, desc, ws, ym, lane, bm);
 }
 
 // Even split: warp-chunks of 32*IPT effective nonzeros; the listed column of
@@ -676,7 +714,7 @@ static int bitlen64(int64_t v) {
 }
 
 template <class T>
-static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s) {
+static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s, int64_t bits_below) {
     const T* valc = (const T*)H->val_csc;
     // a few blocks per SM for the per-column traversals (they stride over the
     // list, and a large grid of mostly idle blocks costs launch time on short
@@ -703,7 +741,7 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
 #define TRAV(WBV)                                                                                   \
     do {                                                                                            \
         if (dist == 0) k_push_thread<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
-        else if (dist == 1) k_push_warp<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
+        else if (dist == 1) k_push_warp<T, WBV><<<grid, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate, H->n, bits_below); \
         else k_push_bal<T, WBV><<<grid * 4, 256, 0, s>>>(H->colptr, H->rowidx, valc, d, ws, gate); \
     } while (0)
     if (wb == WB_ATOM_N) {
@@ -742,12 +780,12 @@ static void push_dtype(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStre
     if (wb != WB_ATOM_N) launch_finalize(H, true, out_mode, s);
 }
 
-void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s) {
+void launch_push(asv_matrix_s* H, int dist, int wb, int out_mode, cudaStream_t s, int64_t bits_below) {
     switch (H->dtype) {
-        case ASV_F32: push_dtype<float>(H, dist, wb, out_mode, s); break;
-        case ASV_F64: push_dtype<double>(H, dist, wb, out_mode, s); break;
-        case ASV_I32: push_dtype<int32_t>(H, dist, wb, out_mode, s); break;
-        case ASV_BOOL: push_dtype<bool8>(H, dist, wb, out_mode, s); break;
+        case ASV_F32: push_dtype<float>(H, dist, wb, out_mode, s, bits_below); break;
+        case ASV_F64: push_dtype<double>(H, dist, wb, out_mode, s, bits_below); break;
+        case ASV_I32: push_dtype<int32_t>(H, dist, wb, out_mode, s, bits_below); break;
+        case ASV_BOOL: push_dtype<bool8>(H, dist, wb, out_mode, s, bits_below); break;
     }
 }
 

@@ -371,16 +371,29 @@ __global__ void __launch_bounds__(B) k_feat_sparse(const int64_t* __restrict__ n
         cs += (unsigned long long)d;
         ch += d > kLongSeg;
     }
-    // the order check: four indices per thread and step (16-byte loads where
-    // the list is 16-byte aligned), counting entries t whose column is not t
+    // the order check: four indices per 16-byte load (where the list is
+    // 16-byte aligned), four loads per thread in flight, counting entries t
+    // whose column is not t
     unsigned long long cm = 0;
     if (ident) {
         const int64_t gt = blockIdx.x * (int64_t)B + threadIdx.x;
         int64_t q0 = 0;
         if (((uintptr_t)xidx & 15) == 0) {
             const int64_t n4 = n / 4;
-            for (int64_t q = gt; q < n4; q += stride) {
-                const int4 v = __ldg(reinterpret_cast<const int4*>(xidx) + q);
+            const int4* __restrict__ xv = reinterpret_cast<const int4*>(xidx);
+            int64_t q = gt;
+            for (; q + 3 * stride < n4; q += 4 * stride) {
+                int4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = __ldg(xv + q + u * stride);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t j = (int32_t)(4 * (q + u * stride));
+                    cm += (v[u].x != j) + (v[u].y != j + 1) + (v[u].z != j + 2) + (v[u].w != j + 3);
+                }
+            }
+            for (; q < n4; q += stride) {
+                const int4 v = __ldg(xv + q);
                 const int32_t j = (int32_t)(4 * q);
                 cm += (v.x != j) + (v.y != j + 1) + (v.z != j + 2) + (v.w != j + 3);
             }
@@ -579,8 +592,8 @@ __device__ __forceinline__ void load_run(const uint32_t* __restrict__ words, int
 // thread and round.
 template <int B, bool BYTES>
 __global__ void __launch_bounds__(B) k_items_count(const uint32_t* __restrict__ words, int64_t nwords, int32_t* blk,
-                                                   Gate gate, const int32_t* skip) {
-    if (gate.off() || (skip && *skip)) return;
+                                                   Gate gate, CompactSkip skip) {
+    if (gate.off() || skip.on()) return;
     __shared__ int32_t sm[B / 32 + 1];
     int64_t lo, hi;
     block_range(nwords, lo, hi);
@@ -615,8 +628,8 @@ __global__ void __launch_bounds__(B) k_items_write(uint32_t* words, int64_t nwor
     __shared__ int32_t stage[CAP + CAP / 32];
     int64_t lo, hi;
     block_range(nwords, lo, hi);
-    if (pol.every_item()) {
-        pol.write_every(words, lo, hi);
+    if (pol.bypass()) {
+        pol.write_bypass(words, lo, hi);
         return;
     }
     const bool vec = ((uintptr_t)words & 15) == 0;
@@ -683,9 +696,10 @@ struct XListPolicy {
     int32_t* idx;
     T* val;
     const T* x;
+    int64_t bits_below;  // > 0: a list shorter than this is not built (the warp push reads the bitmap)
     __device__ void begin() { x = (const T*)desc->x_dense; }
-    __device__ bool every_item() const { return false; }
-    __device__ void write_every(uint32_t*, int64_t, int64_t) {}
+    __device__ bool bypass() const { return bits_below > 0 && desc->nnz_x < bits_below; }
+    __device__ void write_bypass(uint32_t*, int64_t, int64_t) {}
     __device__ void clear_word(uint32_t*, int64_t) {}
     __device__ T load(int32_t j) const { return Sr<T>::kPattern ? Sr<T>::one() : x[j]; }
     __device__ void store(int32_t pos, int32_t j, T v) const {
@@ -704,8 +718,8 @@ struct PublicCompactPolicy {
     T* val;
     int64_t* count_out;
     __device__ void begin() {}
-    __device__ bool every_item() const { return false; }
-    __device__ void write_every(uint32_t*, int64_t, int64_t) {}
+    __device__ bool bypass() const { return false; }
+    __device__ void write_bypass(uint32_t*, int64_t, int64_t) {}
     __device__ void clear_word(uint32_t*, int64_t) {}
     __device__ T load(int32_t j) const { return val ? x[j] : T(0); }
     __device__ void store(int32_t pos, int32_t j, T v) const {
@@ -745,8 +759,8 @@ struct OutSparsePolicy {
     // every row is in the set (y_ident): the pull wrote the values in place,
     // so this block clears its range of flag words and writes the indices
     // of its rows; block 0 publishes the count m
-    __device__ bool every_item() const { return !FROM_ACC && desc->y_ident; }
-    __device__ void write_every(uint32_t* words, int64_t lo, int64_t hi) const {
+    __device__ bool bypass() const { return !FROM_ACC && desc->y_ident; }
+    __device__ void write_bypass(uint32_t* words, int64_t lo, int64_t hi) const {
         int32_t* __restrict__ yi = desc->yidx;
         for (int64_t w = lo + threadIdx.x; w < hi; w += blockDim.x) words[w] = 0u;
         const int64_t e = min(4 * hi, m);
@@ -774,7 +788,7 @@ struct OutSparsePolicy {
 
 template <bool BYTES, class Policy>
 static void compact_items(asv_matrix_s* H, uint32_t* words, int64_t nitems, const Policy& pol, cudaStream_t s,
-                          const int32_t* skip = nullptr) {
+                          CompactSkip skip = CompactSkip{}) {
     const int64_t nwords = BYTES ? (nitems + 3) / 4 : (nitems + 31) / 32;
     const int G = H->G;
     const Gate gate = gate_of(H);
@@ -783,17 +797,18 @@ static void compact_items(asv_matrix_s* H, uint32_t* words, int64_t nitems, cons
 }
 
 template <class T>
-static void x_list_dtype(asv_matrix_s* H, cudaStream_t s) {
-    XListPolicy<T> pol{H->d_desc, H->ws.xlist_idx, (T*)H->ws.xlist_val, nullptr};
-    compact_items<false>(H, H->ws.xbits_dense, H->n, pol, s);
+static void x_list_dtype(asv_matrix_s* H, cudaStream_t s, int64_t bits_below) {
+    XListPolicy<T> pol{H->d_desc, H->ws.xlist_idx, (T*)H->ws.xlist_val, nullptr, bits_below};
+    compact_items<false>(H, H->ws.xbits_dense, H->n, pol, s,
+                         CompactSkip{nullptr, bits_below > 0 ? &H->d_desc->nnz_x : nullptr, bits_below});
 }
 
-void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s) {
+void launch_x_compact_list(asv_matrix_s* H, cudaStream_t s, int64_t bits_below) {
     switch (H->dtype) {
-        case ASV_F32: x_list_dtype<float>(H, s); break;
-        case ASV_F64: x_list_dtype<double>(H, s); break;
-        case ASV_I32: x_list_dtype<int32_t>(H, s); break;
-        case ASV_BOOL: x_list_dtype<bool8>(H, s); break;
+        case ASV_F32: x_list_dtype<float>(H, s, bits_below); break;
+        case ASV_F64: x_list_dtype<double>(H, s, bits_below); break;
+        case ASV_I32: x_list_dtype<int32_t>(H, s, bits_below); break;
+        case ASV_BOOL: x_list_dtype<bool8>(H, s, bits_below); break;
     }
 }
 
@@ -860,7 +875,7 @@ static void finalize_acc(asv_matrix_s* H, bool from_acc, int out_mode, cudaStrea
     } else {
         OutSparsePolicy<T, false> pol{H->d_desc, nullptr, (const T*)H->ws.ywork, H->ws.status, nullptr, nullptr, 0,
                                       H->m};
-        compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s, &H->d_desc->y_ident);
+        compact_items<true>(H, (uint32_t*)H->ws.yflag, H->m, pol, s, CompactSkip{&H->d_desc->y_ident, nullptr, 0});
     }
 }
 

@@ -121,3 +121,32 @@ def test_full_lists_int32_bit_exact():
         for k in PULLS:
             y = A.spmspv(xidx=to_dev(idx), xval=to_dev(val), kernel=k).cpu().numpy()
             assert np.array_equal(y, want), f"int32 {label} k={k}"
+
+
+def test_long_list_in_order_and_with_one_swap():
+    # a list of 2^21 + 5 columns spans several rounds of every thread of the
+    # feature pass's order check; the same list with two entries swapped
+    # (one in the first and one in the last round) must take the scatter
+    m = (1 << 21) + 5
+    i = np.arange(m, dtype=np.int64)
+    cols = np.stack([i - 1, i, i + 1], axis=1)
+    ok = (cols >= 0) & (cols < m)
+    rp = np.concatenate([[0], np.cumsum(ok.sum(axis=1))]).astype(np.int32)
+    c = cols[ok].astype(np.int32)
+    v = gen.uniform(len(c), -1, 1, 79, 0, np.float64).astype(np.float32)
+    A = asv.Matrix(m, m, to_dev(rp), to_dev(c), to_dev(v))
+    val = gen.uniform(m, -1, 1, 80, 0, np.float64).astype(np.float32)
+    ident = np.arange(m, dtype=np.int32)
+    swap = ident.copy()
+    swap[[17, m - 9]] = swap[[m - 9, 17]]
+    for label, idx in (("in order", ident), ("one swap", swap)):
+        xv = val[idx]
+        y_ref, s, hit = oracle.spmspv_rowmajor(m, rp, c, v.astype(np.float64), idx, xv.astype(np.float64))
+        for k in ("pull_thread", "auto"):
+            y = A.spmspv(xidx=to_dev(idx), xval=to_dev(xv), kernel=k).cpu().numpy()
+            assert_rows_close(y, y_ref, s, "f32", f"tridiagonal {m} {label} k={k}")
+            yidx, yval, nnz_y = A.spmspv(xidx=to_dev(idx), xval=to_dev(xv), kernel=k, sparse_out=True)
+            cnt = int(nnz_y.item())
+            got = yidx[:cnt].cpu().numpy()
+            assert np.array_equal(got, np.flatnonzero(hit)), f"tridiagonal {m} {label} k={k} (structural set)"
+            assert_rows_close(yval[:cnt].cpu().numpy(), y_ref[got], s[got], "f32", f"tridiagonal {m} {label} k={k}")

@@ -200,15 +200,20 @@ def test_long_columns_all_kernels(k):
     # (a list of every column takes the feature pass's shortcut: no gathers),
     # and a fifth of the columns
     every_shuffled = np.argsort(gen.uniform(n, 0, 1, seed=20)).astype(np.int32)
+    # Each as a list and as a dense x (the warp push reads a dense x of this
+    # size from its bitmap, hub columns queued by column id).
     for idx in (hubs, np.arange(n, dtype=np.int32), every_shuffled, gen.sample_positions(n, n // 5, seed=18)):
         xv = gen.uniform(len(idx), -1, 1, seed=19, dtype=np.float64)
-        for sparse_out in (False, True):
-            check(A, k, "long_columns", n, rp, c, v, idx, xv, np.float32, "f32", False, sparse_out)
+        for dense_in in (False, True):
+            for sparse_out in (False, True):
+                check(A, k, "long_columns", n, rp, c, v, idx, xv, np.float32, "f32", dense_in, sparse_out)
         xb = np.zeros(n, np.uint8)
         xb[idx] = 1
         want = oracle.bool_pull(rp, c, xb)
         y = Ab.spmspv(xidx=to_dev(idx), kernel=k).cpu().numpy()
         assert np.array_equal(y != 0, want != 0), f"bool long columns k={k}"
+        y = Ab.spmspv(x_dense=to_dev(xb), kernel=k).cpu().numpy()
+        assert np.array_equal(y != 0, want != 0), f"bool long columns dense x k={k}"
 
 
 @pytest.mark.parametrize("k", ["auto"] + ALL_K)
