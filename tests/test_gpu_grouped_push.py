@@ -131,3 +131,55 @@ def test_stencil_long_lists_boolean_and_int32_bit_exact(k):
         keep = xi != 0
         got = I.spmspv(xidx=to_dev(idx[keep]), xval=to_dev(xi[keep]), kernel=k).cpu().numpy()
         assert np.array_equal(got, wi), f"int32 list k={k} rho={rho}"
+
+
+def test_dense_x_read_from_the_bitmap():
+    # A dense x of fewer nonzeros than the group threshold, on a matrix wide
+    # enough (1,024 columns per warp of the push's grid) with columns of at
+    # most 32 entries on average: the warp push reads the feature pass's
+    # bitmap instead of a compacted list. A tridiagonal matrix plus one column
+    # of 10,000 entries (a hub, queued by its column id); x at three
+    # densities, the last above the threshold (list and group form).
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    m = 1024 * 64 * sms + 5
+    rp0, c0, _ = tridiagonal(m, seed=81)
+    # column 5 joins rows 0, 7, ..., 69993 (the first 70,000 rows are rebuilt)
+    cut = 70000
+    head = np.repeat(np.arange(cut, dtype=np.int64), np.diff(rp0[:cut + 1]))
+    hub_rows = np.arange(0, 10000, dtype=np.int64) * 7
+    key = np.unique(np.concatenate([head * m + c0[:rp0[cut]], hub_rows * m + 5]))
+    rp_head = np.cumsum(np.bincount(key // m, minlength=cut))
+    rp = np.concatenate([[0], rp_head, rp_head[-1] + (rp0[cut + 1:] - rp0[cut])]).astype(np.int32)
+    c = np.concatenate([(key % m), c0[rp0[cut]:]]).astype(np.int32)
+    v = gen.uniform(len(c), -1, 1, seed=82, dtype=np.float64).astype(np.float32)
+    A = asv.Matrix(m, m, to_dev(rp), to_dev(c), to_dev(v))
+    B = asv.Matrix(m, m, to_dev(rp), to_dev(c), None)
+    masked = gen.sample_positions(m, m // 5, seed=83)
+    keep = np.ones(m, bool)
+    keep[masked] = False
+    mk = to_dev(mask_bits(m, masked.astype(np.int64)))
+    for rho in (1e-4, 1e-2, 0.1):
+        idx, val = gen.sparse_x(m, int(rho * m), seed=84, stream=int(rho * 1e4))
+        idx = np.union1d(idx, [5]).astype(np.int32)  # the hub column is always in x
+        val = gen.uniform(len(idx), -1, 1, seed=85, stream=int(rho * 1e4), dtype=np.float64)
+        y_ref, s, hit = oracle.spmspv_rowmajor(m, rp, c, v.astype(np.float64), idx, val)
+        xd = to_dev(gen.densify(m, idx, val.astype(np.float32), np.float32))
+        for k in ("push_warp_atom", "auto"):
+            for use_mask in (False, True):
+                ym = np.where(keep, y_ref, 0.0) if use_mask else y_ref
+                sm = np.where(keep, s, 0.0) if use_mask else s
+                want = np.flatnonzero(hit.astype(bool) & keep) if use_mask else np.flatnonzero(hit)
+                extra = dict(ymask=mk) if use_mask else {}
+                what = f"bitmap push rho={rho} k={k} masked={use_mask}"
+                y = A.spmspv(x_dense=xd, kernel=k, **extra).cpu().numpy()
+                assert_rows_close(y, ym, sm, "f32", what)
+                yidx, yval, nnz_y = A.spmspv(x_dense=xd, kernel=k, sparse_out=True, **extra)
+                cnt = int(nnz_y.item())
+                got = yidx[:cnt].cpu().numpy()
+                assert np.array_equal(got, want), what + " (structural set)"
+                assert_rows_close(yval[:cnt].cpu().numpy(), ym[got], sm[got], "f32", what)
+        xb = np.zeros(m, np.uint8)
+        xb[idx] = 1
+        wb = oracle.bool_pull(rp, c, xb)
+        yb = B.spmspv(x_dense=to_dev(xb), kernel="push_warp_atom").cpu().numpy()
+        assert np.array_equal(yb != 0, wb != 0), f"bitmap push Boolean rho={rho}"
