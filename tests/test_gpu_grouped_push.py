@@ -139,7 +139,8 @@ def test_dense_x_read_from_the_bitmap():
     # most 32 entries on average: the warp push reads the feature pass's
     # bitmap instead of a compacted list. A tridiagonal matrix plus one column
     # of 10,000 entries (a hub, queued by its column id); x at three
-    # densities, the last above the threshold (list and group form).
+    # densities, the last above the threshold (list and group form); FP32 and
+    # FP64 within their per-row tolerances, int32 and Boolean bit for bit.
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     m = 1024 * 64 * sms + 5
     rp0, c0, _ = tridiagonal(m, seed=81)
@@ -151,8 +152,12 @@ def test_dense_x_read_from_the_bitmap():
     rp_head = np.cumsum(np.bincount(key // m, minlength=cut))
     rp = np.concatenate([[0], rp_head, rp_head[-1] + (rp0[cut + 1:] - rp0[cut])]).astype(np.int32)
     c = np.concatenate([(key % m), c0[rp0[cut]:]]).astype(np.int32)
-    v = gen.uniform(len(c), -1, 1, seed=82, dtype=np.float64).astype(np.float32)
+    v64 = gen.uniform(len(c), -1, 1, seed=82, dtype=np.float64)
+    v = v64.astype(np.float32)
     A = asv.Matrix(m, m, to_dev(rp), to_dev(c), to_dev(v))
+    A64 = asv.Matrix(m, m, to_dev(rp), to_dev(c), to_dev(v64))
+    vi = gen.small_ints(len(c), -50, 50, 1.0, seed=86).astype(np.int32)
+    I = asv.Matrix(m, m, to_dev(rp), to_dev(c), to_dev(vi))
     B = asv.Matrix(m, m, to_dev(rp), to_dev(c), None)
     masked = gen.sample_positions(m, m // 5, seed=83)
     keep = np.ones(m, bool)
@@ -178,6 +183,14 @@ def test_dense_x_read_from_the_bitmap():
                 got = yidx[:cnt].cpu().numpy()
                 assert np.array_equal(got, want), what + " (structural set)"
                 assert_rows_close(yval[:cnt].cpu().numpy(), ym[got], sm[got], "f32", what)
+        y64_ref, s64, _ = oracle.spmspv_rowmajor(m, rp, c, v64, idx, val)
+        y64 = A64.spmspv(x_dense=to_dev(gen.densify(m, idx, val, np.float64)), kernel="push_warp_atom").cpu().numpy()
+        assert_rows_close(y64, y64_ref, s64, "f64", f"bitmap push FP64 rho={rho}")
+        xi = np.zeros(m, np.int32)
+        xi[idx] = gen.small_ints(len(idx), -50, 50, 1.0, seed=87, stream=int(rho * 1e4)).astype(np.int32)
+        wi = oracle.i32_pull(rp, c, vi, xi)
+        yi = I.spmspv(x_dense=to_dev(xi), kernel="push_warp_atom").cpu().numpy()
+        assert np.array_equal(yi, wi), f"bitmap push int32 rho={rho}"
         xb = np.zeros(m, np.uint8)
         xb[idx] = 1
         wb = oracle.bool_pull(rp, c, xb)
