@@ -173,7 +173,8 @@ asv_status asv_matrix_update_values(asv_matrix A, const void* d_val, void* strea
 /* ---------------------------------------------------------------- products */
 
 /* y = A x with x dense (d_x[n]) and y dense (d_y[m]), overwritten
- * (the traditional SpMV of Sec. IV-A when a pull kernel runs). `kernel` is a
+ * (the traditional SpMV of Sec. IV-A when a pull kernel runs); d_y must not
+ * overlap d_x. `kernel` is a
  * candidate id or ASV_K_AUTO; with AUTO the device computes the vector
  * features of x, evaluates the selector and runs the chosen candidate
  * (which may be a push kernel when x is sparse in value). */
@@ -193,7 +194,12 @@ asv_status asv_spmv(asv_matrix A, const void* d_x, void* d_y, int32_t kernel, vo
  *    ASV_BOOL), and its size to the device int64 *d_nnz_y. At most y_cap
  *    entries are written; a larger set latches ASV_ERR_CAPACITY.
  * Dense/sparse conversion of x happens on the device only when the chosen
- * kernel needs the other format (Sec. VI-A/VI-C). No synchronisation. */
+ * kernel needs the other format (Sec. VI-A/VI-C); a list of every column in
+ * order (d_xidx[t] = t) is read in place, and a list output that holds every
+ * row is written in place, so the output arrays (d_y, d_yidx, d_yval,
+ * d_nnz_y) must not overlap any input array (x's count, list or dense
+ * vector): the kernels may still read x while they write y. No
+ * synchronisation. */
 asv_status asv_spmspv(asv_matrix A, const int64_t* d_nnz_x, const int32_t* d_xidx,
                       const void* d_xval, const void* d_x_dense, int32_t out_mode,
                       void* d_y, int32_t* d_yidx, void* d_yval, int64_t* d_nnz_y,
